@@ -1,0 +1,169 @@
+/*
+ * kzk.h -- C ABI of the B300 (sm_103a) ExpRK22 / WENO5 / FFT propagator for the
+ * KZK-type sonic-boom equation of Einkemmer, Ostermann & Residori,
+ * "An exponential integrator/WENO discretization for sonic-boom simulation on
+ * modern computer hardware" (arXiv:2103.06080).
+ *
+ * The operation advanced by kzk_advance is one step of the second-order
+ * exponential Runge-Kutta scheme ExpRK22 (Eq. 5), evaluated in Fourier space
+ * (Eq. 11, Algorithm 2 STEP 1-4), for
+ *     d_sigma V = L V + b(sigma, V),                                 (Eq. 2a)
+ *     L = diffraction * d_tau^{-1} d_y^2 + A d_tau^2                 (Eq. 2)
+ *     b = (B(sigma)/2) d_tau V^2 + (A(sigma) - A) d_tau^2 V          (Eq. 3)
+ * on a grid periodic in retarded time tau (x, contiguous) and transverse y
+ * (Sec. 3.3).  b's flux derivative is discretised with WENO5 (Jiang-Shu
+ * weights, global Lax-Friedrichs splitting with alpha = B(sigma) * lf_umax)
+ * on the gradient form of Eq. 7; L is applied exactly through the diagonal
+ * tables E = e^z, Phi1 = (e^z - 1)/z, Phi2 = (e^z - 1 - z)/z^2 with
+ *     z = dsigma * ( -diffraction * k_y^2 / (i k_tau + reg_eps * diffraction)
+ *                    - A k_tau^2 )                                   (Eq. 11)
+ * (the regularised multiplier of the paper; at the tau-Nyquist frequency only
+ * the even part -A k_tau^2 is kept).  Wavenumbers are physical:
+ * k = 2 pi m / (max - min) for the signed FFT index m.
+ *
+ * Conventions for every entry point:
+ *   - All state buffers are owned by the caller, contiguous, row-major
+ *     [batch][ny][nx] (tau fastest), of the plan's precision (double for
+ *     KZK_FP64, float for KZK_FP32).  "device" pointers must be CUDA device
+ *     memory of the current device; "host" pointers ordinary host memory.
+ *   - The plan owns its tables and workspace (device memory, allocated in
+ *     kzk_plan_create, freed in kzk_plan_destroy).
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; calls that return host data synchronise it.
+ *   - No exception crosses the ABI.  Every function returns a kzk_status;
+ *     kzk_last_error() gives a one-line description of the last failure on
+ *     the calling thread.  CUDA errors map to KZK_ERR_CUDA.
+ *   - A plan is not thread-safe: use it from one host thread and one stream
+ *     at a time.
+ */
+#ifndef KZK_H
+#define KZK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KZK_OK = 0,
+    KZK_ERR_ARG = 1,        /* null pointer, bad enum, non-positive extent, bad dt      */
+    KZK_ERR_SIZE = 2,       /* nx, ny not powers of two or outside [8, 8192] x [2, 4096] */
+    KZK_ERR_CFL = 3,        /* max|u| exceeded lf_umax (LF splitting no longer upwind)  */
+    KZK_ERR_NONFINITE = 4,  /* a NaN or Inf appeared in the state                       */
+    KZK_ERR_CUDA = 5,       /* a CUDA runtime call failed                                */
+    KZK_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up                       */
+    KZK_ERR_OOM = 7,        /* device allocation failed                                 */
+    KZK_ERR_STATE = 8       /* call not valid for this plan (e.g. wrong plan kind)      */
+} kzk_status;
+
+typedef enum { KZK_FP64 = 0, KZK_FP32 = 1 } kzk_precision;
+
+/* Grid of Sec. 3.3: tau_k = tau_min + k (tau_max - tau_min)/nx, y_j likewise. */
+typedef struct {
+    int32_t nx, ny;                 /* powers of two; nx: tau (contiguous), ny: y */
+    double tau_min, tau_max, y_min, y_max;
+    int32_t prec;                   /* kzk_precision of state and bulk arithmetic */
+} kzk_grid;
+
+/* Coefficients of Eq. 0 / Eq. 2a.  B(sigma) = B * pB(sigma) and
+ * A(sigma) = A * pA(sigma) with cubic pX(sigma) = c0 + c1 s + c2 s^2 + c3 s^3
+ * when has_profile != 0 (stratified atmosphere), else constant. */
+typedef struct {
+    double B;                       /* nonlinearity, > 0                             */
+    double A;                       /* absorption, >= 0 (kept exactly in L)          */
+    double diffraction;             /* 1/(4 pi) in the paper; <= 0 selects 1/(4 pi)   */
+    double reg_eps;                 /* epsilon of z; <= 0 selects 2^-53 (FP64) / 2^-24 (FP32) */
+    double weno_eps;                /* Jiang-Shu epsilon; <= 0 selects 1e-6          */
+    double lf_umax;                 /* M of the LF speed alpha = B(sigma) * M, > 0   */
+    double B_prof[4];
+    double A_prof[4];
+    int32_t has_profile;
+} kzk_coeffs;
+
+/* Diagnostics (FP64): of the state after the last step, and over the run. */
+typedef struct {
+    double mean;                    /* sum u / (nx ny)                               */
+    double energy;                  /* dtau dy sum u^2                               */
+    double max_abs;                 /* max |u|                                       */
+    double nonfinite;               /* number of NaN/Inf values                      */
+    double run_max_abs;             /* max over the states at the start of each step and the final one */
+    double run_nonfinite;           /* NaN/Inf count summed over those states        */
+} kzk_diag;
+
+typedef struct kzk_plan_s kzk_plan;
+
+/* Create a plan for `batch` independent propagations sharing grid,
+ * coefficients and step dt (= dsigma of Eq. 5).  Builds the FP64 phi tables of
+ * Eq. 11 on the device (rounded once to float for KZK_FP32), the twiddle
+ * tables, and the workspace (4 spectral arrays per instance).
+ * Errors: KZK_ERR_ARG (null, dt <= 0, B <= 0, A < 0, lf_umax <= 0, batch < 1),
+ * KZK_ERR_SIZE, KZK_ERR_OOM, KZK_ERR_CUDA.  *out is NULL on failure. */
+kzk_status kzk_plan_create(const kzk_grid *grid, const kzk_coeffs *coeffs, double dt,
+                           int32_t batch, kzk_plan **out);
+
+/* Advance u (device, [batch][ny][nx], in place, physical space) by n_steps
+ * ExpRK22 steps from sigma0 (Eq. 11 / Algorithm 2).  n_steps = 0 is a no-op.
+ * diag_out (host, nullable, `batch` entries): when given, the call
+ * synchronises the stream, fills the diagnostics and returns
+ * KZK_ERR_NONFINITE if any NaN/Inf was seen, else KZK_ERR_CFL if max|u|
+ * exceeded lf_umax, else KZK_OK.  Without diag_out the call is asynchronous
+ * and performs no host synchronisation. */
+kzk_status kzk_advance(kzk_plan *plan, void *u, int64_t n_steps, double sigma0, void *stream,
+                       kzk_diag *diag_out);
+
+/* Per-step diagnostics of the last kzk_advance call: hist (host) receives
+ * min(n, steps of that call) records [step][batch] of {mean, energy, max|u|,
+ * nonfinite} (4 doubles each) of the state at the start of each step.
+ * Synchronises the stream. */
+kzk_status kzk_diag_history(kzk_plan *plan, double *hist, int64_t n, void *stream);
+
+/* Nonlinear term b(sigma, u) of Eq. 3 in physical space, discretised as in
+ * kzk_advance (WENO5 flux derivative plus the absorption-deviation term).
+ * u, b: device, [batch][ny][nx]; b may not alias u. */
+kzk_status kzk_rhs(kzk_plan *plan, const void *u, void *b, double sigma, void *stream);
+
+/* One step from u (device) into u_next (device) that also returns the first
+ * stage V^{n,*} of Eq. 5 (device, physical).  u_next may alias u. */
+kzk_status kzk_step_stages(kzk_plan *plan, const void *u, void *u_star, void *u_next,
+                           double sigma0, void *stream);
+
+/* tau-direction real FFT of every row (Sec. 3.3): forward (dir = -1) maps
+ * physical u [batch][ny][nx] to the packed half spectrum v [batch][ny][nx/2]
+ * complex (interleaved re, im) with v[m] = F(u)[m] / nx for 0 < m < nx/2 and
+ * v[0] = (F(u)[0] / nx, F(u)[nx/2] / nx); dir = +1 is its exact inverse.
+ * Both pointers device, precision of the plan, no aliasing. */
+kzk_status kzk_tau_fft(kzk_plan *plan, const void *in, void *out, int32_t dir, void *stream);
+
+/* Copy the plan's tables back, unscaled: E, Phi1, Phi2 (host, each
+ * (ny/2+1) * (nx/2+1) complex128 interleaved, row l = |k_y| index, column m =
+ * k_tau index 0..nx/2).  Synchronises. */
+kzk_status kzk_get_tables(kzk_plan *plan, double *E, double *Phi1, double *Phi2);
+
+/* Gradient of a loss with respect to the initial state u0 (device), given its
+ * gradient g_end (device) with respect to the state after n_steps steps from
+ * sigma0: g0 (device) = (d u_end / d u0)^T g_end.  Reverse sweep of the exact
+ * transpose of the ExpRK22 step (transposed WENO5 including the derivatives
+ * of the nonlinear weights, conjugated multipliers, adjoint FFTs), with a
+ * checkpoint of the forward state every ckpt_every steps (>= 1) and
+ * recomputation of each segment.  u0 is not modified.  g0 may alias g_end. */
+kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *g0,
+                       int64_t n_steps, double sigma0, int32_t ckpt_every, void *stream);
+
+/* Release the plan and all device memory it owns.  NULL is accepted. */
+kzk_status kzk_plan_destroy(kzk_plan *plan);
+
+/* Static description of a status code. */
+const char *kzk_status_string(kzk_status s);
+
+/* One-line description of the last failure on the calling thread. */
+const char *kzk_last_error(void);
+
+/* Number of kernel launches the library has issued since load (all plans). */
+int64_t kzk_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KZK_H */

@@ -1,0 +1,152 @@
+"""Python face of the CUDA propagator: a Plan wrapping the C ABI.
+
+PyTorch supplies device memory and streams; all computation happens in
+libkzk.so.  State tensors are CUDA tensors of shape [batch, ny, nx] (or
+[ny, nx] for batch 1), contiguous, float64 for FP64 plans and float32 for
+FP32 plans.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Plan:
+    """One plan: grid, coefficients and step dsigma shared by `batch` propagations."""
+
+    def __init__(self, nx: int, ny: int, dt: float, precision: str = "fp64", batch: int = 1,
+                 B: float = 0.05, A: float = 7e-6, lf_umax: float = 1.0,
+                 tau_min: float = -4.0, tau_max: float = 4.0, y_min: float = -8.0, y_max: float = 8.0,
+                 B_prof: Sequence[float] = (1.0, 0.0, 0.0, 0.0), A_prof: Sequence[float] = (1.0, 0.0, 0.0, 0.0),
+                 has_profile: bool = False, diffraction: float = 0.0, reg_eps: float = 0.0,
+                 weno_eps: float = 0.0):
+        if precision not in ("fp64", "fp32"):
+            raise ValueError("precision must be 'fp64' or 'fp32'")
+        self.nx, self.ny, self.dt, self.batch = int(nx), int(ny), float(dt), int(batch)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        g = L.KzkGrid(nx=self.nx, ny=self.ny, tau_min=tau_min, tau_max=tau_max, y_min=y_min, y_max=y_max,
+                      prec=L.KZK_FP64 if precision == "fp64" else L.KZK_FP32)
+        c = L.KzkCoeffs(B=B, A=A, diffraction=diffraction, reg_eps=reg_eps, weno_eps=weno_eps, lf_umax=lf_umax,
+                        B_prof=(ctypes.c_double * 4)(*B_prof), A_prof=(ctypes.c_double * 4)(*A_prof),
+                        has_profile=int(bool(has_profile)))
+        self._grid, self._coeffs = g, c
+        h = ctypes.c_void_p()
+        L.check(L.lib().kzk_plan_create(ctypes.byref(g), ctypes.byref(c), self.dt, self.batch, ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, w, precision: Optional[str] = None, batch: int = 1, **over) -> "Plan":
+        kw = dict(nx=w.nx, ny=w.ny, dt=w.dt, precision=precision or w.precision, batch=batch, B=w.B, A=w.A,
+                  lf_umax=w.lf_umax, tau_min=w.tau_min, tau_max=w.tau_max, y_min=w.y_min, y_max=w.y_max,
+                  B_prof=w.B_prof, A_prof=w.A_prof, has_profile=w.has_profile)
+        kw.update(over)
+        return cls(**kw)
+
+    # -- helpers -------------------------------------------------------------
+    def _check_state(self, t: torch.Tensor, name: str) -> None:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.dtype:
+            raise TypeError(f"{name} must be {self.dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        want = self.batch * self.ny * self.nx
+        if t.numel() != want or t.shape[-1] != self.nx or t.shape[-2] != self.ny:
+            raise ValueError(f"{name} must have shape [{self.batch}, {self.ny}, {self.nx}], got {tuple(t.shape)}")
+
+    @property
+    def handle(self) -> int:
+        if self._h is None or not self._h.value:
+            raise RuntimeError("plan has been destroyed")
+        return self._h.value
+
+    # -- operations ----------------------------------------------------------
+    def advance(self, u: torch.Tensor, n_steps: int, sigma0: float = 0.0, diag: bool = False,
+                stream: Optional[torch.cuda.Stream] = None, raise_on_error: bool = True):
+        """Advance u in place by n_steps ExpRK22 steps; with diag=True returns
+        (status, [per-instance diagnostics dict])."""
+        self._check_state(u, "u")
+        d = (L.KzkDiag * self.batch)() if diag else None
+        st = L.lib().kzk_advance(self.handle, u.data_ptr(), int(n_steps), float(sigma0), _stream_ptr(stream),
+                                 d if diag else None)
+        if diag:
+            if raise_on_error and st not in (L.KZK_OK, L.KZK_ERR_CFL, L.KZK_ERR_NONFINITE):
+                L.check(st)
+            return st, [d[i].as_dict() for i in range(self.batch)]
+        L.check(st)
+        return None
+
+    def diag_history(self, n: int, stream: Optional[torch.cuda.Stream] = None) -> np.ndarray:
+        out = np.zeros((max(int(n), 1), self.batch, 4))
+        L.check(L.lib().kzk_diag_history(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         int(n), _stream_ptr(stream)))
+        return out[:n]
+
+    def rhs(self, u: torch.Tensor, sigma: float = 0.0, stream=None) -> torch.Tensor:
+        self._check_state(u, "u")
+        b = torch.empty_like(u)
+        L.check(L.lib().kzk_rhs(self.handle, u.data_ptr(), b.data_ptr(), float(sigma), _stream_ptr(stream)))
+        return b
+
+    def step_stages(self, u: torch.Tensor, sigma0: float = 0.0, stream=None):
+        self._check_state(u, "u")
+        us, un = torch.empty_like(u), torch.empty_like(u)
+        L.check(L.lib().kzk_step_stages(self.handle, u.data_ptr(), us.data_ptr(), un.data_ptr(), float(sigma0),
+                                        _stream_ptr(stream)))
+        return us, un
+
+    def tau_fft(self, x: torch.Tensor, direction: int, stream=None) -> torch.Tensor:
+        """direction -1: physical [.., ny, nx] -> packed complex [.., ny, nx/2, 2];
+        +1: the inverse."""
+        if direction == -1:
+            self._check_state(x, "x")
+            out = torch.empty(x.shape[:-1] + (self.nx // 2, 2), dtype=self.dtype, device=x.device)
+        else:
+            if x.shape[-2:] != (self.nx // 2, 2) or not x.is_contiguous() or x.dtype != self.dtype:
+                raise ValueError("packed spectrum must be contiguous [.., ny, nx/2, 2] of the plan dtype")
+            out = torch.empty(x.shape[:-2] + (self.nx,), dtype=self.dtype, device=x.device)
+        L.check(L.lib().kzk_tau_fft(self.handle, x.data_ptr(), out.data_ptr(), int(direction), _stream_ptr(stream)))
+        return out
+
+    def tables(self):
+        """(E, Phi1, Phi2) as complex128 arrays [(ny/2+1), (nx/2+1)], unscaled."""
+        shape = (self.ny // 2 + 1, self.nx // 2 + 1, 2)
+        arrs = [np.zeros(shape) for _ in range(3)]
+        P = ctypes.POINTER(ctypes.c_double)
+        L.check(L.lib().kzk_get_tables(self.handle, *[a.ctypes.data_as(P) for a in arrs]))
+        return tuple(a[..., 0] + 1j * a[..., 1] for a in arrs)
+
+    def adjoint(self, u0: torch.Tensor, g_end: torch.Tensor, n_steps: int, sigma0: float = 0.0,
+                ckpt_every: int = 32, stream=None) -> torch.Tensor:
+        self._check_state(u0, "u0")
+        self._check_state(g_end, "g_end")
+        g0 = torch.empty_like(u0)
+        L.check(L.lib().kzk_adjoint(self.handle, u0.data_ptr(), g_end.data_ptr(), g0.data_ptr(), int(n_steps),
+                                    float(sigma0), int(ckpt_every), _stream_ptr(stream)))
+        return g0
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.lib().kzk_plan_destroy(self._h.value)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launch_count() -> int:
+    return int(L.lib().kzk_launch_count())

@@ -1,0 +1,296 @@
+// kzk_adjoint.cuh -- kernels of the transposed ExpRK22 step.
+//
+// With P_X u := Re F^{-1}(X o F u) (a real operator for the Hermitian-
+// symmetric tables of Eq. 11) one forward step reads
+//   b1 = G_n(u),  u* = P_E u + P_{ds Phi1} b1,  b2 = G_{n+1}(u*),
+//   u' = u* + P_{ds Phi2}(b2 - b1),
+// with G_s(u) = WENO_s(u) + (A(s) - A) d_tau^2 u.  Its transpose, for a
+// cotangent lam' of u', is
+//   mu2  = P_{conj(ds Phi2)} lam'                     (adjoint C2, column pass)
+//   lam* = lam' + J_{G_{n+1}}(u*)^T mu2               (adjoint R2, row pass)
+//   lam_lin = P_{conj E} lam*,  nu1 = P_{conj(ds Phi1)} lam* - mu2   (adjoint C1)
+//   lam  = lam_lin + J_{G_n}(u)^T nu1                 (adjoint R1, row pass)
+// All adjoint arrays use the packed spectral layout of the state (tau-spectrum
+// divided by nx), so P_X is a column pass with the conjugated, rescaled table.
+//
+// WENO transpose: with psi_{k+1/2} = (mu_{k+1} - mu_k)/dtau,
+//   (J^T mu)_i = sum_k psi_{k+1/2} dF_{k+1/2}/du_i,
+// and for one reconstruction F = sum omega_r q_r, omega_r = a_r / sum a,
+// a_r = d_r/(eps + beta_r)^2:
+//   dF/dv_j = sum_r omega_r dq_r/dv_j - 2 sum_r omega_r (q_r - F)/(eps + beta_r) dbeta_r/dv_j
+// (the derivative through the nonlinear weights), times df+-/du = (-B u +- alpha)/2.
+#pragma once
+#include "kzk_common.cuh"
+#include "kzk_fft.cuh"
+#include "kzk_kernels.cuh"
+
+namespace kzk {
+
+// Gradient of one reconstruction w.r.t. v_{-2..2}, scaled by w: g[j] = w dF/dv_j.
+template <typename T>
+__device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps, T w, T* g)
+{
+    const T s6 = T(1) / T(6);
+    const T q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0)) * s6;
+    const T q1 = fma(T(-1), vm1, fma(T(5), v0, T(2) * v1)) * s6;
+    const T q2 = fma(T(2), v0, fma(T(5), v1, -v2)) * s6;
+    const T c13 = T(13) / T(12);
+    const T sa = vm2 - T(2) * vm1 + v0, ta = vm2 - T(4) * vm1 + T(3) * v0;
+    const T sb = vm1 - T(2) * v0 + v1, tb = vm1 - v1;
+    const T sc = v0 - T(2) * v1 + v2, tc = T(3) * v0 - T(4) * v1 + v2;
+    const T e0 = eps + fma(c13 * sa, sa, T(0.25) * ta * ta);
+    const T e1 = eps + fma(c13 * sb, sb, T(0.25) * tb * tb);
+    const T e2 = eps + fma(c13 * sc, sc, T(0.25) * tc * tc);
+    const T t0 = e0 * e0, t1 = e1 * e1, t2 = e2 * e2;
+    const T a0 = T(0.1) * t1 * t2, a1 = T(0.6) * t0 * t2, a2 = T(0.3) * t0 * t1;
+    const T inv = T(1) / (a0 + a1 + a2);
+    const T o0 = a0 * inv, o1 = a1 * inv, o2 = a2 * inv;     // omega_r
+    const T F = o0 * q0 + o1 * q1 + o2 * q2;
+    // c_r = -2 omega_r (q_r - F) / e_r
+    const T c0 = T(-2) * o0 * (q0 - F) / e0;
+    const T c1 = T(-2) * o1 * (q1 - F) / e1;
+    const T c2 = T(-2) * o2 * (q2 - F) / e2;
+    const T A0 = T(2) * c13 * sa * c0, B0 = T(0.5) * ta * c0;
+    const T A1 = T(2) * c13 * sb * c1, B1 = T(0.5) * tb * c1;
+    const T A2 = T(2) * c13 * sc * c2, B2 = T(0.5) * tc * c2;
+    g[0] = w * (T(2) * s6 * o0 + A0 + B0);
+    g[1] = w * (-T(7) * s6 * o0 - s6 * o1 - T(2) * A0 - T(4) * B0 + A1 + B1);
+    g[2] = w * (T(11) * s6 * o0 + T(5) * s6 * o1 + T(2) * s6 * o2 + A0 + T(3) * B0 - T(2) * A1 + A2 + T(3) * B2);
+    g[3] = w * (T(2) * s6 * o1 + T(5) * s6 * o2 + A1 - B1 - T(2) * A2 - T(4) * B2);
+    g[4] = w * (-s6 * o2 + A2 + B2);
+}
+
+// J_WENO(u)^T mu over the points [k0, k0+Q) of one periodic row: own-point
+// sums go to g[], the two contributions left of k0 to spl[0..1] and the three
+// right of k0+Q-1 to spr[0..2] (added by the neighbours afterwards).
+template <typename T>
+__device__ __forceinline__ void weno_row_chunk_T(const T* __restrict__ u, const T* __restrict__ mu,
+                                                 T* __restrict__ g, T* spl, T* spr, int nx, int k0, int Q,
+                                                 const WenoCoef<T>& c)
+{
+    const int msk = nx - 1;
+    const T half = T(0.5);
+    T fp[6], fm[6], dp[6], dm[6], acc[6];
+    // window slot s <-> point k - 2 + s for interface k + 1/2, starting at k = k0
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const T v = u[(k0 - 2 + s) & msk];
+        const T f = -half * c.B * v * v;
+        fp[s] = half * fma(c.alpha, v, f);
+        fm[s] = half * fma(-c.alpha, v, f);
+        dp[s] = half * (c.alpha - c.B * v);
+        dm[s] = half * (-c.alpha - c.B * v);
+        acc[s] = T(0);
+    }
+    T mk_ = mu[k0 & msk];
+    for (int i = 0; i < Q; i++) {
+        const int k = k0 + i;
+        const T mk1 = mu[(k + 1) & msk];
+        const T psi = (mk1 - mk_) * c.inv_dtau;
+        mk_ = mk1;
+        T gp[5], gm[5];
+        weno5_grad<T>(fp[0], fp[1], fp[2], fp[3], fp[4], c.eps, psi, gp);
+        weno5_grad<T>(fm[5], fm[4], fm[3], fm[2], fm[1], c.eps, psi, gm);
+#pragma unroll
+        for (int s = 0; s < 5; s++) acc[s] = fma(gp[s], dp[s], acc[s]);
+#pragma unroll
+        for (int s = 0; s < 5; s++) acc[5 - s] = fma(gm[s], dm[5 - s], acc[5 - s]);
+        // point k - 2 is complete
+        const int pt = k - 2;
+        if (pt < k0) spl[pt - (k0 - 2)] = acc[0];
+        else g[pt] = acc[0];
+#pragma unroll
+        for (int s = 0; s < 5; s++) {
+            fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; dp[s] = dp[s + 1]; dm[s] = dm[s + 1]; acc[s] = acc[s + 1];
+        }
+        const T v = u[(k + 4) & msk];
+        const T f = -half * c.B * v * v;
+        fp[5] = half * fma(c.alpha, v, f);
+        fm[5] = half * fma(-c.alpha, v, f);
+        dp[5] = half * (c.alpha - c.B * v);
+        dm[5] = half * (-c.alpha - c.B * v);
+        acc[5] = T(0);
+    }
+    // remaining points k0+Q-2 .. k0+Q+2 in acc[0..4]
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const int pt = k0 + Q - 2 + s;
+        if (pt < k0 + Q) g[pt] = acc[s];
+        else spr[pt - (k0 + Q)] = acc[s];
+    }
+}
+
+template <typename T>
+struct AdjRowArgs {
+    const cx<T>* m;         // cotangent of b (mu2 or nu1), packed spectral
+    const cx<T>* v;         // state the step linearises at (V* or V^n), packed spectral
+    const cx<T>* l;         // additive term (lam' or lam_lin), packed spectral
+    cx<T>* out;             // l + F(J_G(u)^T m) / nx
+    const cx<T>* tw;
+    int log2nx;
+    long long inst_stride;
+    WenoCoef<T> wc;
+    T dA;                   // A(sigma) - A
+    T kscale;
+    T inv_nx;
+};
+
+enum AdjRowMode { ADJ_ROW_2 = 0, ADJ_ROW_1 = 1 };
+
+template <typename T, int PPT, int MODE>
+__global__ void __launch_bounds__(1024) adj_row_kernel(AdjRowArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nx = 1 << a.log2nx, n = nx >> 1, log2n = a.log2nx - 1;
+    const int row = blockIdx.x, inst = blockIdx.y;
+    cx<T>* U = reinterpret_cast<cx<T>*>(smem_raw);
+    cx<T>* M = U + n;
+    cx<T>* G = M + n;
+    T* spl = reinterpret_cast<T*>(G + n);
+    T* spr = spl + 2 * nthr;
+    const long long base = (long long)inst * a.inst_stride + (long long)row * n;
+
+    for (int i = tid; i < n; i += nthr) { U[i] = a.v[base + i]; M[i] = a.m[base + i]; }
+    __syncthreads();
+    c2r_pre<T>(U, n, a.tw, tid, nthr);
+    c2r_pre<T>(M, n, a.tw, tid, nthr);
+    __syncthreads();
+    fft_batched<T, PPT, false, true>(U, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+    fft_batched<T, PPT, false, true>(M, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+
+    const int Q = nx / nthr >= 4 ? nx / nthr : 4;
+    const int nact = nx / Q;
+    const int k0 = tid * Q;
+    T* gphys = reinterpret_cast<T*>(G);
+    if (tid < nact)
+        weno_row_chunk_T<T>(reinterpret_cast<const T*>(U), reinterpret_cast<const T*>(M), gphys,
+                            spl + 2 * tid, spr + 3 * tid, nx, k0, Q, a.wc);
+    __syncthreads();
+    if (tid < nact) {
+        const int left = (tid + nact - 1) % nact, right = (tid + 1) % nact;
+        // neighbours' spills: right spill of the left neighbour covers k0..k0+2,
+        // left spill of the right neighbour covers k0+Q-2, k0+Q-1
+        for (int s = 0; s < 3; s++) gphys[k0 + s] += spr[3 * left + s];
+        gphys[(k0 + Q - 2)] += spl[2 * right + 0];
+        gphys[(k0 + Q - 1)] += spl[2 * right + 1];
+    }
+    __syncthreads();
+    fft_batched<T, PPT, false, false>(G, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+    for (int k = tid; k <= n / 2; k += nthr) {
+        cx<T> xk, xnk;
+        r2c_post_pair<T>(G, n, k, a.tw, xk, xnk);
+        xk = scale<T>(xk, a.inv_nx);
+        xnk = scale<T>(xnk, a.inv_nx);
+        const cx<T> mk0 = a.m[base + k];
+        const cx<T> lk = a.l[base + k];
+        if (k == 0) {
+            const T kN = a.kscale * T(n);
+            xk.y -= a.dA * kN * kN * mk0.y;
+            a.out[base] = add<T>(lk, xk);
+        } else {
+            const T kt = a.kscale * T(k);
+            xk.x -= a.dA * kt * kt * mk0.x;
+            xk.y -= a.dA * kt * kt * mk0.y;
+            a.out[base + k] = add<T>(lk, xk);
+            if (2 * k != n) {
+                const T kt2 = a.kscale * T(n - k);
+                const cx<T> mk2 = a.m[base + n - k];
+                xnk.x -= a.dA * kt2 * kt2 * mk2.x;
+                xnk.y -= a.dA * kt2 * kt2 * mk2.y;
+                a.out[base + n - k] = add<T>(a.l[base + n - k], xnk);
+            }
+        }
+    }
+}
+
+template <typename T>
+size_t adj_row_smem_bytes(int n, int nthr)
+{
+    return 3 * (size_t)n * sizeof(cx<T>) + 5 * (size_t)nthr * sizeof(T);
+}
+
+enum AdjColMode { ADJ_COL_2 = 0, ADJ_COL_1 = 1 };
+
+template <typename T>
+struct AdjColArgs {
+    const cx<T>* a;     // ADJ_COL_2: lam';  ADJ_COL_1: lam*
+    const cx<T>* b;     // ADJ_COL_1: mu2
+    cx<T>* out;         // ADJ_COL_2: mu2;   ADJ_COL_1: lam_lin (may alias a)
+    cx<T>* out2;        // ADJ_COL_1: nu1
+    const cx<T>* Ta;    // ADJ_COL_2: P2';   ADJ_COL_1: E'
+    const cx<T>* Tb;    // ADJ_COL_1: P1'
+    T sa, sb;           // rescale of conj(Ta), conj(Tb)
+    const cx<T>* tw;
+    int log2ny, log2n, log2tc;
+    long long inst_stride;
+};
+
+// conj(M) applied to the column-FFT'd tile (column 0 packs two real tables).
+template <typename T>
+__device__ __forceinline__ cx<T> apply_mult_conj(const cx<T>* __restrict__ tab, const cx<T>* S, int l, int c, int m,
+                                                 int ny, int n, int log2tc, T s)
+{
+    const int lf = l <= (ny >> 1) ? l : ny - l;
+    const cx<T> M = scale<T>(tab[(long long)lf * n + m], s);
+    const cx<T> z = S[(l << log2tc) + c];
+    if (m != 0) return mulc<T>(z, M);
+    const cx<T> zm = S[(((ny - l) & (ny - 1)) << log2tc) + c];
+    const T h = T(0.5) * (M.x + M.y), g = T(0.5) * (M.x - M.y);
+    return mk<T>(h * z.x + g * zm.x, h * z.y - g * zm.y);
+}
+
+template <typename T, int PPT, int MODE>
+__global__ void __launch_bounds__(1024) adj_col_kernel(AdjColArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* S = reinterpret_cast<cx<T>*>(smem_raw);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ny = 1 << a.log2ny, n = 1 << a.log2n, TC = 1 << a.log2tc;
+    const int m0 = blockIdx.x * TC, inst = blockIdx.y;
+    const long long ibase = (long long)inst * a.inst_stride;
+    const int total = ny << a.log2tc;
+    auto gidx = [&](int e) -> long long {
+        return ibase + (long long)(e >> a.log2tc) * n + m0 + (e & (TC - 1));
+    };
+    cx<T> acc[PPT], acc2[MODE == ADJ_COL_1 ? PPT : 1];
+
+    for (int e = tid; e < total; e += nthr) S[e] = a.a[gidx(e)];
+    __syncthreads();
+    fft_batched<T, PPT, true, false>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+#pragma unroll
+    for (int q = 0; q < PPT; q++) {
+        const int e = tid + q * nthr;
+        if (e < total) {
+            const int l = e >> a.log2tc, c = e & (TC - 1);
+            acc[q] = apply_mult_conj<T>(a.Ta, S, l, c, m0 + c, ny, n, a.log2tc, a.sa);
+            if constexpr (MODE == ADJ_COL_1)
+                acc2[q] = apply_mult_conj<T>(a.Tb, S, l, c, m0 + c, ny, n, a.log2tc, a.sb);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PPT; q++) {
+        const int e = tid + q * nthr;
+        if (e < total) S[e] = acc[q];
+    }
+    __syncthreads();
+    fft_batched<T, PPT, true, true>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+    for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = S[e];
+    if constexpr (MODE == ADJ_COL_1) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PPT; q++) {
+            const int e = tid + q * nthr;
+            if (e < total) S[e] = acc2[q];
+        }
+        __syncthreads();
+        fft_batched<T, PPT, true, true>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+        for (int e = tid; e < total; e += nthr) {
+            const long long g = gidx(e);
+            a.out2[g] = sub<T>(S[e], a.b[g]);
+        }
+    }
+}
+
+}  // namespace kzk

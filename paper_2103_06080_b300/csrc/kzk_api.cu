@@ -1,0 +1,730 @@
+// kzk_api.cu -- plan management and the C ABI of include/kzk.h.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/kzk.h"
+#include "kzk_adjoint.cuh"
+#include "kzk_kernels.cuh"
+#include "kzk_tables.cuh"
+
+using namespace kzk;
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<long long> g_launches{0};
+
+kzk_status fail(kzk_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define KZK_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? KZK_ERR_OOM : KZK_ERR_CUDA,          \
+                        "%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+#define KZK_LAUNCHED()                                                                         \
+    do {                                                                                       \
+        g_launches.fetch_add(1, std::memory_order_relaxed);                                    \
+        cudaError_t e_ = cudaGetLastError();                                                   \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(KZK_ERR_CUDA, "%s:%d launch: %s", __FILE__, __LINE__,                  \
+                        cudaGetErrorString(e_));                                               \
+    } while (0)
+
+#define KZK_TRY(expr)                                                                          \
+    do {                                                                                       \
+        kzk_status s_ = (expr);                                                                \
+        if (s_ != KZK_OK) return s_;                                                           \
+    } while (0)
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+double horner(const double* c, double s) { return ((c[3] * s + c[2]) * s + c[1]) * s + c[0]; }
+
+}  // namespace
+
+struct kzk_plan_s {
+    kzk_grid g;
+    kzk_coeffs c;
+    double dt;
+    int batch;
+    int prec;
+    int nx, ny, n, log2nx, log2ny;
+    size_t csz;
+    long long inst_stride;      // complex elements per instance: ny * nx / 2
+    void *V, *b1, *vs, *b2;     // spectral work arrays [batch][ny][nx/2]
+    void *E, *P1, *P2;          // folded, scaled tables [(ny/2+1)][nx/2]
+    void *twr, *twc;            // twiddles, exp(-2 pi i k / nx), exp(-2 pi i k / ny)
+    double* diag_rows;          // [batch][ny][4]
+    double* diag_hist;          // [hist_cap][batch][4]
+    double* diag_final;         // [batch][4]
+    long long hist_cap;
+    long long hist_steps;
+    int row_thr, col_thr, log2tc;
+    size_t row_smem, col_smem;
+    // adjoint workspace (allocated on first use)
+    void *lam, *mu, *nu, *ls;   // spectral adjoint arrays
+    void* seg;                  // segment store [(2 k)][batch][ny][nx/2]
+    void* ckpt;                 // checkpoints  [n_ckpt][batch][ny][nx/2]
+    long long seg_cap, ckpt_cap; // in arrays
+};
+
+namespace {
+
+double B_of(const kzk_plan* p, double s) { return p->c.has_profile ? p->c.B * horner(p->c.B_prof, s) : p->c.B; }
+double dA_of(const kzk_plan* p, double s)
+{
+    return p->c.has_profile ? p->c.A * horner(p->c.A_prof, s) - p->c.A : 0.0;
+}
+
+template <typename T> constexpr int row_ppt() { return sizeof(T) == 4 ? 16 : 8; }
+template <typename T> constexpr int col_ppt() { return sizeof(T) == 4 ? 16 : 8; }
+template <typename T> size_t adj_row_smem(const kzk_plan* p) { return adj_row_smem_bytes<T>(p->n, p->row_thr); }
+
+template <typename T, int MODE>
+kzk_status set_row_attr(size_t smem)
+{
+    KZK_CUDA(cudaFuncSetAttribute(row_kernel<T, row_ppt<T>(), MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return KZK_OK;
+}
+template <typename T, int MODE>
+kzk_status set_col_attr(size_t smem)
+{
+    KZK_CUDA(cudaFuncSetAttribute(col_kernel<T, col_ppt<T>(), MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return KZK_OK;
+}
+template <typename T, int MODE>
+kzk_status set_adj_row_attr(size_t smem)
+{
+    KZK_CUDA(cudaFuncSetAttribute(adj_row_kernel<T, row_ppt<T>(), MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return KZK_OK;
+}
+template <typename T, int MODE>
+kzk_status set_adj_col_attr(size_t smem)
+{
+    KZK_CUDA(cudaFuncSetAttribute(adj_col_kernel<T, col_ppt<T>(), MODE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return KZK_OK;
+}
+
+template <typename T>
+kzk_status configure(kzk_plan* p)
+{
+    const int PR = row_ppt<T>(), PC = col_ppt<T>();
+    p->row_thr = std::max(32, p->n / PR);
+    if (p->row_thr > 1024) return fail(KZK_ERR_SIZE, "nx = %d too large for one row per CTA", p->nx);
+    p->row_smem = 2 * (size_t)p->n * p->csz + 4 * (size_t)p->row_thr * sizeof(double);
+    const size_t budget = 128 * 1024;
+    int tc = std::min(16, p->n);
+    while (tc > 1 && ((size_t)p->ny * tc * p->csz > budget || (long long)p->ny * tc / PC > 1024)) tc >>= 1;
+    if ((size_t)p->ny * tc * p->csz > budget || (long long)p->ny * tc / PC > 1024)
+        return fail(KZK_ERR_SIZE, "ny = %d too large for a shared-memory column tile", p->ny);
+    p->log2tc = ilog2((unsigned)tc);
+    p->col_thr = std::max(32, p->ny * tc / PC);
+    p->col_smem = std::max((size_t)p->ny * tc * p->csz, 4 * (size_t)p->col_thr * sizeof(double));
+    // Every kernel may use up to the device's opt-in maximum; the launch's own
+    // dynamic size decides occupancy.  (Setting the plan's size here would
+    // shrink the limit for plans created earlier.)
+    int dev = 0, optin = 0;
+    KZK_CUDA(cudaGetDevice(&dev));
+    KZK_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (p->row_smem > (size_t)optin || adj_row_smem<T>(p) > (size_t)optin || p->col_smem > (size_t)optin)
+        return fail(KZK_ERR_SIZE, "grid %d x %d needs more shared memory than the device offers", p->nx, p->ny);
+    const size_t sm = (size_t)optin;
+    KZK_TRY((set_row_attr<T, ROW_RHS>(sm)));
+    KZK_TRY((set_row_attr<T, ROW_FWD>(sm)));
+    KZK_TRY((set_row_attr<T, ROW_INV>(sm)));
+    KZK_TRY((set_col_attr<T, COL_STAGE1>(sm)));
+    KZK_TRY((set_col_attr<T, COL_STAGE2>(sm)));
+    KZK_TRY((set_adj_row_attr<T, ADJ_ROW_2>(sm)));
+    KZK_TRY((set_adj_row_attr<T, ADJ_ROW_1>(sm)));
+    KZK_TRY((set_adj_col_attr<T, ADJ_COL_2>(sm)));
+    KZK_TRY((set_adj_col_attr<T, ADJ_COL_1>(sm)));
+    return KZK_OK;
+}
+
+// twiddle table exp(-2 pi i k / N), k in [0, N), evaluated in long double
+template <typename T>
+std::vector<cx<T>> twiddles(int N)
+{
+    std::vector<cx<T>> w(N);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int k = 0; k < N; k++) {
+        // reduce to the first octant by symmetry for exact 0 / +-1 entries
+        long double a = two_pi * (long double)k / (long double)N;
+        long double c = cosl(a), s = -sinl(a);
+        if (4 * k == N) { c = 0; s = -1; }
+        if (2 * k == N) { c = -1; s = 0; }
+        if (4 * k == 3 * N) { c = 0; s = 1; }
+        w[k] = mk<T>((T)(double)c, (T)(double)s);
+    }
+    return w;
+}
+
+template <typename T>
+RowArgs<T> row_args(const kzk_plan* p, const void* in, void* out, double sigma, double* diag_rows)
+{
+    RowArgs<T> a;
+    a.in = (const cx<T>*)in;
+    a.out = (cx<T>*)out;
+    a.tw = (const cx<T>*)p->twr;
+    a.diag_rows = diag_rows;
+    a.log2nx = p->log2nx;
+    a.ny = p->ny;
+    a.inst_stride = p->inst_stride;
+    const double Bs = B_of(p, sigma);
+    a.wc.B = (T)Bs;
+    a.wc.alpha = (T)(Bs * p->c.lf_umax);
+    a.wc.eps = (T)p->c.weno_eps;
+    a.wc.inv_dtau = (T)(p->nx / (p->g.tau_max - p->g.tau_min));
+    a.cA = (T)(p->nx * dA_of(p, sigma));
+    a.kscale = (T)(2.0 * M_PI / (p->g.tau_max - p->g.tau_min));
+    a.out_scale = (T)1;
+    return a;
+}
+
+template <typename T, int MODE>
+kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st)
+{
+    row_kernel<T, row_ppt<T>(), MODE><<<dim3(p->ny, p->batch), p->row_thr, p->row_smem, st>>>(a);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
+template <typename T, int MODE>
+kzk_status launch_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
+{
+    col_kernel<T, col_ppt<T>(), MODE><<<dim3(p->n >> p->log2tc, p->batch), p->col_thr, p->col_smem, st>>>(a);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
+template <typename T>
+ColArgs<T> col_args(const kzk_plan* p)
+{
+    ColArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.tw = (const cx<T>*)p->twc;
+    a.log2ny = p->log2ny;
+    a.log2n = p->log2nx - 1;
+    a.log2tc = p->log2tc;
+    a.inst_stride = p->inst_stride;
+    a.inv_count = 1.0 / ((double)p->nx * p->ny);
+    a.cell = (p->g.tau_max - p->g.tau_min) / p->nx * (p->g.y_max - p->g.y_min) / p->ny;
+    return a;
+}
+
+// One ExpRK22 step on the spectral state p->V (Algorithm 2, STEP 1-4).
+// diag_hist_step: where C1 writes this step's diagnostics (nullable).
+// vs_out / b1_out / b2_out: destinations (default: plan workspace).
+template <typename T>
+kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_step, void* V, void* vs)
+{
+    RowArgs<T> r1 = row_args<T>(p, V, p->b1, sigma, diag_hist_step ? p->diag_rows : nullptr);
+    KZK_TRY((launch_row<T, ROW_RHS>(p, r1, st)));
+    ColArgs<T> c1 = col_args<T>(p);
+    c1.a = (const cx<T>*)V;
+    c1.b = (const cx<T>*)p->b1;
+    c1.out = (cx<T>*)vs;
+    c1.Ta = (const cx<T>*)p->E;
+    c1.Tb = (const cx<T>*)p->P1;
+    c1.diag_rows = diag_hist_step ? p->diag_rows : nullptr;
+    c1.diag_hist = diag_hist_step;
+    KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
+    RowArgs<T> r2 = row_args<T>(p, vs, p->b2, sigma + p->dt, nullptr);
+    KZK_TRY((launch_row<T, ROW_RHS>(p, r2, st)));
+    ColArgs<T> c2 = col_args<T>(p);
+    c2.a = (const cx<T>*)p->b1;
+    c2.b = (const cx<T>*)p->b2;
+    c2.c = (const cx<T>*)vs;
+    c2.out = (cx<T>*)V;
+    c2.Ta = (const cx<T>*)p->P2;
+    KZK_TRY((launch_col<T, COL_STAGE2>(p, c2, st)));
+    return KZK_OK;
+}
+
+template <typename T>
+kzk_status to_spectral(kzk_plan* p, const void* u, void* V, cudaStream_t st)
+{
+    RowArgs<T> a = row_args<T>(p, u, V, 0.0, nullptr);
+    a.out_scale = (T)(1.0 / p->nx);
+    return launch_row<T, ROW_FWD>(p, a, st);
+}
+
+template <typename T>
+kzk_status to_physical(kzk_plan* p, const void* V, void* u, double scale, double* diag_rows, cudaStream_t st)
+{
+    RowArgs<T> a = row_args<T>(p, V, u, 0.0, diag_rows);
+    a.out_scale = (T)scale;
+    return launch_row<T, ROW_INV>(p, a, st);
+}
+
+kzk_status ensure_hist(kzk_plan* p, long long steps)
+{
+    if (steps <= p->hist_cap) return KZK_OK;
+    long long cap = std::max(steps, 2 * p->hist_cap);
+    if (p->diag_hist) KZK_CUDA(cudaFree(p->diag_hist));
+    p->diag_hist = nullptr;
+    KZK_CUDA(cudaMalloc(&p->diag_hist, (size_t)cap * p->batch * 4 * sizeof(double)));
+    p->hist_cap = cap;
+    return KZK_OK;
+}
+
+kzk_status finish_diag(kzk_plan* p, long long n_steps, cudaStream_t st, kzk_diag* out)
+{
+    KZK_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> hist((size_t)n_steps * p->batch * 4), fin((size_t)p->batch * 4);
+    if (n_steps > 0)
+        KZK_CUDA(cudaMemcpy(hist.data(), p->diag_hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    KZK_CUDA(cudaMemcpy(fin.data(), p->diag_final, fin.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    bool nonfinite = false, cfl = false;
+    for (int b = 0; b < p->batch; b++) {
+        kzk_diag d;
+        d.mean = fin[4 * b];
+        d.energy = fin[4 * b + 1];
+        d.max_abs = fin[4 * b + 2];
+        d.nonfinite = fin[4 * b + 3];
+        d.run_max_abs = d.max_abs;
+        d.run_nonfinite = d.nonfinite;
+        for (long long s = 0; s < n_steps; s++) {
+            const double* h = &hist[((size_t)s * p->batch + b) * 4];
+            d.run_max_abs = std::max(d.run_max_abs, h[2]);
+            d.run_nonfinite += h[3];
+        }
+        out[b] = d;
+        if (d.run_nonfinite > 0 || !std::isfinite(d.run_max_abs)) nonfinite = true;
+        if (d.run_max_abs > p->c.lf_umax) cfl = true;
+    }
+    if (nonfinite) return fail(KZK_ERR_NONFINITE, "non-finite values in the state");
+    if (cfl) return fail(KZK_ERR_CFL, "max|u| exceeded lf_umax = %g", p->c.lf_umax);
+    return KZK_OK;
+}
+
+template <typename T>
+kzk_status advance_impl(kzk_plan* p, void* u, long long n_steps, double sigma0, cudaStream_t st, kzk_diag* dout)
+{
+    KZK_TRY(ensure_hist(p, std::max(1LL, n_steps)));
+    KZK_TRY(to_spectral<T>(p, u, p->V, st));
+    for (long long s = 0; s < n_steps; s++) {
+        const double sigma = sigma0 + (double)s * p->dt;
+        KZK_TRY(step<T>(p, sigma, st, p->diag_hist + (size_t)s * p->batch * 4, p->V, p->vs));
+    }
+    KZK_TRY(to_physical<T>(p, p->V, u, 1.0, p->diag_rows, st));
+    diag_reduce_kernel<<<p->batch, 256, 0, st>>>(p->diag_rows, p->ny, 1.0 / ((double)p->nx * p->ny),
+                                                 (p->g.tau_max - p->g.tau_min) / p->nx *
+                                                     (p->g.y_max - p->g.y_min) / p->ny,
+                                                 p->diag_final);
+    KZK_LAUNCHED();
+    p->hist_steps = n_steps;
+    if (dout) return finish_diag(p, n_steps, st, dout);
+    return KZK_OK;
+}
+
+template <typename T>
+kzk_status build_tables(kzk_plan* p, cudaStream_t st)
+{
+    TabArgs a;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.dt = p->dt;
+    a.A = p->c.A;
+    a.diffraction = p->c.diffraction;
+    a.reg_eps = p->c.reg_eps;
+    a.kts = 2.0 * M_PI / (p->g.tau_max - p->g.tau_min);
+    a.kys = 2.0 * M_PI / (p->g.y_max - p->g.y_min);
+    a.E = p->E;
+    a.P1 = p->P1;
+    a.P2 = p->P2;
+    const long long count = (long long)(p->ny / 2 + 1) * p->n;
+    tables_kernel<T><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a);
+    KZK_LAUNCHED();
+    auto tr = twiddles<T>(p->nx);
+    auto tc = twiddles<T>(p->ny);
+    KZK_CUDA(cudaMemcpy(p->twr, tr.data(), tr.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    KZK_CUDA(cudaMemcpy(p->twc, tc.data(), tc.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    KZK_CUDA(cudaStreamSynchronize(st));
+    return KZK_OK;
+}
+
+void plan_free(kzk_plan* p)
+{
+    if (!p) return;
+    void* ptrs[] = {p->V, p->b1, p->vs, p->b2, p->E, p->P1, p->P2, p->twr, p->twc,
+                    p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
+                    p->seg, p->ckpt};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Adjoint driver (kernels in kzk_adjoint.cuh)
+// ---------------------------------------------------------------------------
+namespace {
+
+kzk_status ensure_buf(void** ptr, long long* cap, long long need, size_t unit)
+{
+    if (need <= *cap) return KZK_OK;
+    if (*ptr) KZK_CUDA(cudaFree(*ptr));
+    *ptr = nullptr;
+    *cap = 0;
+    KZK_CUDA(cudaMalloc(ptr, (size_t)need * unit));
+    *cap = need;
+    return KZK_OK;
+}
+
+template <typename T>
+AdjRowArgs<T> adj_row_args(const kzk_plan* p, const void* m, const void* v, const void* l, void* out, double sigma)
+{
+    AdjRowArgs<T> a;
+    a.m = (const cx<T>*)m;
+    a.v = (const cx<T>*)v;
+    a.l = (const cx<T>*)l;
+    a.out = (cx<T>*)out;
+    a.tw = (const cx<T>*)p->twr;
+    a.log2nx = p->log2nx;
+    a.inst_stride = p->inst_stride;
+    const double Bs = B_of(p, sigma);
+    a.wc.B = (T)Bs;
+    a.wc.alpha = (T)(Bs * p->c.lf_umax);
+    a.wc.eps = (T)p->c.weno_eps;
+    a.wc.inv_dtau = (T)(p->nx / (p->g.tau_max - p->g.tau_min));
+    a.dA = (T)dA_of(p, sigma);
+    a.kscale = (T)(2.0 * M_PI / (p->g.tau_max - p->g.tau_min));
+    a.inv_nx = (T)(1.0 / p->nx);
+    return a;
+}
+
+template <typename T>
+AdjColArgs<T> adj_col_args(const kzk_plan* p)
+{
+    AdjColArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.tw = (const cx<T>*)p->twc;
+    a.log2ny = p->log2ny;
+    a.log2n = p->log2nx - 1;
+    a.log2tc = p->log2tc;
+    a.inst_stride = p->inst_stride;
+    return a;
+}
+
+// Transposed step on the plan's cotangent p->lam (packed spectral), given the
+// step's stage states V^n and V* (packed spectral).
+template <typename T>
+kzk_status adjoint_step(kzk_plan* p, double sigma, const void* Vn, const void* Vs, cudaStream_t st)
+{
+    const dim3 cgrid(p->n >> p->log2tc, p->batch), rgrid(p->ny, p->batch);
+    const size_t rsm = adj_row_smem<T>(p);
+    // mu2 = P_{conj(ds Phi2)} lam'
+    AdjColArgs<T> c2 = adj_col_args<T>(p);
+    c2.a = (const cx<T>*)p->lam;
+    c2.out = (cx<T>*)p->mu;
+    c2.Ta = (const cx<T>*)p->P2;
+    c2.sa = (T)p->nx;
+    adj_col_kernel<T, col_ppt<T>(), ADJ_COL_2><<<cgrid, p->col_thr, p->col_smem, st>>>(c2);
+    KZK_LAUNCHED();
+    // lam* = lam' + J_{G_{n+1}}(u*)^T mu2
+    AdjRowArgs<T> r2 = adj_row_args<T>(p, p->mu, Vs, p->lam, p->ls, sigma + p->dt);
+    adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_2><<<rgrid, p->row_thr, rsm, st>>>(r2);
+    KZK_LAUNCHED();
+    // lam_lin = P_{conj E} lam*,  nu1 = P_{conj(ds Phi1)} lam* - mu2
+    AdjColArgs<T> c1 = adj_col_args<T>(p);
+    c1.a = (const cx<T>*)p->ls;
+    c1.b = (const cx<T>*)p->mu;
+    c1.out = (cx<T>*)p->ls;
+    c1.out2 = (cx<T>*)p->nu;
+    c1.Ta = (const cx<T>*)p->E;
+    c1.sa = (T)1;
+    c1.Tb = (const cx<T>*)p->P1;
+    c1.sb = (T)p->nx;
+    adj_col_kernel<T, col_ppt<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
+    KZK_LAUNCHED();
+    // lam = lam_lin + J_{G_n}(u)^T nu1
+    AdjRowArgs<T> r1 = adj_row_args<T>(p, p->nu, Vn, p->ls, p->lam, sigma);
+    adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_1><<<rgrid, p->row_thr, rsm, st>>>(r1);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
+template <typename T>
+kzk_status adjoint_impl(kzk_plan* p, const void* u0, const void* g_end, void* g0, long long n_steps,
+                        double sigma0, int ckpt_every, cudaStream_t st)
+{
+    const size_t arr = (size_t)p->batch * p->inst_stride * p->csz;   // bytes of one spectral array
+    if (!p->lam) {
+        KZK_CUDA(cudaMalloc(&p->lam, arr));
+        KZK_CUDA(cudaMalloc(&p->mu, arr));
+        KZK_CUDA(cudaMalloc(&p->nu, arr));
+        KZK_CUDA(cudaMalloc(&p->ls, arr));
+    }
+    const long long k = ckpt_every;
+    const long long n_ckpt = (n_steps + k - 1) / k;
+    KZK_TRY(ensure_buf(&p->ckpt, &p->ckpt_cap, std::max(1LL, n_ckpt), arr));
+    KZK_TRY(ensure_buf(&p->seg, &p->seg_cap, 2 * std::min(k, std::max(1LL, n_steps)), arr));
+    auto arr_at = [&](void* base, long long i) { return (void*)((char*)base + (size_t)i * arr); };
+
+    // forward sweep: checkpoints of the spectral state at steps 0, k, 2k, ...
+    KZK_TRY(to_spectral<T>(p, u0, p->V, st));
+    for (long long s = 0; s < n_steps; s++) {
+        if (s % k == 0) KZK_CUDA(cudaMemcpyAsync(arr_at(p->ckpt, s / k), p->V, arr, cudaMemcpyDeviceToDevice, st));
+        KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, p->V, p->vs));
+    }
+    // cotangent of the final state in spectral form
+    KZK_TRY(to_spectral<T>(p, g_end, p->lam, st));
+    for (long long c = n_ckpt - 1; c >= 0; c--) {
+        const long long s0 = c * k, s1 = std::min(n_steps, s0 + k);
+        // recompute the segment, storing (V^n, V*^n) per step
+        KZK_CUDA(cudaMemcpyAsync(p->V, arr_at(p->ckpt, c), arr, cudaMemcpyDeviceToDevice, st));
+        for (long long s = s0; s < s1; s++) {
+            void* Vn = arr_at(p->seg, 2 * (s - s0));
+            void* Vs = arr_at(p->seg, 2 * (s - s0) + 1);
+            KZK_CUDA(cudaMemcpyAsync(Vn, p->V, arr, cudaMemcpyDeviceToDevice, st));
+            KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, p->V, Vs));
+        }
+        for (long long s = s1 - 1; s >= s0; s--) {
+            const void* Vn = arr_at(p->seg, 2 * (s - s0));
+            const void* Vs = arr_at(p->seg, 2 * (s - s0) + 1);
+            KZK_TRY(adjoint_step<T>(p, sigma0 + (double)s * p->dt, Vn, Vs, st));
+        }
+    }
+    return to_physical<T>(p, p->lam, g0, 1.0, nullptr, st);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* kzk_status_string(kzk_status s)
+{
+    switch (s) {
+    case KZK_OK: return "ok";
+    case KZK_ERR_ARG: return "invalid argument";
+    case KZK_ERR_SIZE: return "unsupported grid size";
+    case KZK_ERR_CFL: return "max|u| exceeded the Lax-Friedrichs bound lf_umax";
+    case KZK_ERR_NONFINITE: return "non-finite value in the state";
+    case KZK_ERR_CUDA: return "CUDA error";
+    case KZK_ERR_TIMEOUT: return "bounded device wait timed out";
+    case KZK_ERR_OOM: return "device out of memory";
+    case KZK_ERR_STATE: return "call not valid for this plan";
+    }
+    return "unknown status";
+}
+
+const char* kzk_last_error(void) { return g_err; }
+
+int64_t kzk_launch_count(void) { return (int64_t)g_launches.load(); }
+
+kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, double dt, int32_t batch,
+                           kzk_plan** out)
+{
+    if (!out) return fail(KZK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !coeffs) return fail(KZK_ERR_ARG, "grid or coeffs is NULL");
+    if (grid->prec != KZK_FP64 && grid->prec != KZK_FP32) return fail(KZK_ERR_ARG, "bad precision %d", grid->prec);
+    if (!is_pow2(grid->nx) || !is_pow2(grid->ny) || grid->nx < 8 || grid->nx > 8192 || grid->ny < 2 ||
+        grid->ny > 4096)
+        return fail(KZK_ERR_SIZE, "nx = %d, ny = %d: powers of two in [8, 8192] x [2, 4096] required",
+                    grid->nx, grid->ny);
+    if (!(grid->tau_max > grid->tau_min) || !(grid->y_max > grid->y_min))
+        return fail(KZK_ERR_ARG, "empty domain");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(KZK_ERR_ARG, "dt must be positive and finite");
+    if (!(coeffs->B > 0) || !(coeffs->A >= 0) || !(coeffs->lf_umax > 0))
+        return fail(KZK_ERR_ARG, "need B > 0, A >= 0, lf_umax > 0");
+    if (batch < 1) return fail(KZK_ERR_ARG, "batch must be >= 1");
+
+    kzk_plan* p = new (std::nothrow) kzk_plan_s();
+    if (!p) return fail(KZK_ERR_OOM, "host allocation failed");
+    memset(p, 0, sizeof(*p));
+    p->g = *grid;
+    p->c = *coeffs;
+    if (!(p->c.diffraction > 0)) p->c.diffraction = 1.0 / (4.0 * M_PI);
+    if (!(p->c.reg_eps > 0)) p->c.reg_eps = grid->prec == KZK_FP64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+    if (!(p->c.weno_eps > 0)) p->c.weno_eps = 1e-6;
+    if (!p->c.has_profile) {
+        const double one[4] = {1, 0, 0, 0};
+        memcpy(p->c.B_prof, one, sizeof(one));
+        memcpy(p->c.A_prof, one, sizeof(one));
+    }
+    p->dt = dt;
+    p->batch = batch;
+    p->prec = grid->prec;
+    p->nx = grid->nx;
+    p->ny = grid->ny;
+    p->n = grid->nx / 2;
+    p->log2nx = ilog2(grid->nx);
+    p->log2ny = ilog2(grid->ny);
+    p->csz = p->prec == KZK_FP64 ? sizeof(double2) : sizeof(float2);
+    p->inst_stride = (long long)p->ny * p->n;
+
+    kzk_status s = p->prec == KZK_FP64 ? configure<double>(p) : configure<float>(p);
+    if (s != KZK_OK) { plan_free(p); return s; }
+
+    const size_t arr = (size_t)batch * p->inst_stride * p->csz;
+    const size_t tab = (size_t)(p->ny / 2 + 1) * p->n * p->csz;
+    cudaError_t e = cudaSuccess;
+    void** bufs[] = {&p->V, &p->b1, &p->vs, &p->b2};
+    for (void** b : bufs)
+        if (e == cudaSuccess) e = cudaMalloc(b, arr);
+    void** tabs[] = {&p->E, &p->P1, &p->P2};
+    for (void** t : tabs)
+        if (e == cudaSuccess) e = cudaMalloc(t, tab);
+    if (e == cudaSuccess) e = cudaMalloc(&p->twr, (size_t)p->nx * p->csz);
+    if (e == cudaSuccess) e = cudaMalloc(&p->twc, (size_t)p->ny * p->csz);
+    if (e == cudaSuccess) e = cudaMalloc(&p->diag_rows, (size_t)batch * p->ny * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p->diag_final, (size_t)batch * 4 * sizeof(double));
+    if (e != cudaSuccess) {
+        plan_free(p);
+        return fail(e == cudaErrorMemoryAllocation ? KZK_ERR_OOM : KZK_ERR_CUDA, "plan allocation: %s",
+                    cudaGetErrorString(e));
+    }
+    s = p->prec == KZK_FP64 ? build_tables<double>(p, 0) : build_tables<float>(p, 0);
+    if (s != KZK_OK) { plan_free(p); return s; }
+    *out = p;
+    return KZK_OK;
+}
+
+kzk_status kzk_plan_destroy(kzk_plan* plan)
+{
+    plan_free(plan);
+    return KZK_OK;
+}
+
+kzk_status kzk_advance(kzk_plan* p, void* u, int64_t n_steps, double sigma0, void* stream, kzk_diag* diag_out)
+{
+    if (!p || !u) return fail(KZK_ERR_ARG, "plan or u is NULL");
+    if (n_steps < 0) return fail(KZK_ERR_ARG, "n_steps < 0");
+    if (n_steps == 0 && !diag_out) return KZK_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    return p->prec == KZK_FP64 ? advance_impl<double>(p, u, n_steps, sigma0, st, diag_out)
+                               : advance_impl<float>(p, u, n_steps, sigma0, st, diag_out);
+}
+
+kzk_status kzk_diag_history(kzk_plan* p, double* hist, int64_t n, void* stream)
+{
+    if (!p || !hist) return fail(KZK_ERR_ARG, "plan or hist is NULL");
+    const long long m = std::min<long long>(n, p->hist_steps);
+    KZK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (m > 0)
+        KZK_CUDA(cudaMemcpy(hist, p->diag_hist, (size_t)m * p->batch * 4 * sizeof(double), cudaMemcpyDeviceToHost));
+    return KZK_OK;
+}
+
+kzk_status kzk_rhs(kzk_plan* p, const void* u, void* b, double sigma, void* stream)
+{
+    if (!p || !u || !b) return fail(KZK_ERR_ARG, "NULL argument");
+    if (u == b) return fail(KZK_ERR_ARG, "b may not alias u");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prec == KZK_FP64) {
+        KZK_TRY(to_spectral<double>(p, u, p->V, st));
+        KZK_TRY((launch_row<double, ROW_RHS>(p, row_args<double>(p, p->V, p->b1, sigma, nullptr), st)));
+        return to_physical<double>(p, p->b1, b, 1.0 / p->nx, nullptr, st);
+    }
+    KZK_TRY(to_spectral<float>(p, u, p->V, st));
+    KZK_TRY((launch_row<float, ROW_RHS>(p, row_args<float>(p, p->V, p->b1, sigma, nullptr), st)));
+    return to_physical<float>(p, p->b1, b, 1.0 / p->nx, nullptr, st);
+}
+
+kzk_status kzk_step_stages(kzk_plan* p, const void* u, void* u_star, void* u_next, double sigma0, void* stream)
+{
+    if (!p || !u || !u_star || !u_next) return fail(KZK_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prec == KZK_FP64) {
+        KZK_TRY(to_spectral<double>(p, u, p->V, st));
+        KZK_TRY(step<double>(p, sigma0, st, nullptr, p->V, p->vs));
+        KZK_TRY(to_physical<double>(p, p->vs, u_star, 1.0, nullptr, st));
+        return to_physical<double>(p, p->V, u_next, 1.0, nullptr, st);
+    }
+    KZK_TRY(to_spectral<float>(p, u, p->V, st));
+    KZK_TRY(step<float>(p, sigma0, st, nullptr, p->V, p->vs));
+    KZK_TRY(to_physical<float>(p, p->vs, u_star, 1.0, nullptr, st));
+    return to_physical<float>(p, p->V, u_next, 1.0, nullptr, st);
+}
+
+kzk_status kzk_tau_fft(kzk_plan* p, const void* in, void* out, int32_t dir, void* stream)
+{
+    if (!p || !in || !out) return fail(KZK_ERR_ARG, "NULL argument");
+    if (in == out) return fail(KZK_ERR_ARG, "in and out may not alias");
+    if (dir != -1 && dir != 1) return fail(KZK_ERR_ARG, "dir must be -1 or +1");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prec == KZK_FP64)
+        return dir < 0 ? to_spectral<double>(p, in, out, st) : to_physical<double>(p, in, out, 1.0, nullptr, st);
+    return dir < 0 ? to_spectral<float>(p, in, out, st) : to_physical<float>(p, in, out, 1.0, nullptr, st);
+}
+
+kzk_status kzk_get_tables(kzk_plan* p, double* E, double* Phi1, double* Phi2)
+{
+    if (!p || !E || !Phi1 || !Phi2) return fail(KZK_ERR_ARG, "NULL argument");
+    KZK_CUDA(cudaDeviceSynchronize());
+    const int nl = p->ny / 2 + 1, n = p->n;
+    const size_t cnt = (size_t)nl * n;
+    std::vector<double> raw(cnt * 2);
+    void* src[3] = {p->E, p->P1, p->P2};
+    double* dst[3] = {E, Phi1, Phi2};
+    const double unscale[3] = {(double)p->ny, (double)p->nx * p->ny / p->dt, (double)p->nx * p->ny / p->dt};
+    for (int t = 0; t < 3; t++) {
+        if (p->prec == KZK_FP64) {
+            KZK_CUDA(cudaMemcpy(raw.data(), src[t], cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f(cnt * 2);
+            KZK_CUDA(cudaMemcpy(f.data(), src[t], cnt * sizeof(float2), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < f.size(); i++) raw[i] = f[i];
+        }
+        const int w = n + 1;
+        for (int l = 0; l < nl; l++) {
+            for (int m = 0; m < n; m++) {
+                const double re = raw[2 * ((size_t)l * n + m)] * unscale[t];
+                const double im = raw[2 * ((size_t)l * n + m) + 1] * unscale[t];
+                if (m == 0) {
+                    dst[t][2 * ((size_t)l * w + 0)] = re;
+                    dst[t][2 * ((size_t)l * w + 0) + 1] = 0.0;
+                    dst[t][2 * ((size_t)l * w + n)] = im;
+                    dst[t][2 * ((size_t)l * w + n) + 1] = 0.0;
+                } else {
+                    dst[t][2 * ((size_t)l * w + m)] = re;
+                    dst[t][2 * ((size_t)l * w + m) + 1] = im;
+                }
+            }
+        }
+    }
+    return KZK_OK;
+}
+
+kzk_status kzk_adjoint(kzk_plan* p, const void* u0, const void* g_end, void* g0, int64_t n_steps, double sigma0,
+                       int32_t ckpt_every, void* stream)
+{
+    if (!p || !u0 || !g_end || !g0) return fail(KZK_ERR_ARG, "NULL argument");
+    if (n_steps < 0 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 0 and ckpt_every >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_steps == 0) {
+        if (g0 != g_end)
+            KZK_CUDA(cudaMemcpyAsync(g0, g_end, (size_t)p->batch * p->ny * p->nx * (p->csz / 2),
+                                     cudaMemcpyDeviceToDevice, st));
+        return KZK_OK;
+    }
+    return p->prec == KZK_FP64 ? adjoint_impl<double>(p, u0, g_end, g0, n_steps, sigma0, ckpt_every, st)
+                               : adjoint_impl<float>(p, u0, g_end, g0, n_steps, sigma0, ckpt_every, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// kzk_common.cuh -- complex arithmetic and small helpers shared by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kzk {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cx = typename cplx_of<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T r, T i) { cx<T> c; c.x = r; c.y = i; return c; }
+template <typename T> __device__ __forceinline__ cx<T> add(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cx<T> sub(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cx<T> conj(cx<T> a) { return mk<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ cx<T> scale(cx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ cx<T> mul(cx<T> a, cx<T> b)
+{
+    return mk<T>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ cx<T> mulc(cx<T> a, cx<T> b)
+{
+    return mk<T>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// a * (s i) with s = +1 / -1 (exact)
+template <typename T, int S> __device__ __forceinline__ cx<T> mul_si(cx<T> a)
+{
+    return S > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+// acc + a * b
+template <typename T> __device__ __forceinline__ cx<T> fma_c(cx<T> a, cx<T> b, cx<T> acc)
+{
+    return mk<T>(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+
+__host__ __device__ __forceinline__ int ilog2(unsigned v)
+{
+    int r = 0;
+    while ((1u << r) < v) ++r;
+    return r;
+}
+
+// Launch-time error flags (bit set in plan->flags by device code).
+enum : int { FLAG_TIMEOUT = 1, FLAG_BAD_LAUNCH = 2 };
+
+}  // namespace kzk

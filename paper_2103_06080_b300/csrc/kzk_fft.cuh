@@ -1,0 +1,176 @@
+// kzk_fft.cuh -- shared-memory Stockham FFTs (power-of-two lengths).
+//
+// A batch of nb independent complex transforms of length n = 2^log2n lives in
+// shared memory; element i of transform b sits at buf[b * sb + i * si].  Each
+// stage is an autosort (Stockham) pass of radix R in {2, 4, 8, 16}: a thread
+// loads R points with stride n/R into registers, applies the inter-stage
+// twiddles, runs an in-register DFT of size R and writes the results to
+// their sorted positions, so the output is in natural order with no bit
+// reversal.  Twiddles come from a plan-time table tw[k] = exp(-2 pi i k / Ntw)
+// (Ntw = 2^tw_log2 >= n), built in FP64 on the host.
+//
+// Forward transforms use exp(-2 pi i ...), inverse ones exp(+2 pi i ...); no
+// transform is normalised (the 1/N factors are folded into the tables).
+#pragma once
+#include "kzk_common.cuh"
+
+namespace kzk {
+
+// cos(2 pi j / 16), exact to double rounding
+__host__ __device__ constexpr double cos16(int j)
+{
+    switch (j & 15) {
+    case 0: return 1.0;
+    case 1: return 0.92387953251128675613;
+    case 2: return 0.70710678118654752440;
+    case 3: return 0.38268343236508977173;
+    case 4: return 0.0;
+    case 5: return -0.38268343236508977173;
+    case 6: return -0.70710678118654752440;
+    case 7: return -0.92387953251128675613;
+    case 8: return -1.0;
+    case 9: return -0.92387953251128675613;
+    case 10: return -0.70710678118654752440;
+    case 11: return -0.38268343236508977173;
+    case 12: return 0.0;
+    case 13: return 0.38268343236508977173;
+    case 14: return 0.70710678118654752440;
+    default: return 0.92387953251128675613;
+    }
+}
+__host__ __device__ constexpr double sin16(int j) { return cos16(j - 4); }
+
+// x * exp(S 2 pi i k / R) for compile-time R | 16, k; trivial factors are exact.
+template <typename T, int R, int K, int S>
+__device__ __forceinline__ cx<T> rot(cx<T> x)
+{
+    constexpr int j = (K * (16 / R)) & 15;          // angle 2 pi j / 16
+    if constexpr (j == 0) return x;
+    else if constexpr (j == 4) return mul_si<T, S>(x);
+    else if constexpr (j == 8) return mk<T>(-x.x, -x.y);
+    else if constexpr (j == 12) return mul_si<T, -S>(x);
+    else {
+        constexpr T c = (T)cos16(j);
+        constexpr T s = (T)(S * sin16(j));
+        return mk<T>(fma(x.x, c, -x.y * s), fma(x.x, s, x.y * c));
+    }
+}
+
+// In-register DFT of size R (natural order in and out), sign S.
+template <typename T, int R, int S> struct RegDFT {
+    template <int K>
+    static __device__ __forceinline__ void combine(cx<T>* v, const cx<T>* e, const cx<T>* o)
+    {
+        if constexpr (K < R / 2) {
+            cx<T> t = rot<T, R, K, S>(o[K]);
+            v[K] = add<T>(e[K], t);
+            v[K + R / 2] = sub<T>(e[K], t);
+            combine<K + 1>(v, e, o);
+        }
+    }
+    static __device__ __forceinline__ void run(cx<T>* v)
+    {
+        if constexpr (R == 1) {
+            return;
+        } else if constexpr (R == 2) {
+            cx<T> a = v[0], b = v[1];
+            v[0] = add<T>(a, b);
+            v[1] = sub<T>(a, b);
+        } else if constexpr (R == 4) {
+            cx<T> a0 = add<T>(v[0], v[2]), a1 = sub<T>(v[0], v[2]);
+            cx<T> a2 = add<T>(v[1], v[3]), a3 = mul_si<T, S>(sub<T>(v[1], v[3]));
+            v[0] = add<T>(a0, a2);
+            v[2] = sub<T>(a0, a2);
+            v[1] = add<T>(a1, a3);
+            v[3] = sub<T>(a1, a3);
+        } else {
+            cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+            for (int i = 0; i < R / 2; i++) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+            RegDFT<T, R / 2, S>::run(e);
+            RegDFT<T, R / 2, S>::run(o);
+            combine<0>(v, e, o);
+        }
+    }
+};
+
+// One Stockham pass of radix R over a batch.  PPT = points each thread holds
+// (PPT / R butterflies per pass).  COLS: consecutive threads take consecutive
+// transforms (column tiles, transform index fastest in memory); otherwise
+// consecutive threads take consecutive butterflies of one transform.
+template <typename T, int R, int PPT, bool COLS, bool INV>
+__device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int si, int sb,
+                                         int log2Ns, const cx<T>* __restrict__ tw, int tw_log2,
+                                         int tid, int nthr)
+{
+    constexpr int NB = PPT / R;
+    constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
+    constexpr int S = INV ? 1 : -1;
+    const int log2nbf = log2n - LR;                 // butterflies per transform = n / R
+    const int total = 1 << (log2nb + log2nbf);
+    const int Ns = 1 << log2Ns;
+    const int twsh = tw_log2 - log2Ns - LR;         // table index = r * k << twsh
+    cx<T> v[NB][R];
+    int obase[NB];
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+        int t = tid + q * nthr;
+        obase[q] = -1;
+        if (t < total) {
+            int b, j;
+            if (COLS) { b = t & ((1 << log2nb) - 1); j = t >> log2nb; }
+            else { b = t >> log2nbf; j = t & ((1 << log2nbf) - 1); }
+            const int k = j & (Ns - 1);
+            const int ib = b * sb + j * si;
+            const int stride = (1 << log2nbf) * si;
+#pragma unroll
+            for (int r = 0; r < R; r++) v[q][r] = buf[ib + r * stride];
+            if (log2Ns > 0) {
+#pragma unroll
+                for (int r = 1; r < R; r++) {
+                    cx<T> w = tw[(r * k) << twsh];
+                    v[q][r] = INV ? mulc<T>(v[q][r], w) : mul<T>(v[q][r], w);
+                }
+            }
+            RegDFT<T, R, S>::run(v[q]);
+            obase[q] = b * sb + (((j - k) << LR) + k) * si;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NB; q++) {
+        if (obase[q] >= 0) {
+#pragma unroll
+            for (int r = 0; r < R; r++) buf[obase[q] + r * Ns * si] = v[q][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Full transform: radix-16 passes while possible, then one smaller pass.
+// Requires nthr * PPT >= nb * n.  Ends with a __syncthreads().
+template <typename T, int PPT, bool COLS, bool INV>
+__device__ __forceinline__ void fft_batched(cx<T>* buf, int log2n, int log2nb, int si, int sb,
+                                            const cx<T>* __restrict__ tw, int tw_log2, int tid,
+                                            int nthr)
+{
+    int done = 0;
+    while (done < log2n) {
+        const int rem = log2n - done;
+        if (PPT >= 16 && rem >= 4) {
+            fft_pass<T, (PPT >= 16 ? 16 : 2), PPT, COLS, INV>(buf, log2n, log2nb, si, sb, done, tw, tw_log2, tid, nthr);
+            done += (PPT >= 16 ? 4 : 1);
+        } else if (PPT >= 8 && rem >= 3) {
+            fft_pass<T, (PPT >= 8 ? 8 : 2), PPT, COLS, INV>(buf, log2n, log2nb, si, sb, done, tw, tw_log2, tid, nthr);
+            done += (PPT >= 8 ? 3 : 1);
+        } else if (PPT >= 4 && rem >= 2) {
+            fft_pass<T, (PPT >= 4 ? 4 : 2), PPT, COLS, INV>(buf, log2n, log2nb, si, sb, done, tw, tw_log2, tid, nthr);
+            done += (PPT >= 4 ? 2 : 1);
+        } else {
+            fft_pass<T, 2, PPT, COLS, INV>(buf, log2n, log2nb, si, sb, done, tw, tw_log2, tid, nthr);
+            done += 1;
+        }
+    }
+}
+
+}  // namespace kzk

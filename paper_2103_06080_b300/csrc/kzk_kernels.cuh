@@ -1,0 +1,371 @@
+// kzk_kernels.cuh -- row (tau) and column (y) kernels of one ExpRK22 step.
+//
+// Spectral state layout (device, per instance): V[ny][nx/2] complex, row j
+// holding the tau-spectrum of grid row j divided by nx, packed: slot 0 holds
+// (F(u)[0], F(u)[nx/2]) / nx, both real for real rows.  Every array of the
+// step (V, b1, V*, b2) uses this layout, so a tau-row is contiguous and a
+// column tile is a strided band.
+//
+// One step (Algorithm 2, STEP 1-4) is four passes over HBM:
+//   R(V -> b1):       tau-C2R into shared memory, WENO5, tau-R2C     (STEP 1)
+//   C1(V, b1 -> V*):  y-FFT of both, V* = E V + dsigma Phi1 b1, y-IFFT (STEP 2)
+//   R(V* -> b2):                                                      (STEP 3)
+//   C2(V*, b1, b2 -> V): y-FFT of b2 - b1,
+//                     V' = V* + IFFT(dsigma Phi2 (b2 - b1))           (STEP 4)
+// The last line is STEP 4 rewritten with STEP 2:
+//   E V + ds[(Phi1 - Phi2) b1 + Phi2 b2] = V* + ds Phi2 (b2 - b1),
+// which needs neither E nor Phi1 again.  The 1/nx, 1/ny normalisations and
+// dsigma are folded into the tables (powers of two: exact).
+#pragma once
+#include "kzk_common.cuh"
+#include "kzk_fft.cuh"
+#include "kzk_weno.cuh"
+
+namespace kzk {
+
+enum RowMode { ROW_RHS = 0, ROW_FWD = 1, ROW_INV = 2 };
+
+template <typename T>
+struct RowArgs {
+    const cx<T>* in;        // ROW_RHS / ROW_INV: spectral rows; ROW_FWD: physical rows (as T)
+    cx<T>* out;             // ROW_RHS / ROW_FWD: spectral rows; ROW_INV: physical rows (as T)
+    const cx<T>* tw;        // exp(-2 pi i k / nx), k in [0, nx)
+    double* diag_rows;      // [batch][ny][4] or nullptr
+    int log2nx;
+    int ny;
+    long long inst_stride;  // complex elements per instance (ny * nx / 2)
+    WenoCoef<T> wc;
+    T cA;                   // nx * (A(sigma) - A): absorption-deviation term
+    T kscale;               // 2 pi / (tau_max - tau_min)
+    T out_scale;            // ROW_FWD: 1/nx; ROW_INV: scale of the result
+};
+
+// Block reduction of the four diagnostics (FP64 across threads, fixed
+// order: deterministic).  blockDim.x must be a power of two; red holds
+// 4 * blockDim.x doubles.
+__device__ __forceinline__ void block_diag(double* red, double s1, double s2, double mx, double nf,
+                                           double* dst)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    double* r0 = red;
+    double* r1 = red + nthr;
+    double* r2 = red + 2 * nthr;
+    double* r3 = red + 3 * nthr;
+    r0[tid] = s1; r1[tid] = s2; r2[tid] = mx; r3[tid] = nf;
+    __syncthreads();
+    for (int h = nthr >> 1; h > 0; h >>= 1) {
+        if (tid < h) {
+            r0[tid] += r0[tid + h];
+            r1[tid] += r1[tid + h];
+            r2[tid] = fmax(r2[tid], r2[tid + h]);
+            r3[tid] += r3[tid + h];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) { dst[0] = r0[0]; dst[1] = r1[0]; dst[2] = r2[0]; dst[3] = r3[0]; }
+    __syncthreads();
+}
+
+// C2R pre-processing in place: packed half spectrum X (n = nx/2 slots) ->
+// Z with IFFT_n(Z) = nx * (x_even + i x_odd), Z_k = (X_k + conj X_{n-k})
+// + i conj(W^k) (X_k - conj X_{n-k}), W = exp(-2 pi i / nx).
+template <typename T>
+__device__ __forceinline__ void c2r_pre(cx<T>* X, int n, const cx<T>* __restrict__ tw, int tid, int nthr)
+{
+    for (int k = tid; k <= n / 2; k += nthr) {
+        if (k == 0) {
+            const T x0 = X[0].x, xn = X[0].y;
+            X[0] = mk<T>(x0 + xn, x0 - xn);
+            if (n == 1) continue;
+        } else if (2 * k == n) {
+            const cx<T> a = X[k];
+            X[k] = mk<T>(T(2) * a.x, T(-2) * a.y);
+        } else {
+            const cx<T> a = X[k], b = X[n - k];
+            const cx<T> w = tw[k];                      // W^k
+            // k
+            cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
+            cx<T> r = mul_si<T, 1>(mulc<T>(d, w));      // i conj(W^k) d
+            const cx<T> zk = add<T>(s, r);
+            // n - k: W^{n-k} = -conj(W^k)  =>  conj(W^{n-k}) = -W^k
+            s = add<T>(b, conj<T>(a)); d = sub<T>(b, conj<T>(a));
+            r = mul_si<T, -1>(mul<T>(d, w));            // i (-W^k) d
+            X[k] = zk;
+            X[n - k] = add<T>(s, r);
+        }
+    }
+}
+
+// R2C post-processing: Z = FFT_n(x_even + i x_odd) -> packed X = FFT_nx(x),
+// X_k = 1/2 [(Z_k + conj Z_{n-k}) - i W^k (Z_k - conj Z_{n-k})].
+// Returns the pair (X_k, X_{n-k}) for 0 < k < n/2, handles k = 0 and n/2.
+template <typename T>
+__device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, const cx<T>* __restrict__ tw,
+                                              cx<T>& Xk, cx<T>& Xnk)
+{
+    const T h = T(0.5);
+    if (k == 0) {
+        const cx<T> z = Z[0];
+        Xk = mk<T>(z.x + z.y, z.x - z.y);    // (X_0, X_{nx/2}) packed
+        Xnk = Xk;
+    } else if (2 * k == n) {
+        Xk = conj<T>(Z[k]);
+        Xnk = Xk;
+    } else {
+        const cx<T> a = Z[k], b = Z[n - k];
+        const cx<T> w = tw[k];
+        cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
+        cx<T> r = mul_si<T, -1>(mul<T>(w, d));            // -i W^k d
+        Xk = scale<T>(add<T>(s, r), h);
+        // n-k: W^{n-k} = -conj(W^k)  =>  -i W^{n-k} d' = i conj(W^k) d'
+        s = add<T>(b, conj<T>(a)); d = sub<T>(b, conj<T>(a));
+        r = mul_si<T, 1>(mulc<T>(d, w));
+        Xnk = scale<T>(add<T>(s, r), h);
+    }
+}
+
+// Row kernel.  One CTA per (row, instance).  Shared memory: two buffers of
+// nx reals (= n complex) each, plus a reduction area.
+template <typename T, int PPT, int MODE>
+__global__ void __launch_bounds__(1024) row_kernel(RowArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nx = 1 << a.log2nx, n = nx >> 1, log2n = a.log2nx - 1;
+    const int row = blockIdx.x, inst = blockIdx.y;
+    cx<T>* X = reinterpret_cast<cx<T>*>(smem_raw);       // buffer U
+    cx<T>* Y = X + n;                                      // buffer B
+    double* red = reinterpret_cast<double*>(Y + n);
+    const long long base = (long long)inst * a.inst_stride + (long long)row * n;
+
+    if (MODE == ROW_FWD) {
+        // physical row -> packed half spectrum / nx
+        const T* src = reinterpret_cast<const T*>(a.in + base);
+        T* y = reinterpret_cast<T*>(Y);
+        for (int i = tid; i < nx; i += nthr) y[i] = src[i];
+        __syncthreads();
+        fft_batched<T, PPT, false, false>(Y, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+        for (int k = tid; k <= n / 2; k += nthr) {
+            cx<T> xk, xnk;
+            r2c_post_pair<T>(Y, n, k, a.tw, xk, xnk);
+            a.out[base + k] = scale<T>(xk, a.out_scale);
+            if (k != 0 && 2 * k != n) a.out[base + n - k] = scale<T>(xnk, a.out_scale);
+        }
+        return;
+    }
+
+    // spectral row -> physical row in X
+    for (int i = tid; i < n; i += nthr) X[i] = a.in[base + i];
+    __syncthreads();
+    c2r_pre<T>(X, n, a.tw, tid, nthr);
+    __syncthreads();
+    fft_batched<T, PPT, false, true>(X, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+    const T* u = reinterpret_cast<const T*>(X);
+
+    T s1 = 0, s2 = 0, mx = 0;
+    int nf = 0;
+    if (MODE == ROW_INV) {
+        T* dst = reinterpret_cast<T*>(a.out + base);
+        for (int i = tid; i < nx; i += nthr) {
+            const T v = u[i] * a.out_scale;
+            dst[i] = v;
+            if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf++; }
+        }
+        if (a.diag_rows) block_diag(red, (double)s1, (double)s2, (double)mx, (double)nf,
+                                    a.diag_rows + ((long long)inst * a.ny + row) * 4);
+        return;
+    }
+
+    // ROW_RHS: WENO5 flux derivative into Y, then tau-R2C of Y
+    {
+        T* bphys = reinterpret_cast<T*>(Y);
+        const int Q = nx >= nthr ? nx / nthr : 1;
+        const int k0 = tid * Q;
+        if (k0 < nx) weno_row_chunk<T>(u, bphys, nx, k0, Q, a.wc, s1, s2, mx, nf);
+    }
+    __syncthreads();
+    fft_batched<T, PPT, false, false>(Y, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+    const cx<T>* vin = a.in + base;
+    for (int k = tid; k <= n / 2; k += nthr) {
+        cx<T> xk, xnk;
+        r2c_post_pair<T>(Y, n, k, a.tw, xk, xnk);
+        if (a.cA != T(0)) {
+            // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
+            if (k == 0) {
+                const T kN = a.kscale * T(n);
+                xk.y -= a.cA * kN * kN * vin[0].y;
+            } else {
+                const T kt = a.kscale * T(k);
+                const cx<T> v = vin[k];
+                xk.x -= a.cA * kt * kt * v.x;
+                xk.y -= a.cA * kt * kt * v.y;
+                if (2 * k != n) {
+                    const T kt2 = a.kscale * T(n - k);
+                    const cx<T> w = vin[n - k];
+                    xnk.x -= a.cA * kt2 * kt2 * w.x;
+                    xnk.y -= a.cA * kt2 * kt2 * w.y;
+                }
+            }
+        }
+        a.out[base + k] = xk;
+        if (k != 0 && 2 * k != n) a.out[base + n - k] = xnk;
+    }
+    if (a.diag_rows) block_diag(red, (double)s1, (double)s2, (double)mx, (double)nf,
+                                a.diag_rows + ((long long)inst * a.ny + row) * 4);
+}
+
+enum ColMode { COL_STAGE1 = 0, COL_STAGE2 = 1 };
+
+template <typename T>
+struct ColArgs {
+    const cx<T>* a;         // STAGE1: V;    STAGE2: b1
+    const cx<T>* b;         // STAGE1: b1;   STAGE2: b2
+    const cx<T>* c;         // STAGE1: -;    STAGE2: V*
+    cx<T>* out;             // STAGE1: V*;   STAGE2: V'
+    const cx<T>* Ta;        // STAGE1: E';   STAGE2: P2'
+    const cx<T>* Tb;        // STAGE1: P1';  STAGE2: -
+    const cx<T>* tw;        // exp(-2 pi i k / ny), k in [0, ny)
+    int log2ny, log2n, log2tc;
+    long long inst_stride;
+    // diagnostics of the step (STAGE1, CTA x = 0 of each instance)
+    const double* diag_rows;  // [batch][ny][4] or nullptr
+    double* diag_hist;        // [batch][4] for this step
+    double inv_count, cell;   // 1/(nx ny), dtau dy
+};
+
+// Multiplier at (l, m) applied to the column-FFT'd tile S ([ny][TC], natural
+// order).  Column m = 0 packs the tau-DC (real part) and tau-Nyquist (imag
+// part) sequences; their spectra are separated through the pair (l, ny - l)
+// and each is multiplied by its own real table entry.
+template <typename T>
+__device__ __forceinline__ cx<T> apply_mult(const cx<T>* __restrict__ tab, const cx<T>* S, int l, int c, int m,
+                                            int ny, int n, int log2tc)
+{
+    const int lf = l <= (ny >> 1) ? l : ny - l;
+    const cx<T> M = tab[(long long)lf * n + m];
+    const cx<T> z = S[(l << log2tc) + c];
+    if (m != 0) return mul<T>(M, z);
+    const cx<T> zm = S[(((ny - l) & (ny - 1)) << log2tc) + c];
+    const T h = T(0.5) * (M.x + M.y), g = T(0.5) * (M.x - M.y);
+    return mk<T>(h * z.x + g * zm.x, h * z.y - g * zm.y);
+}
+
+template <typename T, int PPT, int MODE>
+__global__ void __launch_bounds__(1024) col_kernel(ColArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* S = reinterpret_cast<cx<T>*>(smem_raw);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ny = 1 << a.log2ny, n = 1 << a.log2n, TC = 1 << a.log2tc;
+    const int m0 = blockIdx.x * TC, inst = blockIdx.y;
+    const long long ibase = (long long)inst * a.inst_stride;
+    const int total = ny << a.log2tc;
+    cx<T> acc[PPT];
+
+    auto gidx = [&](int e) -> long long {
+        return ibase + (long long)(e >> a.log2tc) * n + m0 + (e & (TC - 1));
+    };
+
+    if (MODE == COL_STAGE1) {
+        // diagnostics of the state this step started from (rows written by R)
+        if (blockIdx.x == 0 && a.diag_rows) {
+            double* red = reinterpret_cast<double*>(smem_raw);
+            double s1 = 0, s2 = 0, mx = 0, nf = 0;
+            const double* dr = a.diag_rows + (long long)inst * ny * 4;
+            for (int r = tid; r < ny; r += nthr) {
+                s1 += dr[4 * r]; s2 += dr[4 * r + 1]; mx = fmax(mx, dr[4 * r + 2]); nf += dr[4 * r + 3];
+            }
+            double tmp[4];
+            block_diag(red, s1, s2, mx, nf, tmp);
+            if (tid == 0) {
+                double* d = a.diag_hist + inst * 4;
+                d[0] = tmp[0] * a.inv_count;
+                d[1] = tmp[1] * a.cell;
+                d[2] = tmp[2];
+                d[3] = tmp[3];
+            }
+        }
+        for (int e = tid; e < total; e += nthr) S[e] = a.a[gidx(e)];
+        __syncthreads();
+        fft_batched<T, PPT, true, false>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+#pragma unroll
+        for (int q = 0; q < PPT; q++) {
+            const int e = tid + q * nthr;
+            if (e < total) acc[q] = apply_mult<T>(a.Ta, S, e >> a.log2tc, e & (TC - 1), m0 + (e & (TC - 1)), ny, n, a.log2tc);
+        }
+        __syncthreads();
+        for (int e = tid; e < total; e += nthr) S[e] = a.b[gidx(e)];
+        __syncthreads();
+        fft_batched<T, PPT, true, false>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+#pragma unroll
+        for (int q = 0; q < PPT; q++) {
+            const int e = tid + q * nthr;
+            if (e < total) acc[q] = add<T>(acc[q], apply_mult<T>(a.Tb, S, e >> a.log2tc, e & (TC - 1), m0 + (e & (TC - 1)), ny, n, a.log2tc));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PPT; q++) {
+            const int e = tid + q * nthr;
+            if (e < total) S[e] = acc[q];
+        }
+        __syncthreads();
+        fft_batched<T, PPT, true, true>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+        for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = S[e];
+    } else {
+        for (int e = tid; e < total; e += nthr) {
+            const long long g = gidx(e);
+            S[e] = sub<T>(a.b[g], a.a[g]);
+        }
+        __syncthreads();
+        fft_batched<T, PPT, true, false>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+#pragma unroll
+        for (int q = 0; q < PPT; q++) {
+            const int e = tid + q * nthr;
+            if (e < total) acc[q] = apply_mult<T>(a.Ta, S, e >> a.log2tc, e & (TC - 1), m0 + (e & (TC - 1)), ny, n, a.log2tc);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PPT; q++) {
+            const int e = tid + q * nthr;
+            if (e < total) S[e] = acc[q];
+        }
+        __syncthreads();
+        fft_batched<T, PPT, true, true>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+        for (int e = tid; e < total; e += nthr) {
+            const long long g = gidx(e);
+            a.out[g] = add<T>(a.c[g], S[e]);
+        }
+    }
+}
+
+// Final diagnostics of each instance from its per-row partials.
+__global__ void diag_reduce_kernel(const double* __restrict__ rows, int ny, double inv_count, double cell,
+                                   double* __restrict__ out)
+{
+    __shared__ double red[4 * 256];
+    const int tid = threadIdx.x, inst = blockIdx.x;
+    double s1 = 0, s2 = 0, mx = 0, nf = 0;
+    const double* dr = rows + (long long)inst * ny * 4;
+    for (int r = tid; r < ny; r += blockDim.x) {
+        s1 += dr[4 * r]; s2 += dr[4 * r + 1]; mx = fmax(mx, dr[4 * r + 2]); nf += dr[4 * r + 3];
+    }
+    red[tid] = s1; red[256 + tid] = s2; red[512 + tid] = mx; red[768 + tid] = nf;
+    __syncthreads();
+    for (int h = blockDim.x >> 1; h > 0; h >>= 1) {
+        if (tid < h) {
+            red[tid] += red[tid + h];
+            red[256 + tid] += red[256 + tid + h];
+            red[512 + tid] = fmax(red[512 + tid], red[512 + tid + h]);
+            red[768 + tid] += red[768 + tid + h];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        out[inst * 4 + 0] = red[0] * inv_count;
+        out[inst * 4 + 1] = red[256] * cell;
+        out[inst * 4 + 2] = red[512];
+        out[inst * 4 + 3] = red[768];
+    }
+}
+
+}  // namespace kzk

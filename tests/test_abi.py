@@ -1,0 +1,64 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every function include/kzk.h declares, and rejects bad arguments before any
+device work (status codes, no exception across the boundary)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2103_06080_b300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "kzk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(kzk_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    lib = L.lib()
+    names = header_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(L.exported_names()) == names
+
+
+def test_status_strings():
+    lib = L.lib()
+    for s in range(9):
+        assert lib.kzk_status_string(s)
+
+
+def _create(nx=64, ny=32, prec=0, dt=0.01, B=0.05, A=7e-6, M=1.0, batch=1):
+    g = L.KzkGrid(nx=nx, ny=ny, tau_min=-4, tau_max=4, y_min=-8, y_max=8, prec=prec)
+    c = L.KzkCoeffs(B=B, A=A, lf_umax=M)
+    h = ctypes.c_void_p()
+    st = L.lib().kzk_plan_create(ctypes.byref(g), ctypes.byref(c), dt, batch, ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nx=48), L.KZK_ERR_SIZE), (dict(nx=4), L.KZK_ERR_SIZE), (dict(nx=16384), L.KZK_ERR_SIZE),
+    (dict(ny=1), L.KZK_ERR_SIZE), (dict(ny=3000), L.KZK_ERR_SIZE), (dict(ny=8192), L.KZK_ERR_SIZE),
+    (dict(prec=7), L.KZK_ERR_ARG), (dict(dt=0.0), L.KZK_ERR_ARG), (dict(dt=float("nan")), L.KZK_ERR_ARG),
+    (dict(B=0.0), L.KZK_ERR_ARG), (dict(A=-1.0), L.KZK_ERR_ARG), (dict(M=0.0), L.KZK_ERR_ARG),
+    (dict(batch=0), L.KZK_ERR_ARG),
+])
+def test_plan_create_rejects_bad_arguments(kw, code):
+    st, h = _create(**kw)
+    assert st == code and not h.value
+    assert L.lib().kzk_last_error()
+
+
+def test_null_arguments_are_rejected():
+    lib = L.lib()
+    assert lib.kzk_plan_create(None, None, 0.1, 1, None) == L.KZK_ERR_ARG
+    assert lib.kzk_advance(None, None, 1, 0.0, None, None) == L.KZK_ERR_ARG
+    assert lib.kzk_rhs(None, None, None, 0.0, None) == L.KZK_ERR_ARG
+    assert lib.kzk_tau_fft(None, None, None, 1, None) == L.KZK_ERR_ARG
+    assert lib.kzk_adjoint(None, None, None, None, 1, 0.0, 1, None) == L.KZK_ERR_ARG
+    assert lib.kzk_plan_destroy(None) == L.KZK_OK

@@ -1,0 +1,225 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64: element-wise relative L-infinity (max|gpu - oracle| / max|oracle|)
+within 1e-11 after whole runs, tighter for single operations.  FP32: relative
+l2 within 1e-5 (error of FP32 bulk arithmetic with FP64 tables, against the
+FP64 oracle).  Sizes span several column tiles and row blocks; edge cases
+cover the smallest and largest supported grids and batches.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_06080_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _api():
+    from paper_2103_06080_b300 import api
+    return api
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 2), (64, 8), (512, 4), (8192, 2)])
+def test_tau_fft_matches_dft(nx, ny):
+    api = _api()
+    rng = np.random.default_rng(nx + ny)
+    u = rng.standard_normal((ny, nx))
+    plan = api.Plan(nx=nx, ny=ny, dt=0.01)
+    V = plan.tau_fft(_dev(u), -1).cpu().numpy()
+    ref = np.stack([oracle.fft1d(u[j]) for j in range(ny)]) / nx
+    got = V[..., 0] + 1j * V[..., 1]
+    assert np.max(np.abs(got[:, 1:] - ref[:, 1:nx // 2])) < 1e-14 * np.max(np.abs(ref)) + 1e-15
+    assert np.max(np.abs(got[:, 0].real - ref[:, 0].real)) < 1e-14
+    assert np.max(np.abs(got[:, 0].imag - ref[:, nx // 2].real)) < 1e-14
+    back = plan.tau_fft(torch.tensor(V, device="cuda"), +1).cpu().numpy()
+    assert np.max(np.abs(back - u)) < 1e-13 * np.max(np.abs(u))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tables_match_oracle(prec):
+    api = _api()
+    w = inputs.config(1, nx=64, ny=32)
+    plan = api.Plan.from_workload(w, precision=prec)
+    E, P1, P2 = plan.tables()
+    eps = 2.0 ** -53 if prec == "fp64" else 2.0 ** -24
+    p = oracle.Params(**inputs.oracle_params(w, reg_eps=eps))
+    oE, oP1, oP2 = oracle.tables(p)
+    nl, nm = w.ny // 2 + 1, w.nx // 2 + 1
+    tol = 1e-13 if prec == "fp64" else 2e-7
+    for got, ref in ((E, oE), (P1, oP1), (P2, oP2)):
+        ref = ref[:nl, :nm]
+        err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+        assert np.max(err[np.abs(ref) > 1e-280]) < tol
+
+
+@pytest.mark.parametrize("nx,ny,profile", [(64, 8, False), (512, 64, True), (2048, 4, True)])
+def test_rhs_matches_oracle(nx, ny, profile):
+    api = _api()
+    w = inputs.config(2 if profile else 1, nx=nx, ny=ny, n_steps=50)
+    plan = api.Plan.from_workload(w, precision="fp64")
+    sigma = 0.37 * w.n_steps * w.dt
+    b = plan.rhs(_dev(w.u0), sigma=sigma).cpu().numpy()
+    ref = oracle.rhs(oracle.Params(**inputs.oracle_params(w)), w.u0, sigma=sigma)
+    assert rel_linf(b, ref) < 1e-12
+
+
+def test_one_step_stages_match_oracle():
+    api = _api()
+    w = inputs.config(2, nx=256, ny=64, n_steps=20)
+    plan = api.Plan.from_workload(w, precision="fp64")
+    s0 = 3 * w.dt
+    us, un = plan.step_stages(_dev(w.u0), sigma0=s0)
+    p = oracle.Params(**inputs.oracle_params(w))
+    ref_un, ref_us = oracle.run(p, w.u0, 1, sigma0=s0, want_ustar=True)
+    assert rel_linf(us.cpu().numpy(), ref_us) < 1e-13
+    assert rel_linf(un.cpu().numpy(), ref_un) < 1e-13
+
+
+def test_config1_full_run_fp64_parity():
+    # the full plain-method workload: 512 x 256, 200 steps, relative L-inf <= 1e-11
+    api = _api()
+    w = inputs.config(1)
+    plan = api.Plan.from_workload(w, precision="fp64")
+    u = _dev(w.u0)
+    st, d = plan.advance(u, w.n_steps, diag=True)
+    assert st == 0
+    p = oracle.Params(**inputs.oracle_params(w))
+    ref, hist = oracle.run(p, w.u0, w.n_steps, threads=True, want_hist=True)
+    assert rel_linf(u.cpu().numpy(), ref) < 1e-11
+    # diagnostics (FP64): state at the start of every step, and the final state
+    gh = plan.diag_history(w.n_steps)[:, 0, :]
+    od = oracle.diag(p, w.u0)
+    assert abs(gh[0, 0] - od[0]) < 1e-15 and abs(gh[0, 1] - od[1]) < 1e-12 * od[1]
+    assert np.allclose(gh[1:, 1], hist[:-1, 1], rtol=1e-11)
+    assert np.allclose(gh[1:, 2], hist[:-1, 2], rtol=1e-11)
+    assert abs(d[0]["energy"] - hist[-1, 1]) < 1e-11 * hist[-1, 1]
+    # mean conserved to roundoff over the run
+    assert np.max(np.abs(gh[:, 0] - gh[0, 0])) < 1e-14
+
+
+def test_stratified_run_fp64_parity():
+    api = _api()
+    w = inputs.config(2, nx=512, ny=128, n_steps=60)
+    plan = api.Plan.from_workload(w, precision="fp64")
+    u = _dev(w.u0)
+    plan.advance(u, w.n_steps, sigma0=0.0)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    assert rel_linf(u.cpu().numpy(), ref) < 1e-11
+
+
+def test_fp32_error_against_fp64_oracle():
+    api = _api()
+    w = inputs.config(3, nx=512, ny=256, n_steps=100)
+    plan = api.Plan.from_workload(w, precision="fp32")
+    u = _dev(w.u0, torch.float32)
+    plan.advance(u, w.n_steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    got = u.double().cpu().numpy()
+    assert rel_l2(got, ref) < 1e-5
+    assert rel_linf(got, ref) < 1e-4
+
+
+def test_batch_instances_are_independent():
+    api = _api()
+    ws = [inputs.config(1, nx=128, ny=32) for _ in range(3)]
+    u0 = np.stack([inputs.nwave(128, 32, a0=a, seed=s) for a, s in ((1.0, 1), (0.7, 2), (1.2, 3))])
+    w = ws[0]
+    plan = api.Plan.from_workload(w, precision="fp64", batch=3, lf_umax=1.5)
+    u = _dev(u0)
+    plan.advance(u, 7)
+    for i in range(3):
+        ref = oracle.run(oracle.Params(**inputs.oracle_params(w, lf_umax=1.5)), u0[i], 7)
+        assert rel_linf(u[i].cpu().numpy(), ref) < 1e-12
+
+
+def test_extreme_sizes():
+    api = _api()
+    for nx, ny, steps in ((8, 2, 5), (8192, 2, 2), (16, 4096, 2)):
+        w = inputs.config(1, nx=nx, ny=ny)
+        plan = api.Plan.from_workload(w, precision="fp64")
+        u = _dev(w.u0)
+        plan.advance(u, steps)
+        ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, steps, threads=True)
+        assert rel_linf(u.cpu().numpy(), ref) < 1e-12, (nx, ny)
+
+
+def test_runs_are_bitwise_deterministic():
+    api = _api()
+    w = inputs.config(1, nx=256, ny=128)
+    plan = api.Plan.from_workload(w, precision="fp32")
+    a = _dev(w.u0, torch.float32)
+    b = a.clone()
+    plan.advance(a, 10)
+    plan.advance(b, 10)
+    assert torch.equal(a, b)
+
+
+def test_nonfinite_input_is_reported():
+    api = _api()
+    w = inputs.config(1, nx=64, ny=16)
+    plan = api.Plan.from_workload(w, precision="fp64")
+    u0 = w.u0.copy()
+    u0[3, 5] = np.nan
+    st, d = plan.advance(_dev(u0), 2, diag=True)
+    assert st == 4 and d[0]["run_nonfinite"] > 0
+
+
+def test_cfl_bound_violation_is_reported():
+    api = _api()
+    w = inputs.config(1, nx=64, ny=16)
+    plan = api.Plan.from_workload(w, precision="fp64", lf_umax=0.5)
+    st, d = plan.advance(_dev(w.u0), 1, diag=True)
+    assert st == 3 and d[0]["run_max_abs"] > 0.5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-3)])
+def test_adjoint_matches_oracle_adjoint(prec, tol):
+    api = _api()
+    w = inputs.config(2, nx=128, ny=32, n_steps=10)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = api.Plan.from_workload(w, precision=prec)
+    p = oracle.Params(**inputs.oracle_params(w))
+    u_end = oracle.run(p, w.u0, w.n_steps)
+    g_end = 2 * w.dtau * u_end
+    ref = oracle.adjoint(p, w.u0, g_end, w.n_steps)
+    g0 = plan.adjoint(_dev(w.u0, dt), _dev(g_end, dt), w.n_steps, ckpt_every=4)   # segments 4, 4, 2
+    assert rel_linf(g0.double().cpu().numpy(), ref) < tol
+
+
+def test_adjoint_finite_differences_fp64():
+    # central differences with h = 1e-6 on seeded unit directions (FP64)
+    api = _api()
+    w = inputs.config(4, nx=256, ny=64, n_steps=40)
+    plan = api.Plan.from_workload(w, precision="fp64")
+    u0 = _dev(w.u0)
+
+    def loss(x):
+        y = x.clone()
+        plan.advance(y, w.n_steps)
+        return float((y * y).sum()) * w.dtau
+
+    y = u0.clone()
+    plan.advance(y, w.n_steps)
+    g0 = plan.adjoint(u0, 2 * w.dtau * y, w.n_steps, ckpt_every=8)
+    gen = torch.Generator(device="cpu").manual_seed(4)
+    for _ in range(4):
+        v = torch.randn(u0.shape, generator=gen, dtype=torch.float64).cuda()
+        v /= v.norm()
+        h = 1e-6
+        fd = (loss(u0 + h * v) - loss(u0 - h * v)) / (2 * h)
+        ad = float((g0 * v).sum())
+        assert abs(ad - fd) <= 1e-6 * max(abs(fd), 1e-3 * float(g0.norm()))
