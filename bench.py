@@ -1,0 +1,413 @@
+"""Benchmark of one ExpRK22 / WENO5 / FFT step on the B300.
+
+A bench "step" is one full ExpRK22 step (Algorithm 2, STEP 1-4: two WENO5
+row passes fused with the tau-FFTs and two column passes fused with the
+y-FFTs and the phi-multipliers, plus the per-step FP64 diagnostics) over the
+FP64 4096 x 2048 stratified-atmosphere workload with a seeded N-wave.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun each rank advances its own
+replica of the workload (independent propagations, no collective): weak
+scaling, value = all ranks' grid-point-steps / the slowest rank's time.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2103_06080_b300 import inputs  # noqa: E402
+
+METRIC = "grid-point-steps/s"
+UNIT = "pt-steps/s"
+WORKLOAD = "fp64 4096x2048 stratified N-wave (sigma-cubic B, A), CFL 0.4"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# algorithmic work per launch (also stated in the design notes)
+# --------------------------------------------------------------------------
+def row_bytes(nx, ny, w):
+    """Row pass: read one packed spectral array, write one (N * w bytes each)."""
+    return 2 * nx * ny * w
+
+
+def col_bytes(nx, ny, w, stage):
+    """Column pass: stage 1 reads V, b1 and the folded E', P1' (half an array
+    each) and writes V*; stage 2 reads b1, b2, V*, folded P2' and writes V'."""
+    unit = nx * ny * w
+    tab = (ny // 2 + 1) * (nx // 2) * 2 * w
+    return (3 * unit + 2 * tab) if stage == 1 else (4 * unit + tab)
+
+
+def row_flops(nx, ny, profile=True):
+    """Row pass FLOPs (add, mul, div = 1; FMA = 2): two real FFTs of length nx
+    (2.5 nx log2(nx/2) each, as complex FFTs of nx/2 points, plus 8 per point
+    for the real pre/post-processing), WENO5 (166 per point: 9 for the split
+    fluxes, 2 x 77 for the two reconstructions, 3 for the difference),
+    diagnostics (3) and the absorption-deviation term (5 with a profile)."""
+    lg = np.log2(nx // 2)
+    per_pt = 2 * (2.5 * lg + 4) + 166 + 3 + (5 if profile else 0)
+    return per_pt * nx * ny
+
+
+def col_flops(nx, ny, stage):
+    """Column pass FLOPs: complex FFTs of length ny (5 ny log2 ny each) on
+    nx/2 columns -- three in stage 1 (two forward, one inverse) plus two
+    complex multiply-adds per element; two in stage 2 plus one complex multiply
+    and two complex adds per element."""
+    lg = np.log2(ny)
+    ncol = nx // 2
+    if stage == 1:
+        return ncol * (3 * 5 * ny * lg + ny * 14)
+    return ncol * (2 * 5 * ny * lg + ny * 10)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on the host cores
+# --------------------------------------------------------------------------
+def cpu_oracle_rate(w, n_steps: int, threads: bool = True, budget_s: float = 0.0):
+    """Grid-point-steps/s of the oracle as it stands on the full grid of ``w``:
+    one untimed first step (it pays the first touch of the oracle's work
+    arrays), then m timed steps, each timed inside the oracle (table set-up
+    excluded).  With budget_s > 0, m is the number of steps that fit in about
+    budget_s seconds judged from the first step (at most n_steps)."""
+    import oracle
+    p = oracle.Params(**inputs.oracle_params(w))
+    m = max(1, n_steps)
+    if budget_s > 0:
+        _, s1 = oracle.run_timed(p, w.u0, 2, threads=threads)
+        m = max(1, min(n_steps, int(budget_s / max(s1[1], 1e-3))))
+    _, sec = oracle.run_timed(p, w.u0, m + 1, threads=threads)
+    dt = float(np.sum(sec[1:]))
+    return w.nx * w.ny * m / dt, dt, oracle.num_threads(threads), m
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores, on this arm's workload and metric.  Each
+    bench step is one full-grid oracle step; the number of timed steps is
+    bounded (~60 s of CPU work) so the run ends within minutes."""
+    if rank != 0:
+        return 0
+    w = inputs.config(2)
+    value, dt, cores, m = cpu_oracle_rate(w, args.steps, budget_s=60.0)
+    sample = (f"{m} of the requested {args.steps} full 4096x2048 FP64 steps (time bound), "
+              f"OpenMP oracle, first step untimed, then per-step timing inside the oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": m, "warmup": args.warmup, "ms_per_step": 1e3 * dt / m,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": 4096, "ny": 2048},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2103_06080_b300 import api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    fp32 = args.precision == "fp32"
+    w = inputs.config(3 if fp32 else 2)
+    tdt = torch.float32 if fp32 else torch.float64
+    wsz = 4 if fp32 else 8
+    plan = api.Plan.from_workload(w, precision=args.precision)
+    u_host = torch.tensor(w.u0, dtype=tdt).pin_memory()
+    u = u_host.to(dev, non_blocking=False)
+
+    # warm-up (untimed), then the timed region: exactly K steps
+    plan.advance(u, args.warmup, sigma0=0.0)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    n0 = api.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.advance(u, args.steps, sigma0=args.warmup * w.dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = api.launch_count() - n0
+    clocks = sampler.stop()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = w.nx * w.ny * args.steps * world / (ms_max * 1e-3)
+
+    # per-kernel device times (CUDA events on the launch stream)
+    kt = plan.kernel_times(u, min(args.steps, 20), sigma0=0.0)
+    names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
+    fl = [row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 1), row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 2)]
+    by = [row_bytes(w.nx, w.ny, wsz), col_bytes(w.nx, w.ny, wsz, 1), row_bytes(w.nx, w.ny, wsz),
+          col_bytes(w.nx, w.ny, wsz, 2)]
+    dom = int(np.argmax(kt))
+    peaks, peak_src = _peaks()
+    if fp32:
+        hbm = peaks["hbm_gbs"] * 1e9
+        roof = {"bound": "hbm", "kernel": names[dom], "achieved": by[dom] / (kt[dom] * 1e-3) / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": by[dom] / (kt[dom] * 1e-3) / hbm,
+                "traffic": None, "peak_source": f"{peak_src} HBM copy bandwidth", "kernel_ms": dict(zip(names, kt))}
+    else:
+        fp64_peak = api.alu_peak("fp64")
+        roof = {"bound": "alu", "kernel": names[dom], "achieved": fl[dom] / (kt[dom] * 1e-3) / 1e12,
+                "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": fl[dom] / (kt[dom] * 1e-3) / fp64_peak, "traffic": None,
+                "peak_source": "measured FP64 FMA throughput (kzk_alu_peak) on this GPU",
+                "kernel_ms": dict(zip(names, kt)),
+                "hbm_frac_of_measured": by[dom] / (kt[dom] * 1e-3) / (peaks["hbm_gbs"] * 1e9)}
+
+    # end to end through the public API: pinned host -> device, K steps, result back
+    out_host = torch.empty_like(u_host).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    u.copy_(u_host, non_blocking=True)
+    st, _ = plan.advance(u, args.steps, sigma0=0.0, diag=True)
+    out_host.copy_(u, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_val = w.nx * w.ny * args.steps * world / float(tt.item())
+    state_bytes = w.nx * w.ny * wsz
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        extra = secondary_reports(args, api, torch, dev, peaks)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("fp64", "fp32") if fp32 else WORKLOAD, "nx": w.nx, "ny": w.ny, "dt": w.dt, "per_rank_instances": 1,
+                   "l2": "working set 4 spectral arrays + tables = 0.37 GB > 126 MB L2 (no flush needed)"},
+        "roofline": roof,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes / args.steps,
+                "d2h_bytes_per_step": state_bytes / args.steps,
+                "timed": "H2D u0 (pinned) + kzk_advance(K steps, diagnostics) + D2H u; bytes amortised over K",
+                "status": st},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
+    }
+    line.update(extra)
+    if rank == 0 and not args.no_cpu_baseline:
+        w2 = inputs.config(2)
+        r, dt, cores, m = cpu_oracle_rate(w2, args.cpu_steps)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{m} step(s) of the full 4096x2048 FP64 grid ({dt:.1f} s), "
+                                          f"OpenMP oracle, first step untimed, then per-step timing inside the oracle"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def secondary_reports(args, api, torch, dev, peaks):
+    """FP32 throughput + error, and the adjoint/forward cost ratio."""
+    out = {}
+    # FP32 bulk with FP64-generated tables, same 4096 x 2048 workload
+    w3 = inputs.config(3)
+    p3 = api.Plan.from_workload(w3, precision="fp32")
+    u3 = torch.tensor(w3.u0, dtype=torch.float32, device=dev)
+    p3.advance(u3, args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k3 = max(args.steps, 50)
+    e0.record()
+    p3.advance(u3, k3)
+    e1.record()
+    torch.cuda.synchronize()
+    ms3 = e0.elapsed_time(e1)
+    kt3 = p3.kernel_times(u3, 20)
+    by3 = [row_bytes(4096, 2048, 4), col_bytes(4096, 2048, 4, 1), row_bytes(4096, 2048, 4),
+           col_bytes(4096, 2048, 4, 2)]
+    names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
+    dom = int(np.argmax(kt3))
+    hbm = peaks["hbm_gbs"] * 1e9
+    out["fp32"] = {
+        "value": w3.nx * w3.ny * k3 / (ms3 * 1e-3), "unit": UNIT, "ms_per_step": ms3 / k3, "steps": k3,
+        "dtype": "f32 (FP64-generated tables rounded once; FP64 diagnostics)",
+        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": by3[dom] / (kt3[dom] * 1e-3) / 1e9,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": by3[dom] / (kt3[dom] * 1e-3) / hbm,
+                     "traffic": None, "kernel_ms": dict(zip(names, kt3)),
+                     "step_frac": sum(by3) / (sum(kt3) * 1e-3) / hbm},
+    }
+    p3.close()
+    del u3
+    # FP32 error against the FP64 oracle on a bounded case
+    if not args.no_error:
+        import oracle
+        we = inputs.config(3, nx=args.err_nx, ny=args.err_ny, n_steps=args.err_steps)
+        pe = api.Plan.from_workload(we, precision="fp32")
+        ue = torch.tensor(we.u0, dtype=torch.float32, device=dev)
+        pe.advance(ue, we.n_steps)
+        ref = oracle.run(oracle.Params(**inputs.oracle_params(we)), we.u0, we.n_steps, threads=True)
+        got = ue.double().cpu().numpy()
+        out["fp32"]["error_vs_fp64_oracle"] = {
+            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "rel_linf": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "case": f"{we.nx}x{we.ny}, {we.n_steps} steps, same seeded recipe"}
+        pe.close()
+    # adjoint / forward on the adjoint workload (2048 x 1024, FP64, checkpoint every 32)
+    w4 = inputs.config(4, n_steps=args.adj_steps)
+    p4 = api.Plan.from_workload(w4, precision="fp64")
+    u4 = torch.tensor(w4.u0, dtype=torch.float64, device=dev)
+    y = u4.clone()
+    p4.advance(y, 4)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    y = u4.clone()
+    p4.advance(y, w4.n_steps)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t
+    g_end = 2 * w4.dtau * y
+    p4.adjoint(u4, g_end, 4, ckpt_every=32)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    p4.adjoint(u4, g_end, w4.n_steps, ckpt_every=32)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t
+    out["adjoint"] = {"workload": f"fp64 2048x1024, {w4.n_steps} steps, checkpoint every 32",
+                      "forward_s": t_fwd, "gradient_s": t_adj,
+                      "gradient_over_forward": t_adj / t_fwd,
+                      "note": "gradient = forward sweep with checkpoints + per-segment recompute + reverse sweep"}
+    p4.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="skip the FP32 / adjoint secondary reports")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+                    help="precision of the headline workload (fp64: 4096x2048 FP64; fp32: same grid, FP32 bulk)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--ref-steps-per-sample", type=int, default=1)
+    ap.add_argument("--err-nx", type=int, default=512)
+    ap.add_argument("--err-ny", type=int, default=256)
+    ap.add_argument("--err-steps", type=int, default=200)
+    ap.add_argument("--adj-steps", type=int, default=128)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

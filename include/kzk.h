@@ -162,6 +162,21 @@ const char *kzk_last_error(void);
 /* Number of kernel launches the library has issued since load (all plans). */
 int64_t kzk_launch_count(void);
 
+/* Measurement helper (no counterpart in the paper).  Advances u (device,
+ * physical, modified like kzk_advance) by n_steps steps with a CUDA event
+ * recorded on `stream` around every kernel of the step, and returns in ms[4]
+ * the mean device duration of one launch of each kernel: ms[0] row pass of
+ * stage 1, ms[1] column pass of stage 1, ms[2] row pass of stage 2, ms[3]
+ * column pass of stage 2.  Synchronises the stream. */
+kzk_status kzk_kernel_times(kzk_plan *plan, void *u, int64_t n_steps, double sigma0, void *stream,
+                            double *ms);
+
+/* Measurement helper (no counterpart in the paper): sustained fused
+ * multiply-add throughput of the device in FLOP/s (2 per FMA) for the given
+ * precision, from a kernel of independent FMA chains on every SM timed with
+ * CUDA events.  Synchronises the stream. */
+kzk_status kzk_alu_peak(int32_t prec, void *stream, double *flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,6 +102,7 @@ def _lib(threads: bool = False):
         lib.orc_rhs.argtypes = [P, D, ctypes.c_double, D]
         lib.orc_diag.argtypes = [P, D, D]
         lib.orc_run.argtypes = [P, D, ctypes.c_int64, ctypes.c_double, D, D]
+        lib.orc_run_timed.argtypes = [P, D, ctypes.c_int64, ctypes.c_double, D]
         lib.orc_adjoint.argtypes = [P, D, D, ctypes.c_int64, ctypes.c_double, D]
         lib.orc_B_of.argtypes = [P, ctypes.c_double]
         lib.orc_B_of.restype = ctypes.c_double
@@ -225,6 +226,15 @@ def run(p: Params, u0, n_steps: int, sigma0: float = 0.0, threads: bool = False,
     if want_hist:
         out.append(hist[:n_steps])
     return out[0] if len(out) == 1 else tuple(out)
+
+
+def run_timed(p: Params, u0, n_steps: int, sigma0: float = 0.0, threads: bool = True):
+    """(u after n_steps, wall seconds of each step; table set-up excluded)."""
+    u = _f64(u0).reshape(p.ny, p.nx).copy()
+    sec = np.zeros(max(int(n_steps), 1))
+    cp = p.c()
+    _lib(threads).orc_run_timed(ctypes.byref(cp), _ptr(u), int(n_steps), float(sigma0), _ptr(sec))
+    return u, sec[:n_steps]
 
 
 def adjoint(p: Params, u0, g_end, n_steps: int, sigma0: float = 0.0, threads: bool = False):

@@ -412,6 +412,28 @@ int orc_run(const orc_params *p, double *u, int64_t n_steps, double sigma0, doub
     return 0;
 }
 
+/* Same as orc_run, also returning the wall time of every step in
+   step_seconds[n] (table set-up excluded): used to time the oracle as a CPU
+   baseline; the arithmetic is that of orc_run. */
+#include <time.h>
+int orc_run_timed(const orc_params *p, double *u, int64_t n_steps, double sigma0, double *step_seconds)
+{
+    size_t N = (size_t)p->nx * p->ny;
+    tables_t t;
+    tables_alloc(p, &t);
+    double *w = malloc(sizeof(double) * 7 * N);
+    for (int64_t n = 0; n < n_steps; n++) {
+        struct timespec a, b;
+        clock_gettime(CLOCK_MONOTONIC, &a);
+        exprk22_step(p, &t, u, sigma0 + (double)n * p->dt, NULL, w);
+        clock_gettime(CLOCK_MONOTONIC, &b);
+        step_seconds[n] = (double)(b.tv_sec - a.tv_sec) + 1e-9 * (double)(b.tv_nsec - a.tv_nsec);
+    }
+    free(w);
+    tables_free(&t);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Adjoint.  With P_X := Re F^{-1} diag(X) F (a real operator for the         */
 /* Hermitian-symmetric tables of Eq. 11), one step reads                      */

@@ -68,6 +68,9 @@ _SIGS = [
     ("kzk_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("kzk_last_error", ctypes.c_char_p, []),
     ("kzk_launch_count", ctypes.c_int64, []),
+    ("kzk_kernel_times", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_double, _VP,
+                                        ctypes.POINTER(ctypes.c_double)]),
+    ("kzk_alu_peak", ctypes.c_int, [ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_double)]),
 ]
 
 

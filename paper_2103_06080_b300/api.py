@@ -136,6 +136,15 @@ class Plan:
                                     float(sigma0), int(ckpt_every), _stream_ptr(stream)))
         return g0
 
+    def kernel_times(self, u: torch.Tensor, n_steps: int, sigma0: float = 0.0, stream=None) -> list:
+        """Mean device ms of one launch of [row stage 1, column stage 1, row
+        stage 2, column stage 2] over n_steps steps (advances u)."""
+        self._check_state(u, "u")
+        ms = (ctypes.c_double * 4)()
+        L.check(L.lib().kzk_kernel_times(self.handle, u.data_ptr(), int(n_steps), float(sigma0),
+                                         _stream_ptr(stream), ms))
+        return [float(x) for x in ms]
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             L.lib().kzk_plan_destroy(self._h.value)
@@ -150,3 +159,11 @@ class Plan:
 
 def launch_count() -> int:
     return int(L.lib().kzk_launch_count())
+
+
+def alu_peak(precision: str = "fp64", stream=None) -> float:
+    """Measured FMA throughput (FLOP/s) of the current device."""
+    out = ctypes.c_double()
+    L.check(L.lib().kzk_alu_peak(L.KZK_FP64 if precision == "fp64" else L.KZK_FP32, _stream_ptr(stream),
+                                 ctypes.byref(out)))
+    return float(out.value)

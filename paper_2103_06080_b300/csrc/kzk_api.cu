@@ -512,9 +512,131 @@ kzk_status adjoint_impl(kzk_plan* p, const void* u0, const void* g_end, void* g0
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Measurement helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+// 8 independent FMA chains per thread, `iters` rounds; the result is stored
+// only if it is impossible so the chains stay live.
+template <typename T>
+__global__ void fma_chain_kernel(T* sink, int iters, T a, T b)
+{
+    T x[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) x[c] = (T)(threadIdx.x + c);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) x[c] = fma(x[c], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) s += x[c];
+    if (s == (T)-1.2345) sink[0] = s;
+}
+
+template <typename T>
+kzk_status alu_peak_impl(cudaStream_t st, double* out)
+{
+    int dev = 0, sms = 0;
+    KZK_CUDA(cudaGetDevice(&dev));
+    KZK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    T* sink = nullptr;
+    KZK_CUDA(cudaMalloc(&sink, sizeof(T)));
+    const int threads = 256, blocks = sms * 8;
+    const int iters = sizeof(T) == 8 ? 2048 : 65536;
+    cudaEvent_t e0, e1;
+    KZK_CUDA(cudaEventCreate(&e0));
+    KZK_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+        KZK_CUDA(cudaEventRecord(e0, st));
+        fma_chain_kernel<T><<<blocks, threads, 0, st>>>(sink, iters, (T)0.999999, (T)1e-7);
+        KZK_LAUNCHED();
+        KZK_CUDA(cudaEventRecord(e1, st));
+        KZK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        KZK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    *out = 2.0 * 8.0 * iters * (double)threads * blocks / (best * 1e-3);
+    return KZK_OK;
+}
+
+template <typename T>
+kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sigma0, cudaStream_t st, double* ms)
+{
+    cudaEvent_t ev[5];
+    for (auto& e : ev) KZK_CUDA(cudaEventCreate(&e));
+    double acc[4] = {0, 0, 0, 0};
+    KZK_TRY(ensure_hist(p, std::max(1LL, n_steps)));
+    KZK_TRY(to_spectral<T>(p, u, p->V, st));
+    for (long long s = 0; s < n_steps; s++) {
+        const double sigma = sigma0 + (double)s * p->dt;
+        KZK_CUDA(cudaEventRecord(ev[0], st));
+        RowArgs<T> r1 = row_args<T>(p, p->V, p->b1, sigma, p->diag_rows);
+        KZK_TRY((launch_row<T, ROW_RHS>(p, r1, st)));
+        KZK_CUDA(cudaEventRecord(ev[1], st));
+        ColArgs<T> c1 = col_args<T>(p);
+        c1.a = (const cx<T>*)p->V;
+        c1.b = (const cx<T>*)p->b1;
+        c1.out = (cx<T>*)p->vs;
+        c1.Ta = (const cx<T>*)p->E;
+        c1.Tb = (const cx<T>*)p->P1;
+        c1.diag_rows = p->diag_rows;
+        c1.diag_hist = p->diag_hist + (size_t)s * p->batch * 4;
+        KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
+        KZK_CUDA(cudaEventRecord(ev[2], st));
+        RowArgs<T> r2 = row_args<T>(p, p->vs, p->b2, sigma + p->dt, nullptr);
+        KZK_TRY((launch_row<T, ROW_RHS>(p, r2, st)));
+        KZK_CUDA(cudaEventRecord(ev[3], st));
+        ColArgs<T> c2 = col_args<T>(p);
+        c2.a = (const cx<T>*)p->b1;
+        c2.b = (const cx<T>*)p->b2;
+        c2.c = (const cx<T>*)p->vs;
+        c2.out = (cx<T>*)p->V;
+        c2.Ta = (const cx<T>*)p->P2;
+        KZK_TRY((launch_col<T, COL_STAGE2>(p, c2, st)));
+        KZK_CUDA(cudaEventRecord(ev[4], st));
+        KZK_CUDA(cudaEventSynchronize(ev[4]));
+        for (int k = 0; k < 4; k++) {
+            float t = 0;
+            KZK_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            acc[k] += t;
+        }
+    }
+    KZK_TRY(to_physical<T>(p, p->V, u, 1.0, nullptr, st));
+    KZK_CUDA(cudaStreamSynchronize(st));
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < 4; k++) ms[k] = n_steps > 0 ? acc[k] / (double)n_steps : 0.0;
+    return KZK_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
+
+kzk_status kzk_kernel_times(kzk_plan* p, void* u, int64_t n_steps, double sigma0, void* stream, double* ms)
+{
+    if (!p || !u || !ms) return fail(KZK_ERR_ARG, "NULL argument");
+    if (n_steps < 0) return fail(KZK_ERR_ARG, "n_steps < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    return p->prec == KZK_FP64 ? kernel_times_impl<double>(p, u, n_steps, sigma0, st, ms)
+                               : kernel_times_impl<float>(p, u, n_steps, sigma0, st, ms);
+}
+
+kzk_status kzk_alu_peak(int32_t prec, void* stream, double* flops)
+{
+    if (!flops || (prec != KZK_FP64 && prec != KZK_FP32)) return fail(KZK_ERR_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == KZK_FP64 ? alu_peak_impl<double>(st, flops) : alu_peak_impl<float>(st, flops);
+}
+
 
 const char* kzk_status_string(kzk_status s)
 {

@@ -222,4 +222,6 @@ def test_adjoint_finite_differences_fp64():
         h = 1e-6
         fd = (loss(u0 + h * v) - loss(u0 - h * v)) / (2 * h)
         ad = float((g0 * v).sum())
-        assert abs(ad - fd) <= 1e-6 * max(abs(fd), 1e-3 * float(g0.norm()))
+        # |v| = 1 bounds the directional derivative by |g0|; FD in FP64 with
+        # h = 1e-6 carries ~1e-8 |g0| of rounding noise
+        assert abs(ad - fd) <= 1e-6 * float(g0.norm()), (ad, fd)
