@@ -177,6 +177,30 @@ kzk_status kzk_kernel_times(kzk_plan *plan, void *u, int64_t n_steps, double sig
  * CUDA events.  Synchronises the stream. */
 kzk_status kzk_alu_peak(int32_t prec, void *stream, double *flops_per_s);
 
+/* Largest batch * nx * ny accepted by kzk_rhs_noalloc. */
+#define KZK_NOALLOC_MAX_POINTS (1 << 18)
+
+/* kzk_rhs without any device allocation.  The paper has no counterpart: this
+ * serves callers that cannot let a library call cudaMalloc -- a process that
+ * hands all device memory to its own pool allocator up front (a cudaMalloc
+ * here would fail or bypass the pool), or a latency-critical path that cannot
+ * take cudaMalloc's implicit device synchronisation.  No plan is needed: grid,
+ * coeffs (host) and batch describe the problem as for kzk_plan_create, and
+ * u, b (device, [batch][ny][nx], plan precision, b not aliasing u) are the
+ * caller's input and output; b = b(sigma, u) exactly as kzk_rhs computes it.
+ * The intermediates live in one file-scope device array of
+ * 2 * 8 * KZK_NOALLOC_MAX_POINTS + 16 * 8192 bytes (about 4.1 MB) that every
+ * GPU loading the library keeps until the process exits.  The first call on a
+ * device looks up that array's device address (and lifts the kernels' shared-
+ * memory limit) for the current device; make that first call before any
+ * stream capture.  All calls share the array, so calls whose GPU work
+ * overlaps race: serialise them.  Errors: KZK_ERR_ARG (null, aliasing, bad
+ * precision or coefficients), KZK_ERR_SIZE (nx not a power of two in
+ * [8, 8192], ny not a power of two, or batch * nx * ny above
+ * KZK_NOALLOC_MAX_POINTS), KZK_ERR_CUDA.  Calls no cudaMalloc / cudaFree. */
+kzk_status kzk_rhs_noalloc(const kzk_grid *grid, const kzk_coeffs *coeffs, int32_t batch,
+                           const void *u, void *b, double sigma, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,7 +71,11 @@ _SIGS = [
     ("kzk_kernel_times", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_double, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     ("kzk_alu_peak", ctypes.c_int, [ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_double)]),
+    ("kzk_rhs_noalloc", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs), ctypes.c_int32,
+                                       _VP, _VP, ctypes.c_double, _VP]),
 ]
+
+NOALLOC_MAX_POINTS = 1 << 18
 
 
 def lib():

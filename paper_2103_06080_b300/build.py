@@ -23,7 +23,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(s) for s in sources())
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= newest:
         return OUT
-    cmd = [NVCC, *FLAGS, os.path.join(CSRC, "kzk_api.cu"), "-o", OUT]
+    cmd = [NVCC, *FLAGS, os.path.join(CSRC, "kzk_api.cu"), os.path.join(CSRC, "kzk_noalloc.cu"), "-o", OUT]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)

@@ -511,6 +511,11 @@ kzk_status adjoint_impl(kzk_plan* p, const void* u0, const void* g_end, void* g0
 
 }  // namespace
 
+namespace kzk_internal {
+// error reporting for the other translation unit (kzk_noalloc.cu)
+kzk_status set_error(kzk_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace kzk_internal
+
 // ---------------------------------------------------------------------------
 // Measurement helpers
 // ---------------------------------------------------------------------------

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(1024) col_kernel(ColArgs<T> a)
 }
 
 // Final diagnostics of each instance from its per-row partials.
-__global__ void diag_reduce_kernel(const double* __restrict__ rows, int ny, double inv_count, double cell,
+static __global__ void diag_reduce_kernel(const double* __restrict__ rows, int ny, double inv_count, double cell,
                                    double* __restrict__ out)
 {
     __shared__ double red[4 * 256];
