@@ -73,7 +73,8 @@ typedef struct {
     double B;                       /* nonlinearity, > 0                             */
     double A;                       /* absorption, >= 0 (kept exactly in L)          */
     double diffraction;             /* 1/(4 pi) in the paper; <= 0 selects 1/(4 pi)   */
-    double reg_eps;                 /* epsilon of z; <= 0 selects 2^-53 (FP64) / 2^-24 (FP32) */
+    double reg_eps;                 /* epsilon of z; <= 0 selects 2^-53, the epsilon of the FP64 table
+                                       generation used by both plan precisions */
     double weno_eps;                /* Jiang-Shu epsilon; <= 0 selects 1e-6          */
     double lf_umax;                 /* M of the LF speed alpha = B(sigma) * M, > 0   */
     double B_prof[4];

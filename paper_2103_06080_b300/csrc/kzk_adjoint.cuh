@@ -138,7 +138,7 @@ struct AdjRowArgs {
 enum AdjRowMode { ADJ_ROW_2 = 0, ADJ_ROW_1 = 1 };
 
 template <typename T, int PPT, int MODE>
-__global__ void __launch_bounds__(1024) adj_row_kernel(AdjRowArgs<T> a)
+__global__ void __launch_bounds__(512) adj_row_kernel(AdjRowArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -241,7 +241,7 @@ __device__ __forceinline__ cx<T> apply_mult_conj(const cx<T>* __restrict__ tab, 
 }
 
 template <typename T, int PPT, int MODE>
-__global__ void __launch_bounds__(1024) adj_col_kernel(AdjColArgs<T> a)
+__global__ void __launch_bounds__(col_max_threads<T>()) adj_col_kernel(AdjColArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* S = reinterpret_cast<cx<T>*>(smem_raw);

@@ -68,14 +68,16 @@ struct kzk_plan_s {
     long long inst_stride;      // complex elements per instance: ny * nx / 2
     void *V, *b1, *vs, *b2;     // spectral work arrays [batch][ny][nx/2]
     void *E, *P1, *P2;          // folded, scaled tables [(ny/2+1)][nx/2]
+    void* E_lo;                 // FP32 plans: lo part of E' (two-float E')
     void *twr, *twc;            // twiddles, exp(-2 pi i k / nx), exp(-2 pi i k / ny)
+    void* twc_lo;               // FP32 plans: lo part of the y twiddles
     double* diag_rows;          // [batch][ny][4]
     double* diag_hist;          // [hist_cap][batch][4]
     double* diag_final;         // [batch][4]
     long long hist_cap;
     long long hist_steps;
-    int row_thr, col_thr, log2tc;
-    size_t row_smem, col_smem;
+    int row_thr, col_thr, log2tc, adj_row_thr;
+    size_t row_smem, col_smem, adj_smem;
     // adjoint workspace (allocated on first use)
     void *lam, *mu, *nu, *ls;   // spectral adjoint arrays
     void* seg;                  // segment store [(2 k)][batch][ny][nx/2]
@@ -92,20 +94,19 @@ double dA_of(const kzk_plan* p, double s)
 }
 
 template <typename T> constexpr int row_ppt() { return sizeof(T) == 4 ? 16 : 8; }
-template <typename T> constexpr int col_ppt() { return sizeof(T) == 4 ? 16 : 8; }
-template <typename T> size_t adj_row_smem(const kzk_plan* p) { return adj_row_smem_bytes<T>(p->n, p->row_thr); }
+template <typename T> size_t adj_row_smem(const kzk_plan* p) { return adj_row_smem_bytes<T>(p->n, p->adj_row_thr); }
 
 template <typename T, int MODE>
 kzk_status set_row_attr(size_t smem)
 {
-    KZK_CUDA(cudaFuncSetAttribute(row_kernel<T, row_ppt<T>(), MODE>,
+    KZK_CUDA(cudaFuncSetAttribute(row_kernel<T, MODE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return KZK_OK;
 }
 template <typename T, int MODE>
 kzk_status set_col_attr(size_t smem)
 {
-    KZK_CUDA(cudaFuncSetAttribute(col_kernel<T, col_ppt<T>(), MODE>,
+    KZK_CUDA(cudaFuncSetAttribute(col_kernel<T, MODE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return KZK_OK;
 }
@@ -119,7 +120,7 @@ kzk_status set_adj_row_attr(size_t smem)
 template <typename T, int MODE>
 kzk_status set_adj_col_attr(size_t smem)
 {
-    KZK_CUDA(cudaFuncSetAttribute(adj_col_kernel<T, col_ppt<T>(), MODE>,
+    KZK_CUDA(cudaFuncSetAttribute(adj_col_kernel<T, col_ppt_of<T>(), MODE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return KZK_OK;
 }
@@ -127,18 +128,15 @@ kzk_status set_adj_col_attr(size_t smem)
 template <typename T>
 kzk_status configure(kzk_plan* p)
 {
-    const int PR = row_ppt<T>(), PC = col_ppt<T>();
-    p->row_thr = std::max(32, p->n / PR);
-    if (p->row_thr > 1024) return fail(KZK_ERR_SIZE, "nx = %d too large for one row per CTA", p->nx);
-    p->row_smem = 2 * (size_t)p->n * p->csz + 4 * (size_t)p->row_thr * sizeof(double);
-    const size_t budget = 128 * 1024;
-    int tc = std::min(16, p->n);
-    while (tc > 1 && ((size_t)p->ny * tc * p->csz > budget || (long long)p->ny * tc / PC > 1024)) tc >>= 1;
-    if ((size_t)p->ny * tc * p->csz > budget || (long long)p->ny * tc / PC > 1024)
+    p->row_thr = row_threads<T>(p->nx);
+    if (p->row_thr > ROW_MAX_THREADS) return fail(KZK_ERR_SIZE, "nx = %d too large for one row per CTA", p->nx);
+    p->row_smem = row_smem_bytes<T>(p->nx);
+    p->adj_row_thr = std::max(32, p->n / row_ppt<T>());
+    p->log2tc = col_log2tc<T>(p->nx, p->ny);
+    p->col_thr = col_threads<T>(p->ny, p->log2tc);
+    if (p->col_thr > col_max_threads<T>() || 2 * ((size_t)p->ny << p->log2tc) * sizeof(cx<T>) > 128 * 1024)
         return fail(KZK_ERR_SIZE, "ny = %d too large for a shared-memory column tile", p->ny);
-    p->log2tc = ilog2((unsigned)tc);
-    p->col_thr = std::max(32, p->ny * tc / PC);
-    p->col_smem = std::max((size_t)p->ny * tc * p->csz, 4 * (size_t)p->col_thr * sizeof(double));
+    p->col_smem = col_smem_bytes<T>(p->ny, p->log2tc);
     // Every kernel may use up to the device's opt-in maximum; the launch's own
     // dynamic size decides occupancy.  (Setting the plan's size here would
     // shrink the limit for plans created earlier.)
@@ -160,11 +158,13 @@ kzk_status configure(kzk_plan* p)
     return KZK_OK;
 }
 
-// twiddle table exp(-2 pi i k / N), k in [0, N), evaluated in long double
+// twiddle table exp(-2 pi i k / N), k in [0, N), evaluated in long double;
+// with lo != nullptr also the lo parts (value - hi) for a two-float table
 template <typename T>
-std::vector<cx<T>> twiddles(int N)
+std::vector<cx<T>> twiddles(int N, std::vector<cx<T>>* lo = nullptr)
 {
     std::vector<cx<T>> w(N);
+    if (lo) lo->resize(N);
     const long double two_pi = 6.283185307179586476925286766559005768L;
     for (int k = 0; k < N; k++) {
         // reduce to the first octant by symmetry for exact 0 / +-1 entries
@@ -174,6 +174,7 @@ std::vector<cx<T>> twiddles(int N)
         if (2 * k == N) { c = -1; s = 0; }
         if (4 * k == 3 * N) { c = 0; s = 1; }
         w[k] = mk<T>((T)(double)c, (T)(double)s);
+        if (lo) (*lo)[k] = mk<T>((T)(double)(c - (long double)w[k].x), (T)(double)(s - (long double)w[k].y));
     }
     return w;
 }
@@ -203,7 +204,7 @@ RowArgs<T> row_args(const kzk_plan* p, const void* in, void* out, double sigma, 
 template <typename T, int MODE>
 kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st)
 {
-    row_kernel<T, row_ppt<T>(), MODE><<<dim3(p->ny, p->batch), p->row_thr, p->row_smem, st>>>(a);
+    row_kernel<T, MODE><<<dim3(p->ny, p->batch), p->row_thr, p->row_smem, st>>>(a);
     KZK_LAUNCHED();
     return KZK_OK;
 }
@@ -211,7 +212,7 @@ kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st)
 template <typename T, int MODE>
 kzk_status launch_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
 {
-    col_kernel<T, col_ppt<T>(), MODE><<<dim3(p->n >> p->log2tc, p->batch), p->col_thr, p->col_smem, st>>>(a);
+    col_kernel<T, MODE><<<dim3(p->n >> p->log2tc, p->batch), p->col_thr, p->col_smem, st>>>(a);
     KZK_LAUNCHED();
     return KZK_OK;
 }
@@ -222,6 +223,8 @@ ColArgs<T> col_args(const kzk_plan* p)
     ColArgs<T> a;
     memset(&a, 0, sizeof(a));
     a.tw = (const cx<T>*)p->twc;
+    a.tw_lo = (const cx<T>*)p->twc_lo;
+    a.Ta_lo = nullptr;
     a.log2ny = p->log2ny;
     a.log2n = p->log2nx - 1;
     a.log2tc = p->log2tc;
@@ -244,6 +247,7 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     c1.b = (const cx<T>*)p->b1;
     c1.out = (cx<T>*)vs;
     c1.Ta = (const cx<T>*)p->E;
+    c1.Ta_lo = (const cx<T>*)p->E_lo;
     c1.Tb = (const cx<T>*)p->P1;
     c1.diag_rows = diag_hist_step ? p->diag_rows : nullptr;
     c1.diag_hist = diag_hist_step;
@@ -352,13 +356,17 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
     a.E = p->E;
     a.P1 = p->P1;
     a.P2 = p->P2;
+    a.E_lo = p->E_lo;
     const long long count = (long long)(p->ny / 2 + 1) * p->n;
     tables_kernel<T><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a);
     KZK_LAUNCHED();
     auto tr = twiddles<T>(p->nx);
-    auto tc = twiddles<T>(p->ny);
+    std::vector<cx<T>> tcl;
+    auto tc = twiddles<T>(p->ny, &tcl);
     KZK_CUDA(cudaMemcpy(p->twr, tr.data(), tr.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
     KZK_CUDA(cudaMemcpy(p->twc, tc.data(), tc.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    if (p->twc_lo)
+        KZK_CUDA(cudaMemcpy(p->twc_lo, tcl.data(), tcl.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
     KZK_CUDA(cudaStreamSynchronize(st));
     return KZK_OK;
 }
@@ -366,7 +374,7 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
 void plan_free(kzk_plan* p)
 {
     if (!p) return;
-    void* ptrs[] = {p->V, p->b1, p->vs, p->b2, p->E, p->P1, p->P2, p->twr, p->twc,
+    void* ptrs[] = {p->V, p->b1, p->vs, p->b2, p->E, p->P1, p->P2, p->E_lo, p->twr, p->twc, p->twc_lo,
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
                     p->seg, p->ckpt};
     for (void* q : ptrs)
@@ -434,17 +442,18 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* Vn, const void* V
 {
     const dim3 cgrid(p->n >> p->log2tc, p->batch), rgrid(p->ny, p->batch);
     const size_t rsm = adj_row_smem<T>(p);
+    const int rthr = p->adj_row_thr;
     // mu2 = P_{conj(ds Phi2)} lam'
     AdjColArgs<T> c2 = adj_col_args<T>(p);
     c2.a = (const cx<T>*)p->lam;
     c2.out = (cx<T>*)p->mu;
     c2.Ta = (const cx<T>*)p->P2;
     c2.sa = (T)p->nx;
-    adj_col_kernel<T, col_ppt<T>(), ADJ_COL_2><<<cgrid, p->col_thr, p->col_smem, st>>>(c2);
+    adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_2><<<cgrid, p->col_thr, p->col_smem, st>>>(c2);
     KZK_LAUNCHED();
     // lam* = lam' + J_{G_{n+1}}(u*)^T mu2
     AdjRowArgs<T> r2 = adj_row_args<T>(p, p->mu, Vs, p->lam, p->ls, sigma + p->dt);
-    adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_2><<<rgrid, p->row_thr, rsm, st>>>(r2);
+    adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_2><<<rgrid, rthr, rsm, st>>>(r2);
     KZK_LAUNCHED();
     // lam_lin = P_{conj E} lam*,  nu1 = P_{conj(ds Phi1)} lam* - mu2
     AdjColArgs<T> c1 = adj_col_args<T>(p);
@@ -456,11 +465,11 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* Vn, const void* V
     c1.sa = (T)1;
     c1.Tb = (const cx<T>*)p->P1;
     c1.sb = (T)p->nx;
-    adj_col_kernel<T, col_ppt<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
+    adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
     KZK_LAUNCHED();
     // lam = lam_lin + J_{G_n}(u)^T nu1
     AdjRowArgs<T> r1 = adj_row_args<T>(p, p->nu, Vn, p->ls, p->lam, sigma);
-    adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_1><<<rgrid, p->row_thr, rsm, st>>>(r1);
+    adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_1><<<rgrid, rthr, rsm, st>>>(r1);
     KZK_LAUNCHED();
     return KZK_OK;
 }
@@ -589,6 +598,7 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
         c1.b = (const cx<T>*)p->b1;
         c1.out = (cx<T>*)p->vs;
         c1.Ta = (const cx<T>*)p->E;
+        c1.Ta_lo = (const cx<T>*)p->E_lo;
         c1.Tb = (const cx<T>*)p->P1;
         c1.diag_rows = p->diag_rows;
         c1.diag_hist = p->diag_hist + (size_t)s * p->batch * 4;
@@ -687,7 +697,9 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     p->g = *grid;
     p->c = *coeffs;
     if (!(p->c.diffraction > 0)) p->c.diffraction = 1.0 / (4.0 * M_PI);
-    if (!(p->c.reg_eps > 0)) p->c.reg_eps = grid->prec == KZK_FP64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+    // epsilon of the precision the multiplier is evaluated in: the tables are
+    // generated in FP64 for both plan precisions
+    if (!(p->c.reg_eps > 0)) p->c.reg_eps = std::ldexp(1.0, -53);
     if (!(p->c.weno_eps > 0)) p->c.weno_eps = 1e-6;
     if (!p->c.has_profile) {
         const double one[4] = {1, 0, 0, 0};
@@ -717,6 +729,8 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     void** tabs[] = {&p->E, &p->P1, &p->P2};
     for (void** t : tabs)
         if (e == cudaSuccess) e = cudaMalloc(t, tab);
+    if (e == cudaSuccess && p->prec == KZK_FP32) e = cudaMalloc(&p->E_lo, tab);
+    if (e == cudaSuccess && p->prec == KZK_FP32) e = cudaMalloc(&p->twc_lo, (size_t)p->ny * p->csz);
     if (e == cudaSuccess) e = cudaMalloc(&p->twr, (size_t)p->nx * p->csz);
     if (e == cudaSuccess) e = cudaMalloc(&p->twc, (size_t)p->ny * p->csz);
     if (e == cudaSuccess) e = cudaMalloc(&p->diag_rows, (size_t)batch * p->ny * 4 * sizeof(double));

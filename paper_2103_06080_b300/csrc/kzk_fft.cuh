@@ -1,13 +1,22 @@
 // kzk_fft.cuh -- shared-memory Stockham FFTs (power-of-two lengths).
 //
 // A batch of nb independent complex transforms of length n = 2^log2n lives in
-// shared memory; element i of transform b sits at buf[b * sb + i * si].  Each
-// stage is an autosort (Stockham) pass of radix R in {2, 4, 8, 16}: a thread
-// loads R points with stride n/R into registers, applies the inter-stage
-// twiddles, runs an in-register DFT of size R and writes the results to
-// their sorted positions, so the output is in natural order with no bit
-// reversal.  Twiddles come from a plan-time table tw[k] = exp(-2 pi i k / Ntw)
+// shared memory; element i of transform b sits at buf[idx(b * sb + i * si)],
+// where idx() is the identity or, with PAD, i + i/16 (one padding slot per
+// 16 elements, which removes the bank conflicts of the first pass's strided
+// stores and of the WENO sweep over the same buffer).  Each stage is an
+// autosort (Stockham) pass of radix R in {2, 4, 8, 16}: a thread loads R
+// points with stride n/R into registers, applies the inter-stage twiddles,
+// runs an in-register DFT of size R and writes the results to their sorted
+// positions, so the output is in natural order with no bit reversal.
+// Twiddles come from a plan-time table tw[k] = exp(-2 pi i k / Ntw)
 // (Ntw = 2^tw_log2 >= n), built in FP64 on the host.
+//
+// ACC (float only): every multiplication by a fixed constant -- table
+// twiddles and the DFT's own roots of unity -- uses a two-float (hi + lo)
+// representation of the constant.  A transform applied to the propagated
+// state once per step then carries no systematic rounding of its constants,
+// which would otherwise compound linearly over thousands of steps.
 //
 // Forward transforms use exp(-2 pi i ...), inverse ones exp(+2 pi i ...); no
 // transform is normalised (the 1/N factors are folded into the tables).
@@ -40,8 +49,11 @@ __host__ __device__ constexpr double cos16(int j)
 }
 __host__ __device__ constexpr double sin16(int j) { return cos16(j - 4); }
 
+__device__ __forceinline__ int padx(int i) { return i + (i >> 4); }
+template <bool PAD> __device__ __forceinline__ int sidx(int i) { return PAD ? padx(i) : i; }
+
 // x * exp(S 2 pi i k / R) for compile-time R | 16, k; trivial factors are exact.
-template <typename T, int R, int K, int S>
+template <typename T, int R, int K, int S, bool ACC>
 __device__ __forceinline__ cx<T> rot(cx<T> x)
 {
     constexpr int j = (K * (16 / R)) & 15;          // angle 2 pi j / 16
@@ -52,17 +64,25 @@ __device__ __forceinline__ cx<T> rot(cx<T> x)
     else {
         constexpr T c = (T)cos16(j);
         constexpr T s = (T)(S * sin16(j));
-        return mk<T>(fma(x.x, c, -x.y * s), fma(x.x, s, x.y * c));
+        if constexpr (ACC && sizeof(T) == 4) {
+            constexpr T cl = (T)(cos16(j) - (double)c);
+            constexpr T sl = (T)(S * sin16(j) - (double)s);
+            const T re = fma(x.x, c, fma(x.x, cl, -fma(x.y, s, x.y * sl)));
+            const T im = fma(x.x, s, fma(x.x, sl, fma(x.y, c, x.y * cl)));
+            return mk<T>(re, im);
+        } else {
+            return mk<T>(fma(x.x, c, -x.y * s), fma(x.x, s, x.y * c));
+        }
     }
 }
 
 // In-register DFT of size R (natural order in and out), sign S.
-template <typename T, int R, int S> struct RegDFT {
+template <typename T, int R, int S, bool ACC> struct RegDFT {
     template <int K>
     static __device__ __forceinline__ void combine(cx<T>* v, const cx<T>* e, const cx<T>* o)
     {
         if constexpr (K < R / 2) {
-            cx<T> t = rot<T, R, K, S>(o[K]);
+            cx<T> t = rot<T, R, K, S, ACC>(o[K]);
             v[K] = add<T>(e[K], t);
             v[K + R / 2] = sub<T>(e[K], t);
             combine<K + 1>(v, e, o);
@@ -87,21 +107,29 @@ template <typename T, int R, int S> struct RegDFT {
             cx<T> e[R / 2], o[R / 2];
 #pragma unroll
             for (int i = 0; i < R / 2; i++) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
-            RegDFT<T, R / 2, S>::run(e);
-            RegDFT<T, R / 2, S>::run(o);
+            RegDFT<T, R / 2, S, ACC>::run(e);
+            RegDFT<T, R / 2, S, ACC>::run(o);
             combine<0>(v, e, o);
         }
     }
+};
+
+// Twiddle tables: hi part and, for ACC, the lo correction (lo == nullptr
+// otherwise).
+template <typename T>
+struct Tw {
+    const cx<T>* __restrict__ hi;
+    const cx<T>* __restrict__ lo;
+    int log2;
 };
 
 // One Stockham pass of radix R over a batch.  PPT = points each thread holds
 // (PPT / R butterflies per pass).  COLS: consecutive threads take consecutive
 // transforms (column tiles, transform index fastest in memory); otherwise
 // consecutive threads take consecutive butterflies of one transform.
-template <typename T, int R, int PPT, bool COLS, bool INV>
-__device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int si, int sb,
-                                         int log2Ns, const cx<T>* __restrict__ tw, int tw_log2,
-                                         int tid, int nthr)
+template <typename T, int R, int PPT, bool COLS, bool INV, bool PAD, bool ACC>
+__device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int si, int sb, int log2Ns,
+                                         const Tw<T>& tw, int tid, int nthr)
 {
     constexpr int NB = PPT / R;
     constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
@@ -109,7 +137,7 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
     const int log2nbf = log2n - LR;                 // butterflies per transform = n / R
     const int total = 1 << (log2nb + log2nbf);
     const int Ns = 1 << log2Ns;
-    const int twsh = tw_log2 - log2Ns - LR;         // table index = r * k << twsh
+    const int twsh = tw.log2 - log2Ns - LR;         // table index = r * k << twsh
     cx<T> v[NB][R];
     int obase[NB];
 #pragma unroll
@@ -124,15 +152,22 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
             const int ib = b * sb + j * si;
             const int stride = (1 << log2nbf) * si;
 #pragma unroll
-            for (int r = 0; r < R; r++) v[q][r] = buf[ib + r * stride];
+            for (int r = 0; r < R; r++) v[q][r] = buf[sidx<PAD>(ib + r * stride)];
             if (log2Ns > 0) {
 #pragma unroll
                 for (int r = 1; r < R; r++) {
-                    cx<T> w = tw[(r * k) << twsh];
-                    v[q][r] = INV ? mulc<T>(v[q][r], w) : mul<T>(v[q][r], w);
+                    const int ti = (r * k) << twsh;
+                    const cx<T> w = tw.hi[ti];
+                    if constexpr (ACC && sizeof(T) == 4) {
+                        const cx<T> wl = tw.lo[ti];
+                        const cx<T> x = v[q][r];
+                        v[q][r] = INV ? fma_c<T>(x, conj<T>(wl), mulc<T>(x, w)) : fma_c<T>(x, wl, mul<T>(x, w));
+                    } else {
+                        v[q][r] = INV ? mulc<T>(v[q][r], w) : mul<T>(v[q][r], w);
+                    }
                 }
             }
-            RegDFT<T, R, S>::run(v[q]);
+            RegDFT<T, R, S, ACC>::run(v[q]);
             obase[q] = b * sb + (((j - k) << LR) + k) * si;
         }
     }
@@ -141,7 +176,7 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
     for (int q = 0; q < NB; q++) {
         if (obase[q] >= 0) {
 #pragma unroll
-            for (int r = 0; r < R; r++) buf[obase[q] + r * Ns * si] = v[q][r];
+            for (int r = 0; r < R; r++) buf[sidx<PAD>(obase[q] + r * Ns * si)] = v[q][r];
         }
     }
     __syncthreads();
@@ -149,28 +184,36 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
 
 // Full transform: radix-16 passes while possible, then one smaller pass.
 // Requires nthr * PPT >= nb * n.  Ends with a __syncthreads().
-template <typename T, int PPT, bool COLS, bool INV>
-__device__ __forceinline__ void fft_batched(cx<T>* buf, int log2n, int log2nb, int si, int sb,
-                                            const cx<T>* __restrict__ tw, int tw_log2, int tid,
-                                            int nthr)
+template <typename T, int PPT, bool COLS, bool INV, bool PAD = false, bool ACC = false>
+__device__ __forceinline__ void fft_batched(cx<T>* buf, int log2n, int log2nb, int si, int sb, const Tw<T>& tw,
+                                            int tid, int nthr)
 {
     int done = 0;
     while (done < log2n) {
         const int rem = log2n - done;
         if (PPT >= 16 && rem >= 4) {
-            fft_pass<T, (PPT >= 16 ? 16 : 2), PPT, COLS, INV>(buf, log2n, log2nb, si, sb, done, tw, tw_log2, tid, nthr);
+            fft_pass<T, (PPT >= 16 ? 16 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, tid, nthr);
             done += (PPT >= 16 ? 4 : 1);
         } else if (PPT >= 8 && rem >= 3) {
-            fft_pass<T, (PPT >= 8 ? 8 : 2), PPT, COLS, INV>(buf, log2n, log2nb, si, sb, done, tw, tw_log2, tid, nthr);
+            fft_pass<T, (PPT >= 8 ? 8 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, tid, nthr);
             done += (PPT >= 8 ? 3 : 1);
         } else if (PPT >= 4 && rem >= 2) {
-            fft_pass<T, (PPT >= 4 ? 4 : 2), PPT, COLS, INV>(buf, log2n, log2nb, si, sb, done, tw, tw_log2, tid, nthr);
+            fft_pass<T, (PPT >= 4 ? 4 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, tid, nthr);
             done += (PPT >= 4 ? 2 : 1);
         } else {
-            fft_pass<T, 2, PPT, COLS, INV>(buf, log2n, log2nb, si, sb, done, tw, tw_log2, tid, nthr);
+            fft_pass<T, 2, PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, tid, nthr);
             done += 1;
         }
     }
+}
+
+// Older call form (no padding, single-precision constants).
+template <typename T, int PPT, bool COLS, bool INV>
+__device__ __forceinline__ void fft_batched(cx<T>* buf, int log2n, int log2nb, int si, int sb,
+                                            const cx<T>* __restrict__ tw, int tw_log2, int tid, int nthr)
+{
+    Tw<T> t{tw, nullptr, tw_log2};
+    fft_batched<T, PPT, COLS, INV, false, false>(buf, log2n, log2nb, si, sb, t, tid, nthr);
 }
 
 }  // namespace kzk

@@ -20,6 +20,7 @@
 #include "kzk_common.cuh"
 #include "kzk_fft.cuh"
 #include "kzk_weno.cuh"
+#include <algorithm>
 
 namespace kzk {
 
@@ -69,29 +70,27 @@ __device__ __forceinline__ void block_diag(double* red, double s1, double s2, do
 // C2R pre-processing in place: packed half spectrum X (n = nx/2 slots) ->
 // Z with IFFT_n(Z) = nx * (x_even + i x_odd), Z_k = (X_k + conj X_{n-k})
 // + i conj(W^k) (X_k - conj X_{n-k}), W = exp(-2 pi i / nx).
-template <typename T>
+template <typename T, bool PAD = false>
 __device__ __forceinline__ void c2r_pre(cx<T>* X, int n, const cx<T>* __restrict__ tw, int tid, int nthr)
 {
     for (int k = tid; k <= n / 2; k += nthr) {
         if (k == 0) {
             const T x0 = X[0].x, xn = X[0].y;
             X[0] = mk<T>(x0 + xn, x0 - xn);
-            if (n == 1) continue;
         } else if (2 * k == n) {
-            const cx<T> a = X[k];
-            X[k] = mk<T>(T(2) * a.x, T(-2) * a.y);
+            const cx<T> a = X[sidx<PAD>(k)];
+            X[sidx<PAD>(k)] = mk<T>(T(2) * a.x, T(-2) * a.y);
         } else {
-            const cx<T> a = X[k], b = X[n - k];
+            const cx<T> a = X[sidx<PAD>(k)], b = X[sidx<PAD>(n - k)];
             const cx<T> w = tw[k];                      // W^k
-            // k
             cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
             cx<T> r = mul_si<T, 1>(mulc<T>(d, w));      // i conj(W^k) d
             const cx<T> zk = add<T>(s, r);
             // n - k: W^{n-k} = -conj(W^k)  =>  conj(W^{n-k}) = -W^k
             s = add<T>(b, conj<T>(a)); d = sub<T>(b, conj<T>(a));
             r = mul_si<T, -1>(mul<T>(d, w));            // i (-W^k) d
-            X[k] = zk;
-            X[n - k] = add<T>(s, r);
+            X[sidx<PAD>(k)] = zk;
+            X[sidx<PAD>(n - k)] = add<T>(s, r);
         }
     }
 }
@@ -99,7 +98,7 @@ __device__ __forceinline__ void c2r_pre(cx<T>* X, int n, const cx<T>* __restrict
 // R2C post-processing: Z = FFT_n(x_even + i x_odd) -> packed X = FFT_nx(x),
 // X_k = 1/2 [(Z_k + conj Z_{n-k}) - i W^k (Z_k - conj Z_{n-k})].
 // Returns the pair (X_k, X_{n-k}) for 0 < k < n/2, handles k = 0 and n/2.
-template <typename T>
+template <typename T, bool PAD = false>
 __device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, const cx<T>* __restrict__ tw,
                                               cx<T>& Xk, cx<T>& Xnk)
 {
@@ -109,10 +108,10 @@ __device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, cons
         Xk = mk<T>(z.x + z.y, z.x - z.y);    // (X_0, X_{nx/2}) packed
         Xnk = Xk;
     } else if (2 * k == n) {
-        Xk = conj<T>(Z[k]);
+        Xk = conj<T>(Z[sidx<PAD>(k)]);
         Xnk = Xk;
     } else {
-        const cx<T> a = Z[k], b = Z[n - k];
+        const cx<T> a = Z[sidx<PAD>(k)], b = Z[sidx<PAD>(n - k)];
         const cx<T> w = tw[k];
         cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
         cx<T> r = mul_si<T, -1>(mul<T>(w, d));            // -i W^k d
@@ -124,94 +123,110 @@ __device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, cons
     }
 }
 
-// Row kernel.  One CTA per (row, instance).  Shared memory: two buffers of
-// nx reals (= n complex) each, plus a reduction area.
-template <typename T, int PPT, int MODE>
-__global__ void __launch_bounds__(1024) row_kernel(RowArgs<T> a)
+// Padded length of one row buffer (n complex + one slot per 16).
+__host__ __device__ constexpr int row_buf_len(int n) { return n + (n >> 4); }
+
+// points per thread in the row FFTs (FP32: 16, radix-16 passes; FP64: 8,
+// radix-8 passes, which keeps a double-complex butterfly in registers)
+template <typename T> __host__ __device__ constexpr int row_ppt_of() { return 8; }
+constexpr int ROW_MAX_THREADS = 512; // n / 8 for nx = 8192
+
+// Row kernel.  One CTA per (row, instance), n / PPT threads (at least 32).
+// Shared memory: two padded buffers of n complex (= nx reals) each, plus a
+// reduction area of 4 doubles per thread.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(ROW_MAX_THREADS) row_kernel(RowArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int nx = 1 << a.log2nx, n = nx >> 1, log2n = a.log2nx - 1;
     const int row = blockIdx.x, inst = blockIdx.y;
     cx<T>* X = reinterpret_cast<cx<T>*>(smem_raw);       // buffer U
-    cx<T>* Y = X + n;                                      // buffer B
-    double* red = reinterpret_cast<double*>(Y + n);
+    cx<T>* Y = X + row_buf_len(n);                         // buffer B
+    double* red = reinterpret_cast<double*>(Y + row_buf_len(n));
     const long long base = (long long)inst * a.inst_stride + (long long)row * n;
+    const Tw<T> tw{a.tw, nullptr, a.log2nx};
+    constexpr int ROW_PPT = row_ppt_of<T>();
 
-    if (MODE == ROW_FWD) {
+    if constexpr (MODE == ROW_FWD) {
         // physical row -> packed half spectrum / nx
         const T* src = reinterpret_cast<const T*>(a.in + base);
-        T* y = reinterpret_cast<T*>(Y);
-        for (int i = tid; i < nx; i += nthr) y[i] = src[i];
+        for (int i = tid; i < nx; i += nthr) st_real<T, true>(Y, i, src[i]);
         __syncthreads();
-        fft_batched<T, PPT, false, false>(Y, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+        fft_batched<T, ROW_PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
         for (int k = tid; k <= n / 2; k += nthr) {
             cx<T> xk, xnk;
-            r2c_post_pair<T>(Y, n, k, a.tw, xk, xnk);
+            r2c_post_pair<T, true>(Y, n, k, a.tw, xk, xnk);
             a.out[base + k] = scale<T>(xk, a.out_scale);
             if (k != 0 && 2 * k != n) a.out[base + n - k] = scale<T>(xnk, a.out_scale);
         }
-        return;
-    }
+    } else {
+        // spectral row -> physical row in X
+        for (int i = tid; i < n; i += nthr) X[padx(i)] = a.in[base + i];
+        __syncthreads();
+        c2r_pre<T, true>(X, n, a.tw, tid, nthr);
+        __syncthreads();
+        fft_batched<T, ROW_PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
 
-    // spectral row -> physical row in X
-    for (int i = tid; i < n; i += nthr) X[i] = a.in[base + i];
-    __syncthreads();
-    c2r_pre<T>(X, n, a.tw, tid, nthr);
-    __syncthreads();
-    fft_batched<T, PPT, false, true>(X, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
-    const T* u = reinterpret_cast<const T*>(X);
-
-    T s1 = 0, s2 = 0, mx = 0;
-    int nf = 0;
-    if (MODE == ROW_INV) {
-        T* dst = reinterpret_cast<T*>(a.out + base);
-        for (int i = tid; i < nx; i += nthr) {
-            const T v = u[i] * a.out_scale;
-            dst[i] = v;
-            if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf++; }
-        }
-        if (a.diag_rows) block_diag(red, (double)s1, (double)s2, (double)mx, (double)nf,
-                                    a.diag_rows + ((long long)inst * a.ny + row) * 4);
-        return;
-    }
-
-    // ROW_RHS: WENO5 flux derivative into Y, then tau-R2C of Y
-    {
-        T* bphys = reinterpret_cast<T*>(Y);
-        const int Q = nx >= nthr ? nx / nthr : 1;
-        const int k0 = tid * Q;
-        if (k0 < nx) weno_row_chunk<T>(u, bphys, nx, k0, Q, a.wc, s1, s2, mx, nf);
-    }
-    __syncthreads();
-    fft_batched<T, PPT, false, false>(Y, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
-    const cx<T>* vin = a.in + base;
-    for (int k = tid; k <= n / 2; k += nthr) {
-        cx<T> xk, xnk;
-        r2c_post_pair<T>(Y, n, k, a.tw, xk, xnk);
-        if (a.cA != T(0)) {
-            // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
-            if (k == 0) {
-                const T kN = a.kscale * T(n);
-                xk.y -= a.cA * kN * kN * vin[0].y;
-            } else {
-                const T kt = a.kscale * T(k);
-                const cx<T> v = vin[k];
-                xk.x -= a.cA * kt * kt * v.x;
-                xk.y -= a.cA * kt * kt * v.y;
-                if (2 * k != n) {
-                    const T kt2 = a.kscale * T(n - k);
-                    const cx<T> w = vin[n - k];
-                    xnk.x -= a.cA * kt2 * kt2 * w.x;
-                    xnk.y -= a.cA * kt2 * kt2 * w.y;
-                }
+        T s1 = 0, s2 = 0, mx = 0;
+        int nf = 0;
+        if constexpr (MODE == ROW_INV) {
+            T* dst = reinterpret_cast<T*>(a.out + base);
+            for (int i = tid; i < nx; i += nthr) {
+                const T v = ld_real<T, true>(X, i) * a.out_scale;
+                dst[i] = v;
+                if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf++; }
             }
+            if (a.diag_rows) block_diag(red, (double)s1, (double)s2, (double)mx, (double)nf,
+                                        a.diag_rows + ((long long)inst * a.ny + row) * 4);
+        } else {
+            // ROW_RHS: WENO5 flux derivative into Y, then tau-R2C of Y
+            const int Q = nx >= nthr ? nx / nthr : 1;
+            const int k0 = tid * Q;
+            if (k0 < nx) weno_row_chunk<T, true>(X, Y, nx, k0, Q, a.wc, s1, s2, mx, nf);
+            __syncthreads();
+            fft_batched<T, ROW_PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
+            const cx<T>* vin = a.in + base;
+            for (int k = tid; k <= n / 2; k += nthr) {
+                cx<T> xk, xnk;
+                r2c_post_pair<T, true>(Y, n, k, a.tw, xk, xnk);
+                if (a.cA != T(0)) {
+                    // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
+                    if (k == 0) {
+                        const T kN = a.kscale * T(n);
+                        xk.y -= a.cA * kN * kN * vin[0].y;
+                    } else {
+                        const T kt = a.kscale * T(k);
+                        const cx<T> v = vin[k];
+                        xk.x -= a.cA * kt * kt * v.x;
+                        xk.y -= a.cA * kt * kt * v.y;
+                        if (2 * k != n) {
+                            const T kt2 = a.kscale * T(n - k);
+                            const cx<T> w = vin[n - k];
+                            xnk.x -= a.cA * kt2 * kt2 * w.x;
+                            xnk.y -= a.cA * kt2 * kt2 * w.y;
+                        }
+                    }
+                }
+                a.out[base + k] = xk;
+                if (k != 0 && 2 * k != n) a.out[base + n - k] = xnk;
+            }
+            if (a.diag_rows) block_diag(red, (double)s1, (double)s2, (double)mx, (double)nf,
+                                        a.diag_rows + ((long long)inst * a.ny + row) * 4);
         }
-        a.out[base + k] = xk;
-        if (k != 0 && 2 * k != n) a.out[base + n - k] = xnk;
     }
-    if (a.diag_rows) block_diag(red, (double)s1, (double)s2, (double)mx, (double)nf,
-                                a.diag_rows + ((long long)inst * a.ny + row) * 4);
+}
+
+// Threads and dynamic shared memory of one row CTA.
+template <typename T>
+__host__ __forceinline__ int row_threads(int nx)
+{
+    return (nx / 2) / row_ppt_of<T>() > 32 ? (nx / 2) / row_ppt_of<T>() : 32;
+}
+template <typename T>
+__host__ __forceinline__ size_t row_smem_bytes(int nx)
+{
+    return 2 * (size_t)row_buf_len(nx / 2) * sizeof(cx<T>) + 4 * (size_t)row_threads<T>(nx) * sizeof(double);
 }
 
 enum ColMode { COL_STAGE1 = 0, COL_STAGE2 = 1 };
@@ -223,8 +238,10 @@ struct ColArgs {
     const cx<T>* c;         // STAGE1: -;    STAGE2: V*
     cx<T>* out;             // STAGE1: V*;   STAGE2: V'
     const cx<T>* Ta;        // STAGE1: E';   STAGE2: P2'
+    const cx<T>* Ta_lo;     // STAGE1, FP32: lo part of E' (hi + lo = FP64 value)
     const cx<T>* Tb;        // STAGE1: P1';  STAGE2: -
     const cx<T>* tw;        // exp(-2 pi i k / ny), k in [0, ny)
+    const cx<T>* tw_lo;     // FP32: lo parts of tw
     int log2ny, log2n, log2tc;
     long long inst_stride;
     // diagnostics of the step (STAGE1, CTA x = 0 of each instance)
@@ -233,25 +250,31 @@ struct ColArgs {
     double inv_count, cell;   // 1/(nx ny), dtau dy
 };
 
-// Multiplier at (l, m) applied to the column-FFT'd tile S ([ny][TC], natural
-// order).  Column m = 0 packs the tau-DC (real part) and tau-Nyquist (imag
-// part) sequences; their spectra are separated through the pair (l, ny - l)
-// and each is multiplied by its own real table entry.
+// Table entry at (l, m) applied to a column-FFT'd value z (zm: the value at
+// row ny - l of the same column, used only by the packed column m = 0, which
+// holds the tau-DC sequence in its real part and the tau-Nyquist one in its
+// imaginary part; their spectra are separated through the pair (l, ny - l)
+// and each is multiplied by its own real table entry).
 template <typename T>
-__device__ __forceinline__ cx<T> apply_mult(const cx<T>* __restrict__ tab, const cx<T>* S, int l, int c, int m,
-                                            int ny, int n, int log2tc)
+__device__ __forceinline__ cx<T> mult_entry(cx<T> M, cx<T> z, cx<T> zm, bool packed)
 {
-    const int lf = l <= (ny >> 1) ? l : ny - l;
-    const cx<T> M = tab[(long long)lf * n + m];
-    const cx<T> z = S[(l << log2tc) + c];
-    if (m != 0) return mul<T>(M, z);
-    const cx<T> zm = S[(((ny - l) & (ny - 1)) << log2tc) + c];
+    if (!packed) return mul<T>(M, z);
     const T h = T(0.5) * (M.x + M.y), g = T(0.5) * (M.x - M.y);
     return mk<T>(h * z.x + g * zm.x, h * z.y - g * zm.y);
 }
 
-template <typename T, int PPT, int MODE>
-__global__ void __launch_bounds__(1024) col_kernel(ColArgs<T> a)
+template <typename T> __host__ __device__ constexpr int col_ppt_of() { return 8; }
+template <typename T> __host__ __device__ constexpr int col_max_threads() { return sizeof(T) == 4 ? 1024 : 512; }
+constexpr int COL_MAX_THREADS = 1024;
+
+// Column kernel.  One CTA per (tile of TC columns, instance).
+//  STAGE1 (STEP 2): shared memory holds two tiles [ny][2 TC]: columns [0, TC)
+//    the state V, [TC, 2 TC) b1.  FFT both along y (the state's transform
+//    with two-float constants in FP32), combine E' V + P1' b1 into the state
+//    half, inverse FFT it (two-float again) and store V*.
+//  STAGE2 (STEP 4): one tile of b2 - b1, FFT, times P2', inverse FFT, plus V*.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* S = reinterpret_cast<cx<T>*>(smem_raw);
@@ -259,14 +282,17 @@ __global__ void __launch_bounds__(1024) col_kernel(ColArgs<T> a)
     const int ny = 1 << a.log2ny, n = 1 << a.log2n, TC = 1 << a.log2tc;
     const int m0 = blockIdx.x * TC, inst = blockIdx.y;
     const long long ibase = (long long)inst * a.inst_stride;
-    const int total = ny << a.log2tc;
-    cx<T> acc[PPT];
+    const int total = ny << a.log2tc;                   // elements of one tile
+    constexpr bool ACC = sizeof(T) == 4;
+    constexpr int COL_PPT = col_ppt_of<T>();
+    const Tw<T> twp{a.tw, nullptr, a.log2ny};
+    const Tw<T> twa{a.tw, a.tw_lo, a.log2ny};
 
     auto gidx = [&](int e) -> long long {
         return ibase + (long long)(e >> a.log2tc) * n + m0 + (e & (TC - 1));
     };
 
-    if (MODE == COL_STAGE1) {
+    if constexpr (MODE == COL_STAGE1) {
         // diagnostics of the state this step started from (rows written by R)
         if (blockIdx.x == 0 && a.diag_rows) {
             double* red = reinterpret_cast<double*>(smem_raw);
@@ -285,57 +311,107 @@ __global__ void __launch_bounds__(1024) col_kernel(ColArgs<T> a)
                 d[3] = tmp[3];
             }
         }
-        for (int e = tid; e < total; e += nthr) S[e] = a.a[gidx(e)];
-        __syncthreads();
-        fft_batched<T, PPT, true, false>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
-#pragma unroll
-        for (int q = 0; q < PPT; q++) {
-            const int e = tid + q * nthr;
-            if (e < total) acc[q] = apply_mult<T>(a.Ta, S, e >> a.log2tc, e & (TC - 1), m0 + (e & (TC - 1)), ny, n, a.log2tc);
+        const int W = 2 * TC;                              // row pitch of the two tiles
+        for (int e = tid; e < total; e += nthr) {
+            const long long g = gidx(e);
+            const int l = e >> a.log2tc, c = e & (TC - 1);
+            S[l * W + c] = a.a[g];
+            S[l * W + TC + c] = a.b[g];
         }
         __syncthreads();
-        for (int e = tid; e < total; e += nthr) S[e] = a.b[gidx(e)];
-        __syncthreads();
-        fft_batched<T, PPT, true, false>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
-#pragma unroll
-        for (int q = 0; q < PPT; q++) {
-            const int e = tid + q * nthr;
-            if (e < total) acc[q] = add<T>(acc[q], apply_mult<T>(a.Tb, S, e >> a.log2tc, e & (TC - 1), m0 + (e & (TC - 1)), ny, n, a.log2tc));
+        // state tile: accurate transform; b1 tile: plain
+        fft_batched<T, COL_PPT, true, false, false, ACC>(S, a.log2ny, a.log2tc, W, 1, twa, tid, nthr);
+        fft_batched<T, COL_PPT, true, false, false, false>(S + TC, a.log2ny, a.log2tc, W, 1, twp, tid, nthr);
+        // V*_hat = E' V_hat + P1' b1_hat, in place in the state half.  Every
+        // element is combined by its owner; the packed column 0 (first tile
+        // only) couples rows l and ny - l, so one thread owns each such pair.
+        const bool has_packed = (m0 == 0);
+        for (int e = tid; e < total; e += nthr) {
+            const int l = e >> a.log2tc, c = e & (TC - 1), m = m0 + c;
+            if (m == 0) continue;
+            const int lf = l <= (ny >> 1) ? l : ny - l;
+            const long long ti = (long long)lf * n + m;
+            const cx<T> zv = S[l * W + c], zb = S[l * W + TC + c];
+            cx<T> r = mul<T>(a.Ta[ti], zv);
+            if constexpr (ACC) r = fma_c<T>(a.Ta_lo[ti], zv, r);
+            S[l * W + c] = fma_c<T>(a.Tb[ti], zb, r);
+        }
+        if (has_packed) {
+            for (int l = tid; l <= (ny >> 1); l += nthr) {
+                const int lm = (ny - l) & (ny - 1);
+                const long long ti = (long long)l * n;        // l <= ny/2: folded row l
+                const cx<T> zv = S[l * W], zvm = S[lm * W], zb = S[l * W + TC], zbm = S[lm * W + TC];
+                cx<T> r = mult_entry<T>(a.Ta[ti], zv, zvm, true);
+                cx<T> rm = mult_entry<T>(a.Ta[ti], zvm, zv, true);
+                if constexpr (ACC) {
+                    r = add<T>(r, mult_entry<T>(a.Ta_lo[ti], zv, zvm, true));
+                    rm = add<T>(rm, mult_entry<T>(a.Ta_lo[ti], zvm, zv, true));
+                }
+                r = add<T>(r, mult_entry<T>(a.Tb[ti], zb, zbm, true));
+                rm = add<T>(rm, mult_entry<T>(a.Tb[ti], zbm, zb, true));
+                S[l * W] = r;
+                if (lm != l) S[lm * W] = rm;
+            }
         }
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PPT; q++) {
-            const int e = tid + q * nthr;
-            if (e < total) S[e] = acc[q];
-        }
-        __syncthreads();
-        fft_batched<T, PPT, true, true>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
-        for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = S[e];
+        fft_batched<T, COL_PPT, true, true, false, ACC>(S, a.log2ny, a.log2tc, W, 1, twa, tid, nthr);
+        for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = S[(e >> a.log2tc) * W + (e & (TC - 1))];
     } else {
         for (int e = tid; e < total; e += nthr) {
             const long long g = gidx(e);
             S[e] = sub<T>(a.b[g], a.a[g]);
         }
         __syncthreads();
-        fft_batched<T, PPT, true, false>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
-#pragma unroll
-        for (int q = 0; q < PPT; q++) {
-            const int e = tid + q * nthr;
-            if (e < total) acc[q] = apply_mult<T>(a.Ta, S, e >> a.log2tc, e & (TC - 1), m0 + (e & (TC - 1)), ny, n, a.log2tc);
+        fft_batched<T, COL_PPT, true, false, false, false>(S, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
+        for (int e = tid; e < total; e += nthr) {
+            const int l = e >> a.log2tc, c = e & (TC - 1), m = m0 + c;
+            if (m == 0) continue;
+            const int lf = l <= (ny >> 1) ? l : ny - l;
+            S[e] = mul<T>(a.Ta[(long long)lf * n + m], S[e]);
+        }
+        if (m0 == 0) {
+            for (int l = tid; l <= (ny >> 1); l += nthr) {
+                const int lm = (ny - l) & (ny - 1);
+                const cx<T> M = a.Ta[(long long)l * n];
+                const cx<T> z = S[l << a.log2tc], zm = S[lm << a.log2tc];
+                S[l << a.log2tc] = mult_entry<T>(M, z, zm, true);
+                if (lm != l) S[lm << a.log2tc] = mult_entry<T>(M, zm, z, true);
+            }
         }
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PPT; q++) {
-            const int e = tid + q * nthr;
-            if (e < total) S[e] = acc[q];
-        }
-        __syncthreads();
-        fft_batched<T, PPT, true, true>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
+        fft_batched<T, COL_PPT, true, true, false, false>(S, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
         for (int e = tid; e < total; e += nthr) {
             const long long g = gidx(e);
             a.out[g] = add<T>(a.c[g], S[e]);
         }
     }
+}
+
+// Column tile width (log2) and threads: STAGE1 holds two tiles of
+// ny x TC complex in at most 128 KB, with TC * ny / COL_PPT <= 512 threads.
+template <typename T>
+__host__ __forceinline__ int col_log2tc(int nx, int ny)
+{
+    int tc = std::min(16, nx / 2);
+    while (tc > 1 && (2 * (size_t)ny * tc * sizeof(cx<T>) > 128 * 1024 ||
+                      (long long)ny * tc / col_ppt_of<T>() > col_max_threads<T>()))
+        tc >>= 1;
+    int l = 0;
+    while ((1 << l) < tc) ++l;
+    return l;
+}
+template <typename T>
+__host__ __forceinline__ int col_threads(int ny, int log2tc)
+{
+    const long long t = ((long long)ny << log2tc) / col_ppt_of<T>();
+    return t > 32 ? (int)t : 32;
+}
+template <typename T>
+__host__ __forceinline__ size_t col_smem_bytes(int ny, int log2tc)
+{
+    const size_t tiles = 2 * ((size_t)ny << log2tc) * sizeof(cx<T>);
+    const size_t red = 4 * (size_t)col_threads<T>(ny, log2tc) * sizeof(double);
+    return tiles > red ? tiles : red;
 }
 
 // Final diagnostics of each instance from its per-row partials.

@@ -53,7 +53,7 @@ __global__ void noalloc_twiddles(cx<T>* tw, int nx)
 
 double horner4(const double* c, double s) { return ((c[3] * s + c[2]) * s + c[1]) * s + c[0]; }
 
-template <typename T, int PPT>
+template <typename T>
 kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch, const void* u, void* b,
                double sigma, cudaStream_t st, int dev)
 {
@@ -63,8 +63,8 @@ kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch,
     cx<T>* V = (cx<T>*)base;
     cx<T>* Bh = (cx<T>*)(base + kSpecBytes);
     cx<T>* tw = (cx<T>*)(base + 2 * kSpecBytes);
-    const int thr = n / PPT > 32 ? n / PPT : 32;
-    const size_t smem = 2 * (size_t)n * sizeof(cx<T>) + 4 * (size_t)thr * sizeof(double);
+    const int thr = row_threads<T>(nx);
+    const size_t smem = row_smem_bytes<T>(nx);
     {
         std::lock_guard<std::mutex> lk(g_mu);
         if (!g_attr_done[dev]) {
@@ -73,12 +73,12 @@ kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch,
             int optin = 0;
             if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
                 return KZK_ERR_CUDA;
-            for (cudaError_t e : {cudaFuncSetAttribute(row_kernel<double, 8, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<double, 8, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<double, 8, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<float, 16, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<float, 16, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<float, 16, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)})
+            for (cudaError_t e : {cudaFuncSetAttribute(row_kernel<double, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<double, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<double, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<float, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<float, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<float, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)})
                 if (e != cudaSuccess) return KZK_ERR_CUDA;
             g_attr_done[dev] = true;
         }
@@ -104,17 +104,17 @@ kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch,
     a.in = (const cx<T>*)u;
     a.out = V;
     a.out_scale = (T)(1.0 / nx);
-    row_kernel<T, PPT, ROW_FWD><<<grid, thr, smem, st>>>(a);
+    row_kernel<T, ROW_FWD><<<grid, thr, smem, st>>>(a);
     // WENO5 flux derivative and absorption deviation, spectral
     a.in = V;
     a.out = Bh;
     a.out_scale = (T)1;
-    row_kernel<T, PPT, ROW_RHS><<<grid, thr, smem, st>>>(a);
+    row_kernel<T, ROW_RHS><<<grid, thr, smem, st>>>(a);
     // back to physical space (the spectrum carries a factor nx)
     a.in = Bh;
     a.out = (cx<T>*)b;
     a.out_scale = (T)(1.0 / nx);
-    row_kernel<T, PPT, ROW_INV><<<grid, thr, smem, st>>>(a);
+    row_kernel<T, ROW_INV><<<grid, thr, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? KZK_OK : KZK_ERR_CUDA;
 }
 
@@ -159,7 +159,7 @@ extern "C" kzk_status kzk_rhs_noalloc(const kzk_grid* grid, const kzk_coeffs* co
     }
     cudaStream_t st = (cudaStream_t)stream;
     const kzk_status s = grid->prec == KZK_FP64
-                             ? run<double, 8>(scratch, grid, coeffs, batch, u, b, sigma, st, dev)
-                             : run<float, 16>(scratch, grid, coeffs, batch, u, b, sigma, st, dev);
+                             ? run<double>(scratch, grid, coeffs, batch, u, b, sigma, st, dev)
+                             : run<float>(scratch, grid, coeffs, batch, u, b, sigma, st, dev);
     return s == KZK_OK ? s : set_error(s, "kzk_rhs_noalloc: CUDA launch or attribute call failed");
 }

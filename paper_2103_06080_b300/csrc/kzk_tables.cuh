@@ -22,6 +22,7 @@ struct TabArgs {
     void* E;
     void* P1;
     void* P2;
+    void* E_lo;      // float plans: E' - (float)E' (nullptr for double)
 };
 
 // phi-functions at z.  |z| < 1/2: Phi2 from its Taylor series
@@ -99,6 +100,21 @@ __global__ void tables_kernel(TabArgs a)
         oP2 = mk<T>((T)(P2.x * sP), (T)(P2.y * sP));
     }
     reinterpret_cast<cx<T>*>(a.E)[idx] = oE;
+    if (a.E_lo) {
+        // two-float E': the lo part carries the rounding error of the hi part
+        double ex, ey;
+        if (m == 0) {
+            double2 E0, P10, P20, EN, P1N, P2N;
+            const double2 z0 = z_of(a, 0.0, ky, false);
+            const double2 zN = z_of(a, a.kts * n, ky, true);
+            phi_eval(z0.x, z0.y, E0, P10, P20);
+            phi_eval(zN.x, zN.y, EN, P1N, P2N);
+            ex = E0.x * sE; ey = EN.x * sE;
+        } else {
+            ex = E.x * sE; ey = E.y * sE;
+        }
+        reinterpret_cast<cx<T>*>(a.E_lo)[idx] = mk<T>((T)(ex - (double)oE.x), (T)(ey - (double)oE.y));
+    }
     reinterpret_cast<cx<T>*>(a.P1)[idx] = oP1;
     reinterpret_cast<cx<T>*>(a.P2)[idx] = oP2;
 }

@@ -1,5 +1,4 @@
-// kzk_weno.cuh -- WENO5 flux derivative along tau (Sec. 3.3, Eq. 7) and its
-// transpose.
+// kzk_weno.cuh -- WENO5 flux derivative along tau (Sec. 3.3, Eq. 7).
 //
 // Flux of the homogeneous medium: f(u) = -B(sigma) u^2 / 2, split globally
 // (Lax-Friedrichs) into f+- = (f +- alpha u)/2 with alpha = B(sigma) * M.
@@ -7,10 +6,26 @@
 // from f+ at k-2..k+2, the downwind part F- the mirrored one from f- at
 // k+3..k-1; the nonlinear term is b_k = -(F_{k+1/2} - F_{k-1/2}) / dtau.
 // Jiang-Shu weights omega_r = a_r / sum a, a_r = d_r / (eps + beta_r)^2,
-// d = (1/10, 6/10, 3/10); the quotient is formed with one division by
-// multiplying numerator and denominator by the three (eps + beta)^2.
+// d = (1/10, 6/10, 3/10).
+//
+// Arithmetic organisation (same mathematics, fewer operations):
+//  * every smoothness indicator is a function of one 3-point stencil centred
+//    at c: with S = f_{c-1} - 2 f_c + f_{c+1}, D = f_{c+1} - f_{c-1},
+//      left   13/12 S^2 + 1/4 (D + 2S)^2   (beta_0 of the + side at c+1/2+1,
+//                                           beta_2 of the - side at c+1/2),
+//      centre 13/12 S^2 + 1/4 D^2          (beta_1),
+//      right  13/12 S^2 + 1/4 (D - 2S)^2   (beta_2 of the + side at c-1/2,
+//                                           beta_0 of the - side at c-3/2);
+//    each is computed once per centre and reused by the three interfaces
+//    that need it (a sliding window over the row);
+//  * the quotient sum a_r q_r / sum a_r is formed after multiplying numerator
+//    and denominator by prod (eps + beta_r)^2, so a_r -> d_r prod_{s != r} t_s;
+//  * the 1/6 of the candidate values q_r is folded into 1/dtau;
+//  * FP64: both halves F+ and F- share one division; FP32: two hardware
+//    reciprocals (the product of the two denominators could underflow).
 #pragma once
 #include "kzk_common.cuh"
+#include "kzk_fft.cuh"
 
 namespace kzk {
 
@@ -22,72 +37,121 @@ struct WenoCoef {
     T inv_dtau;  // 1 / dtau
 };
 
-// Reconstruction at one interface from v_{-2..2} (upwind side first).
-template <typename T>
-__device__ __forceinline__ T weno5_rec(T vm2, T vm1, T v0, T v1, T v2, T eps)
+template <typename T, bool PAD>
+__device__ __forceinline__ T ld_real(const cx<T>* buf, int k)
 {
-    const T s6 = T(1) / T(6);
-    const T q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0)) * s6;
-    const T q1 = fma(T(-1), vm1, fma(T(5), v0, T(2) * v1)) * s6;
-    const T q2 = fma(T(2), v0, fma(T(5), v1, -v2)) * s6;
-    const T c13 = T(13) / T(12);
-    T s, t;
-    s = vm2 - T(2) * vm1 + v0; t = vm2 - T(4) * vm1 + T(3) * v0;
-    T b0 = fma(c13 * s, s, T(0.25) * t * t);
-    s = vm1 - T(2) * v0 + v1; t = vm1 - v1;
-    T b1 = fma(c13 * s, s, T(0.25) * t * t);
-    s = v0 - T(2) * v1 + v2; t = T(3) * v0 - T(4) * v1 + v2;
-    T b2 = fma(c13 * s, s, T(0.25) * t * t);
-    T t0 = eps + b0; t0 *= t0;
-    T t1 = eps + b1; t1 *= t1;
-    T t2 = eps + b2; t2 *= t2;
-    const T a0 = T(0.1) * t1 * t2;
-    const T a1 = T(0.6) * t0 * t2;
-    const T a2 = T(0.3) * t0 * t1;
-    return fma(a0, q0, fma(a1, q1, a2 * q2)) / (a0 + a1 + a2);
+    const T* p = reinterpret_cast<const T*>(buf);
+    return PAD ? p[2 * padx(k >> 1) + (k & 1)] : p[k];
+}
+template <typename T, bool PAD>
+__device__ __forceinline__ void st_real(cx<T>* buf, int k, T v)
+{
+    T* p = reinterpret_cast<T*>(buf);
+    if (PAD) p[2 * padx(k >> 1) + (k & 1)] = v;
+    else p[k] = v;
+}
+
+// (eps + beta)^2 of the left, centre and right indicators of the stencil
+// (fm1, f0, fp1) centred at c.
+template <typename T>
+__device__ __forceinline__ void indicators(T fm1, T f0, T fp1, T eps, T& tl, T& tc, T& tr)
+{
+    const T S = fm1 - T(2) * f0 + fp1;
+    const T D = fp1 - fm1;
+    const T P = (T(13) / T(12)) * S * S;
+    const T xl = fma(T(2), S, D), xr = fma(T(-2), S, D);
+    const T bl = fma(T(0.25) * xl, xl, P);
+    const T bc = fma(T(0.25) * D, D, P);
+    const T br = fma(T(0.25) * xr, xr, P);
+    tl = (eps + bl) * (eps + bl);
+    tc = (eps + bc) * (eps + bc);
+    tr = (eps + br) * (eps + br);
+}
+
+// 6 * numerator and denominator of one reconstruction from v_{-2..2} and the
+// squared shifted indicators t0 (stencil -2..0), t1 (-1..1), t2 (0..2).
+template <typename T>
+__device__ __forceinline__ void rec_parts(T vm2, T vm1, T v0, T v1, T v2, T t0, T t1, T t2, T& num6, T& den)
+{
+    const T q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0));
+    const T q1 = fma(T(5), v0, fma(T(2), v1, -vm1));
+    const T q2 = fma(T(2), v0, fma(T(5), v1, -v2));
+    const T a0 = T(0.1) * (t1 * t2);
+    const T a1 = T(0.6) * (t0 * t2);
+    const T a2 = T(0.3) * (t0 * t1);
+    den = a0 + a1 + a2;
+    num6 = fma(a0, q0, fma(a1, q1, a2 * q2));
+}
+
+// 6 * F_{k+1/2} (both halves) from the window state.
+template <typename T>
+__device__ __forceinline__ T flux6(const T* fp, const T* fm, T tLp, T tCp, T tRp, T tLm, T tCm, T tRm)
+{
+    T np, dp, nm, dm;
+    rec_parts<T>(fp[0], fp[1], fp[2], fp[3], fp[4], tLp, tCp, tRp, np, dp);
+    rec_parts<T>(fm[5], fm[4], fm[3], fm[2], fm[1], tRm, tCm, tLm, nm, dm);
+    if constexpr (sizeof(T) == 8) {
+        return fma(np, dm, nm * dp) / (dp * dm);
+    } else {
+        return __fdividef(np, dp) + __fdividef(nm, dm);
+    }
 }
 
 // b over the points [k0, k0 + Q) of one periodic row u[0..nx) (shared
-// memory), written to out[k0 ..).  Also accumulates sum u, sum u^2, max|u|
-// and the non-finite count of the owned points.
-template <typename T>
-__device__ __forceinline__ void weno_row_chunk(const T* __restrict__ u, T* __restrict__ out, int nx,
-                                               int k0, int Q, const WenoCoef<T>& c, T& s1, T& s2,
-                                               T& mx, int& nf)
+// memory, PAD layout), written to out at the same points.  Also accumulates
+// sum u, sum u^2, max|u| and the non-finite count of the owned points.
+template <typename T, bool PAD>
+__device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int nx, int k0, int Q,
+                                               const WenoCoef<T>& c, T& s1, T& s2, T& mx, int& nf)
 {
     const int msk = nx - 1;
-    // window: slot s <-> point k - 2 + s for the interface k + 1/2
-    T fp[6], fm[6];
     const T half = T(0.5);
+    const T scale = -c.inv_dtau * (T(1) / T(6));
+    T fp[6], fm[6];
+    // window slot s <-> point k - 2 + s; start at k = k0 - 4 (three pre-roll
+    // iterations fill the indicator history before the first interface)
+    int k = k0 - 4;
 #pragma unroll
     for (int s = 0; s < 6; s++) {
-        const T v = u[(k0 - 3 + s) & msk];                   // interface k0 - 1/2: k = k0 - 1
+        const T v = ld_real<T, PAD>(u, (k - 2 + s) & msk);
         const T f = -half * c.B * v * v;
         fp[s] = half * fma(c.alpha, v, f);
         fm[s] = half * fma(-c.alpha, v, f);
     }
-    T Fprev = weno5_rec<T>(fp[0], fp[1], fp[2], fp[3], fp[4], c.eps) +
-              weno5_rec<T>(fm[5], fm[4], fm[3], fm[2], fm[1], c.eps);
-    for (int i = 0; i < Q; i++) {
-        const int k = k0 + i;
+    // history of the indicators (by age relative to the newest centre k+2)
+    T tLp1 = 0, tLp2 = 0, tLp3 = 0, tCp1 = 0, tCp2 = 0, tRp1 = 0, tLm1 = 0, tLm2 = 0, tCm1 = 0;
+    T Fprev = 0;
+#pragma unroll 1
+    for (; k < k0 + Q; k++) {
+        if (k > k0 - 4) {
+            // advance the window by one point: new point k + 3
 #pragma unroll
-        for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
-        const T v = u[(k + 3) & msk];
-        const T f = -half * c.B * v * v;
-        fp[5] = half * fma(c.alpha, v, f);
-        fm[5] = half * fma(-c.alpha, v, f);
-        const T F = weno5_rec<T>(fp[0], fp[1], fp[2], fp[3], fp[4], c.eps) +
-                    weno5_rec<T>(fm[5], fm[4], fm[3], fm[2], fm[1], c.eps);
-        out[k] = -(F - Fprev) * c.inv_dtau;
-        Fprev = F;
-        const T uk = u[k];
-        if (isfinite(uk)) {
-            s1 += uk;
-            s2 = fma(uk, uk, s2);
-            mx = fmax(mx, fabs(uk));
-        } else {
-            nf += 1;
+            for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
+            const int kn = k + 3;
+            const T v = ld_real<T, PAD>(u, kn & msk);
+            const T f = -half * c.B * v * v;
+            fp[5] = half * fma(c.alpha, v, f);
+            fm[5] = half * fma(-c.alpha, v, f);
+            if (kn >= k0 && kn < k0 + Q) {
+                if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf += 1; }
+            }
         }
+        // newest centre c = k + 2 (window slots 3, 4, 5)
+        T tLpN, tCpN, tRpN, tLmN, tCmN, tRmN;
+        indicators<T>(fp[3], fp[4], fp[5], c.eps, tLpN, tCpN, tRpN);
+        indicators<T>(fm[3], fm[4], fm[5], c.eps, tLmN, tCmN, tRmN);
+        if (k >= k0 - 1) {
+            // interface k+1/2: + side uses left(k-1), centre(k), right(k+1);
+            // - side uses right(k+2), centre(k+1), left(k)
+            const T F = flux6<T>(fp, fm, tLp3, tCp2, tRp1, tLm2, tCm1, tRmN);
+            if (k >= k0) st_real<T, PAD>(out, k, (F - Fprev) * scale);
+            Fprev = F;
+        }
+        tLp3 = tLp2; tLp2 = tLp1; tLp1 = tLpN;
+        tCp2 = tCp1; tCp1 = tCpN;
+        tRp1 = tRpN;
+        tLm2 = tLm1; tLm1 = tLmN;
+        tCm1 = tCmN;
     }
 }
 

@@ -55,8 +55,7 @@ def test_tables_match_oracle(prec):
     w = inputs.config(1, nx=64, ny=32)
     plan = api.Plan.from_workload(w, precision=prec)
     E, P1, P2 = plan.tables()
-    eps = 2.0 ** -53 if prec == "fp64" else 2.0 ** -24
-    p = oracle.Params(**inputs.oracle_params(w, reg_eps=eps))
+    p = oracle.Params(**inputs.oracle_params(w))
     oE, oP1, oP2 = oracle.tables(p)
     nl, nm = w.ny // 2 + 1, w.nx // 2 + 1
     tol = 1e-13 if prec == "fp64" else 2e-7
