@@ -190,7 +190,7 @@ kzk_status kzk_alu_peak(int32_t prec, void *stream, double *flops_per_s);
  * u, b (device, [batch][ny][nx], plan precision, b not aliasing u) are the
  * caller's input and output; b = b(sigma, u) exactly as kzk_rhs computes it.
  * The intermediates live in one file-scope device array of
- * 2 * 8 * KZK_NOALLOC_MAX_POINTS + 16 * 8192 bytes (about 4.1 MB) that every
+ * 2 * 8 * KZK_NOALLOC_MAX_POINTS + 16 * 12288 bytes (about 4.2 MB) that every
  * GPU loading the library keeps until the process exits.  The first call on a
  * device looks up that array's device address (and lifts the kernels' shared-
  * memory limit) for the current device; make that first call before any

@@ -70,7 +70,9 @@ struct kzk_plan_s {
     void *E, *P1, *P2;          // folded, scaled tables [(ny/2+1)][nx/2]
     void* E_lo;                 // FP32 plans: lo part of E' (two-float E')
     void *twr, *twc;            // twiddles, exp(-2 pi i k / nx), exp(-2 pi i k / ny)
-    void* twc_lo;               // FP32 plans: lo part of the y twiddles
+    void* twc_lo;               // FP32 plans: lo part of the staged y twiddles
+    void* tws_row;              // staged twiddles of the row (length nx/2) FFT
+    void* twc_full;             // full y twiddle table exp(-2 pi i k / ny) (adjoint kernels)
     double* diag_rows;          // [batch][ny][4]
     double* diag_hist;          // [hist_cap][batch][4]
     double* diag_final;         // [batch][4]
@@ -93,7 +95,7 @@ double dA_of(const kzk_plan* p, double s)
     return p->c.has_profile ? p->c.A * horner(p->c.A_prof, s) - p->c.A : 0.0;
 }
 
-template <typename T> constexpr int row_ppt() { return sizeof(T) == 4 ? 16 : 8; }
+template <typename T> constexpr int row_ppt() { return 8; }
 template <typename T> size_t adj_row_smem(const kzk_plan* p) { return adj_row_smem_bytes<T>(p->n, p->adj_row_thr); }
 
 template <typename T, int MODE>
@@ -134,7 +136,7 @@ kzk_status configure(kzk_plan* p)
     p->adj_row_thr = std::max(32, p->n / row_ppt<T>());
     p->log2tc = col_log2tc<T>(p->nx, p->ny);
     p->col_thr = col_threads<T>(p->ny, p->log2tc);
-    if (p->col_thr > col_max_threads<T>() || 2 * ((size_t)p->ny << p->log2tc) * sizeof(cx<T>) > 128 * 1024)
+    if (p->col_thr > col_max_threads<T>())
         return fail(KZK_ERR_SIZE, "ny = %d too large for a shared-memory column tile", p->ny);
     p->col_smem = col_smem_bytes<T>(p->ny, p->log2tc);
     // Every kernel may use up to the device's opt-in maximum; the launch's own
@@ -179,6 +181,41 @@ std::vector<cx<T>> twiddles(int N, std::vector<cx<T>>* lo = nullptr)
     return w;
 }
 
+// staged twiddles of fft_batched for length 2^log2n with ppt points per
+// thread (see Tw in kzk_fft.cuh), evaluated in long double; lo parts too when
+// lo != nullptr
+template <typename T>
+std::vector<cx<T>> staged_twiddles(int log2n, int ppt, std::vector<cx<T>>* lo = nullptr)
+{
+    int lr[32], lns[32];
+    const int P = fft_schedule(log2n, ppt, lr, lns);
+    std::vector<cx<T>> w;
+    if (lo) lo->clear();
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int pidx = 0; pidx < P; pidx++) {
+        if (lns[pidx] == 0) continue;
+        const long long Ns = 1LL << lns[pidx], R = 1LL << lr[pidx];
+        for (long long r = 1; r < R; r++)
+            for (long long k = 0; k < Ns; k++) {
+                const long long num = r * k, den = Ns * R;
+                long double c, sn;
+                if (4 * num == den) { c = 0; sn = -1; }
+                else if (2 * num == den) { c = -1; sn = 0; }
+                else if (4 * num == 3 * den) { c = 0; sn = 1; }
+                else {
+                    const long double a = two_pi * (long double)num / (long double)den;
+                    c = cosl(a); sn = -sinl(a);
+                }
+                const cx<T> h = mk<T>((T)(double)c, (T)(double)sn);
+                w.push_back(h);
+                if (lo) lo->push_back(mk<T>((T)(double)(c - (long double)h.x), (T)(double)(sn - (long double)h.y)));
+            }
+    }
+    if (w.empty()) w.push_back(mk<T>((T)1, (T)0));
+    if (lo && lo->empty()) lo->push_back(mk<T>((T)0, (T)0));
+    return w;
+}
+
 template <typename T>
 RowArgs<T> row_args(const kzk_plan* p, const void* in, void* out, double sigma, double* diag_rows)
 {
@@ -186,6 +223,7 @@ RowArgs<T> row_args(const kzk_plan* p, const void* in, void* out, double sigma, 
     a.in = (const cx<T>*)in;
     a.out = (cx<T>*)out;
     a.tw = (const cx<T>*)p->twr;
+    a.tws = (const cx<T>*)p->tws_row;
     a.diag_rows = diag_rows;
     a.log2nx = p->log2nx;
     a.ny = p->ny;
@@ -361,10 +399,16 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
     tables_kernel<T><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a);
     KZK_LAUNCHED();
     auto tr = twiddles<T>(p->nx);
+    auto tcf = twiddles<T>(p->ny);
+    auto trs = staged_twiddles<T>(p->log2nx - 1, row_ppt_of<T>());
     std::vector<cx<T>> tcl;
-    auto tc = twiddles<T>(p->ny, &tcl);
+    auto tcs = staged_twiddles<T>(p->log2ny, col_ppt_of<T>(), &tcl);
+    if ((long long)trs.size() > p->n || (long long)tcs.size() > p->ny)
+        return fail(KZK_ERR_SIZE, "staged twiddle table larger than its transform");
     KZK_CUDA(cudaMemcpy(p->twr, tr.data(), tr.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
-    KZK_CUDA(cudaMemcpy(p->twc, tc.data(), tc.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    KZK_CUDA(cudaMemcpy(p->twc_full, tcf.data(), tcf.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    KZK_CUDA(cudaMemcpy(p->tws_row, trs.data(), trs.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    KZK_CUDA(cudaMemcpy(p->twc, tcs.data(), tcs.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
     if (p->twc_lo)
         KZK_CUDA(cudaMemcpy(p->twc_lo, tcl.data(), tcl.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
     KZK_CUDA(cudaStreamSynchronize(st));
@@ -375,6 +419,7 @@ void plan_free(kzk_plan* p)
 {
     if (!p) return;
     void* ptrs[] = {p->V, p->b1, p->vs, p->b2, p->E, p->P1, p->P2, p->E_lo, p->twr, p->twc, p->twc_lo,
+                    p->tws_row, p->twc_full,
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
                     p->seg, p->ckpt};
     for (void* q : ptrs)
@@ -427,7 +472,7 @@ AdjColArgs<T> adj_col_args(const kzk_plan* p)
 {
     AdjColArgs<T> a;
     memset(&a, 0, sizeof(a));
-    a.tw = (const cx<T>*)p->twc;
+    a.tw = (const cx<T>*)p->twc_full;
     a.log2ny = p->log2ny;
     a.log2n = p->log2nx - 1;
     a.log2tc = p->log2tc;
@@ -732,6 +777,8 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     if (e == cudaSuccess && p->prec == KZK_FP32) e = cudaMalloc(&p->E_lo, tab);
     if (e == cudaSuccess && p->prec == KZK_FP32) e = cudaMalloc(&p->twc_lo, (size_t)p->ny * p->csz);
     if (e == cudaSuccess) e = cudaMalloc(&p->twr, (size_t)p->nx * p->csz);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tws_row, (size_t)p->n * p->csz);
+    if (e == cudaSuccess) e = cudaMalloc(&p->twc_full, (size_t)p->ny * p->csz);
     if (e == cudaSuccess) e = cudaMalloc(&p->twc, (size_t)p->ny * p->csz);
     if (e == cudaSuccess) e = cudaMalloc(&p->diag_rows, (size_t)batch * p->ny * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->diag_final, (size_t)batch * 4 * sizeof(double));

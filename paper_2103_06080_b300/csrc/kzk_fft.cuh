@@ -115,7 +115,11 @@ template <typename T, int R, int S, bool ACC> struct RegDFT {
 };
 
 // Twiddle tables: hi part and, for ACC, the lo correction (lo == nullptr
-// otherwise).
+// otherwise).  log2 >= 0: one table exp(-2 pi i k / 2^log2) indexed
+// (r k) << shift.  log2 < 0: a per-pass ("staged") table for this transform
+// length and radix schedule: pass p with Ns_p, R_p occupies
+// (R_p - 1) * Ns_p entries, entry (r - 1) * Ns_p + k = exp(-2 pi i r k / (Ns_p R_p)),
+// so the lanes of a warp (consecutive k) read consecutive entries.
 template <typename T>
 struct Tw {
     const cx<T>* __restrict__ hi;
@@ -129,7 +133,7 @@ struct Tw {
 // consecutive threads take consecutive butterflies of one transform.
 template <typename T, int R, int PPT, bool COLS, bool INV, bool PAD, bool ACC>
 __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int si, int sb, int log2Ns,
-                                         const Tw<T>& tw, int tid, int nthr)
+                                         const Tw<T>& tw, int stage_off, int tid, int nthr)
 {
     constexpr int NB = PPT / R;
     constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
@@ -151,12 +155,19 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
             const int k = j & (Ns - 1);
             const int ib = b * sb + j * si;
             const int stride = (1 << log2nbf) * si;
+            if (!PAD || (stride & 15) == 0) {
+                // padded index of ib + r * stride is padx(ib) + r * padded stride
+                const int pb = sidx<PAD>(ib), ps = PAD ? stride + (stride >> 4) : stride;
 #pragma unroll
-            for (int r = 0; r < R; r++) v[q][r] = buf[sidx<PAD>(ib + r * stride)];
+                for (int r = 0; r < R; r++) v[q][r] = buf[pb + r * ps];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; r++) v[q][r] = buf[sidx<PAD>(ib + r * stride)];
+            }
             if (log2Ns > 0) {
 #pragma unroll
                 for (int r = 1; r < R; r++) {
-                    const int ti = (r * k) << twsh;
+                    const int ti = tw.log2 >= 0 ? (r * k) << twsh : stage_off + (r - 1) * Ns + k;
                     const cx<T> w = tw.hi[ti];
                     if constexpr (ACC && sizeof(T) == 4) {
                         const cx<T> wl = tw.lo[ti];
@@ -172,11 +183,18 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
         }
     }
     __syncthreads();
+    const int ostride = Ns * si;
 #pragma unroll
     for (int q = 0; q < NB; q++) {
         if (obase[q] >= 0) {
+            if (!PAD || (ostride & 15) == 0) {
+                const int pb = sidx<PAD>(obase[q]), ps = PAD ? ostride + (ostride >> 4) : ostride;
 #pragma unroll
-            for (int r = 0; r < R; r++) buf[sidx<PAD>(obase[q] + r * Ns * si)] = v[q][r];
+                for (int r = 0; r < R; r++) buf[pb + r * ps] = v[q][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; r++) buf[sidx<PAD>(obase[q] + r * ostride)] = v[q][r];
+            }
         }
     }
     __syncthreads();
@@ -188,23 +206,46 @@ template <typename T, int PPT, bool COLS, bool INV, bool PAD = false, bool ACC =
 __device__ __forceinline__ void fft_batched(cx<T>* buf, int log2n, int log2nb, int si, int sb, const Tw<T>& tw,
                                             int tid, int nthr)
 {
-    int done = 0;
+    int done = 0, off = 0;
     while (done < log2n) {
         const int rem = log2n - done;
         if (PPT >= 16 && rem >= 4) {
-            fft_pass<T, (PPT >= 16 ? 16 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, tid, nthr);
+            fft_pass<T, (PPT >= 16 ? 16 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, off, tid, nthr);
+            off += (done > 0 ? ((PPT >= 16 ? 16 : 2) - 1) << done : 0);
             done += (PPT >= 16 ? 4 : 1);
         } else if (PPT >= 8 && rem >= 3) {
-            fft_pass<T, (PPT >= 8 ? 8 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, tid, nthr);
+            fft_pass<T, (PPT >= 8 ? 8 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, off, tid, nthr);
+            off += (done > 0 ? ((PPT >= 8 ? 8 : 2) - 1) << done : 0);
             done += (PPT >= 8 ? 3 : 1);
         } else if (PPT >= 4 && rem >= 2) {
-            fft_pass<T, (PPT >= 4 ? 4 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, tid, nthr);
+            fft_pass<T, (PPT >= 4 ? 4 : 2), PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, off, tid, nthr);
+            off += (done > 0 ? ((PPT >= 4 ? 4 : 2) - 1) << done : 0);
             done += (PPT >= 4 ? 2 : 1);
         } else {
-            fft_pass<T, 2, PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, tid, nthr);
+            fft_pass<T, 2, PPT, COLS, INV, PAD, ACC>(buf, log2n, log2nb, si, sb, done, tw, off, tid, nthr);
+            off += (done > 0 ? 1 << done : 0);
             done += 1;
         }
     }
+}
+
+// Radix schedule of fft_batched for a length 2^log2n with PPT points
+// per thread, as (log2 R, log2 Ns) pairs.
+__host__ __device__ inline int fft_schedule(int log2n, int ppt, int* lr, int* lns)
+{
+    int done = 0, p = 0;
+    while (done < log2n) {
+        const int rem = log2n - done;
+        int l = 1;
+        if (ppt >= 16 && rem >= 4) l = 4;
+        else if (ppt >= 8 && rem >= 3) l = 3;
+        else if (ppt >= 4 && rem >= 2) l = 2;
+        lr[p] = l;
+        lns[p] = done;
+        done += l;
+        p++;
+    }
+    return p;
 }
 
 // Older call form (no padding, single-precision constants).

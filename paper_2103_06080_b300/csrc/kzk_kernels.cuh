@@ -30,7 +30,8 @@ template <typename T>
 struct RowArgs {
     const cx<T>* in;        // ROW_RHS / ROW_INV: spectral rows; ROW_FWD: physical rows (as T)
     cx<T>* out;             // ROW_RHS / ROW_FWD: spectral rows; ROW_INV: physical rows (as T)
-    const cx<T>* tw;        // exp(-2 pi i k / nx), k in [0, nx)
+    const cx<T>* tw;        // exp(-2 pi i k / nx), k in [0, nx) (real-FFT pre/post-processing)
+    const cx<T>* tws;       // staged twiddles of the length-nx/2 complex FFT
     double* diag_rows;      // [batch][ny][4] or nullptr
     int log2nx;
     int ny;
@@ -65,6 +66,34 @@ __device__ __forceinline__ void block_diag(double* red, double s1, double s2, do
     }
     if (tid == 0) { dst[0] = r0[0]; dst[1] = r1[0]; dst[2] = r2[0]; dst[3] = r3[0]; }
     __syncthreads();
+}
+
+// Block reduction of one row's statistics: within each warp in the working
+// precision (shuffles, fixed order), across warps in FP64 by thread 0 (fixed
+// order); red holds one double4 per warp.  Deterministic.
+template <typename T>
+__device__ __forceinline__ void block_diag_t(double* red, T s1, T s2, T mx, int nf, double* dst)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    }
+    if (lane == 0) {
+        red[4 * warp] = (double)s1; red[4 * warp + 1] = (double)s2;
+        red[4 * warp + 2] = (double)mx; red[4 * warp + 3] = (double)nf;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0, b = 0, c = 0, d = 0;
+        for (int w = 0; w < nw; w++) {
+            a += red[4 * w]; b += red[4 * w + 1]; c = fmax(c, red[4 * w + 2]); d += red[4 * w + 3];
+        }
+        dst[0] = a; dst[1] = b; dst[2] = c; dst[3] = d;
+    }
 }
 
 // C2R pre-processing in place: packed half spectrum X (n = nx/2 slots) ->
@@ -135,7 +164,7 @@ constexpr int ROW_MAX_THREADS = 512; // n / 8 for nx = 8192
 // Shared memory: two padded buffers of n complex (= nx reals) each, plus a
 // reduction area of 4 doubles per thread.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(ROW_MAX_THREADS) row_kernel(RowArgs<T> a)
+__global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_kernel(RowArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -145,7 +174,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS) row_kernel(RowArgs<T> a)
     cx<T>* Y = X + row_buf_len(n);                         // buffer B
     double* red = reinterpret_cast<double*>(Y + row_buf_len(n));
     const long long base = (long long)inst * a.inst_stride + (long long)row * n;
-    const Tw<T> tw{a.tw, nullptr, a.log2nx};
+    const Tw<T> tw{a.tws, nullptr, -1};
     constexpr int ROW_PPT = row_ppt_of<T>();
 
     if constexpr (MODE == ROW_FWD) {
@@ -177,13 +206,15 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS) row_kernel(RowArgs<T> a)
                 dst[i] = v;
                 if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf++; }
             }
-            if (a.diag_rows) block_diag(red, (double)s1, (double)s2, (double)mx, (double)nf,
-                                        a.diag_rows + ((long long)inst * a.ny + row) * 4);
+            if (a.diag_rows) block_diag_t<T>(red, s1, s2, mx, nf, a.diag_rows + ((long long)inst * a.ny + row) * 4);
         } else {
             // ROW_RHS: WENO5 flux derivative into Y, then tau-R2C of Y
             const int Q = nx >= nthr ? nx / nthr : 1;
             const int k0 = tid * Q;
-            if (k0 < nx) weno_row_chunk<T, true>(X, Y, nx, k0, Q, a.wc, s1, s2, mx, nf);
+            if (k0 < nx) {
+                weno_row_chunk<T, true>(X, Y, nx, k0, Q, a.wc);
+                if (a.diag_rows) row_stats<T, true>(X, k0, Q, s1, s2, mx, nf);
+            }
             __syncthreads();
             fft_batched<T, ROW_PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
             const cx<T>* vin = a.in + base;
@@ -211,8 +242,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS) row_kernel(RowArgs<T> a)
                 a.out[base + k] = xk;
                 if (k != 0 && 2 * k != n) a.out[base + n - k] = xnk;
             }
-            if (a.diag_rows) block_diag(red, (double)s1, (double)s2, (double)mx, (double)nf,
-                                        a.diag_rows + ((long long)inst * a.ny + row) * 4);
+            if (a.diag_rows) block_diag_t<T>(red, s1, s2, mx, nf, a.diag_rows + ((long long)inst * a.ny + row) * 4);
         }
     }
 }
@@ -240,7 +270,7 @@ struct ColArgs {
     const cx<T>* Ta;        // STAGE1: E';   STAGE2: P2'
     const cx<T>* Ta_lo;     // STAGE1, FP32: lo part of E' (hi + lo = FP64 value)
     const cx<T>* Tb;        // STAGE1: P1';  STAGE2: -
-    const cx<T>* tw;        // exp(-2 pi i k / ny), k in [0, ny)
+    const cx<T>* tw;        // staged twiddles of the length-ny FFT
     const cx<T>* tw_lo;     // FP32: lo parts of tw
     int log2ny, log2n, log2tc;
     long long inst_stride;
@@ -264,7 +294,22 @@ __device__ __forceinline__ cx<T> mult_entry(cx<T> M, cx<T> z, cx<T> zm, bool pac
 }
 
 template <typename T> __host__ __device__ constexpr int col_ppt_of() { return 8; }
-template <typename T> __host__ __device__ constexpr int col_max_threads() { return sizeof(T) == 4 ? 1024 : 512; }
+template <typename T> __host__ __device__ constexpr int col_max_threads() { return 512; }
+// shared memory for the two tiles of stage 1: small enough that two CTAs
+// (plus their twiddle copies) share an SM, so one CTA's loads overlap the
+// other's transforms
+constexpr size_t COL_TILE_BYTES = 64 * 1024;
+
+// bytes of the tile area (or of the diagnostics reduction area, if larger)
+template <typename T>
+__host__ __device__ __forceinline__ size_t col_tile_area(int ny, int log2tc, int nthr)
+{
+    const size_t e = (size_t)ny << log2tc;
+    const size_t tiles = 2 * (e + (e >> 4)) * sizeof(cx<T>);
+    const size_t red = 4 * (size_t)nthr * sizeof(double);
+    return tiles > red ? tiles : red;
+}
+
 constexpr int COL_MAX_THREADS = 1024;
 
 // Column kernel.  One CTA per (tile of TC columns, instance).
@@ -285,12 +330,23 @@ __global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
     const int total = ny << a.log2tc;                   // elements of one tile
     constexpr bool ACC = sizeof(T) == 4;
     constexpr int COL_PPT = col_ppt_of<T>();
-    const Tw<T> twp{a.tw, nullptr, a.log2ny};
-    const Tw<T> twa{a.tw, a.tw_lo, a.log2ny};
+    // y twiddles in shared memory after the tile area
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + col_tile_area<T>(ny, a.log2tc, nthr));
+    cx<T>* twl = tws + ny;
+    for (int i = tid; i < ny; i += nthr) {
+        tws[i] = a.tw[i];
+        if constexpr (ACC) twl[i] = a.tw_lo[i];
+    }
+    const Tw<T> twp{tws, nullptr, -1};
+    const Tw<T> twa{tws, twl, -1};
 
     auto gidx = [&](int e) -> long long {
         return ibase + (long long)(e >> a.log2tc) * n + m0 + (e & (TC - 1));
     };
+    // tile element e = l * TC + c lives at padx(e) of its region (one padding
+    // slot per 16 elements: conflict-free strided Stockham stores)
+    cx<T>* SA = S;                                  // state / b2 - b1 tile
+    cx<T>* SB = S + (total + (total >> 4));         // b1 tile (stage 1)
 
     if constexpr (MODE == COL_STAGE1) {
         // diagnostics of the state this step started from (rows written by R)
@@ -311,36 +367,34 @@ __global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
                 d[3] = tmp[3];
             }
         }
-        const int W = 2 * TC;                              // row pitch of the two tiles
         for (int e = tid; e < total; e += nthr) {
             const long long g = gidx(e);
-            const int l = e >> a.log2tc, c = e & (TC - 1);
-            S[l * W + c] = a.a[g];
-            S[l * W + TC + c] = a.b[g];
+            SA[padx(e)] = a.a[g];
+            SB[padx(e)] = a.b[g];
         }
         __syncthreads();
         // state tile: accurate transform; b1 tile: plain
-        fft_batched<T, COL_PPT, true, false, false, ACC>(S, a.log2ny, a.log2tc, W, 1, twa, tid, nthr);
-        fft_batched<T, COL_PPT, true, false, false, false>(S + TC, a.log2ny, a.log2tc, W, 1, twp, tid, nthr);
-        // V*_hat = E' V_hat + P1' b1_hat, in place in the state half.  Every
+        fft_batched<T, COL_PPT, true, false, true, ACC>(SA, a.log2ny, a.log2tc, TC, 1, twa, tid, nthr);
+        fft_batched<T, COL_PPT, true, false, true, false>(SB, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
+        // V*_hat = E' V_hat + P1' b1_hat, in place in the state tile.  Every
         // element is combined by its owner; the packed column 0 (first tile
         // only) couples rows l and ny - l, so one thread owns each such pair.
-        const bool has_packed = (m0 == 0);
         for (int e = tid; e < total; e += nthr) {
             const int l = e >> a.log2tc, c = e & (TC - 1), m = m0 + c;
             if (m == 0) continue;
             const int lf = l <= (ny >> 1) ? l : ny - l;
             const long long ti = (long long)lf * n + m;
-            const cx<T> zv = S[l * W + c], zb = S[l * W + TC + c];
+            const cx<T> zv = SA[padx(e)], zb = SB[padx(e)];
             cx<T> r = mul<T>(a.Ta[ti], zv);
             if constexpr (ACC) r = fma_c<T>(a.Ta_lo[ti], zv, r);
-            S[l * W + c] = fma_c<T>(a.Tb[ti], zb, r);
+            SA[padx(e)] = fma_c<T>(a.Tb[ti], zb, r);
         }
-        if (has_packed) {
+        if (m0 == 0) {
             for (int l = tid; l <= (ny >> 1); l += nthr) {
                 const int lm = (ny - l) & (ny - 1);
                 const long long ti = (long long)l * n;        // l <= ny/2: folded row l
-                const cx<T> zv = S[l * W], zvm = S[lm * W], zb = S[l * W + TC], zbm = S[lm * W + TC];
+                const int e = padx(l << a.log2tc), em = padx(lm << a.log2tc);
+                const cx<T> zv = SA[e], zvm = SA[em], zb = SB[e], zbm = SB[em];
                 cx<T> r = mult_entry<T>(a.Ta[ti], zv, zvm, true);
                 cx<T> rm = mult_entry<T>(a.Ta[ti], zvm, zv, true);
                 if constexpr (ACC) {
@@ -349,40 +403,41 @@ __global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
                 }
                 r = add<T>(r, mult_entry<T>(a.Tb[ti], zb, zbm, true));
                 rm = add<T>(rm, mult_entry<T>(a.Tb[ti], zbm, zb, true));
-                S[l * W] = r;
-                if (lm != l) S[lm * W] = rm;
+                SA[e] = r;
+                if (lm != l) SA[em] = rm;
             }
         }
         __syncthreads();
-        fft_batched<T, COL_PPT, true, true, false, ACC>(S, a.log2ny, a.log2tc, W, 1, twa, tid, nthr);
-        for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = S[(e >> a.log2tc) * W + (e & (TC - 1))];
+        fft_batched<T, COL_PPT, true, true, true, ACC>(SA, a.log2ny, a.log2tc, TC, 1, twa, tid, nthr);
+        for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = SA[padx(e)];
     } else {
         for (int e = tid; e < total; e += nthr) {
             const long long g = gidx(e);
-            S[e] = sub<T>(a.b[g], a.a[g]);
+            SA[padx(e)] = sub<T>(a.b[g], a.a[g]);
         }
         __syncthreads();
-        fft_batched<T, COL_PPT, true, false, false, false>(S, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
+        fft_batched<T, COL_PPT, true, false, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
         for (int e = tid; e < total; e += nthr) {
             const int l = e >> a.log2tc, c = e & (TC - 1), m = m0 + c;
             if (m == 0) continue;
             const int lf = l <= (ny >> 1) ? l : ny - l;
-            S[e] = mul<T>(a.Ta[(long long)lf * n + m], S[e]);
+            SA[padx(e)] = mul<T>(a.Ta[(long long)lf * n + m], SA[padx(e)]);
         }
         if (m0 == 0) {
             for (int l = tid; l <= (ny >> 1); l += nthr) {
                 const int lm = (ny - l) & (ny - 1);
                 const cx<T> M = a.Ta[(long long)l * n];
-                const cx<T> z = S[l << a.log2tc], zm = S[lm << a.log2tc];
-                S[l << a.log2tc] = mult_entry<T>(M, z, zm, true);
-                if (lm != l) S[lm << a.log2tc] = mult_entry<T>(M, zm, z, true);
+                const int e = padx(l << a.log2tc), em = padx(lm << a.log2tc);
+                const cx<T> z = SA[e], zm = SA[em];
+                SA[e] = mult_entry<T>(M, z, zm, true);
+                if (lm != l) SA[em] = mult_entry<T>(M, zm, z, true);
             }
         }
         __syncthreads();
-        fft_batched<T, COL_PPT, true, true, false, false>(S, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
+        fft_batched<T, COL_PPT, true, true, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
         for (int e = tid; e < total; e += nthr) {
             const long long g = gidx(e);
-            a.out[g] = add<T>(a.c[g], S[e]);
+            a.out[g] = add<T>(a.c[g], SA[padx(e)]);
         }
     }
 }
@@ -393,7 +448,7 @@ template <typename T>
 __host__ __forceinline__ int col_log2tc(int nx, int ny)
 {
     int tc = std::min(16, nx / 2);
-    while (tc > 1 && (2 * (size_t)ny * tc * sizeof(cx<T>) > 128 * 1024 ||
+    while (tc > 1 && (2 * (size_t)ny * tc * sizeof(cx<T>) > COL_TILE_BYTES ||
                       (long long)ny * tc / col_ppt_of<T>() > col_max_threads<T>()))
         tc >>= 1;
     int l = 0;
@@ -406,12 +461,12 @@ __host__ __forceinline__ int col_threads(int ny, int log2tc)
     const long long t = ((long long)ny << log2tc) / col_ppt_of<T>();
     return t > 32 ? (int)t : 32;
 }
+// tiles (or the diagnostics reduction area, if larger), then the y twiddles
+// (hi, and lo for FP32) copied to shared memory
 template <typename T>
 __host__ __forceinline__ size_t col_smem_bytes(int ny, int log2tc)
 {
-    const size_t tiles = 2 * ((size_t)ny << log2tc) * sizeof(cx<T>);
-    const size_t red = 4 * (size_t)col_threads<T>(ny, log2tc) * sizeof(double);
-    return tiles > red ? tiles : red;
+    return col_tile_area<T>(ny, log2tc, col_threads<T>(ny, log2tc)) + (sizeof(T) == 4 ? 2 : 1) * (size_t)ny * sizeof(cx<T>);
 }
 
 // Final diagnostics of each instance from its per-row partials.

@@ -31,7 +31,7 @@ constexpr int kMaxNx = 8192;
 // two packed spectral arrays of kMaxPoints FP64 points (8 bytes per point
 // each) and one FP64 twiddle table of kMaxNx entries
 constexpr size_t kSpecBytes = (size_t)kMaxPoints * 8;
-constexpr size_t kScratchBytes = 2 * kSpecBytes + (size_t)kMaxNx * 16;
+constexpr size_t kScratchBytes = 2 * kSpecBytes + (size_t)kMaxNx * 16 + (size_t)(kMaxNx / 2) * 16;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -51,6 +51,28 @@ __global__ void noalloc_twiddles(cx<T>* tw, int nx)
     tw[k] = mk<T>((T)c, (T)(-s));
 }
 
+// staged twiddles of the row FFT (length 2^log2n, ppt points per thread),
+// one thread per table entry
+template <typename T>
+__global__ void noalloc_staged_twiddles(cx<T>* tws, int log2n, int ppt)
+{
+    int lr[32], lns[32];
+    const int P = fft_schedule(log2n, ppt, lr, lns);
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int p = 0; p < P; p++) {
+        if (lns[p] == 0) continue;
+        const int Ns = 1 << lns[p], R = 1 << lr[p], cnt = (R - 1) * Ns;
+        if (e < cnt) {
+            const int r = 1 + e / Ns, k = e % Ns;
+            double s, c;
+            sincospi(2.0 * (double)(r * k) / (double)(Ns * R), &s, &c);
+            tws[blockIdx.x * blockDim.x + threadIdx.x] = mk<T>((T)c, (T)(-s));
+            return;
+        }
+        e -= cnt;
+    }
+}
+
 double horner4(const double* c, double s) { return ((c[3] * s + c[2]) * s + c[1]) * s + c[0]; }
 
 template <typename T>
@@ -63,6 +85,7 @@ kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch,
     cx<T>* V = (cx<T>*)base;
     cx<T>* Bh = (cx<T>*)(base + kSpecBytes);
     cx<T>* tw = (cx<T>*)(base + 2 * kSpecBytes);
+    cx<T>* tws = (cx<T>*)(base + 2 * kSpecBytes + (size_t)kMaxNx * 16);
     const int thr = row_threads<T>(nx);
     const size_t smem = row_smem_bytes<T>(nx);
     {
@@ -84,9 +107,11 @@ kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch,
         }
     }
     noalloc_twiddles<T><<<(nx + 255) / 256, 256, 0, st>>>(tw, nx);
+    noalloc_staged_twiddles<T><<<(n + 255) / 256, 256, 0, st>>>(tws, log2nx - 1, row_ppt_of<T>());
 
     RowArgs<T> a;
     a.tw = tw;
+    a.tws = tws;
     a.diag_rows = nullptr;
     a.log2nx = log2nx;
     a.ny = ny;

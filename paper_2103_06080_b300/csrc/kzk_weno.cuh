@@ -98,60 +98,75 @@ __device__ __forceinline__ T flux6(const T* fp, const T* fm, T tLp, T tCp, T tRp
 }
 
 // b over the points [k0, k0 + Q) of one periodic row u[0..nx) (shared
-// memory, PAD layout), written to out at the same points.  Also accumulates
-// sum u, sum u^2, max|u| and the non-finite count of the owned points.
+// memory, PAD layout), written to out at the same points.
 template <typename T, bool PAD>
 __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int nx, int k0, int Q,
-                                               const WenoCoef<T>& c, T& s1, T& s2, T& mx, int& nf)
+                                               const WenoCoef<T>& c)
 {
     const int msk = nx - 1;
     const T half = T(0.5);
     const T scale = -c.inv_dtau * (T(1) / T(6));
     T fp[6], fm[6];
-    // window slot s <-> point k - 2 + s; start at k = k0 - 4 (three pre-roll
-    // iterations fill the indicator history before the first interface)
-    int k = k0 - 4;
-#pragma unroll
-    for (int s = 0; s < 6; s++) {
-        const T v = ld_real<T, PAD>(u, (k - 2 + s) & msk);
+    auto load = [&](int kk, T& p, T& m) {
+        const T v = ld_real<T, PAD>(u, kk & msk);
         const T f = -half * c.B * v * v;
-        fp[s] = half * fma(c.alpha, v, f);
-        fm[s] = half * fma(-c.alpha, v, f);
-    }
-    // history of the indicators (by age relative to the newest centre k+2)
-    T tLp1 = 0, tLp2 = 0, tLp3 = 0, tCp1 = 0, tCp2 = 0, tRp1 = 0, tLm1 = 0, tLm2 = 0, tCm1 = 0;
-    T Fprev = 0;
-#pragma unroll 1
-    for (; k < k0 + Q; k++) {
-        if (k > k0 - 4) {
-            // advance the window by one point: new point k + 3
+        p = half * fma(c.alpha, v, f);
+        m = half * fma(-c.alpha, v, f);
+    };
+    // window slot s <-> point k - 2 + s for interface k + 1/2; start at
+    // k = k0 - 1 with the indicators of centres k0 - 2 .. k0 + 0 (pre-roll)
+    int k = k0 - 1;
 #pragma unroll
-            for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
-            const int kn = k + 3;
-            const T v = ld_real<T, PAD>(u, kn & msk);
-            const T f = -half * c.B * v * v;
-            fp[5] = half * fma(c.alpha, v, f);
-            fm[5] = half * fma(-c.alpha, v, f);
-            if (kn >= k0 && kn < k0 + Q) {
-                if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf += 1; }
-            }
-        }
-        // newest centre c = k + 2 (window slots 3, 4, 5)
+    for (int s = 0; s < 5; s++) load(k - 3 + s, fp[s + 1], fm[s + 1]);   // points k0-4 .. k0
+    T tLp3, tLp2, tLp1, tCp2, tCp1, tRp1, tLm2, tLm1, tCm1, tx;
+    // centre k0 - 2 (points k0-3, k0-2, k0-1 = slots 2, 3, 4)
+    indicators<T>(fp[2], fp[3], fp[4], c.eps, tLp2, tx, tx);
+    indicators<T>(fm[2], fm[3], fm[4], c.eps, tx, tx, tx);
+    // centre k0 - 1 (slots 3, 4, 5)
+    indicators<T>(fp[3], fp[4], fp[5], c.eps, tLp1, tCp1, tx);
+    indicators<T>(fm[3], fm[4], fm[5], c.eps, tLm1, tx, tx);
+    // age the history by one centre before computing centre k0
+    tLp3 = tLp2; tLp2 = tLp1; tCp2 = tCp1;
+    tLm2 = tLm1;
+#pragma unroll
+    for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
+    load(k0 + 1, fp[5], fm[5]);                                           // slots: points k0-3 .. k0+1
+    // centre k0 (slots 3, 4, 5)
+    indicators<T>(fp[3], fp[4], fp[5], c.eps, tLp1, tCp1, tRp1);
+    indicators<T>(fm[3], fm[4], fm[5], c.eps, tLm1, tCm1, tx);
+    // loop invariant at the top of iteration k: tX1 = centre k+1, tX2 = centre
+    // k, tLp3 = centre k-1; the body adds centre k+2
+    T Fprev = 0;
+#pragma unroll 2
+    for (; k < k0 + Q; k++) {
+#pragma unroll
+        for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
+        load(k + 3, fp[5], fm[5]);
         T tLpN, tCpN, tRpN, tLmN, tCmN, tRmN;
         indicators<T>(fp[3], fp[4], fp[5], c.eps, tLpN, tCpN, tRpN);
         indicators<T>(fm[3], fm[4], fm[5], c.eps, tLmN, tCmN, tRmN);
-        if (k >= k0 - 1) {
-            // interface k+1/2: + side uses left(k-1), centre(k), right(k+1);
-            // - side uses right(k+2), centre(k+1), left(k)
-            const T F = flux6<T>(fp, fm, tLp3, tCp2, tRp1, tLm2, tCm1, tRmN);
-            if (k >= k0) st_real<T, PAD>(out, k, (F - Fprev) * scale);
-            Fprev = F;
-        }
+        // at this point tX1 refer to centre k+1, tX2 to centre k, tLp3 to k-1.
+        // interface k+1/2: + side left(k-1), centre(k), right(k+1);
+        //                  - side right(k+2), centre(k+1), left(k)
+        const T F = flux6<T>(fp, fm, tLp3, tCp2, tRp1, tLm2, tCm1, tRmN);
+        if (k >= k0) st_real<T, PAD>(out, k, (F - Fprev) * scale);
+        Fprev = F;
+        // ages for interface k+3/2
         tLp3 = tLp2; tLp2 = tLp1; tLp1 = tLpN;
         tCp2 = tCp1; tCp1 = tCpN;
         tRp1 = tRpN;
         tLm2 = tLm1; tLm1 = tLmN;
         tCm1 = tCmN;
+    }
+}
+
+// sum u, sum u^2, max|u| and non-finite count of the points [k0, k0 + Q).
+template <typename T, bool PAD>
+__device__ __forceinline__ void row_stats(const cx<T>* u, int k0, int Q, T& s1, T& s2, T& mx, int& nf)
+{
+    for (int k = k0; k < k0 + Q; k++) {
+        const T v = ld_real<T, PAD>(u, k);
+        if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf += 1; }
     }
 }
 
