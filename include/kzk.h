@@ -151,6 +151,39 @@ kzk_status kzk_get_tables(kzk_plan *plan, double *E, double *Phi1, double *Phi2)
 kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *g0,
                        int64_t n_steps, double sigma0, int32_t ckpt_every, void *stream);
 
+/* Flags of kzk_plan_create_batched. */
+#define KZK_BATCH_AUTOTUNE 1
+
+/* Plan for n independent propagations with their own grids (same precision),
+ * coefficients and steps dts[i], all advanced by one persistent cooperative
+ * kernel launch per kzk_advance_batched call (captured once in a CUDA graph
+ * and replayed).  The launch runs every pass of every step for all instances
+ * -- rows of all instances for the row passes, column tiles of all instances
+ * for the column passes, the same computation as kzk_advance -- separated by
+ * grid barriers whose waits are bounded (KZK_ERR_TIMEOUT).  With
+ * KZK_BATCH_AUTOTUNE the column-tile width is chosen by timing two steps of
+ * each candidate at creation.  Each nx must be <= 8192. */
+kzk_status kzk_plan_create_batched(const kzk_grid *grids, const kzk_coeffs *coeffs, const double *dts,
+                                   int32_t n, int32_t flags, kzk_plan **out);
+
+/* Advance the n states u[i] (device pointers, [ny_i][nx_i], in place) by
+ * n_steps steps each from sigma0.  diag_out (host, n entries, nullable)
+ * behaves as in kzk_advance.  KZK_ERR_STATE for a non-batched plan. */
+kzk_status kzk_advance_batched(kzk_plan *plan, void *const *u, int64_t n_steps, double sigma0, void *stream,
+                               kzk_diag *diag_out);
+
+/* Launch configuration of a batched plan: CTAs of the persistent launch,
+ * log2 cap on the column-tile width (the autotuner's choice), dynamic shared
+ * memory per CTA. */
+kzk_status kzk_batch_info(kzk_plan *plan, int32_t *grid_ctas, int32_t *tile_cap, int64_t *smem_bytes);
+
+/* Testing hook of the bounded grid barrier: later batched launches of this
+ * plan wait for extra_blocks more CTAs than they launch (extra_blocks > 0
+ * makes every barrier wait run out) with a wait bound of timeout_ms; such
+ * launches are not graph-captured.  extra_blocks = 0 restores normal
+ * operation (the bound stays timeout_ms). */
+kzk_status kzk_batch_test_barrier(kzk_plan *plan, int32_t extra_blocks, int64_t timeout_ms);
+
 /* Release the plan and all device memory it owns.  NULL is accepted. */
 kzk_status kzk_plan_destroy(kzk_plan *plan);
 

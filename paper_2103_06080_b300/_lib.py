@@ -71,11 +71,20 @@ _SIGS = [
     ("kzk_kernel_times", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_double, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     ("kzk_alu_peak", ctypes.c_int, [ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_double)]),
+    ("kzk_plan_create_batched", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(_VP)]),
+    ("kzk_advance_batched", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int64, ctypes.c_double, _VP,
+                                           ctypes.POINTER(KzkDiag)]),
+    ("kzk_batch_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    ("kzk_batch_test_barrier", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int64]),
     ("kzk_rhs_noalloc", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs), ctypes.c_int32,
                                        _VP, _VP, ctypes.c_double, _VP]),
 ]
 
 NOALLOC_MAX_POINTS = 1 << 18
+KZK_BATCH_AUTOTUNE = 1
 
 
 def lib():

@@ -157,6 +157,81 @@ class Plan:
             pass
 
 
+def _grid_coeffs(w, precision):
+    g = L.KzkGrid(nx=w.nx, ny=w.ny, tau_min=w.tau_min, tau_max=w.tau_max, y_min=w.y_min, y_max=w.y_max,
+                  prec=L.KZK_FP64 if precision == "fp64" else L.KZK_FP32)
+    c = L.KzkCoeffs(B=w.B, A=w.A, lf_umax=w.lf_umax, B_prof=(ctypes.c_double * 4)(*w.B_prof),
+                    A_prof=(ctypes.c_double * 4)(*w.A_prof), has_profile=int(bool(w.has_profile)))
+    return g, c
+
+
+class BatchedPlan:
+    """Many independent propagations (own grid, coefficients and dsigma each)
+    advanced by one persistent, graph-captured launch per call."""
+
+    def __init__(self, workloads: Sequence, precision: str = "fp32", autotune: bool = True):
+        if precision not in ("fp64", "fp32"):
+            raise ValueError("precision must be 'fp64' or 'fp32'")
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.shapes = [(w.ny, w.nx) for w in workloads]
+        n = len(workloads)
+        gs = (L.KzkGrid * n)()
+        cs = (L.KzkCoeffs * n)()
+        dts = (ctypes.c_double * n)()
+        for i, w in enumerate(workloads):
+            gs[i], cs[i] = _grid_coeffs(w, precision)
+            dts[i] = w.dt
+        h = ctypes.c_void_p()
+        L.check(L.lib().kzk_plan_create_batched(gs, cs, dts, n, L.KZK_BATCH_AUTOTUNE if autotune else 0,
+                                                ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    @property
+    def handle(self) -> int:
+        if self._h is None or not self._h.value:
+            raise RuntimeError("plan has been destroyed")
+        return self._h.value
+
+    def advance(self, us: Sequence[torch.Tensor], n_steps: int, sigma0: float = 0.0, diag: bool = False,
+                stream=None):
+        if len(us) != self.n:
+            raise ValueError(f"need {self.n} states")
+        for t, (ny, nx) in zip(us, self.shapes):
+            if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != nx * ny:
+                raise ValueError(f"state must be a contiguous CUDA {self.dtype} tensor of {ny}x{nx}")
+        ptrs = (ctypes.c_void_p * self.n)(*[t.data_ptr() for t in us])
+        d = (L.KzkDiag * self.n)() if diag else None
+        st = L.lib().kzk_advance_batched(self.handle, ptrs, int(n_steps), float(sigma0), _stream_ptr(stream),
+                                         d if diag else None)
+        if diag:
+            if st not in (L.KZK_OK, L.KZK_ERR_CFL, L.KZK_ERR_NONFINITE):
+                L.check(st)
+            return st, [d[i].as_dict() for i in range(self.n)]
+        L.check(st)
+        return None
+
+    def info(self) -> dict:
+        g, c, sm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        L.check(L.lib().kzk_batch_info(self.handle, ctypes.byref(g), ctypes.byref(c), ctypes.byref(sm)))
+        return {"grid_ctas": g.value, "tile_cap": c.value, "smem_bytes": sm.value}
+
+    def test_barrier(self, extra_blocks: int, timeout_ms: int) -> None:
+        L.check(L.lib().kzk_batch_test_barrier(self.handle, int(extra_blocks), int(timeout_ms)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.lib().kzk_plan_destroy(self._h.value)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def launch_count() -> int:
     return int(L.lib().kzk_launch_count())
 

@@ -9,6 +9,7 @@
 
 #include "../../include/kzk.h"
 #include "kzk_adjoint.cuh"
+#include "kzk_batched.cuh"
 #include "kzk_kernels.cuh"
 #include "kzk_tables.cuh"
 
@@ -85,6 +86,23 @@ struct kzk_plan_s {
     void* seg;                  // segment store [(2 k)][batch][ny][nx/2]
     void* ckpt;                 // checkpoints  [n_ckpt][batch][ny][nx/2]
     long long seg_cap, ckpt_cap; // in arrays
+    // batched plans (kzk_plan_create_batched): one sub-plan per instance
+    int batched;
+    std::vector<kzk_plan_s*>* subs;
+    void* binst;                // device BatchInst<T>[n]
+    int* row_prefix;            // device [n + 1]
+    int* col_prefix;            // device [n + 1]
+    void* coef;                 // device [coef_cap steps][n][6]
+    long long coef_cap;
+    unsigned* bar;              // device: count, generation, flag
+    int grid_ctas;
+    size_t batch_smem;
+    int tile_cap;               // autotuned cap on log2 of the column tile width
+    long long graph_steps;      // steps the cached graph advances
+    cudaGraphExec_t graph;
+    unsigned test_extra_blocks; // testing hook: barrier waits for this many extra CTAs
+    long long timeout_ns;
+    cudaStream_t cap_stream;    // capturable stream for building the graph
 };
 
 namespace {
@@ -418,6 +436,16 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
 void plan_free(kzk_plan* p)
 {
     if (!p) return;
+    if (p->subs) {
+        for (kzk_plan* q : *p->subs) plan_free(q);
+        delete p->subs;
+        p->subs = nullptr;
+    }
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    void* bptrs[] = {p->binst, p->row_prefix, p->col_prefix, p->coef, p->bar};
+    for (void* q : bptrs)
+        if (q) cudaFree(q);
     void* ptrs[] = {p->V, p->b1, p->vs, p->b2, p->E, p->P1, p->P2, p->E_lo, p->twr, p->twc, p->twc_lo,
                     p->tws_row, p->twc_full,
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
@@ -569,6 +597,244 @@ namespace kzk_internal {
 // error reporting for the other translation unit (kzk_noalloc.cu)
 kzk_status set_error(kzk_status s, const char* msg) { return fail(s, "%s", msg); }
 }  // namespace kzk_internal
+
+// ---------------------------------------------------------------------------
+// Batched plans: one persistent cooperative launch for all instances
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+size_t batch_smem_for(const kzk_plan* q, int log2tc)
+{
+    const size_t row = 2 * (size_t)row_buf_len(q->n) * sizeof(cx<T>) + 4 * (BATCH_THREADS / 32) * sizeof(double);
+    const size_t col = col_tile_area<T>(q->ny, log2tc, BATCH_THREADS) +
+                       (sizeof(T) == 4 ? 2 : 1) * (size_t)q->ny * sizeof(cx<T>);
+    const size_t fin = 4 * (size_t)BATCH_THREADS * sizeof(double);
+    return std::max(std::max(row, col), fin);
+}
+
+// Descriptors of all instances (column tiles capped at 2^tile_cap) and the
+// task prefix sums; returns the dynamic shared memory the launch needs.
+template <typename T>
+kzk_status batch_upload(kzk_plan* p, void* const* u, int tile_cap, size_t* smem_out, cudaStream_t st,
+                        long long n_steps = 1)
+{
+    const int n = (int)p->subs->size();
+    // the history buffers must exist (at their final size) before their
+    // addresses go into the descriptors
+    for (kzk_plan* q : *p->subs) KZK_TRY(ensure_hist(q, std::max(1LL, n_steps)));
+    std::vector<BatchInst<T>> bi(n);
+    std::vector<int> rp(n + 1, 0), cp(n + 1, 0);
+    size_t smem = 0;
+    for (int i = 0; i < n; i++) {
+        kzk_plan* q = (*p->subs)[i];
+        const int l2tc = std::min(q->log2tc, tile_cap);
+        BatchInst<T>& I = bi[i];
+        memset(&I, 0, sizeof(I));
+        I.row = row_args<T>(q, nullptr, nullptr, 0.0, nullptr);
+        I.col = col_args<T>(q);
+        I.col.log2tc = l2tc;
+        I.V = (cx<T>*)q->V; I.b1 = (cx<T>*)q->b1; I.vs = (cx<T>*)q->vs; I.b2 = (cx<T>*)q->b2;
+        I.u = u ? (cx<T>*)u[i] : nullptr;
+        I.E = (const cx<T>*)q->E; I.E_lo = (const cx<T>*)q->E_lo;
+        I.P1 = (const cx<T>*)q->P1; I.P2 = (const cx<T>*)q->P2;
+        I.diag_rows = q->diag_rows; I.diag_hist = q->diag_hist; I.diag_final = q->diag_final;
+        I.ny = q->ny;
+        I.n_tiles = q->n >> l2tc;
+        I.inv_count = 1.0 / ((double)q->nx * q->ny);
+        I.cell = (q->g.tau_max - q->g.tau_min) / q->nx * (q->g.y_max - q->g.y_min) / q->ny;
+        rp[i + 1] = rp[i] + q->ny;
+        cp[i + 1] = cp[i] + I.n_tiles;
+        // every buffer a launch touches must exist before it is described
+        const void* need[] = {I.V, I.b1, I.vs, I.b2, I.E, I.P1, I.P2, I.diag_rows, I.diag_hist, I.diag_final,
+                              I.row.tw, I.row.tws, I.col.tw};
+        for (const void* ptr : need)
+            if (!ptr) return fail(KZK_ERR_STATE, "instance %d: missing device buffer", i);
+        if (sizeof(T) == 4 && (!I.E_lo || !I.col.tw_lo)) return fail(KZK_ERR_STATE, "instance %d: missing lo tables", i);
+        if (u && !I.u) return fail(KZK_ERR_ARG, "u[%d] is NULL", i);
+        if (col_threads<T>(q->ny, l2tc) > BATCH_THREADS || row_threads<T>(q->nx) > BATCH_THREADS)
+            return fail(KZK_ERR_SIZE, "instance %d does not fit a %d-thread task", i, BATCH_THREADS);
+        smem = std::max(smem, batch_smem_for<T>(q, l2tc));
+    }
+    KZK_CUDA(cudaMemcpyAsync(p->binst, bi.data(), n * sizeof(BatchInst<T>), cudaMemcpyHostToDevice, st));
+    KZK_CUDA(cudaMemcpyAsync(p->row_prefix, rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    KZK_CUDA(cudaMemcpyAsync(p->col_prefix, cp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    KZK_CUDA(cudaStreamSynchronize(st));     // host vectors go out of scope
+    *smem_out = smem;
+    return KZK_OK;
+}
+
+// per-step coefficients of every instance: B, alpha, nx dA at sigma_s and sigma_s + dt
+template <typename T>
+kzk_status batch_coefs(kzk_plan* p, long long n_steps, double sigma0, cudaStream_t st)
+{
+    const int n = (int)p->subs->size();
+    if (n_steps > p->coef_cap) {
+        if (p->coef) KZK_CUDA(cudaFree(p->coef));
+        p->coef = nullptr;
+        p->coef_cap = 0;
+        KZK_CUDA(cudaMalloc(&p->coef, (size_t)n_steps * n * 6 * sizeof(T)));
+        p->coef_cap = n_steps;
+    }
+    std::vector<T> c((size_t)n_steps * n * 6);
+    for (long long s = 0; s < n_steps; s++)
+        for (int i = 0; i < n; i++) {
+            kzk_plan* q = (*p->subs)[i];
+            const double s1 = sigma0 + (double)s * q->dt, s2 = s1 + q->dt;
+            T* o = &c[((size_t)s * n + i) * 6];
+            const double B1 = B_of(q, s1), B2 = B_of(q, s2);
+            o[0] = (T)B1; o[1] = (T)(B1 * q->c.lf_umax); o[2] = (T)(q->nx * dA_of(q, s1));
+            o[3] = (T)B2; o[4] = (T)(B2 * q->c.lf_umax); o[5] = (T)(q->nx * dA_of(q, s2));
+        }
+    KZK_CUDA(cudaMemcpyAsync(p->coef, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    KZK_CUDA(cudaStreamSynchronize(st));
+    return KZK_OK;
+}
+
+template <typename T>
+kzk_status batch_launch(kzk_plan* p, long long n_steps, cudaStream_t st, bool use_graph)
+{
+    BatchArgs<T> B;
+    B.inst = (const BatchInst<T>*)p->binst;
+    B.row_prefix = p->row_prefix;
+    B.col_prefix = p->col_prefix;
+    B.coef = (const T*)p->coef;
+    B.n_inst = (int)p->subs->size();
+    B.n_steps = (int)n_steps;
+    B.bar_count = p->bar;
+    B.bar_gen = p->bar + 1;
+    B.flag = (int*)(p->bar + 2);
+    B.expected_blocks = (unsigned)p->grid_ctas + p->test_extra_blocks;
+    B.timeout_ns = p->timeout_ns;
+    void* args[] = {&B};
+    auto enqueue = [&](cudaStream_t on) -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(p->bar, 0, 4 * sizeof(unsigned), on);
+        if (e != cudaSuccess) return e;
+        return cudaLaunchCooperativeKernel((const void*)batched_kernel<T>, dim3(p->grid_ctas), dim3(BATCH_THREADS),
+                                           args, p->batch_smem, on);
+    };
+    if (!use_graph || p->test_extra_blocks) {
+        KZK_CUDA(enqueue(st));
+        KZK_LAUNCHED();
+        return KZK_OK;
+    }
+    if (!p->graph || p->graph_steps != n_steps) {
+        if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+        // capture on the plan's own stream (the caller's may be the legacy
+        // default stream, which cannot be captured); the graph is then
+        // launched on the caller's stream
+        if (!p->cap_stream) KZK_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        KZK_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue(p->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(KZK_ERR_CUDA, "graph capture of the batched launch: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&p->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { p->graph = nullptr; return fail(KZK_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+        p->graph_steps = n_steps;
+    }
+    KZK_CUDA(cudaGraphLaunch(p->graph, st));
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
+template <typename T>
+kzk_status batch_configure(kzk_plan* p, int tile_cap, cudaStream_t st)
+{
+    size_t smem = 0;
+    KZK_TRY(batch_upload<T>(p, nullptr, tile_cap, &smem, st));
+    int dev = 0, sms = 0, optin = 0, nb = 0;
+    KZK_CUDA(cudaGetDevice(&dev));
+    KZK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    KZK_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    KZK_CUDA(cudaFuncGetAttributes(&fa, batched_kernel<T>));
+    const size_t dyn_max = (size_t)optin - fa.sharedSizeBytes;
+    if (smem > dyn_max) return fail(KZK_ERR_SIZE, "batched launch needs %zu B of shared memory", smem);
+    KZK_CUDA(cudaFuncSetAttribute(batched_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
+    KZK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel<T>, BATCH_THREADS, smem));
+    if (nb < 1) return fail(KZK_ERR_SIZE, "batched kernel cannot be resident (shared memory %zu B)", smem);
+    p->grid_ctas = nb * sms;
+    p->batch_smem = smem;
+    p->tile_cap = tile_cap;
+    if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+    return KZK_OK;
+}
+
+// Autotuner: time two steps from zero states for each cap on the column tile
+// width and keep the fastest.
+template <typename T>
+kzk_status batch_autotune(kzk_plan* p, cudaStream_t st)
+{
+    const int n = (int)p->subs->size();
+    std::vector<void*> tmp(n, nullptr);
+    kzk_status status = KZK_OK;
+    for (int i = 0; i < n && status == KZK_OK; i++) {
+        kzk_plan* q = (*p->subs)[i];
+        if (cudaMalloc(&tmp[i], (size_t)q->nx * q->ny * sizeof(T)) != cudaSuccess) status = fail(KZK_ERR_OOM, "autotune buffers");
+        else if (cudaMemsetAsync(tmp[i], 0, (size_t)q->nx * q->ny * sizeof(T), st) != cudaSuccess) status = KZK_ERR_CUDA;
+    }
+    int best_cap = 4;
+    float best = 1e30f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (status == KZK_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        status = fail(KZK_ERR_CUDA, "autotune events");
+    for (int cap = 0; cap <= 3 && status == KZK_OK; cap++) {
+        if ((status = batch_configure<T>(p, cap, st)) != KZK_OK) { status = KZK_OK; continue; }
+        size_t smem = 0;
+        if ((status = batch_upload<T>(p, tmp.data(), cap, &smem, st, 2)) != KZK_OK) break;
+        if ((status = batch_coefs<T>(p, 2, 0.0, st)) != KZK_OK) break;
+        if ((status = batch_launch<T>(p, 2, st, false)) != KZK_OK) break;   // warm-up
+        cudaEventRecord(e0, st);
+        if ((status = batch_launch<T>(p, 2, st, false)) != KZK_OK) break;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_cap = cap; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (void* q : tmp)
+        if (q) cudaFree(q);
+    if (status != KZK_OK) return status;
+    return batch_configure<T>(p, best_cap, st);
+}
+
+template <typename T>
+kzk_status advance_batched_impl(kzk_plan* p, void* const* u, long long n_steps, double sigma0, cudaStream_t st,
+                                kzk_diag* dout)
+{
+    size_t smem = 0;
+    KZK_TRY(batch_upload<T>(p, u, p->tile_cap, &smem, st, n_steps));
+    KZK_TRY(batch_coefs<T>(p, n_steps, sigma0, st));
+    KZK_CUDA(cudaMemsetAsync(p->bar + 2, 0, sizeof(unsigned), st));
+    KZK_TRY(batch_launch<T>(p, n_steps, st, true));
+    for (kzk_plan* q : *p->subs) q->hist_steps = n_steps;
+    unsigned flag = 0;
+    if (dout || p->test_extra_blocks) {
+        KZK_CUDA(cudaStreamSynchronize(st));
+        KZK_CUDA(cudaMemcpy(&flag, p->bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    }
+    if (flag & FLAG_TIMEOUT) return fail(KZK_ERR_TIMEOUT, "a grid barrier of the batched launch timed out");
+    if (dout) {
+        kzk_status worst = KZK_OK;
+        for (size_t i = 0; i < p->subs->size(); i++) {
+            kzk_status s = finish_diag((*p->subs)[i], n_steps, st, &dout[i]);
+            if (s == KZK_ERR_NONFINITE || (s == KZK_ERR_CFL && worst == KZK_OK)) worst = s;
+            else if (s != KZK_OK && s != KZK_ERR_CFL && s != KZK_ERR_NONFINITE) return s;
+        }
+        return worst;
+    }
+    return KZK_OK;
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // Measurement helpers
@@ -793,6 +1059,77 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     return KZK_OK;
 }
 
+kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coeffs, const double* dts, int32_t n,
+                                   int32_t flags, kzk_plan** out)
+{
+    if (!out) return fail(KZK_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grids || !coeffs || !dts || n < 1) return fail(KZK_ERR_ARG, "need grids, coeffs, dts and n >= 1");
+    for (int i = 1; i < n; i++)
+        if (grids[i].prec != grids[0].prec) return fail(KZK_ERR_ARG, "all instances must share one precision");
+    kzk_plan* p = new (std::nothrow) kzk_plan_s();
+    if (!p) return fail(KZK_ERR_OOM, "host allocation failed");
+    memset(p, 0, sizeof(*p));
+    p->batched = 1;
+    p->prec = grids[0].prec;
+    p->batch = n;
+    p->timeout_ns = 2000000000LL;
+    p->subs = new (std::nothrow) std::vector<kzk_plan_s*>();
+    if (!p->subs) { delete p; return fail(KZK_ERR_OOM, "host allocation failed"); }
+    for (int i = 0; i < n; i++) {
+        kzk_plan* q = nullptr;
+        kzk_status s = kzk_plan_create(&grids[i], &coeffs[i], dts[i], 1, &q);
+        if (s != KZK_OK) { plan_free(p); return s; }
+        p->subs->push_back(q);
+        if (q->nx > 8192) { plan_free(p); return fail(KZK_ERR_SIZE, "instance %d too large", i); }
+    }
+    cudaError_t e = cudaMalloc(&p->binst, (size_t)n * std::max(sizeof(BatchInst<float>), sizeof(BatchInst<double>)));
+    if (e == cudaSuccess) e = cudaMalloc(&p->row_prefix, (n + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->col_prefix, (n + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->bar, 4 * sizeof(unsigned));
+    if (e != cudaSuccess) { plan_free(p); return fail(KZK_ERR_OOM, "batched plan allocation: %s", cudaGetErrorString(e)); }
+    kzk_status s;
+    if (flags & KZK_BATCH_AUTOTUNE)
+        s = p->prec == KZK_FP64 ? batch_autotune<double>(p, 0) : batch_autotune<float>(p, 0);
+    else
+        s = p->prec == KZK_FP64 ? batch_configure<double>(p, 4, 0) : batch_configure<float>(p, 4, 0);
+    if (s != KZK_OK) { plan_free(p); return s; }
+    *out = p;
+    return KZK_OK;
+}
+
+kzk_status kzk_advance_batched(kzk_plan* p, void* const* u, int64_t n_steps, double sigma0, void* stream,
+                               kzk_diag* diag_out)
+{
+    if (!p || !u) return fail(KZK_ERR_ARG, "plan or u is NULL");
+    if (!p->batched) return fail(KZK_ERR_STATE, "not a batched plan");
+    if (n_steps < 0 || n_steps > (1LL << 30)) return fail(KZK_ERR_ARG, "bad n_steps");
+    for (int i = 0; i < p->batch; i++)
+        if (!u[i]) return fail(KZK_ERR_ARG, "u[%d] is NULL", i);
+    if (n_steps == 0 && !diag_out) return KZK_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    return p->prec == KZK_FP64 ? advance_batched_impl<double>(p, u, n_steps, sigma0, st, diag_out)
+                               : advance_batched_impl<float>(p, u, n_steps, sigma0, st, diag_out);
+}
+
+kzk_status kzk_batch_info(kzk_plan* p, int32_t* grid_ctas, int32_t* tile_cap, int64_t* smem_bytes)
+{
+    if (!p || !p->batched) return fail(KZK_ERR_STATE, "not a batched plan");
+    if (grid_ctas) *grid_ctas = p->grid_ctas;
+    if (tile_cap) *tile_cap = p->tile_cap;
+    if (smem_bytes) *smem_bytes = (int64_t)p->batch_smem;
+    return KZK_OK;
+}
+
+kzk_status kzk_batch_test_barrier(kzk_plan* p, int32_t extra_blocks, int64_t timeout_ms)
+{
+    if (!p || !p->batched) return fail(KZK_ERR_STATE, "not a batched plan");
+    if (extra_blocks < 0 || timeout_ms < 1 || timeout_ms > 60000) return fail(KZK_ERR_ARG, "bad barrier test values");
+    p->test_extra_blocks = (unsigned)extra_blocks;
+    p->timeout_ns = timeout_ms * 1000000LL;
+    return KZK_OK;
+}
+
 kzk_status kzk_plan_destroy(kzk_plan* plan)
 {
     plan_free(plan);
@@ -802,6 +1139,7 @@ kzk_status kzk_plan_destroy(kzk_plan* plan)
 kzk_status kzk_advance(kzk_plan* p, void* u, int64_t n_steps, double sigma0, void* stream, kzk_diag* diag_out)
 {
     if (!p || !u) return fail(KZK_ERR_ARG, "plan or u is NULL");
+    if (p->batched) return fail(KZK_ERR_STATE, "batched plan: use kzk_advance_batched");
     if (n_steps < 0) return fail(KZK_ERR_ARG, "n_steps < 0");
     if (n_steps == 0 && !diag_out) return KZK_OK;
     cudaStream_t st = (cudaStream_t)stream;

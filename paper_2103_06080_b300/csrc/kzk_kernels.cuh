@@ -163,13 +163,16 @@ constexpr int ROW_MAX_THREADS = 512; // n / 8 for nx = 8192
 // Row kernel.  One CTA per (row, instance), n / PPT threads (at least 32).
 // Shared memory: two padded buffers of n complex (= nx reals) each, plus a
 // reduction area of 4 doubles per thread.
+// Body of one row task, run by all nthr = blockDim.x threads of a CTA
+// (nthr may exceed n / PPT; extra threads idle through the barriers).
+// State arrays are read with L2-coherent loads (__ldcg) so that the body is
+// also correct inside one persistent launch, where they are rewritten by
+// other CTAs between passes.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_kernel(RowArgs<T> a)
+__device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst, unsigned char* smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int nx = 1 << a.log2nx, n = nx >> 1, log2n = a.log2nx - 1;
-    const int row = blockIdx.x, inst = blockIdx.y;
     cx<T>* X = reinterpret_cast<cx<T>*>(smem_raw);       // buffer U
     cx<T>* Y = X + row_buf_len(n);                         // buffer B
     double* red = reinterpret_cast<double*>(Y + row_buf_len(n));
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_k
     if constexpr (MODE == ROW_FWD) {
         // physical row -> packed half spectrum / nx
         const T* src = reinterpret_cast<const T*>(a.in + base);
-        for (int i = tid; i < nx; i += nthr) st_real<T, true>(Y, i, src[i]);
+        for (int i = tid; i < nx; i += nthr) st_real<T, true>(Y, i, __ldcg(src + i));
         __syncthreads();
         fft_batched<T, ROW_PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
         for (int k = tid; k <= n / 2; k += nthr) {
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_k
         }
     } else {
         // spectral row -> physical row in X
-        for (int i = tid; i < n; i += nthr) X[padx(i)] = a.in[base + i];
+        for (int i = tid; i < n; i += nthr) X[padx(i)] = __ldcg(a.in + base + i);
         __syncthreads();
         c2r_pre<T, true>(X, n, a.tw, tid, nthr);
         __syncthreads();
@@ -209,7 +212,8 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_k
             if (a.diag_rows) block_diag_t<T>(red, s1, s2, mx, nf, a.diag_rows + ((long long)inst * a.ny + row) * 4);
         } else {
             // ROW_RHS: WENO5 flux derivative into Y, then tau-R2C of Y
-            const int Q = nx >= nthr ? nx / nthr : 1;
+            // chunks of at least 16 points (the sweep's pre-roll is 3 centres)
+            const int Q = nx / nthr >= 16 ? nx / nthr : (nx >= 16 ? 16 : nx);
             const int k0 = tid * Q;
             if (k0 < nx) {
                 weno_row_chunk<T, true>(X, Y, nx, k0, Q, a.wc);
@@ -225,15 +229,15 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_k
                     // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
                     if (k == 0) {
                         const T kN = a.kscale * T(n);
-                        xk.y -= a.cA * kN * kN * vin[0].y;
+                        xk.y -= a.cA * kN * kN * __ldcg(vin).y;
                     } else {
                         const T kt = a.kscale * T(k);
-                        const cx<T> v = vin[k];
+                        const cx<T> v = __ldcg(vin + k);
                         xk.x -= a.cA * kt * kt * v.x;
                         xk.y -= a.cA * kt * kt * v.y;
                         if (2 * k != n) {
                             const T kt2 = a.kscale * T(n - k);
-                            const cx<T> w = vin[n - k];
+                            const cx<T> w = __ldcg(vin + n - k);
                             xnk.x -= a.cA * kt2 * kt2 * w.x;
                             xnk.y -= a.cA * kt2 * kt2 * w.y;
                         }
@@ -245,6 +249,13 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_k
             if (a.diag_rows) block_diag_t<T>(red, s1, s2, mx, nf, a.diag_rows + ((long long)inst * a.ny + row) * 4);
         }
     }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_kernel(RowArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    row_body<T, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // Threads and dynamic shared memory of one row CTA.
@@ -318,14 +329,15 @@ constexpr int COL_MAX_THREADS = 1024;
 //    with two-float constants in FP32), combine E' V + P1' b1 into the state
 //    half, inverse FFT it (two-float again) and store V*.
 //  STAGE2 (STEP 4): one tile of b2 - b1, FFT, times P2', inverse FFT, plus V*.
+// Body of one column-tile task (tile index `tile`), run by all nthr =
+// blockDim.x threads of a CTA (nthr * PPT >= ny * TC).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
+__device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst, unsigned char* smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* S = reinterpret_cast<cx<T>*>(smem_raw);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int ny = 1 << a.log2ny, n = 1 << a.log2n, TC = 1 << a.log2tc;
-    const int m0 = blockIdx.x * TC, inst = blockIdx.y;
+    const int m0 = tile * TC;
     const long long ibase = (long long)inst * a.inst_stride;
     const int total = ny << a.log2tc;                   // elements of one tile
     constexpr bool ACC = sizeof(T) == 4;
@@ -350,12 +362,13 @@ __global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
 
     if constexpr (MODE == COL_STAGE1) {
         // diagnostics of the state this step started from (rows written by R)
-        if (blockIdx.x == 0 && a.diag_rows) {
+        if (tile == 0 && a.diag_rows && a.diag_hist) {
             double* red = reinterpret_cast<double*>(smem_raw);
             double s1 = 0, s2 = 0, mx = 0, nf = 0;
             const double* dr = a.diag_rows + (long long)inst * ny * 4;
             for (int r = tid; r < ny; r += nthr) {
-                s1 += dr[4 * r]; s2 += dr[4 * r + 1]; mx = fmax(mx, dr[4 * r + 2]); nf += dr[4 * r + 3];
+                s1 += __ldcg(dr + 4 * r); s2 += __ldcg(dr + 4 * r + 1);
+                mx = fmax(mx, __ldcg(dr + 4 * r + 2)); nf += __ldcg(dr + 4 * r + 3);
             }
             double tmp[4];
             block_diag(red, s1, s2, mx, nf, tmp);
@@ -369,8 +382,8 @@ __global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
         }
         for (int e = tid; e < total; e += nthr) {
             const long long g = gidx(e);
-            SA[padx(e)] = a.a[g];
-            SB[padx(e)] = a.b[g];
+            SA[padx(e)] = __ldcg(a.a + g);
+            SB[padx(e)] = __ldcg(a.b + g);
         }
         __syncthreads();
         // state tile: accurate transform; b1 tile: plain
@@ -413,7 +426,7 @@ __global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
     } else {
         for (int e = tid; e < total; e += nthr) {
             const long long g = gidx(e);
-            SA[padx(e)] = sub<T>(a.b[g], a.a[g]);
+            SA[padx(e)] = sub<T>(__ldcg(a.b + g), __ldcg(a.a + g));
         }
         __syncthreads();
         fft_batched<T, COL_PPT, true, false, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
@@ -437,9 +450,16 @@ __global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
         fft_batched<T, COL_PPT, true, true, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
         for (int e = tid; e < total; e += nthr) {
             const long long g = gidx(e);
-            a.out[g] = add<T>(a.c[g], SA[padx(e)]);
+            a.out[g] = add<T>(__ldcg(a.c + g), SA[padx(e)]);
         }
     }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    col_body<T, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // Column tile width (log2) and threads: STAGE1 holds two tiles of
