@@ -85,6 +85,27 @@ def col_flops(nx, ny, stage):
 
 
 # --------------------------------------------------------------------------
+# multi-rank aggregation (replicas: independent work per rank, no collective
+# on the data path; only the timing is reduced)
+# --------------------------------------------------------------------------
+def reduce_max(x: float, device, world: int) -> float:
+    """Max of a per-rank scalar over all ranks (identity on one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank_step: float, steps: int, world: int, seconds_max: float) -> float:
+    """Weak scaling: every rank advances its own replica; the job's rate is
+    all ranks' grid-point-steps over the slowest rank's time."""
+    return points_per_rank_step * steps * world / seconds_max
+
+
+# --------------------------------------------------------------------------
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
@@ -223,11 +244,8 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     launches = api.launch_count() - n0
     clocks = sampler.stop()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = w.nx * w.ny * args.steps * world / (ms_max * 1e-3)
+    ms_max = reduce_max(ms, dev, world)
+    value = whole_job_rate(w.nx * w.ny, args.steps, world, ms_max * 1e-3)
 
     # per-kernel device times (CUDA events on the launch stream)
     kt = plan.kernel_times(u, min(args.steps, 20), sigma0=0.0)
@@ -261,10 +279,7 @@ def run_ours(args, rank, world, local_rank):
     out_host.copy_(u, non_blocking=True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_val = w.nx * w.ny * args.steps * world / float(tt.item())
+    e2e_val = whole_job_rate(w.nx * w.ny, args.steps, world, reduce_max(t_e2e, dev, world))
     state_bytes = w.nx * w.ny * wsz
 
     extra = {}
@@ -349,26 +364,53 @@ def secondary_reports(args, api, torch, dev, peaks):
     w4 = inputs.config(4, n_steps=args.adj_steps)
     p4 = api.Plan.from_workload(w4, precision="fp64")
     u4 = torch.tensor(w4.u0, dtype=torch.float64, device=dev)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
     y = u4.clone()
-    p4.advance(y, 4)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
+    p4.advance(y, 4)                                            # warm-up
+    t_fwd, _ = timed(lambda: p4.advance(y, w4.n_steps))
     y = u4.clone()
-    p4.advance(y, w4.n_steps)
-    torch.cuda.synchronize()
-    t_fwd = time.perf_counter() - t
+    t_fwd_ck, _ = timed(lambda: p4.advance_checkpointed(y, w4.n_steps, 0.0, 32))
     g_end = 2 * w4.dtau * y
-    p4.adjoint(u4, g_end, 4, ckpt_every=32)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    p4.adjoint(u4, g_end, w4.n_steps, ckpt_every=32)
-    torch.cuda.synchronize()
-    t_adj = time.perf_counter() - t
+    t_bwd, _ = timed(lambda: p4.adjoint_checkpointed(g_end))
+    t_full, _ = timed(lambda: p4.adjoint(u4, g_end, w4.n_steps, ckpt_every=32))
     out["adjoint"] = {"workload": f"fp64 2048x1024, {w4.n_steps} steps, checkpoint every 32",
-                      "forward_s": t_fwd, "gradient_s": t_adj,
-                      "gradient_over_forward": t_adj / t_fwd,
-                      "note": "gradient = forward sweep with checkpoints + per-segment recompute + reverse sweep"}
+                      "forward_s": t_fwd, "forward_with_checkpoints_s": t_fwd_ck, "backward_s": t_bwd,
+                      "backward_over_forward": t_bwd / t_fwd,
+                      "full_gradient_s": t_full, "full_gradient_over_forward": t_full / t_fwd,
+                      "note": "backward = per-segment recompute from stored checkpoints + reverse sweep "
+                              "(the autograd backward); full gradient = kzk_adjoint from u0 (forward sweep "
+                              "with checkpoints + backward)"}
     p4.close()
+    # batched persistent launch: 64 heterogeneous FP32 propagations
+    if not args.no_batched:
+        ws = inputs.batched_config(seed=5, count=args.batch_count, n_steps=500)
+        t0 = time.perf_counter()
+        bp = api.BatchedPlan(ws, precision="fp32", autotune=True)
+        t_plan = time.perf_counter() - t0
+        us = [torch.tensor(w.u0, dtype=torch.float32, device=dev) for w in ws]
+        bp.advance(us, 2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bp.advance(us, args.batch_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        msb = e0.elapsed_time(e1)
+        pts = sum(w.nx * w.ny for w in ws)
+        out["batched"] = {"workload": f"{len(ws)} FP32 N-wave propagations, Nx in 1024..8192, Ny in 256..2048 "
+                                      f"(seeded), own dsigma and profiles each; {args.batch_steps} steps per call",
+                          "value": pts * args.batch_steps / (msb * 1e-3), "unit": UNIT,
+                          "ms_per_step": msb / args.batch_steps, "points_per_step": pts,
+                          "launch": bp.info(), "plan_create_s": t_plan,
+                          "note": "one cooperative persistent kernel per call, replayed from a CUDA graph"}
+        bp.close()
     return out
 
 
@@ -389,6 +431,9 @@ def main():
     ap.add_argument("--err-ny", type=int, default=256)
     ap.add_argument("--err-steps", type=int, default=200)
     ap.add_argument("--adj-steps", type=int, default=128)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

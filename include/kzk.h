@@ -184,6 +184,19 @@ kzk_status kzk_batch_info(kzk_plan *plan, int32_t *grid_ctas, int32_t *tile_cap,
  * operation (the bound stays timeout_ms). */
 kzk_status kzk_batch_test_barrier(kzk_plan *plan, int32_t extra_blocks, int64_t timeout_ms);
 
+/* kzk_advance that also keeps, inside the plan, the spectral state every
+ * ckpt_every steps (the checkpoints kzk_adjoint would recompute).  u is
+ * advanced in place; no diagnostics.  A later kzk_adjoint_checkpointed on the
+ * same plan reuses the checkpoints until the next kzk_advance_checkpointed or
+ * kzk_adjoint call on the plan (which replace them). */
+kzk_status kzk_advance_checkpointed(kzk_plan *plan, void *u, int64_t n_steps, double sigma0,
+                                    int32_t ckpt_every, void *stream);
+
+/* Adjoint of the last kzk_advance_checkpointed run of this plan: g0 (device)
+ * = (d u_end / d u0)^T g_end, recomputing each segment from its checkpoint
+ * (the reverse half of kzk_adjoint).  KZK_ERR_STATE without such a run. */
+kzk_status kzk_adjoint_checkpointed(kzk_plan *plan, const void *g_end, void *g0, void *stream);
+
 /* Release the plan and all device memory it owns.  NULL is accepted. */
 kzk_status kzk_plan_destroy(kzk_plan *plan);
 

@@ -71,6 +71,8 @@ _SIGS = [
     ("kzk_kernel_times", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_double, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     ("kzk_alu_peak", ctypes.c_int, [ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_double)]),
+    ("kzk_advance_checkpointed", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, _VP]),
+    ("kzk_adjoint_checkpointed", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("kzk_plan_create_batched", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs),
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(_VP)]),

@@ -136,6 +136,20 @@ class Plan:
                                     float(sigma0), int(ckpt_every), _stream_ptr(stream)))
         return g0
 
+    def advance_checkpointed(self, u: torch.Tensor, n_steps: int, sigma0: float = 0.0, ckpt_every: int = 32,
+                             stream=None) -> None:
+        """advance() that keeps the adjoint's checkpoints in the plan."""
+        self._check_state(u, "u")
+        L.check(L.lib().kzk_advance_checkpointed(self.handle, u.data_ptr(), int(n_steps), float(sigma0),
+                                                 int(ckpt_every), _stream_ptr(stream)))
+
+    def adjoint_checkpointed(self, g_end: torch.Tensor, stream=None) -> torch.Tensor:
+        """Adjoint of the last advance_checkpointed run of this plan."""
+        self._check_state(g_end, "g_end")
+        g0 = torch.empty_like(g_end)
+        L.check(L.lib().kzk_adjoint_checkpointed(self.handle, g_end.data_ptr(), g0.data_ptr(), _stream_ptr(stream)))
+        return g0
+
     def kernel_times(self, u: torch.Tensor, n_steps: int, sigma0: float = 0.0, stream=None) -> list:
         """Mean device ms of one launch of [row stage 1, column stage 1, row
         stage 2, column stage 2] over n_steps steps (advances u)."""

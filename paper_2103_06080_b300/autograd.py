@@ -1,10 +1,12 @@
 """torch.autograd.Function around kzk_advance / kzk_adjoint.
 
-Forward advances a copy of u0 by n_steps ExpRK22 steps; backward returns the
-gradient with respect to u0 through the library's hand-written adjoint
-(transposed WENO5 including the derivatives of the nonlinear weights,
-conjugated phi-multipliers, adjoint FFTs), recomputing the forward sweep from
-checkpoints every `ckpt_every` steps.  This is what a shape-optimisation loop
+Forward advances a copy of u0 by n_steps ExpRK22 steps and keeps the spectral
+state every `ckpt_every` steps inside the plan; backward returns the gradient
+with respect to u0 through the library's hand-written adjoint (transposed
+WENO5 including the derivatives of the nonlinear weights, conjugated
+phi-multipliers, adjoint FFTs), recomputing each segment from its checkpoint.
+The plan holds one set of checkpoints: run backward before the next forward
+through the same plan.  This is what a shape-optimisation loop
 over the initial pressure profile needs: d loss(u(sigma_end)) / d u0.
 """
 from __future__ import annotations
@@ -16,15 +18,13 @@ class KZKAdvance(torch.autograd.Function):
     @staticmethod
     def forward(ctx, u0, plan, n_steps: int, sigma0: float = 0.0, ckpt_every: int = 32):
         u = u0.detach().clone().contiguous()
-        plan.advance(u, n_steps, sigma0)
-        ctx.save_for_backward(u0.detach().contiguous())
-        ctx.plan, ctx.n_steps, ctx.sigma0, ctx.ckpt_every = plan, n_steps, sigma0, ckpt_every
+        plan.advance_checkpointed(u, n_steps, sigma0, ckpt_every)
+        ctx.plan = plan
         return u
 
     @staticmethod
     def backward(ctx, g):
-        (u0,) = ctx.saved_tensors
-        g0 = ctx.plan.adjoint(u0, g.contiguous(), ctx.n_steps, ctx.sigma0, ctx.ckpt_every)
+        g0 = ctx.plan.adjoint_checkpointed(g.contiguous())
         return g0, None, None, None, None
 
 

@@ -86,6 +86,9 @@ struct kzk_plan_s {
     void* seg;                  // segment store [(2 k)][batch][ny][nx/2]
     void* ckpt;                 // checkpoints  [n_ckpt][batch][ny][nx/2]
     long long seg_cap, ckpt_cap; // in arrays
+    long long ck_steps;         // forward run whose checkpoints are stored (0: none)
+    double ck_sigma0;
+    int ck_every;
     // batched plans (kzk_plan_create_batched): one sub-plan per instance
     int batched;
     std::vector<kzk_plan_s*>* subs;
@@ -294,8 +297,11 @@ ColArgs<T> col_args(const kzk_plan* p)
 // diag_hist_step: where C1 writes this step's diagnostics (nullable).
 // vs_out / b1_out / b2_out: destinations (default: plan workspace).
 template <typename T>
-kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_step, void* V, void* vs)
+kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_step, void* V, void* vs,
+                void* V_out = nullptr)
 {
+    // V is read-only; the result goes to V_out (default: in place)
+    if (!V_out) V_out = V;
     RowArgs<T> r1 = row_args<T>(p, V, p->b1, sigma, diag_hist_step ? p->diag_rows : nullptr);
     KZK_TRY((launch_row<T, ROW_RHS>(p, r1, st)));
     ColArgs<T> c1 = col_args<T>(p);
@@ -314,7 +320,7 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     c2.a = (const cx<T>*)p->b1;
     c2.b = (const cx<T>*)p->b2;
     c2.c = (const cx<T>*)vs;
-    c2.out = (cx<T>*)V;
+    c2.out = (cx<T>*)V_out;
     c2.Ta = (const cx<T>*)p->P2;
     KZK_TRY((launch_col<T, COL_STAGE2>(p, c2, st)));
     return KZK_OK;
@@ -548,47 +554,80 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* Vn, const void* V
 }
 
 template <typename T>
-kzk_status adjoint_impl(kzk_plan* p, const void* u0, const void* g_end, void* g0, long long n_steps,
-                        double sigma0, int ckpt_every, cudaStream_t st)
+kzk_status adjoint_buffers(kzk_plan* p, long long n_steps, int k)
 {
-    const size_t arr = (size_t)p->batch * p->inst_stride * p->csz;   // bytes of one spectral array
+    const size_t arr = (size_t)p->batch * p->inst_stride * p->csz;
     if (!p->lam) {
         KZK_CUDA(cudaMalloc(&p->lam, arr));
         KZK_CUDA(cudaMalloc(&p->mu, arr));
         KZK_CUDA(cudaMalloc(&p->nu, arr));
         KZK_CUDA(cudaMalloc(&p->ls, arr));
     }
-    const long long k = ckpt_every;
     const long long n_ckpt = (n_steps + k - 1) / k;
     KZK_TRY(ensure_buf(&p->ckpt, &p->ckpt_cap, std::max(1LL, n_ckpt), arr));
-    KZK_TRY(ensure_buf(&p->seg, &p->seg_cap, 2 * std::min(k, std::max(1LL, n_steps)), arr));
-    auto arr_at = [&](void* base, long long i) { return (void*)((char*)base + (size_t)i * arr); };
+    // segment store: V^n and V*^n of every step of a segment, plus one slot
+    // for the state after the segment
+    KZK_TRY(ensure_buf(&p->seg, &p->seg_cap, 2 * std::min((long long)k, std::max(1LL, n_steps)) + 1, arr));
+    return KZK_OK;
+}
 
-    // forward sweep: checkpoints of the spectral state at steps 0, k, 2k, ...
+// Forward sweep from the physical u0 keeping the spectral state at steps
+// 0, k, 2k, ... in p->ckpt; the final state is left in p->V.
+template <typename T>
+kzk_status forward_ckpt(kzk_plan* p, const void* u0, long long n_steps, double sigma0, int k, cudaStream_t st)
+{
+    KZK_TRY(adjoint_buffers<T>(p, n_steps, k));
+    const size_t arr = (size_t)p->batch * p->inst_stride * p->csz;
     KZK_TRY(to_spectral<T>(p, u0, p->V, st));
     for (long long s = 0; s < n_steps; s++) {
-        if (s % k == 0) KZK_CUDA(cudaMemcpyAsync(arr_at(p->ckpt, s / k), p->V, arr, cudaMemcpyDeviceToDevice, st));
+        if (s % k == 0)
+            KZK_CUDA(cudaMemcpyAsync((char*)p->ckpt + (size_t)(s / k) * arr, p->V, arr, cudaMemcpyDeviceToDevice, st));
         KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, p->V, p->vs));
     }
-    // cotangent of the final state in spectral form
+    p->ck_steps = n_steps;
+    p->ck_sigma0 = sigma0;
+    p->ck_every = k;
+    return KZK_OK;
+}
+
+// Reverse sweep over the stored checkpoints: per segment, recompute the
+// stage states (V^n, V*^n) into the segment store -- each step reads its
+// V^n in place and writes V^{n+1} into the next slot, so nothing is copied --
+// then apply the transposed steps in reverse order.
+template <typename T>
+kzk_status reverse_sweep(kzk_plan* p, const void* g_end, void* g0, cudaStream_t st)
+{
+    const long long n_steps = p->ck_steps, k = p->ck_every;
+    const double sigma0 = p->ck_sigma0;
+    const long long n_ckpt = (n_steps + k - 1) / k;
+    const size_t arr = (size_t)p->batch * p->inst_stride * p->csz;
+    auto arr_at = [&](void* base, long long i) { return (void*)((char*)base + (size_t)i * arr); };
     KZK_TRY(to_spectral<T>(p, g_end, p->lam, st));
     for (long long c = n_ckpt - 1; c >= 0; c--) {
         const long long s0 = c * k, s1 = std::min(n_steps, s0 + k);
-        // recompute the segment, storing (V^n, V*^n) per step
-        KZK_CUDA(cudaMemcpyAsync(p->V, arr_at(p->ckpt, c), arr, cudaMemcpyDeviceToDevice, st));
         for (long long s = s0; s < s1; s++) {
-            void* Vn = arr_at(p->seg, 2 * (s - s0));
-            void* Vs = arr_at(p->seg, 2 * (s - s0) + 1);
-            KZK_CUDA(cudaMemcpyAsync(Vn, p->V, arr, cudaMemcpyDeviceToDevice, st));
-            KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, p->V, Vs));
+            const long long i = s - s0;
+            void* Vn = i == 0 ? arr_at(p->ckpt, c) : arr_at(p->seg, 2 * i);
+            void* Vs = arr_at(p->seg, 2 * i + 1);
+            void* Vnext = s + 1 < s1 ? arr_at(p->seg, 2 * (i + 1)) : p->V;
+            KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, Vn, Vs, Vnext));
         }
         for (long long s = s1 - 1; s >= s0; s--) {
-            const void* Vn = arr_at(p->seg, 2 * (s - s0));
-            const void* Vs = arr_at(p->seg, 2 * (s - s0) + 1);
+            const long long i = s - s0;
+            const void* Vn = i == 0 ? arr_at(p->ckpt, c) : arr_at(p->seg, 2 * i);
+            const void* Vs = arr_at(p->seg, 2 * i + 1);
             KZK_TRY(adjoint_step<T>(p, sigma0 + (double)s * p->dt, Vn, Vs, st));
         }
     }
     return to_physical<T>(p, p->lam, g0, 1.0, nullptr, st);
+}
+
+template <typename T>
+kzk_status adjoint_impl(kzk_plan* p, const void* u0, const void* g_end, void* g0, long long n_steps,
+                        double sigma0, int ckpt_every, cudaStream_t st)
+{
+    KZK_TRY(forward_ckpt<T>(p, u0, n_steps, sigma0, ckpt_every, st));
+    return reverse_sweep<T>(p, g_end, g0, st);
 }
 
 }  // namespace
@@ -1235,6 +1274,31 @@ kzk_status kzk_get_tables(kzk_plan* p, double* E, double* Phi1, double* Phi2)
         }
     }
     return KZK_OK;
+}
+
+kzk_status kzk_advance_checkpointed(kzk_plan* p, void* u, int64_t n_steps, double sigma0, int32_t ckpt_every,
+                                    void* stream)
+{
+    if (!p || !u) return fail(KZK_ERR_ARG, "plan or u is NULL");
+    if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
+    if (n_steps < 1 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    p->ck_steps = 0;
+    if (p->prec == KZK_FP64) {
+        KZK_TRY(forward_ckpt<double>(p, u, n_steps, sigma0, ckpt_every, st));
+        return to_physical<double>(p, p->V, u, 1.0, nullptr, st);
+    }
+    KZK_TRY(forward_ckpt<float>(p, u, n_steps, sigma0, ckpt_every, st));
+    return to_physical<float>(p, p->V, u, 1.0, nullptr, st);
+}
+
+kzk_status kzk_adjoint_checkpointed(kzk_plan* p, const void* g_end, void* g0, void* stream)
+{
+    if (!p || !g_end || !g0) return fail(KZK_ERR_ARG, "NULL argument");
+    if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
+    if (p->ck_steps < 1) return fail(KZK_ERR_STATE, "no checkpointed forward run stored in this plan");
+    cudaStream_t st = (cudaStream_t)stream;
+    return p->prec == KZK_FP64 ? reverse_sweep<double>(p, g_end, g0, st) : reverse_sweep<float>(p, g_end, g0, st);
 }
 
 kzk_status kzk_adjoint(kzk_plan* p, const void* u0, const void* g_end, void* g0, int64_t n_steps, double sigma0,
