@@ -27,6 +27,11 @@
 namespace kzk {
 
 // Gradient of one reconstruction w.r.t. v_{-2..2}, scaled by w: g[j] = w dF/dv_j.
+// In FP64 all four reciprocals it needs (1/sum a and 1/(eps + beta_r)) come
+// from one division: with e_r = eps + beta_r and S = sum a_r
+// (a_r = d_r prod_{s!=r} e_s^2), r = 1 / (S e0 e1 e2) gives 1/S = r e0 e1 e2
+// and 1/e_0 = r S e1 e2, etc.  In FP32 that product can underflow, so the
+// reciprocals are taken separately.
 template <typename T>
 __device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps, T w, T* g)
 {
@@ -43,13 +48,24 @@ __device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps
     const T e2 = eps + fma(c13 * sc, sc, T(0.25) * tc * tc);
     const T t0 = e0 * e0, t1 = e1 * e1, t2 = e2 * e2;
     const T a0 = T(0.1) * t1 * t2, a1 = T(0.6) * t0 * t2, a2 = T(0.3) * t0 * t1;
-    const T inv = T(1) / (a0 + a1 + a2);
+    const T S = a0 + a1 + a2;
+    T inv, ie0, ie1, ie2;                                    // 1/S, 1/e_r
+    if constexpr (sizeof(T) == 8) {
+        const T e01 = e0 * e1;
+        const T r = T(1) / (S * e01 * e2);                   // >= eps^7: fine in FP64
+        inv = r * (e01 * e2);
+        const T rS = r * S;
+        ie0 = rS * (e1 * e2); ie1 = rS * (e0 * e2); ie2 = rS * e01;
+    } else {
+        // eps^7 underflows FP32: separate hardware reciprocals
+        inv = __frcp_rn(S); ie0 = __frcp_rn(e0); ie1 = __frcp_rn(e1); ie2 = __frcp_rn(e2);
+    }
     const T o0 = a0 * inv, o1 = a1 * inv, o2 = a2 * inv;     // omega_r
     const T F = o0 * q0 + o1 * q1 + o2 * q2;
     // c_r = -2 omega_r (q_r - F) / e_r
-    const T c0 = T(-2) * o0 * (q0 - F) / e0;
-    const T c1 = T(-2) * o1 * (q1 - F) / e1;
-    const T c2 = T(-2) * o2 * (q2 - F) / e2;
+    const T c0 = T(-2) * o0 * (q0 - F) * ie0;
+    const T c1 = T(-2) * o1 * (q1 - F) * ie1;
+    const T c2 = T(-2) * o2 * (q2 - F) * ie2;
     const T A0 = T(2) * c13 * sa * c0, B0 = T(0.5) * ta * c0;
     const T A1 = T(2) * c13 * sb * c1, B1 = T(0.5) * tb * c1;
     const T A2 = T(2) * c13 * sc * c2, B2 = T(0.5) * tc * c2;
@@ -60,13 +76,13 @@ __device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps
     g[4] = w * (-s6 * o2 + A2 + B2);
 }
 
-// J_WENO(u)^T mu over the points [k0, k0+Q) of one periodic row: own-point
-// sums go to g[], the two contributions left of k0 to spl[0..1] and the three
-// right of k0+Q-1 to spr[0..2] (added by the neighbours afterwards).
+// J_WENO(u)^T mu over the points [k0, k0+Q) of one periodic row (u, mu, g:
+// padded row buffers of nx reals): own-point sums go to g, the two
+// contributions left of k0 to spl[0..1] and the three right of k0+Q-1 to
+// spr[0..2] (added by the neighbours afterwards).
 template <typename T>
-__device__ __forceinline__ void weno_row_chunk_T(const T* __restrict__ u, const T* __restrict__ mu,
-                                                 T* __restrict__ g, T* spl, T* spr, int nx, int k0, int Q,
-                                                 const WenoCoef<T>& c)
+__device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu, cx<T>* g, T* spl, T* spr,
+                                                 int nx, int k0, int Q, const WenoCoef<T>& c)
 {
     const int msk = nx - 1;
     const T half = T(0.5);
@@ -74,7 +90,7 @@ __device__ __forceinline__ void weno_row_chunk_T(const T* __restrict__ u, const 
     // window slot s <-> point k - 2 + s for interface k + 1/2, starting at k = k0
 #pragma unroll
     for (int s = 0; s < 6; s++) {
-        const T v = u[(k0 - 2 + s) & msk];
+        const T v = ld_real<T, true>(u, (k0 - 2 + s) & msk);
         const T f = -half * c.B * v * v;
         fp[s] = half * fma(c.alpha, v, f);
         fm[s] = half * fma(-c.alpha, v, f);
@@ -82,10 +98,10 @@ __device__ __forceinline__ void weno_row_chunk_T(const T* __restrict__ u, const 
         dm[s] = half * (-c.alpha - c.B * v);
         acc[s] = T(0);
     }
-    T mk_ = mu[k0 & msk];
+    T mk_ = ld_real<T, true>(mu, k0 & msk);
     for (int i = 0; i < Q; i++) {
         const int k = k0 + i;
-        const T mk1 = mu[(k + 1) & msk];
+        const T mk1 = ld_real<T, true>(mu, (k + 1) & msk);
         const T psi = (mk1 - mk_) * c.inv_dtau;
         mk_ = mk1;
         T gp[5], gm[5];
@@ -98,12 +114,12 @@ __device__ __forceinline__ void weno_row_chunk_T(const T* __restrict__ u, const 
         // point k - 2 is complete
         const int pt = k - 2;
         if (pt < k0) spl[pt - (k0 - 2)] = acc[0];
-        else g[pt] = acc[0];
+        else st_real<T, true>(g, pt, acc[0]);
 #pragma unroll
         for (int s = 0; s < 5; s++) {
             fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; dp[s] = dp[s + 1]; dm[s] = dm[s + 1]; acc[s] = acc[s + 1];
         }
-        const T v = u[(k + 4) & msk];
+        const T v = ld_real<T, true>(u, (k + 4) & msk);
         const T f = -half * c.B * v * v;
         fp[5] = half * fma(c.alpha, v, f);
         fm[5] = half * fma(-c.alpha, v, f);
@@ -115,7 +131,7 @@ __device__ __forceinline__ void weno_row_chunk_T(const T* __restrict__ u, const 
 #pragma unroll
     for (int s = 0; s < 5; s++) {
         const int pt = k0 + Q - 2 + s;
-        if (pt < k0 + Q) g[pt] = acc[s];
+        if (pt < k0 + Q) st_real<T, true>(g, pt, acc[s]);
         else spr[pt - (k0 + Q)] = acc[s];
     }
 }
@@ -126,7 +142,8 @@ struct AdjRowArgs {
     const cx<T>* v;         // state the step linearises at (V* or V^n), packed spectral
     const cx<T>* l;         // additive term (lam' or lam_lin), packed spectral
     cx<T>* out;             // l + F(J_G(u)^T m) / nx
-    const cx<T>* tw;
+    const cx<T>* tw;        // exp(-2 pi i k / nx) (real-FFT pre/post-processing)
+    const cx<T>* tws;       // staged twiddles of the length-nx/2 FFT
     int log2nx;
     long long inst_stride;
     WenoCoef<T> wc;
@@ -137,53 +154,55 @@ struct AdjRowArgs {
 
 enum AdjRowMode { ADJ_ROW_2 = 0, ADJ_ROW_1 = 1 };
 
+// One row of J_G^T: C2R of the state row and of the cotangent row, WENO5
+// transpose, R2C, plus the absorption-deviation term and the additive row.
+// Three padded buffers of nx reals, then the spill slots of the sweep.
 template <typename T, int PPT, int MODE>
-__global__ void __launch_bounds__(512) adj_row_kernel(AdjRowArgs<T> a)
+__global__ void __launch_bounds__(ROW_MAX_THREADS) adj_row_kernel(AdjRowArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int nx = 1 << a.log2nx, n = nx >> 1, log2n = a.log2nx - 1;
     const int row = blockIdx.x, inst = blockIdx.y;
+    const int bl = row_buf_len(n);
     cx<T>* U = reinterpret_cast<cx<T>*>(smem_raw);
-    cx<T>* M = U + n;
-    cx<T>* G = M + n;
-    T* spl = reinterpret_cast<T*>(G + n);
+    cx<T>* M = U + bl;
+    cx<T>* G = M + bl;
+    T* spl = reinterpret_cast<T*>(G + bl);
     T* spr = spl + 2 * nthr;
     const long long base = (long long)inst * a.inst_stride + (long long)row * n;
+    const Tw<T> tw{a.tws, nullptr, -1};
 
-    for (int i = tid; i < n; i += nthr) { U[i] = a.v[base + i]; M[i] = a.m[base + i]; }
+    for (int i = tid; i < n; i += nthr) { U[padx(i)] = __ldcg(a.v + base + i); M[padx(i)] = __ldcg(a.m + base + i); }
     __syncthreads();
-    c2r_pre<T>(U, n, a.tw, tid, nthr);
-    c2r_pre<T>(M, n, a.tw, tid, nthr);
+    c2r_pre<T, true>(U, n, a.tw, tid, nthr);
+    c2r_pre<T, true>(M, n, a.tw, tid, nthr);
     __syncthreads();
-    fft_batched<T, PPT, false, true>(U, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
-    fft_batched<T, PPT, false, true>(M, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+    fft_batched<T, PPT, false, true, true>(U, log2n, 0, 1, 0, tw, tid, nthr);
+    fft_batched<T, PPT, false, true, true>(M, log2n, 0, 1, 0, tw, tid, nthr);
 
     const int Q = nx / nthr >= 4 ? nx / nthr : 4;
     const int nact = nx / Q;
     const int k0 = tid * Q;
-    T* gphys = reinterpret_cast<T*>(G);
-    if (tid < nact)
-        weno_row_chunk_T<T>(reinterpret_cast<const T*>(U), reinterpret_cast<const T*>(M), gphys,
-                            spl + 2 * tid, spr + 3 * tid, nx, k0, Q, a.wc);
+    if (tid < nact) weno_row_chunk_T<T>(U, M, G, spl + 2 * tid, spr + 3 * tid, nx, k0, Q, a.wc);
     __syncthreads();
     if (tid < nact) {
         const int left = (tid + nact - 1) % nact, right = (tid + 1) % nact;
         // neighbours' spills: right spill of the left neighbour covers k0..k0+2,
         // left spill of the right neighbour covers k0+Q-2, k0+Q-1
-        for (int s = 0; s < 3; s++) gphys[k0 + s] += spr[3 * left + s];
-        gphys[(k0 + Q - 2)] += spl[2 * right + 0];
-        gphys[(k0 + Q - 1)] += spl[2 * right + 1];
+        for (int s = 0; s < 3; s++) st_real<T, true>(G, k0 + s, ld_real<T, true>(G, k0 + s) + spr[3 * left + s]);
+        st_real<T, true>(G, k0 + Q - 2, ld_real<T, true>(G, k0 + Q - 2) + spl[2 * right + 0]);
+        st_real<T, true>(G, k0 + Q - 1, ld_real<T, true>(G, k0 + Q - 1) + spl[2 * right + 1]);
     }
     __syncthreads();
-    fft_batched<T, PPT, false, false>(G, log2n, 0, 1, 0, a.tw, a.log2nx, tid, nthr);
+    fft_batched<T, PPT, false, false, true>(G, log2n, 0, 1, 0, tw, tid, nthr);
     for (int k = tid; k <= n / 2; k += nthr) {
         cx<T> xk, xnk;
-        r2c_post_pair<T>(G, n, k, a.tw, xk, xnk);
+        r2c_post_pair<T, true>(G, n, k, a.tw, xk, xnk);
         xk = scale<T>(xk, a.inv_nx);
         xnk = scale<T>(xnk, a.inv_nx);
-        const cx<T> mk0 = a.m[base + k];
-        const cx<T> lk = a.l[base + k];
+        const cx<T> mk0 = __ldcg(a.m + base + k);
+        const cx<T> lk = __ldcg(a.l + base + k);
         if (k == 0) {
             const T kN = a.kscale * T(n);
             xk.y -= a.dA * kN * kN * mk0.y;
@@ -195,10 +214,10 @@ __global__ void __launch_bounds__(512) adj_row_kernel(AdjRowArgs<T> a)
             a.out[base + k] = add<T>(lk, xk);
             if (2 * k != n) {
                 const T kt2 = a.kscale * T(n - k);
-                const cx<T> mk2 = a.m[base + n - k];
+                const cx<T> mk2 = __ldcg(a.m + base + n - k);
                 xnk.x -= a.dA * kt2 * kt2 * mk2.x;
                 xnk.y -= a.dA * kt2 * kt2 * mk2.y;
-                a.out[base + n - k] = add<T>(a.l[base + n - k], xnk);
+                a.out[base + n - k] = add<T>(__ldcg(a.l + base + n - k), xnk);
             }
         }
     }
@@ -207,7 +226,7 @@ __global__ void __launch_bounds__(512) adj_row_kernel(AdjRowArgs<T> a)
 template <typename T>
 size_t adj_row_smem_bytes(int n, int nthr)
 {
-    return 3 * (size_t)n * sizeof(cx<T>) + 5 * (size_t)nthr * sizeof(T);
+    return 3 * (size_t)row_buf_len(n) * sizeof(cx<T>) + 5 * (size_t)nthr * sizeof(T);
 }
 
 enum AdjColMode { ADJ_COL_2 = 0, ADJ_COL_1 = 1 };
@@ -221,27 +240,27 @@ struct AdjColArgs {
     const cx<T>* Ta;    // ADJ_COL_2: P2';   ADJ_COL_1: E'
     const cx<T>* Tb;    // ADJ_COL_1: P1'
     T sa, sb;           // rescale of conj(Ta), conj(Tb)
-    const cx<T>* tw;
+    const cx<T>* tw;    // staged twiddles of the length-ny FFT
     int log2ny, log2n, log2tc;
     long long inst_stride;
 };
 
-// conj(M) applied to the column-FFT'd tile (column 0 packs two real tables).
+// conj(M) (real for the packed column) applied to value z of a column-FFT'd
+// tile; zm is the value at row ny - l (used by the packed column m = 0).
 template <typename T>
-__device__ __forceinline__ cx<T> apply_mult_conj(const cx<T>* __restrict__ tab, const cx<T>* S, int l, int c, int m,
-                                                 int ny, int n, int log2tc, T s)
+__device__ __forceinline__ cx<T> conj_mult_entry(cx<T> M, cx<T> z, cx<T> zm, bool packed)
 {
-    const int lf = l <= (ny >> 1) ? l : ny - l;
-    const cx<T> M = scale<T>(tab[(long long)lf * n + m], s);
-    const cx<T> z = S[(l << log2tc) + c];
-    if (m != 0) return mulc<T>(z, M);
-    const cx<T> zm = S[(((ny - l) & (ny - 1)) << log2tc) + c];
+    if (!packed) return mulc<T>(z, M);
     const T h = T(0.5) * (M.x + M.y), g = T(0.5) * (M.x - M.y);
     return mk<T>(h * z.x + g * zm.x, h * z.y - g * zm.y);
 }
 
+// ADJ_COL_2: out = IFFT(sa conj(Ta) FFT(a)).
+// ADJ_COL_1: z = FFT(a); out = IFFT(sa conj(Ta) z); out2 = IFFT(sb conj(Tb) z) - b.
+// Same tile organisation as the forward column kernel: padded tiles (two for
+// ADJ_COL_1), staged twiddles in shared memory, packed column 0 by pairs.
 template <typename T, int PPT, int MODE>
-__global__ void __launch_bounds__(col_max_threads<T>()) adj_col_kernel(AdjColArgs<T> a)
+__global__ void __launch_bounds__(col_max_threads<T>(), sizeof(T) == 4 ? 2 : 1) adj_col_kernel(AdjColArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* S = reinterpret_cast<cx<T>*>(smem_raw);
@@ -250,46 +269,51 @@ __global__ void __launch_bounds__(col_max_threads<T>()) adj_col_kernel(AdjColArg
     const int m0 = blockIdx.x * TC, inst = blockIdx.y;
     const long long ibase = (long long)inst * a.inst_stride;
     const int total = ny << a.log2tc;
+    cx<T>* tws = reinterpret_cast<cx<T>*>(smem_raw + col_tile_area<T>(ny, a.log2tc, nthr));
+    for (int i = tid; i < ny; i += nthr) tws[i] = a.tw[i];
+    const Tw<T> tw{tws, nullptr, -1};
+    cx<T>* SA = S;
+    cx<T>* SB = S + (total + (total >> 4));
     auto gidx = [&](int e) -> long long {
         return ibase + (long long)(e >> a.log2tc) * n + m0 + (e & (TC - 1));
     };
-    cx<T> acc[PPT], acc2[MODE == ADJ_COL_1 ? PPT : 1];
 
-    for (int e = tid; e < total; e += nthr) S[e] = a.a[gidx(e)];
+    for (int e = tid; e < total; e += nthr) SA[padx(e)] = __ldcg(a.a + gidx(e));
     __syncthreads();
-    fft_batched<T, PPT, true, false>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
-#pragma unroll
-    for (int q = 0; q < PPT; q++) {
-        const int e = tid + q * nthr;
-        if (e < total) {
-            const int l = e >> a.log2tc, c = e & (TC - 1);
-            acc[q] = apply_mult_conj<T>(a.Ta, S, l, c, m0 + c, ny, n, a.log2tc, a.sa);
-            if constexpr (MODE == ADJ_COL_1)
-                acc2[q] = apply_mult_conj<T>(a.Tb, S, l, c, m0 + c, ny, n, a.log2tc, a.sb);
+    fft_batched<T, PPT, true, false, true, false>(SA, a.log2ny, a.log2tc, TC, 1, tw, tid, nthr);
+    for (int e = tid; e < total; e += nthr) {
+        const int l = e >> a.log2tc, c = e & (TC - 1), m = m0 + c;
+        if (m == 0) continue;
+        const int lf = l <= (ny >> 1) ? l : ny - l;
+        const long long ti = (long long)lf * n + m;
+        const cx<T> z = SA[padx(e)];
+        if constexpr (MODE == ADJ_COL_1) SB[padx(e)] = mulc<T>(z, scale<T>(a.Tb[ti], a.sb));
+        SA[padx(e)] = mulc<T>(z, scale<T>(a.Ta[ti], a.sa));
+    }
+    if (m0 == 0) {
+        for (int l = tid; l <= (ny >> 1); l += nthr) {
+            const int lm = (ny - l) & (ny - 1);
+            const long long ti = (long long)l * n;
+            const int e = padx(l << a.log2tc), em = padx(lm << a.log2tc);
+            const cx<T> z = SA[e], zm = SA[em];
+            if constexpr (MODE == ADJ_COL_1) {
+                const cx<T> Mb = scale<T>(a.Tb[ti], a.sb);
+                SB[e] = conj_mult_entry<T>(Mb, z, zm, true);
+                if (lm != l) SB[em] = conj_mult_entry<T>(Mb, zm, z, true);
+            }
+            const cx<T> Ma = scale<T>(a.Ta[ti], a.sa);
+            SA[e] = conj_mult_entry<T>(Ma, z, zm, true);
+            if (lm != l) SA[em] = conj_mult_entry<T>(Ma, zm, z, true);
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PPT; q++) {
-        const int e = tid + q * nthr;
-        if (e < total) S[e] = acc[q];
-    }
-    __syncthreads();
-    fft_batched<T, PPT, true, true>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
-    for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = S[e];
-    if constexpr (MODE == ADJ_COL_1) {
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PPT; q++) {
-            const int e = tid + q * nthr;
-            if (e < total) S[e] = acc2[q];
-        }
-        __syncthreads();
-        fft_batched<T, PPT, true, true>(S, a.log2ny, a.log2tc, TC, 1, a.tw, a.log2ny, tid, nthr);
-        for (int e = tid; e < total; e += nthr) {
-            const long long g = gidx(e);
-            a.out2[g] = sub<T>(S[e], a.b[g]);
-        }
+    fft_batched<T, PPT, true, true, true, false>(SA, a.log2ny, a.log2tc, TC, 1, tw, tid, nthr);
+    if constexpr (MODE == ADJ_COL_1)
+        fft_batched<T, PPT, true, true, true, false>(SB, a.log2ny, a.log2tc, TC, 1, tw, tid, nthr);
+    for (int e = tid; e < total; e += nthr) {
+        const long long g = gidx(e);
+        a.out[g] = SA[padx(e)];
+        if constexpr (MODE == ADJ_COL_1) a.out2[g] = sub<T>(SB[padx(e)], __ldcg(a.b + g));
     }
 }
 

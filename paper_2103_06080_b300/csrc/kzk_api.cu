@@ -488,6 +488,7 @@ AdjRowArgs<T> adj_row_args(const kzk_plan* p, const void* m, const void* v, cons
     a.l = (const cx<T>*)l;
     a.out = (cx<T>*)out;
     a.tw = (const cx<T>*)p->twr;
+    a.tws = (const cx<T>*)p->tws_row;
     a.log2nx = p->log2nx;
     a.inst_stride = p->inst_stride;
     const double Bs = B_of(p, sigma);
@@ -506,7 +507,7 @@ AdjColArgs<T> adj_col_args(const kzk_plan* p)
 {
     AdjColArgs<T> a;
     memset(&a, 0, sizeof(a));
-    a.tw = (const cx<T>*)p->twc_full;
+    a.tw = (const cx<T>*)p->twc;
     a.log2ny = p->log2ny;
     a.log2n = p->log2nx - 1;
     a.log2tc = p->log2tc;

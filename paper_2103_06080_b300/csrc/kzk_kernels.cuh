@@ -456,7 +456,7 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(col_max_threads<T>()) col_kernel(ColArgs<T> a)
+__global__ void __launch_bounds__(col_max_threads<T>(), sizeof(T) == 4 ? 2 : 1) col_kernel(ColArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     col_body<T, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);
