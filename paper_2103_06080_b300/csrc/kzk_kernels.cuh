@@ -152,6 +152,23 @@ __device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, cons
     }
 }
 
+// Row of n complex values from global memory into a padded shared buffer:
+// up to 8 loads per thread are issued before the shared stores, so each
+// thread keeps several requests in flight.
+template <typename T>
+__device__ __forceinline__ void load_row(const cx<T>* __restrict__ src, cx<T>* dst, int n, int tid, int nthr)
+{
+    int i = tid;
+    for (; i + 7 * nthr < n; i += 8 * nthr) {
+        cx<T> v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) v[q] = __ldcg(src + i + q * nthr);
+#pragma unroll
+        for (int q = 0; q < 8; q++) dst[padx(i + q * nthr)] = v[q];
+    }
+    for (; i < n; i += nthr) dst[padx(i)] = __ldcg(src + i);
+}
+
 // Padded length of one row buffer (n complex + one slot per 16).
 __host__ __device__ constexpr int row_buf_len(int n) { return n + (n >> 4); }
 
@@ -182,8 +199,8 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
 
     if constexpr (MODE == ROW_FWD) {
         // physical row -> packed half spectrum / nx
-        const T* src = reinterpret_cast<const T*>(a.in + base);
-        for (int i = tid; i < nx; i += nthr) st_real<T, true>(Y, i, __ldcg(src + i));
+        const cx<T>* src = a.in + base;                   // physical pairs (x_2i, x_2i+1)
+        load_row<T>(src, Y, n, tid, nthr);
         __syncthreads();
         fft_batched<T, ROW_PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
         for (int k = tid; k <= n / 2; k += nthr) {
@@ -194,7 +211,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
         }
     } else {
         // spectral row -> physical row in X
-        for (int i = tid; i < n; i += nthr) X[padx(i)] = __ldcg(a.in + base + i);
+        load_row<T>(a.in + base, X, n, tid, nthr);
         __syncthreads();
         c2r_pre<T, true>(X, n, a.tw, tid, nthr);
         __syncthreads();
@@ -380,10 +397,20 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
                 d[3] = tmp[3];
             }
         }
-        for (int e = tid; e < total; e += nthr) {
-            const long long g = gidx(e);
-            SA[padx(e)] = __ldcg(a.a + g);
-            SB[padx(e)] = __ldcg(a.b + g);
+        {
+            int e = tid;
+            for (; e + 3 * nthr < total; e += 4 * nthr) {
+                cx<T> va[4], vb[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) { va[q] = __ldcg(a.a + gidx(e + q * nthr)); vb[q] = __ldcg(a.b + gidx(e + q * nthr)); }
+#pragma unroll
+                for (int q = 0; q < 4; q++) { SA[padx(e + q * nthr)] = va[q]; SB[padx(e + q * nthr)] = vb[q]; }
+            }
+            for (; e < total; e += nthr) {
+                const long long g = gidx(e);
+                SA[padx(e)] = __ldcg(a.a + g);
+                SB[padx(e)] = __ldcg(a.b + g);
+            }
         }
         __syncthreads();
         // state tile: accurate transform; b1 tile: plain
@@ -424,9 +451,19 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
         fft_batched<T, COL_PPT, true, true, true, ACC>(SA, a.log2ny, a.log2tc, TC, 1, twa, tid, nthr);
         for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = SA[padx(e)];
     } else {
-        for (int e = tid; e < total; e += nthr) {
-            const long long g = gidx(e);
-            SA[padx(e)] = sub<T>(__ldcg(a.b + g), __ldcg(a.a + g));
+        {
+            int e = tid;
+            for (; e + 3 * nthr < total; e += 4 * nthr) {
+                cx<T> va[4], vb[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) { va[q] = __ldcg(a.a + gidx(e + q * nthr)); vb[q] = __ldcg(a.b + gidx(e + q * nthr)); }
+#pragma unroll
+                for (int q = 0; q < 4; q++) SA[padx(e + q * nthr)] = sub<T>(vb[q], va[q]);
+            }
+            for (; e < total; e += nthr) {
+                const long long g = gidx(e);
+                SA[padx(e)] = sub<T>(__ldcg(a.b + g), __ldcg(a.a + g));
+            }
         }
         __syncthreads();
         fft_batched<T, COL_PPT, true, false, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
@@ -448,15 +485,26 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
         }
         __syncthreads();
         fft_batched<T, COL_PPT, true, true, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
-        for (int e = tid; e < total; e += nthr) {
-            const long long g = gidx(e);
-            a.out[g] = add<T>(__ldcg(a.c + g), SA[padx(e)]);
+        {
+            int e = tid;
+            for (; e + 3 * nthr < total; e += 4 * nthr) {
+                cx<T> vc[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) vc[q] = __ldcg(a.c + gidx(e + q * nthr));
+#pragma unroll
+                for (int q = 0; q < 4; q++) a.out[gidx(e + q * nthr)] = add<T>(vc[q], SA[padx(e + q * nthr)]);
+            }
+            for (; e < total; e += nthr) {
+                const long long g = gidx(e);
+                a.out[g] = add<T>(__ldcg(a.c + g), SA[padx(e)]);
+            }
         }
     }
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(col_max_threads<T>(), sizeof(T) == 4 ? 2 : 1) col_kernel(ColArgs<T> a)
+__global__ void __launch_bounds__(col_max_threads<T>(), (sizeof(T) == 4 && MODE == COL_STAGE2) ? 2 : 1)
+    col_kernel(ColArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     col_body<T, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);

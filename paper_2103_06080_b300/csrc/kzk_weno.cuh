@@ -20,7 +20,8 @@
 //    that need it (a sliding window over the row);
 //  * the quotient sum a_r q_r / sum a_r is formed after multiplying numerator
 //    and denominator by prod (eps + beta_r)^2, so a_r -> d_r prod_{s != r} t_s;
-//  * the 1/6 of the candidate values q_r is folded into 1/dtau;
+//  * the 1/6 of the candidate values q_r is folded into 1/dtau, and common
+//    factors of the weights (16 in (eps + beta)^2, 10 in d_r) are dropped;
 //  * FP64: both halves F+ and F- share one division; FP32: two hardware
 //    reciprocals (the product of the two denominators could underflow).
 #pragma once
@@ -51,21 +52,23 @@ __device__ __forceinline__ void st_real(cx<T>* buf, int k, T v)
     else p[k] = v;
 }
 
-// (eps + beta)^2 of the left, centre and right indicators of the stencil
-// (fm1, f0, fp1) centred at c.
+// 16 (eps + beta)^2 of the left, centre and right indicators of the stencil
+// (fm1, f0, fp1) centred at c, formed as (4 eps + 4 beta)^2: the common factor
+// 16 cancels in the weights, and 4 beta = 13/3 S^2 + x^2 needs no 1/4.
+// eps4 = 4 eps.
 template <typename T>
-__device__ __forceinline__ void indicators(T fm1, T f0, T fp1, T eps, T& tl, T& tc, T& tr)
+__device__ __forceinline__ void indicators(T fm1, T f0, T fp1, T eps4, T& tl, T& tc, T& tr)
 {
     const T S = fm1 - T(2) * f0 + fp1;
     const T D = fp1 - fm1;
-    const T P = (T(13) / T(12)) * S * S;
+    const T P = ((T(13) / T(3)) * S) * S;
     const T xl = fma(T(2), S, D), xr = fma(T(-2), S, D);
-    const T bl = fma(T(0.25) * xl, xl, P);
-    const T bc = fma(T(0.25) * D, D, P);
-    const T br = fma(T(0.25) * xr, xr, P);
-    tl = (eps + bl) * (eps + bl);
-    tc = (eps + bc) * (eps + bc);
-    tr = (eps + br) * (eps + br);
+    const T bl = eps4 + fma(xl, xl, P);
+    const T bc = eps4 + fma(D, D, P);
+    const T br = eps4 + fma(xr, xr, P);
+    tl = bl * bl;
+    tc = bc * bc;
+    tr = br * br;
 }
 
 // 6 * numerator and denominator of one reconstruction from v_{-2..2} and the
@@ -76,9 +79,10 @@ __device__ __forceinline__ void rec_parts(T vm2, T vm1, T v0, T v1, T v2, T t0, 
     const T q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0));
     const T q1 = fma(T(5), v0, fma(T(2), v1, -vm1));
     const T q2 = fma(T(2), v0, fma(T(5), v1, -v2));
-    const T a0 = T(0.1) * (t1 * t2);
-    const T a1 = T(0.6) * (t0 * t2);
-    const T a2 = T(0.3) * (t0 * t1);
+    // linear weights 1/10, 6/10, 3/10 scaled by 10 (the factor cancels)
+    const T a0 = t1 * t2;
+    const T a1 = T(6) * (t0 * t2);
+    const T a2 = T(3) * (t0 * t1);
     den = a0 + a1 + a2;
     num6 = fma(a0, q0, fma(a1, q1, a2 * q2));
 }
@@ -106,6 +110,7 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
     const int msk = nx - 1;
     const T half = T(0.5);
     const T scale = -c.inv_dtau * (T(1) / T(6));
+    const T eps4 = T(4) * c.eps;
     T fp[6], fm[6];
     auto load = [&](int kk, T& p, T& m) {
         const T v = ld_real<T, PAD>(u, kk & msk);
@@ -120,11 +125,11 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
     for (int s = 0; s < 5; s++) load(k - 3 + s, fp[s + 1], fm[s + 1]);   // points k0-4 .. k0
     T tLp3, tLp2, tLp1, tCp2, tCp1, tRp1, tLm2, tLm1, tCm1, tx;
     // centre k0 - 2 (points k0-3, k0-2, k0-1 = slots 2, 3, 4)
-    indicators<T>(fp[2], fp[3], fp[4], c.eps, tLp2, tx, tx);
-    indicators<T>(fm[2], fm[3], fm[4], c.eps, tx, tx, tx);
+    indicators<T>(fp[2], fp[3], fp[4], eps4, tLp2, tx, tx);
+    indicators<T>(fm[2], fm[3], fm[4], eps4, tx, tx, tx);
     // centre k0 - 1 (slots 3, 4, 5)
-    indicators<T>(fp[3], fp[4], fp[5], c.eps, tLp1, tCp1, tx);
-    indicators<T>(fm[3], fm[4], fm[5], c.eps, tLm1, tx, tx);
+    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tx);
+    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tx, tx);
     // age the history by one centre before computing centre k0
     tLp3 = tLp2; tLp2 = tLp1; tCp2 = tCp1;
     tLm2 = tLm1;
@@ -132,8 +137,8 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
     for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
     load(k0 + 1, fp[5], fm[5]);                                           // slots: points k0-3 .. k0+1
     // centre k0 (slots 3, 4, 5)
-    indicators<T>(fp[3], fp[4], fp[5], c.eps, tLp1, tCp1, tRp1);
-    indicators<T>(fm[3], fm[4], fm[5], c.eps, tLm1, tCm1, tx);
+    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tRp1);
+    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tCm1, tx);
     // loop invariant at the top of iteration k: tX1 = centre k+1, tX2 = centre
     // k, tLp3 = centre k-1; the body adds centre k+2
     T Fprev = 0;
@@ -143,8 +148,8 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
         for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
         load(k + 3, fp[5], fm[5]);
         T tLpN, tCpN, tRpN, tLmN, tCmN, tRmN;
-        indicators<T>(fp[3], fp[4], fp[5], c.eps, tLpN, tCpN, tRpN);
-        indicators<T>(fm[3], fm[4], fm[5], c.eps, tLmN, tCmN, tRmN);
+        indicators<T>(fp[3], fp[4], fp[5], eps4, tLpN, tCpN, tRpN);
+        indicators<T>(fm[3], fm[4], fm[5], eps4, tLmN, tCmN, tRmN);
         // at this point tX1 refer to centre k+1, tX2 to centre k, tLp3 to k-1.
         // interface k+1/2: + side left(k-1), centre(k), right(k+1);
         //                  - side right(k+2), centre(k+1), left(k)
