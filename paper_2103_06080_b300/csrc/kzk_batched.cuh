@@ -101,28 +101,25 @@ __device__ __forceinline__ int find_inst(const int* prefix, int n, int item)
     return lo;
 }
 
-// Task bodies behind call boundaries: each gets its own register allocation
-// instead of the union of all of them inside one kernel.
-template <typename T, int MODE>
-__device__ __noinline__ void row_task(const RowArgs<T>& a, int row, unsigned char* smem)
-{
-    row_body<T, MODE>(a, row, 0, smem);
-}
-template <typename T, int MODE>
-__device__ __noinline__ void col_task(const ColArgs<T>& a, int tile, unsigned char* smem)
-{
-    col_body<T, MODE>(a, tile, 0, smem);
-}
+// The arguments of the current task are staged in shared memory (one copy
+// per CTA), so the inlined bodies read them like the standalone kernels read
+// their constant-bank parameters instead of holding them in registers.
+template <typename T>
+union TaskArgs {
+    RowArgs<T> row;
+    ColArgs<T> col;
+};
 
 template <typename T, int MODE>
-__device__ __forceinline__ void batched_rows(const BatchArgs<T>& B, int step, unsigned char* smem)
+__device__ __forceinline__ void batched_rows(const BatchArgs<T>& B, int step, unsigned char* smem, TaskArgs<T>* targs)
 {
     const int total = __ldg(B.row_prefix + B.n_inst);
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int i = find_inst(B.row_prefix, B.n_inst, item);
+        const int row = item - __ldg(B.row_prefix + i);
+        if (threadIdx.x == 0) {
         const BatchInst<T>& I = B.inst[i];
         RowArgs<T> a = I.row;
-        const int row = item - __ldg(B.row_prefix + i);
         if (MODE == ROW_FWD) {
             a.in = I.u; a.out = I.V; a.diag_rows = nullptr;
             a.out_scale = T(1) / T(1 << a.log2nx);            // V = F(u) / nx
@@ -137,20 +134,24 @@ __device__ __forceinline__ void batched_rows(const BatchArgs<T>& B, int step, un
             a.out = stage == 0 ? I.b1 : I.b2;
             a.diag_rows = stage == 0 ? I.diag_rows : nullptr;
         }
-        row_task<T, MODE>(a, row, smem);
+        targs->row = a;
+        }
+        __syncthreads();
+        row_body<T, MODE>(targs->row, row, 0, smem);
         __syncthreads();
     }
 }
 
 template <typename T, int MODE>
-__device__ __forceinline__ void batched_cols(const BatchArgs<T>& B, int s, unsigned char* smem)
+__device__ __forceinline__ void batched_cols(const BatchArgs<T>& B, int s, unsigned char* smem, TaskArgs<T>* targs)
 {
     const int total = __ldg(B.col_prefix + B.n_inst);
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int i = find_inst(B.col_prefix, B.n_inst, item);
+        const int tile = item - __ldg(B.col_prefix + i);
+        if (threadIdx.x == 0) {
         const BatchInst<T>& I = B.inst[i];
         ColArgs<T> a = I.col;
-        const int tile = item - __ldg(B.col_prefix + i);
         if (MODE == COL_STAGE1) {
             a.a = I.V; a.b = I.b1; a.out = I.vs;
             a.Ta = I.E; a.Ta_lo = I.E_lo; a.Tb = I.P1;
@@ -161,9 +162,26 @@ __device__ __forceinline__ void batched_cols(const BatchArgs<T>& B, int s, unsig
             a.Ta = I.P2;
             a.diag_rows = nullptr;
         }
-        col_task<T, MODE>(a, tile, smem);
+        targs->col = a;
+        }
+        __syncthreads();
+        col_body<T, MODE>(targs->col, tile, 0, smem);
         __syncthreads();
     }
+}
+
+// One call per pass: the task loop and its body are register-allocated on
+// their own (like a standalone kernel) instead of as part of one function
+// holding every body.
+template <typename T, int MODE>
+__device__ __noinline__ void pass_rows(const BatchArgs<T>* B, int step, unsigned char* smem, TaskArgs<T>* targs)
+{
+    batched_rows<T, MODE>(*B, step, smem, targs);
+}
+template <typename T, int MODE>
+__device__ __noinline__ void pass_cols(const BatchArgs<T>* B, int s, unsigned char* smem, TaskArgs<T>* targs)
+{
+    batched_cols<T, MODE>(*B, s, smem, targs);
 }
 
 constexpr int BATCH_THREADS = 512;
@@ -173,19 +191,20 @@ __global__ void __launch_bounds__(BATCH_THREADS, 1) batched_kernel(BatchArgs<T> 
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sflag;
-    batched_rows<T, ROW_FWD>(B, -1, smem);
+    __shared__ TaskArgs<T> targs;
+    pass_rows<T, ROW_FWD>(&B, -1, smem, &targs);
     if (!grid_sync(B, &sflag)) return;
     for (int s = 0; s < B.n_steps; s++) {
-        batched_rows<T, ROW_RHS>(B, 2 * s, smem);
+        pass_rows<T, ROW_RHS>(&B, 2 * s, smem, &targs);
         if (!grid_sync(B, &sflag)) return;
-        batched_cols<T, COL_STAGE1>(B, s, smem);
+        pass_cols<T, COL_STAGE1>(&B, s, smem, &targs);
         if (!grid_sync(B, &sflag)) return;
-        batched_rows<T, ROW_RHS>(B, 2 * s + 1, smem);
+        pass_rows<T, ROW_RHS>(&B, 2 * s + 1, smem, &targs);
         if (!grid_sync(B, &sflag)) return;
-        batched_cols<T, COL_STAGE2>(B, s, smem);
+        pass_cols<T, COL_STAGE2>(&B, s, smem, &targs);
         if (!grid_sync(B, &sflag)) return;
     }
-    batched_rows<T, ROW_INV>(B, -1, smem);
+    pass_rows<T, ROW_INV>(&B, -1, smem, &targs);
     if (!grid_sync(B, &sflag)) return;
     // final diagnostics: CTA i reduces the rows of instance i (fixed order)
     for (int i = blockIdx.x; i < B.n_inst; i += gridDim.x) {
