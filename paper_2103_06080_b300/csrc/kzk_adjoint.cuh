@@ -252,7 +252,7 @@ __device__ __forceinline__ cx<T> conj_mult_entry(cx<T> M, cx<T> z, cx<T> zm, boo
 {
     if (!packed) return mulc<T>(z, M);
     const T h = T(0.5) * (M.x + M.y), g = T(0.5) * (M.x - M.y);
-    return mk<T>(h * z.x + g * zm.x, h * z.y - g * zm.y);
+    return mk<T>(fma(h, z.x, g * zm.x), fma(h, z.y, -(g * zm.y)));
 }
 
 // ADJ_COL_2: out = IFFT(sa conj(Ta) FFT(a)).

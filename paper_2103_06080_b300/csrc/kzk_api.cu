@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -10,6 +11,7 @@
 #include "../../include/kzk.h"
 #include "kzk_adjoint.cuh"
 #include "kzk_batched.cuh"
+#include "kzk_colpipe.cuh"
 #include "kzk_kernels.cuh"
 #include "kzk_tables.cuh"
 
@@ -81,6 +83,10 @@ struct kzk_plan_s {
     long long hist_steps;
     int row_thr, col_thr, log2tc, adj_row_thr;
     size_t row_smem, col_smem, adj_smem;
+    // persistent TMA-staged column kernels (kzk_colpipe.cuh); colp_log2tc < 0: not used
+    int colp_log2tc, colp_thr, colp_by, colp_nby, colp_bt, colp_nbt, sm_count;
+    size_t colp_smem1, colp_smem2;
+    int* colp_flag;             // device: FLAG_TIMEOUT from a copy wait that ran out
     // adjoint workspace (allocated on first use)
     void *lam, *mu, *nu, *ls;   // spectral adjoint arrays
     void* seg;                  // segment store [(2 k)][batch][ny][nx/2]
@@ -148,6 +154,73 @@ kzk_status set_adj_col_attr(size_t smem)
     return KZK_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Table slices are copied in nbt boxes of bt rows (bt a multiple of 128 bytes
+// / row bytes, so that every box lands 128-byte aligned; rows past ny/2 + 1
+// are filled with zeros by the copy and never read).
+void table_boxes(int nl, int row_bytes, int* bt, int* nbt)
+{
+    const int ra = row_bytes >= 128 ? 1 : 128 / row_bytes;
+    *nbt = (nl + 255) / 256;
+    const int per = (nl + *nbt - 1) / *nbt;
+    *bt = (per + ra - 1) / ra * ra;
+}
+
+// Widest column tile (TC <= 16 columns) of the TMA-staged column kernels:
+// ny TC / 8 threads (at most COLP_THREADS, at least one warp), rows of at
+// least 16 bytes (TMA's innermost extent and coordinate alignment), and both
+// stages' shared memory within the device limit.  FP32 plans only by default;
+// in the environment KZK_COLPIPE=0 selects the per-tile kernels (col_kernel)
+// for every plan, KZK_COLPIPE=2 the TMA-staged ones for FP64 plans too.
+template <typename T>
+void colp_configure(kzk_plan* p, int optin)
+{
+    p->colp_log2tc = -1;
+    const char* env = getenv("KZK_COLPIPE");
+    if ((env && env[0] == '0') || p->log2ny < 4 || !encode_tiled()) return;
+    // FP64 column passes are bound by the FP64 pipe, not by memory latency:
+    // the per-tile kernels (two CTAs per SM) keep it busier
+    if (sizeof(T) == 8 && !(env && env[0] == '2')) return;
+    for (int l2 = 4; l2 >= 0; l2--) {
+        const int TC = 1 << l2;
+        if (TC > p->n || TC * (int)sizeof(cx<T>) < 16) continue;
+        const long long thr = ((long long)p->ny << l2) / 8;
+        if (thr > COLP_THREADS || thr < 32) continue;
+        int bt = 0, nbt = 0;
+        table_boxes(p->ny / 2 + 1, TC * (int)sizeof(cx<T>), &bt, &nbt);
+        const size_t s1 = colp_layout<T, COL_STAGE1>(p->ny, l2, bt, nbt).total;
+        const size_t s2 = colp_layout<T, COL_STAGE2>(p->ny, l2, bt, nbt).total;
+        if (std::max(s1, s2) > (size_t)optin) continue;
+        p->colp_log2tc = l2;
+        p->colp_thr = (int)thr;
+        p->colp_bt = bt;
+        p->colp_nbt = nbt;
+        p->colp_by = std::min(p->ny, 256);
+        p->colp_nby = p->ny / p->colp_by;
+        p->colp_smem1 = s1;
+        p->colp_smem2 = s2;
+        return;
+    }
+}
+
 template <typename T>
 kzk_status configure(kzk_plan* p)
 {
@@ -178,6 +251,12 @@ kzk_status configure(kzk_plan* p)
     KZK_TRY((set_adj_row_attr<T, ADJ_ROW_1>(sm)));
     KZK_TRY((set_adj_col_attr<T, ADJ_COL_2>(sm)));
     KZK_TRY((set_adj_col_attr<T, ADJ_COL_1>(sm)));
+    KZK_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    colp_configure<T>(p, optin);
+    if (p->colp_log2tc >= 0) {
+        KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    }
     return KZK_OK;
 }
 
@@ -268,9 +347,70 @@ kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st)
     return KZK_OK;
 }
 
+template <typename T>
+kzk_status encode_map(CUtensorMap* m, int rank, const void* base, const cuuint64_t* dims, const cuuint64_t* strides,
+                      const cuuint32_t* box)
+{
+    if (!base || ((uintptr_t)base & 15)) return fail(KZK_ERR_ARG, "tensor copy base %p not 16-byte aligned", base);
+    const cuuint32_t es[3] = {1u, 1u, 1u};
+    const CUresult r = encode_tiled()(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                      (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, es,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(KZK_ERR_CUDA, "cuTensorMapEncodeTiled: error %d", (int)r);
+    return KZK_OK;
+}
+// state array [batch][ny][n] complex as {2 n, ny, batch} reals; box = one tile column block of colp_by rows
+template <typename T>
+kzk_status encode_state(CUtensorMap* m, const void* base, const kzk_plan* p)
+{
+    const cuuint64_t dims[3] = {2ull * p->n, (cuuint64_t)p->ny, (cuuint64_t)p->batch};
+    const cuuint64_t strides[2] = {2ull * p->n * sizeof(T), 2ull * p->n * p->ny * sizeof(T)};
+    const cuuint32_t box[3] = {2u << p->colp_log2tc, (cuuint32_t)p->colp_by, 1u};
+    return encode_map<T>(m, 3, base, dims, strides, box);
+}
+// folded table [ny/2 + 1][n] complex as {2 n, ny/2 + 1} reals; box of colp_bt rows
+template <typename T>
+kzk_status encode_table(CUtensorMap* m, const void* base, const kzk_plan* p)
+{
+    const cuuint64_t dims[2] = {2ull * p->n, (cuuint64_t)(p->ny / 2 + 1)};
+    const cuuint64_t strides[1] = {2ull * p->n * sizeof(T)};
+    const cuuint32_t box[2] = {2u << p->colp_log2tc, (cuuint32_t)p->colp_bt};
+    return encode_map<T>(m, 2, base, dims, strides, box);
+}
+
+// TMA-staged column kernel: one CTA per tile, each prefetching into L2 the tile
+// taken one wave (two CTAs per SM) later.
+template <typename T, int MODE>
+kzk_status launch_colp(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
+{
+    ColPipeArgs<T> P;
+    memset(&P, 0, sizeof(P));
+    P.c = a;
+    P.c.log2tc = p->colp_log2tc;
+    KZK_TRY(encode_state<T>(&P.ma, a.a, p));
+    KZK_TRY(encode_state<T>(&P.mb, a.b, p));
+    if (MODE == COL_STAGE2) KZK_TRY(encode_state<T>(&P.mc, a.c, p));
+    if (MODE == COL_STAGE2) KZK_TRY(encode_table<T>(&P.mt0, a.Ta, p));
+    P.by = p->colp_by;
+    P.nby = p->colp_nby;
+    P.bt = p->colp_bt;
+    P.nbt = p->colp_nbt;
+    P.n_tiles = p->n >> p->colp_log2tc;
+    P.total = P.n_tiles * p->batch;
+    P.flag = p->colp_flag;
+    P.timeout_ns = 2000000000LL;
+    P.ahead = 2 * p->sm_count;   // two CTAs per SM: one wave ahead
+    const int grid = P.total;
+    colp_kernel<T, MODE><<<grid, p->colp_thr, MODE == COL_STAGE1 ? p->colp_smem1 : p->colp_smem2, st>>>(P);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
 template <typename T, int MODE>
 kzk_status launch_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
 {
+    if (p->colp_log2tc >= 0) return launch_colp<T, MODE>(p, a, st);
     col_kernel<T, MODE><<<dim3(p->n >> p->log2tc, p->batch), p->col_thr, p->col_smem, st>>>(a);
     KZK_LAUNCHED();
     return KZK_OK;
@@ -356,6 +496,15 @@ kzk_status ensure_hist(kzk_plan* p, long long steps)
 kzk_status finish_diag(kzk_plan* p, long long n_steps, cudaStream_t st, kzk_diag* out)
 {
     KZK_CUDA(cudaStreamSynchronize(st));
+    if (p->colp_flag) {
+        int f = 0;
+        KZK_CUDA(cudaMemcpy(&f, p->colp_flag, sizeof(int), cudaMemcpyDeviceToHost));
+        if (f) {
+            KZK_CUDA(cudaMemset(p->colp_flag, 0, sizeof(int)));
+            if (f & FLAG_BAD_LAUNCH) return fail(KZK_ERR_CUDA, "column kernel: shared memory not 128-byte aligned");
+            return fail(KZK_ERR_TIMEOUT, "a column-tile copy did not arrive within its time limit");
+        }
+    }
     std::vector<double> hist((size_t)n_steps * p->batch * 4), fin((size_t)p->batch * 4);
     if (n_steps > 0)
         KZK_CUDA(cudaMemcpy(hist.data(), p->diag_hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -455,7 +604,7 @@ void plan_free(kzk_plan* p)
     void* ptrs[] = {p->V, p->b1, p->vs, p->b2, p->E, p->P1, p->P2, p->E_lo, p->twr, p->twc, p->twc_lo,
                     p->tws_row, p->twc_full,
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
-                    p->seg, p->ckpt};
+                    p->seg, p->ckpt, p->colp_flag};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1088,6 +1237,8 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     if (e == cudaSuccess) e = cudaMalloc(&p->twc, (size_t)p->ny * p->csz);
     if (e == cudaSuccess) e = cudaMalloc(&p->diag_rows, (size_t)batch * p->ny * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->diag_final, (size_t)batch * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p->colp_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->colp_flag, 0, sizeof(int));
     if (e != cudaSuccess) {
         plan_free(p);
         return fail(e == cudaErrorMemoryAllocation ? KZK_ERR_OOM : KZK_ERR_CUDA, "plan allocation: %s",

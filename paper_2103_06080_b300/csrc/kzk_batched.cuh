@@ -50,13 +50,6 @@ struct BatchArgs {
     long long timeout_ns;
 };
 
-__device__ __forceinline__ long long global_ns()
-{
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Grid-wide barrier with a bounded wait.  Returns false once any CTA has
 // timed out (the caller then leaves the kernel).
 template <typename T>

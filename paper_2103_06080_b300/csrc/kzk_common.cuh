@@ -42,6 +42,14 @@ __host__ __device__ __forceinline__ int ilog2(unsigned v)
     return r;
 }
 
+// Device clock in nanoseconds (bounds every wait in the kernels).
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Launch-time error flags (bit set in plan->flags by device code).
 enum : int { FLAG_TIMEOUT = 1, FLAG_BAD_LAUNCH = 2 };
 

@@ -318,7 +318,8 @@ __device__ __forceinline__ cx<T> mult_entry(cx<T> M, cx<T> z, cx<T> zm, bool pac
 {
     if (!packed) return mul<T>(M, z);
     const T h = T(0.5) * (M.x + M.y), g = T(0.5) * (M.x - M.y);
-    return mk<T>(h * z.x + g * zm.x, h * z.y - g * zm.y);
+    // explicit fused forms: every kernel that inlines this rounds alike
+    return mk<T>(fma(h, z.x, g * zm.x), fma(h, z.y, -(g * zm.y)));
 }
 
 template <typename T> __host__ __device__ constexpr int col_ppt_of() { return 8; }

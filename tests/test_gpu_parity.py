@@ -132,6 +132,35 @@ def test_fp32_error_against_fp64_oracle():
     assert rel_linf(got, ref) < 1e-4
 
 
+# Column kernels: the TMA-staged ones (default for FP32 plans, KZK_COLPIPE=2
+# for FP64) and the per-tile ones (KZK_COLPIPE=0, and every plan the staged
+# ones do not fit: ny = 4096 in FP32 needs 1024 threads per tile).
+@pytest.mark.parametrize("prec,mode,nx,ny,batch,steps", [
+    ("fp32", "1", 1024, 512, 1, 30),
+    ("fp32", "0", 1024, 512, 1, 30),
+    ("fp32", "1", 256, 16, 2, 20),
+    ("fp32", "1", 64, 4096, 1, 6),
+    ("fp64", "2", 512, 128, 2, 20),
+    ("fp64", "2", 32, 16, 1, 20),
+])
+def test_column_kernel_variants(prec, mode, nx, ny, batch, steps, monkeypatch):
+    monkeypatch.setenv("KZK_COLPIPE", mode)
+    api = _api()
+    w = inputs.config(2, nx=nx, ny=ny, n_steps=steps)
+    u0 = np.stack([w.u0, 0.8 * w.u0[::-1]][:batch])
+    plan = api.Plan.from_workload(w, precision=prec, batch=batch)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = _dev(u0 if batch > 1 else u0[0], dt)
+    plan.advance(u, steps)
+    got = u.double().cpu().numpy().reshape(batch, ny, nx)
+    for i in range(batch):
+        ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), np.ascontiguousarray(u0[i]), steps, threads=True)
+        if prec == "fp64":
+            assert rel_linf(got[i], ref) < 1e-11, i
+        else:
+            assert rel_l2(got[i], ref) < 1e-5, i
+
+
 def test_batch_instances_are_independent():
     api = _api()
     ws = [inputs.config(1, nx=128, ny=32) for _ in range(3)]
