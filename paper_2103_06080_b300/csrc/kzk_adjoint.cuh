@@ -139,7 +139,7 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
 template <typename T>
 struct AdjRowArgs {
     const cx<T>* m;         // cotangent of b (mu2 or nu1), packed spectral
-    const cx<T>* v;         // state the step linearises at (V* or V^n), packed spectral
+    const T* u;             // state the step linearises at (u* or u^n), physical [batch][ny][nx]
     const cx<T>* l;         // additive term (lam' or lam_lin), packed spectral
     cx<T>* out;             // l + F(J_G(u)^T m) / nx
     const cx<T>* tw;        // exp(-2 pi i k / nx) (real-FFT pre/post-processing)
@@ -154,8 +154,9 @@ struct AdjRowArgs {
 
 enum AdjRowMode { ADJ_ROW_2 = 0, ADJ_ROW_1 = 1 };
 
-// One row of J_G^T: C2R of the state row and of the cotangent row, WENO5
-// transpose, R2C, plus the absorption-deviation term and the additive row.
+// One row of J_G^T: the physical state row (stored by the forward recompute)
+// and the C2R of the cotangent row, WENO5 transpose, R2C, plus the
+// absorption-deviation term and the additive row.
 // Three padded buffers of nx reals, then the spill slots of the sweep.
 template <typename T, int PPT, int MODE>
 __global__ void __launch_bounds__(ROW_MAX_THREADS) adj_row_kernel(AdjRowArgs<T> a)
@@ -173,12 +174,15 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS) adj_row_kernel(AdjRowArgs<T> 
     const long long base = (long long)inst * a.inst_stride + (long long)row * n;
     const Tw<T> tw{a.tws, nullptr, -1};
 
-    for (int i = tid; i < n; i += nthr) { U[padx(i)] = __ldcg(a.v + base + i); M[padx(i)] = __ldcg(a.m + base + i); }
+    const T* urow = a.u + 2 * base;
+    for (int i = tid; i < n; i += nthr) {
+        st_real<T, true>(U, 2 * i, __ldcg(urow + 2 * i));
+        st_real<T, true>(U, 2 * i + 1, __ldcg(urow + 2 * i + 1));
+        M[padx(i)] = __ldcg(a.m + base + i);
+    }
     __syncthreads();
-    c2r_pre<T, true>(U, n, a.tw, tid, nthr);
     c2r_pre<T, true>(M, n, a.tw, tid, nthr);
     __syncthreads();
-    fft_batched<T, PPT, false, true, true>(U, log2n, 0, 1, 0, tw, tid, nthr);
     fft_batched<T, PPT, false, true, true>(M, log2n, 0, 1, 0, tw, tid, nthr);
 
     const int Q = nx / nthr >= 4 ? nx / nthr : 4;

@@ -89,7 +89,7 @@ struct kzk_plan_s {
     int* colp_flag;             // device: FLAG_TIMEOUT from a copy wait that ran out
     // adjoint workspace (allocated on first use)
     void *lam, *mu, *nu, *ls;   // spectral adjoint arrays
-    void* seg;                  // segment store [(2 k)][batch][ny][nx/2]
+    void* seg;                  // segment store: physical u^n, u*^n of k steps, [(2 k)][batch][ny][nx]
     void* ckpt;                 // checkpoints  [n_ckpt][batch][ny][nx/2]
     long long seg_cap, ckpt_cap; // in arrays
     long long ck_steps;         // forward run whose checkpoints are stored (0: none)
@@ -336,6 +336,7 @@ RowArgs<T> row_args(const kzk_plan* p, const void* in, void* out, double sigma, 
     a.cA = (T)(p->nx * dA_of(p, sigma));
     a.kscale = (T)(2.0 * M_PI / (p->g.tau_max - p->g.tau_min));
     a.out_scale = (T)1;
+    a.u_out = nullptr;
     return a;
 }
 
@@ -438,11 +439,13 @@ ColArgs<T> col_args(const kzk_plan* p)
 // vs_out / b1_out / b2_out: destinations (default: plan workspace).
 template <typename T>
 kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_step, void* V, void* vs,
-                void* V_out = nullptr)
+                void* V_out = nullptr, void* u_n = nullptr, void* u_s = nullptr)
 {
-    // V is read-only; the result goes to V_out (default: in place)
+    // V is read-only; the result goes to V_out (default: in place).  u_n, u_s
+    // (nullable): where the row passes also store the physical u^n and u*.
     if (!V_out) V_out = V;
     RowArgs<T> r1 = row_args<T>(p, V, p->b1, sigma, diag_hist_step ? p->diag_rows : nullptr);
+    r1.u_out = (T*)u_n;
     KZK_TRY((launch_row<T, ROW_RHS>(p, r1, st)));
     ColArgs<T> c1 = col_args<T>(p);
     c1.a = (const cx<T>*)V;
@@ -455,6 +458,7 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     c1.diag_hist = diag_hist_step;
     KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
     RowArgs<T> r2 = row_args<T>(p, vs, p->b2, sigma + p->dt, nullptr);
+    r2.u_out = (T*)u_s;
     KZK_TRY((launch_row<T, ROW_RHS>(p, r2, st)));
     ColArgs<T> c2 = col_args<T>(p);
     c2.a = (const cx<T>*)p->b1;
@@ -629,11 +633,11 @@ kzk_status ensure_buf(void** ptr, long long* cap, long long need, size_t unit)
 }
 
 template <typename T>
-AdjRowArgs<T> adj_row_args(const kzk_plan* p, const void* m, const void* v, const void* l, void* out, double sigma)
+AdjRowArgs<T> adj_row_args(const kzk_plan* p, const void* m, const void* u, const void* l, void* out, double sigma)
 {
     AdjRowArgs<T> a;
     a.m = (const cx<T>*)m;
-    a.v = (const cx<T>*)v;
+    a.u = (const T*)u;
     a.l = (const cx<T>*)l;
     a.out = (cx<T>*)out;
     a.tw = (const cx<T>*)p->twr;
@@ -667,7 +671,7 @@ AdjColArgs<T> adj_col_args(const kzk_plan* p)
 // Transposed step on the plan's cotangent p->lam (packed spectral), given the
 // step's stage states V^n and V* (packed spectral).
 template <typename T>
-kzk_status adjoint_step(kzk_plan* p, double sigma, const void* Vn, const void* Vs, cudaStream_t st)
+kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* us, cudaStream_t st)
 {
     const dim3 cgrid(p->n >> p->log2tc, p->batch), rgrid(p->ny, p->batch);
     const size_t rsm = adj_row_smem<T>(p);
@@ -681,7 +685,7 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* Vn, const void* V
     adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_2><<<cgrid, p->col_thr, p->col_smem, st>>>(c2);
     KZK_LAUNCHED();
     // lam* = lam' + J_{G_{n+1}}(u*)^T mu2
-    AdjRowArgs<T> r2 = adj_row_args<T>(p, p->mu, Vs, p->lam, p->ls, sigma + p->dt);
+    AdjRowArgs<T> r2 = adj_row_args<T>(p, p->mu, us, p->lam, p->ls, sigma + p->dt);
     adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_2><<<rgrid, rthr, rsm, st>>>(r2);
     KZK_LAUNCHED();
     // lam_lin = P_{conj E} lam*,  nu1 = P_{conj(ds Phi1)} lam* - mu2
@@ -697,7 +701,7 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* Vn, const void* V
     adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
     KZK_LAUNCHED();
     // lam = lam_lin + J_{G_n}(u)^T nu1
-    AdjRowArgs<T> r1 = adj_row_args<T>(p, p->nu, Vn, p->ls, p->lam, sigma);
+    AdjRowArgs<T> r1 = adj_row_args<T>(p, p->nu, un, p->ls, p->lam, sigma);
     adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_1><<<rgrid, rthr, rsm, st>>>(r1);
     KZK_LAUNCHED();
     return KZK_OK;
@@ -715,9 +719,9 @@ kzk_status adjoint_buffers(kzk_plan* p, long long n_steps, int k)
     }
     const long long n_ckpt = (n_steps + k - 1) / k;
     KZK_TRY(ensure_buf(&p->ckpt, &p->ckpt_cap, std::max(1LL, n_ckpt), arr));
-    // segment store: V^n and V*^n of every step of a segment, plus one slot
-    // for the state after the segment
-    KZK_TRY(ensure_buf(&p->seg, &p->seg_cap, 2 * std::min((long long)k, std::max(1LL, n_steps)) + 1, arr));
+    // segment store: the physical u^n and u*^n of every step of a segment
+    // (a physical array has the bytes of a spectral one)
+    KZK_TRY(ensure_buf(&p->seg, &p->seg_cap, 2 * std::min((long long)k, std::max(1LL, n_steps)), arr));
     return KZK_OK;
 }
 
@@ -740,10 +744,10 @@ kzk_status forward_ckpt(kzk_plan* p, const void* u0, long long n_steps, double s
     return KZK_OK;
 }
 
-// Reverse sweep over the stored checkpoints: per segment, recompute the
-// stage states (V^n, V*^n) into the segment store -- each step reads its
-// V^n in place and writes V^{n+1} into the next slot, so nothing is copied --
-// then apply the transposed steps in reverse order.
+// Reverse sweep over the stored checkpoints: per segment, recompute the steps
+// from the checkpoint (the spectral state advancing in place in p->V), the
+// row passes storing the physical stage states u^n, u*^n into the segment
+// store, then apply the transposed steps in reverse order.
 template <typename T>
 kzk_status reverse_sweep(kzk_plan* p, const void* g_end, void* g0, cudaStream_t st)
 {
@@ -757,16 +761,14 @@ kzk_status reverse_sweep(kzk_plan* p, const void* g_end, void* g0, cudaStream_t 
         const long long s0 = c * k, s1 = std::min(n_steps, s0 + k);
         for (long long s = s0; s < s1; s++) {
             const long long i = s - s0;
-            void* Vn = i == 0 ? arr_at(p->ckpt, c) : arr_at(p->seg, 2 * i);
-            void* Vs = arr_at(p->seg, 2 * i + 1);
-            void* Vnext = s + 1 < s1 ? arr_at(p->seg, 2 * (i + 1)) : p->V;
-            KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, Vn, Vs, Vnext));
+            void* Vn = i == 0 ? arr_at(p->ckpt, c) : p->V;
+            KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, Vn, p->vs, p->V, arr_at(p->seg, 2 * i),
+                            arr_at(p->seg, 2 * i + 1)));
         }
         for (long long s = s1 - 1; s >= s0; s--) {
             const long long i = s - s0;
-            const void* Vn = i == 0 ? arr_at(p->ckpt, c) : arr_at(p->seg, 2 * i);
-            const void* Vs = arr_at(p->seg, 2 * i + 1);
-            KZK_TRY(adjoint_step<T>(p, sigma0 + (double)s * p->dt, Vn, Vs, st));
+            KZK_TRY(adjoint_step<T>(p, sigma0 + (double)s * p->dt, arr_at(p->seg, 2 * i), arr_at(p->seg, 2 * i + 1),
+                                    st));
         }
     }
     return to_physical<T>(p, p->lam, g0, 1.0, nullptr, st);

@@ -40,6 +40,7 @@ struct RowArgs {
     T cA;                   // nx * (A(sigma) - A): absorption-deviation term
     T kscale;               // 2 pi / (tau_max - tau_min)
     T out_scale;            // ROW_FWD: 1/nx; ROW_INV: scale of the result
+    T* u_out;               // ROW_RHS: also store the physical row here ([batch][ny][nx]; nullable)
 };
 
 // Block reduction of the four diagnostics (FP64 across threads, fixed
@@ -229,6 +230,11 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
             if (a.diag_rows) block_diag_t<T>(red, s1, s2, mx, nf, a.diag_rows + ((long long)inst * a.ny + row) * 4);
         } else {
             // ROW_RHS: WENO5 flux derivative into Y, then tau-R2C of Y
+            if (a.u_out) {
+                // the stage state in physical space, for the adjoint sweep
+                T* dst = a.u_out + 2 * base;
+                for (int i = tid; i < nx; i += nthr) dst[i] = ld_real<T, true>(X, i);
+            }
             // chunks of at least 16 points (the sweep's pre-roll is 3 centres)
             const int Q = nx / nthr >= 16 ? nx / nthr : (nx >= 16 ? 16 : nx);
             const int k0 = tid * Q;
