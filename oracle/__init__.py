@@ -43,6 +43,7 @@ class _Params(ctypes.Structure):
         ("weno_eps", ctypes.c_double), ("lf_umax", ctypes.c_double),
         ("B_prof", ctypes.c_double * 4), ("A_prof", ctypes.c_double * 4),
         ("has_profile", ctypes.c_int32), ("dt", ctypes.c_double),
+        ("n_relax", ctypes.c_int32), ("relax_C", ctypes.c_double * 2), ("relax_theta", ctypes.c_double * 2),
     ]
 
 
@@ -65,14 +66,23 @@ class Params:
     B_prof: tuple = (1.0, 0.0, 0.0, 0.0)
     A_prof: tuple = (1.0, 0.0, 0.0, 0.0)
     has_profile: bool = False
+    relax_C: tuple = ()          # relaxation strengths C_r (at most two processes)
+    relax_theta: tuple = ()      # relaxation times theta_r (tau units), same length
 
     def c(self) -> _Params:
         p = _Params()
         for name, _ in _Params._fields_:
+            if name == "n_relax":
+                p.n_relax = len(self.relax_C)
+                continue
             v = getattr(self, name)
             if name in ("B_prof", "A_prof"):
                 arr = (ctypes.c_double * 4)(*[float(x) for x in v])
                 setattr(p, name, arr)
+            elif name in ("relax_C", "relax_theta"):
+                if len(v) > 2 or len(self.relax_C) != len(self.relax_theta):
+                    raise ValueError("relax_C and relax_theta: equal lengths, at most 2")
+                setattr(p, name, (ctypes.c_double * 2)(*([float(x) for x in v] + [0.0] * (2 - len(v)))))
             elif name in ("nx", "ny", "has_profile"):
                 setattr(p, name, int(v))
             else:

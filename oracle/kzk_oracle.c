@@ -48,6 +48,8 @@ typedef struct {
     double B_prof[4], A_prof[4];          /* p(s) = c0 + c1 s + c2 s^2 + c3 s^3 in sigma */
     int32_t has_profile;                  /* 0: B, A constant */
     double dt;                            /* dsigma */
+    int32_t n_relax;                      /* relaxation processes (0, 1 or 2) */
+    double relax_C[2], relax_theta[2];    /* strength C_r and relaxation time theta_r of each */
 } orc_params;
 
 int orc_num_threads(void)
@@ -178,14 +180,20 @@ static cpx z_of(const orc_params *p, int j, int m)
     double kt = 2.0 * M_PI * signed_index(m, p->nx) / Lx;
     double ky = 2.0 * M_PI * signed_index(j, p->ny) / Ly;
     double absorb = -p->A * kt * kt;
+    /* relaxation: C_r d_tau^2 (1 + theta_r d_tau)^-1 per process; with
+     * d_tau -> i kt its multiplier is C_r (i kt)^2 / (1 + i theta_r kt) */
+    cpx relax = c_mk(0.0, 0.0);
+    for (int r = 0; r < p->n_relax; r++)
+        relax = c_add(relax, c_div(c_mk(-p->relax_C[r] * kt * kt, 0.0), c_mk(1.0, p->relax_theta[r] * kt)));
     if (p->nx > 1 && 2 * m == p->nx) {
-        /* tau-Nyquist: only the even (absorption) part survives */
-        return c_mk(p->dt * absorb, 0.0);
+        /* tau-Nyquist: only the even parts (absorption, the real part of the
+         * relaxation multiplier) survive */
+        return c_mk(p->dt * (absorb + relax.re), 0.0);
     }
     /* -diffraction * ky^2 / (i kt + eps * diffraction) - A kt^2 ; 1/(4 pi) = diffraction */
     cpx den = c_mk(p->reg_eps * p->diffraction, kt);
     cpx q = c_div(c_mk(-p->diffraction * ky * ky, 0.0), den);
-    return c_mk(p->dt * (q.re + absorb), p->dt * q.im);
+    return c_mk(p->dt * (q.re + absorb + relax.re), p->dt * (q.im + relax.im));
 }
 
 /* Full (unfolded) tables, each [ny][nx] complex as separate re/im arrays. */
