@@ -284,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
 
     extra = {}
     if rank == 0 and not args.quick:
-        extra = secondary_reports(args, api, torch, dev, peaks)
+        extra = secondary_reports(args, api, torch, dev, peaks, ms_fp64=None if fp32 else ms_max / args.steps)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -314,8 +314,38 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
-def secondary_reports(args, api, torch, dev, peaks):
-    """FP32 throughput + error, and the adjoint/forward cost ratio."""
+def cufft_transforms_ms(torch, dev, nx, ny, dtype, reps=20):
+    """Device ms of cuFFT (through torch.fft) running only the transforms of
+    one step: the tau C2R + R2C of both row passes and the five y transforms
+    of the two column passes (three forward, two inverse) -- no WENO, no
+    multiplies, no diagnostics.  A timed comparison, not part of the path."""
+    u = torch.randn(ny, nx, dtype=dtype, device=dev)
+    V = torch.fft.rfft(u, dim=1)
+
+    def one_step():
+        for _ in range(2):
+            x = torch.fft.irfft(V, n=nx, dim=1)
+            torch.fft.rfft(x, dim=1)
+        for _ in range(3):
+            torch.fft.fft(V, dim=0)
+        for _ in range(2):
+            torch.fft.ifft(V, dim=0)
+
+    for _ in range(3):
+        one_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        one_step()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
+    """FP32 throughput + error, the adjoint/forward cost ratio, the batched
+    launch and the cuFFT comparison."""
     out = {}
     # FP32 bulk with FP64-generated tables, same 4096 x 2048 workload
     w3 = inputs.config(3)
@@ -411,6 +441,15 @@ def secondary_reports(args, api, torch, dev, peaks):
                           "launch": bp.info(), "plan_create_s": t_plan,
                           "note": "one cooperative persistent kernel per call, replayed from a CUDA graph"}
         bp.close()
+    # cuFFT comparison on the 4096 x 2048 grid
+    cmp = {}
+    for name, dtype, ms_ours in (("fp64", torch.float64, ms_fp64), ("fp32", torch.float32, out["fp32"]["ms_per_step"])):
+        ms_fft = cufft_transforms_ms(torch, dev, 4096, 2048, dtype)
+        cmp[name] = {"cufft_transforms_ms_per_step": ms_fft, "ours_step_ms": ms_ours,
+                     "ours_over_cufft": (ms_ours / ms_fft) if ms_ours else None}
+    cmp["note"] = ("cuFFT through torch.fft doing only the 4 tau and 5 y transforms of one step (no WENO5, "
+                   "no phi-multiplies); ours = the whole fused step through kzk_advance")
+    out["cufft_comparison"] = cmp
     return out
 
 

@@ -66,9 +66,16 @@ typedef struct {
     int32_t prec;                   /* kzk_precision of state and bulk arithmetic */
 } kzk_grid;
 
+#define KZK_MAX_RELAX 2
+
 /* Coefficients of Eq. 0 / Eq. 2a.  B(sigma) = B * pB(sigma) and
  * A(sigma) = A * pA(sigma) with cubic pX(sigma) = c0 + c1 s + c2 s^2 + c3 s^3
- * when has_profile != 0 (stratified atmosphere), else constant. */
+ * when has_profile != 0 (stratified atmosphere), else constant.
+ * Relaxation (optional, n_relax processes): each adds C_r d_tau^2 q_r to the
+ * linear operator, q_r the causal solution of theta_r dq_r/dtau + q_r = V,
+ * i.e. the multiplier C_r (i k_tau)^2 / (1 + i theta_r k_tau) in z of Eq. 11
+ * (at the tau-Nyquist frequency its real part only).  The paper's operator
+ * has none (n_relax = 0). */
 typedef struct {
     double B;                       /* nonlinearity, > 0                             */
     double A;                       /* absorption, >= 0 (kept exactly in L)          */
@@ -80,6 +87,9 @@ typedef struct {
     double B_prof[4];
     double A_prof[4];
     int32_t has_profile;
+    int32_t n_relax;                /* relaxation processes, 0 .. KZK_MAX_RELAX      */
+    double relax_C[KZK_MAX_RELAX];  /* strengths C_r >= 0                            */
+    double relax_theta[KZK_MAX_RELAX]; /* relaxation times theta_r > 0 (tau units)   */
 } kzk_coeffs;
 
 /* Diagnostics (FP64): of the state after the last step, and over the run. */
@@ -98,7 +108,8 @@ typedef struct kzk_plan_s kzk_plan;
  * coefficients and step dt (= dsigma of Eq. 5).  Builds the FP64 phi tables of
  * Eq. 11 on the device (rounded once to float for KZK_FP32), the twiddle
  * tables, and the workspace (4 spectral arrays per instance).
- * Errors: KZK_ERR_ARG (null, dt <= 0, B <= 0, A < 0, lf_umax <= 0, batch < 1),
+ * Errors: KZK_ERR_ARG (null, dt <= 0, B <= 0, A < 0, lf_umax <= 0, batch < 1,
+ * n_relax outside [0, KZK_MAX_RELAX], some C_r < 0 or theta_r <= 0),
  * KZK_ERR_SIZE, KZK_ERR_OOM, KZK_ERR_CUDA.  *out is NULL on failure. */
 kzk_status kzk_plan_create(const kzk_grid *grid, const kzk_coeffs *coeffs, double dt,
                            int32_t batch, kzk_plan **out);

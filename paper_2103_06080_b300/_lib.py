@@ -31,7 +31,8 @@ class KzkCoeffs(ctypes.Structure):
                 ("diffraction", ctypes.c_double), ("reg_eps", ctypes.c_double),
                 ("weno_eps", ctypes.c_double), ("lf_umax", ctypes.c_double),
                 ("B_prof", ctypes.c_double * 4), ("A_prof", ctypes.c_double * 4),
-                ("has_profile", ctypes.c_int32)]
+                ("has_profile", ctypes.c_int32), ("n_relax", ctypes.c_int32),
+                ("relax_C", ctypes.c_double * 2), ("relax_theta", ctypes.c_double * 2)]
 
 
 class KzkDiag(ctypes.Structure):

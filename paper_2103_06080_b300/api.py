@@ -29,7 +29,7 @@ class Plan:
                  tau_min: float = -4.0, tau_max: float = 4.0, y_min: float = -8.0, y_max: float = 8.0,
                  B_prof: Sequence[float] = (1.0, 0.0, 0.0, 0.0), A_prof: Sequence[float] = (1.0, 0.0, 0.0, 0.0),
                  has_profile: bool = False, diffraction: float = 0.0, reg_eps: float = 0.0,
-                 weno_eps: float = 0.0):
+                 weno_eps: float = 0.0, relax_C: Sequence[float] = (), relax_theta: Sequence[float] = ()):
         if precision not in ("fp64", "fp32"):
             raise ValueError("precision must be 'fp64' or 'fp32'")
         self.nx, self.ny, self.dt, self.batch = int(nx), int(ny), float(dt), int(batch)
@@ -37,9 +37,13 @@ class Plan:
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         g = L.KzkGrid(nx=self.nx, ny=self.ny, tau_min=tau_min, tau_max=tau_max, y_min=y_min, y_max=y_max,
                       prec=L.KZK_FP64 if precision == "fp64" else L.KZK_FP32)
+        if len(relax_C) != len(relax_theta) or len(relax_C) > 2:
+            raise ValueError("relax_C and relax_theta: equal lengths, at most 2 processes")
+        pad = lambda v: (ctypes.c_double * 2)(*([float(x) for x in v] + [0.0] * (2 - len(v))))
         c = L.KzkCoeffs(B=B, A=A, diffraction=diffraction, reg_eps=reg_eps, weno_eps=weno_eps, lf_umax=lf_umax,
                         B_prof=(ctypes.c_double * 4)(*B_prof), A_prof=(ctypes.c_double * 4)(*A_prof),
-                        has_profile=int(bool(has_profile)))
+                        has_profile=int(bool(has_profile)), n_relax=len(relax_C), relax_C=pad(relax_C),
+                        relax_theta=pad(relax_theta))
         self._grid, self._coeffs = g, c
         h = ctypes.c_void_p()
         L.check(L.lib().kzk_plan_create(ctypes.byref(g), ctypes.byref(c), self.dt, self.batch, ctypes.byref(h)))

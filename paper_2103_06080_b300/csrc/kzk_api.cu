@@ -572,6 +572,11 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
     a.P1 = p->P1;
     a.P2 = p->P2;
     a.E_lo = p->E_lo;
+    a.n_relax = p->c.n_relax;
+    for (int r = 0; r < 2; r++) {
+        a.relax_C[r] = r < p->c.n_relax ? p->c.relax_C[r] : 0.0;
+        a.relax_theta[r] = r < p->c.n_relax ? p->c.relax_theta[r] : 1.0;
+    }
     const long long count = (long long)(p->ny / 2 + 1) * p->n;
     tables_kernel<T><<<(unsigned)((count + 255) / 256), 256, 0, st>>>(a);
     KZK_LAUNCHED();
@@ -1191,6 +1196,12 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     if (!(dt > 0) || !std::isfinite(dt)) return fail(KZK_ERR_ARG, "dt must be positive and finite");
     if (!(coeffs->B > 0) || !(coeffs->A >= 0) || !(coeffs->lf_umax > 0))
         return fail(KZK_ERR_ARG, "need B > 0, A >= 0, lf_umax > 0");
+    if (coeffs->n_relax < 0 || coeffs->n_relax > KZK_MAX_RELAX)
+        return fail(KZK_ERR_ARG, "n_relax = %d outside [0, %d]", coeffs->n_relax, KZK_MAX_RELAX);
+    for (int r = 0; r < coeffs->n_relax; r++)
+        if (!(coeffs->relax_C[r] >= 0) || !std::isfinite(coeffs->relax_C[r]) || !(coeffs->relax_theta[r] > 0) ||
+            !std::isfinite(coeffs->relax_theta[r]))
+            return fail(KZK_ERR_ARG, "relaxation process %d: need C >= 0 and theta > 0 (finite)", r);
     if (batch < 1) return fail(KZK_ERR_ARG, "batch must be >= 1");
 
     kzk_plan* p = new (std::nothrow) kzk_plan_s();

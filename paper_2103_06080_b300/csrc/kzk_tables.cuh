@@ -2,10 +2,11 @@
 // Eq. 11 (E = e^z, Phi1 = (e^z - 1)/z, Phi2 = (e^z - 1 - z)/z^2) on the device.
 //
 // z(k_tau, k_y) = dsigma * ( -diffraction * k_y^2 / (i k_tau + reg_eps * diffraction)
-//                            - A k_tau^2 ),
+//                            - A k_tau^2 + sum_r C_r (i k_tau)^2 / (1 + i theta_r k_tau) ),
 // the paper's regularised multiplier (reg_eps = machine epsilon of the working
-// precision).  At the tau-Nyquist frequency, where k_tau and -k_tau alias, the
-// odd diffraction part is dropped so that real fields stay real.
+// precision) plus the optional relaxation processes.  At the tau-Nyquist
+// frequency, where k_tau and -k_tau alias, the odd parts (diffraction, the
+// imaginary part of relaxation) are dropped so that real fields stay real.
 //
 // Tables are even in k_y, so only |k_y| indices l = 0..ny/2 are stored:
 // T[l][m] for m = 0..nx/2-1, with column 0 packing the two real values at
@@ -19,6 +20,8 @@ namespace kzk {
 struct TabArgs {
     int nx, ny;
     double dt, A, diffraction, reg_eps, kts, kys;   // kts = 2 pi / tau length, kys = 2 pi / y length
+    int n_relax;                                    // relaxation processes
+    double relax_C[2], relax_theta[2];
     void* E;
     void* P1;
     void* P2;
@@ -63,13 +66,20 @@ __device__ __forceinline__ void phi_eval(double zr, double zi, double2& E, doubl
 __device__ __forceinline__ double2 z_of(const TabArgs& a, double kt, double ky, bool nyquist)
 {
     const double absorb = -a.A * kt * kt;
-    if (nyquist) return make_double2(a.dt * absorb, 0.0);
+    // relaxation: C (i kt)^2 / (1 + i theta kt) = -C kt^2 (1 - i theta kt) / (1 + theta^2 kt^2)
+    double rr = 0.0, ri = 0.0;
+    for (int r = 0; r < a.n_relax; r++) {
+        const double tk = a.relax_theta[r] * kt, g = a.relax_C[r] * kt * kt / (1.0 + tk * tk);
+        rr -= g;
+        ri += g * tk;
+    }
+    if (nyquist) return make_double2(a.dt * (absorb + rr), 0.0);
     // q = -diffraction ky^2 / (eps diffraction + i kt)
     const double dr = a.reg_eps * a.diffraction, di = kt;
     const double num = -a.diffraction * ky * ky;
     const double den = dr * dr + di * di;
     const double qr = num * dr / den, qi = -num * di / den;
-    return make_double2(a.dt * (qr + absorb), a.dt * qi);
+    return make_double2(a.dt * (qr + absorb + rr), a.dt * (qi + ri));
 }
 
 template <typename T>

@@ -33,9 +33,14 @@ def test_status_strings():
         assert lib.kzk_status_string(s)
 
 
-def _create(nx=64, ny=32, prec=0, dt=0.01, B=0.05, A=7e-6, M=1.0, batch=1):
+def _create(nx=64, ny=32, prec=0, dt=0.01, B=0.05, A=7e-6, M=1.0, batch=1, relax=None):
     g = L.KzkGrid(nx=nx, ny=ny, tau_min=-4, tau_max=4, y_min=-8, y_max=8, prec=prec)
     c = L.KzkCoeffs(B=B, A=A, lf_umax=M)
+    if relax is not None:
+        n, C, theta = relax
+        c.n_relax = n
+        c.relax_C = (ctypes.c_double * 2)(*C)
+        c.relax_theta = (ctypes.c_double * 2)(*theta)
     h = ctypes.c_void_p()
     st = L.lib().kzk_plan_create(ctypes.byref(g), ctypes.byref(c), dt, batch, ctypes.byref(h))
     return st, h
@@ -47,6 +52,11 @@ def _create(nx=64, ny=32, prec=0, dt=0.01, B=0.05, A=7e-6, M=1.0, batch=1):
     (dict(prec=7), L.KZK_ERR_ARG), (dict(dt=0.0), L.KZK_ERR_ARG), (dict(dt=float("nan")), L.KZK_ERR_ARG),
     (dict(B=0.0), L.KZK_ERR_ARG), (dict(A=-1.0), L.KZK_ERR_ARG), (dict(M=0.0), L.KZK_ERR_ARG),
     (dict(batch=0), L.KZK_ERR_ARG),
+    (dict(relax=(3, (1e-3, 1e-3), (0.1, 0.1))), L.KZK_ERR_ARG),
+    (dict(relax=(-1, (0.0, 0.0), (1.0, 1.0))), L.KZK_ERR_ARG),
+    (dict(relax=(1, (-1e-3, 0.0), (0.1, 1.0))), L.KZK_ERR_ARG),
+    (dict(relax=(2, (1e-3, 1e-3), (0.1, 0.0))), L.KZK_ERR_ARG),
+    (dict(relax=(1, (float("inf"), 0.0), (0.1, 1.0))), L.KZK_ERR_ARG),
 ])
 def test_plan_create_rejects_bad_arguments(kw, code):
     st, h = _create(**kw)
@@ -62,3 +72,30 @@ def test_null_arguments_are_rejected():
     assert lib.kzk_tau_fft(None, None, None, 1, None) == L.KZK_ERR_ARG
     assert lib.kzk_adjoint(None, None, None, None, 1, 0.0, 1, None) == L.KZK_ERR_ARG
     assert lib.kzk_plan_destroy(None) == L.KZK_OK
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler gives
+    the structs of include/kzk.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"kzk_grid": L.KzkGrid, "kzk_coeffs": L.KzkCoeffs, "kzk_diag": L.KzkDiag}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "kzk.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

@@ -161,6 +161,53 @@ def test_column_kernel_variants(prec, mode, nx, ny, batch, steps, monkeypatch):
             assert rel_l2(got[i], ref) < 1e-5, i
 
 
+# two relaxation processes (an extra diagonal term of the linear multiplier)
+RELAX = dict(relax_C=(2e-4, 6e-4), relax_theta=(0.02, 0.1))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-7)])
+def test_tables_with_relaxation_match_oracle(prec, tol):
+    api = _api()
+    w = inputs.config(1, nx=64, ny=32)
+    plan = api.Plan.from_workload(w, precision=prec, **RELAX)
+    E, P1, P2 = plan.tables()
+    oE, oP1, oP2 = oracle.tables(oracle.Params(**inputs.oracle_params(w, **RELAX)))
+    nl, nm = w.ny // 2 + 1, w.nx // 2 + 1
+    for got, ref in ((E, oE), (P1, oP1), (P2, oP2)):
+        ref = ref[:nl, :nm]
+        err = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+        assert np.max(err[np.abs(ref) > 1e-280]) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_relaxation_run_matches_oracle(prec):
+    api = _api()
+    w = inputs.config(2, nx=512, ny=64, n_steps=40)
+    plan = api.Plan.from_workload(w, precision=prec, **RELAX)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = _dev(w.u0, dt)
+    plan.advance(u, w.n_steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w, **RELAX)), w.u0, w.n_steps, threads=True)
+    plain = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    assert rel_l2(plain, ref) > 1e-4          # the processes change the answer
+    got = u.double().cpu().numpy()
+    if prec == "fp64":
+        assert rel_linf(got, ref) < 1e-11
+    else:
+        assert rel_l2(got, ref) < 1e-5
+
+
+def test_relaxation_adjoint_matches_oracle():
+    api = _api()
+    w = inputs.config(2, nx=128, ny=32, n_steps=10)
+    plan = api.Plan.from_workload(w, precision="fp64", **RELAX)
+    p = oracle.Params(**inputs.oracle_params(w, **RELAX))
+    g_end = 2 * w.dtau * oracle.run(p, w.u0, w.n_steps)
+    ref = oracle.adjoint(p, w.u0, g_end, w.n_steps)
+    g0 = plan.adjoint(_dev(w.u0), _dev(g_end), w.n_steps, ckpt_every=3)
+    assert rel_linf(g0.cpu().numpy(), ref) < 1e-10
+
+
 def test_batch_instances_are_independent():
     api = _api()
     ws = [inputs.config(1, nx=128, ny=32) for _ in range(3)]
