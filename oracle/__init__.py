@@ -44,7 +44,11 @@ class _Params(ctypes.Structure):
         ("B_prof", ctypes.c_double * 4), ("A_prof", ctypes.c_double * 4),
         ("has_profile", ctypes.c_int32), ("dt", ctypes.c_double),
         ("n_relax", ctypes.c_int32), ("relax_C", ctypes.c_double * 2), ("relax_theta", ctypes.c_double * 2),
+        ("n_modes", ctypes.c_int32), ("mode_klam", ctypes.c_void_p), ("mode_theta", ctypes.c_void_p),
+        ("mode_phase", ctypes.c_void_p), ("mode_amp", ctypes.c_void_p),
     ]
+
+_MODE_FIELDS = ("mode_klam", "mode_theta", "mode_phase", "mode_amp")
 
 
 @dataclass
@@ -68,12 +72,30 @@ class Params:
     has_profile: bool = False
     relax_C: tuple = ()          # relaxation strengths C_r (at most two processes)
     relax_theta: tuple = ()      # relaxation times theta_r (tau units), same length
+    # random medium (Algorithm 1): per mode |K_n| lambda, theta_n, phi_n, |U~_n| / c0
+    mode_klam: object = None
+    mode_theta: object = None
+    mode_phase: object = None
+    mode_amp: object = None
 
     def c(self) -> _Params:
         p = _Params()
+        self._mode_arrays = []
+        n_modes = 0 if self.mode_klam is None else len(self.mode_klam)
         for name, _ in _Params._fields_:
             if name == "n_relax":
                 p.n_relax = len(self.relax_C)
+                continue
+            if name == "n_modes":
+                p.n_modes = n_modes
+                continue
+            if name in _MODE_FIELDS:
+                if n_modes:
+                    a = np.ascontiguousarray(getattr(self, name), dtype=np.float64)
+                    if a.shape != (n_modes,):
+                        raise ValueError(f"{name}: expected {n_modes} values")
+                    self._mode_arrays.append(a)          # kept alive with the Params
+                    setattr(p, name, a.ctypes.data)
                 continue
             v = getattr(self, name)
             if name in ("B_prof", "A_prof"):
@@ -114,6 +136,7 @@ def _lib(threads: bool = False):
         lib.orc_run.argtypes = [P, D, ctypes.c_int64, ctypes.c_double, D, D]
         lib.orc_run_timed.argtypes = [P, D, ctypes.c_int64, ctypes.c_double, D]
         lib.orc_adjoint.argtypes = [P, D, D, ctypes.c_int64, ctypes.c_double, D]
+        lib.orc_medium.argtypes = [P, ctypes.c_double, D, D, D]
         lib.orc_B_of.argtypes = [P, ctypes.c_double]
         lib.orc_B_of.restype = ctypes.c_double
         lib.orc_A_of.argtypes = [P, ctypes.c_double]
@@ -182,6 +205,14 @@ def weno_grad(v, eps: float = 1e-6) -> np.ndarray:
     g = np.zeros(5)
     _lib().orc_weno_grad(_ptr(v), eps, _ptr(g))
     return g
+
+
+def medium(p: Params, sigma: float):
+    """U_par, U_perp and d U_perp / dy at (sigma, y_j) for every row (Algorithm 1)."""
+    a, b, c = (np.zeros(p.ny) for _ in range(3))
+    cp = p.c()
+    _lib().orc_medium(ctypes.byref(cp), float(sigma), _ptr(a), _ptr(b), _ptr(c))
+    return a, b, c
 
 
 def weno_rhs(p: Params, u, sigma: float = 0.0, threads: bool = False) -> np.ndarray:
@@ -253,8 +284,10 @@ def adjoint(p: Params, u0, g_end, n_steps: int, sigma0: float = 0.0, threads: bo
     g_end = _f64(g_end).reshape(p.ny, p.nx)
     g0 = np.zeros_like(u0)
     cp = p.c()
-    _lib(threads).orc_adjoint(ctypes.byref(cp), _ptr(u0), _ptr(g_end), int(n_steps),
-                              float(sigma0), _ptr(g0))
+    st = _lib(threads).orc_adjoint(ctypes.byref(cp), _ptr(u0), _ptr(g_end), int(n_steps),
+                                   float(sigma0), _ptr(g0))
+    if st != 0:
+        raise ValueError("the oracle adjoint covers the homogeneous and stratified medium only")
     return g0
 
 

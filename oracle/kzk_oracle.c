@@ -50,6 +50,12 @@ typedef struct {
     double dt;                            /* dsigma */
     int32_t n_relax;                      /* relaxation processes (0, 1 or 2) */
     double relax_C[2], relax_theta[2];    /* strength C_r and relaxation time theta_r of each */
+    /* random inhomogeneous medium (Algorithm 1); n_modes = 0: homogeneous */
+    int32_t n_modes;
+    const double *mode_klam;              /* |K_n| lambda */
+    const double *mode_theta;             /* theta_n: angle between K_n and the sigma axis */
+    const double *mode_phase;             /* phi_n */
+    const double *mode_amp;               /* |U~(K_n)| / c0 */
 } orc_params;
 
 int orc_num_threads(void)
@@ -247,13 +253,15 @@ void orc_weno_parts(const double *v, double eps, double *q, double *beta, double
     *fhat = f;
 }
 
-/* Numerical flux F_hat_{k+1/2} at every interface of one periodic row. */
-static void weno_row_fluxes(const double *u, int n, double B, double alpha, double eps, double *F)
+/* Numerical flux F_hat_{k+1/2} at every interface of one periodic row, for
+ * the tau-flux of Eq. 7, f(u) = -c u - (B/2) u^2 with c = 2 pi U_par of the row
+ * (c = 0: homogeneous medium). */
+static void weno_row_fluxes(const double *u, int n, double c, double B, double alpha, double eps, double *F)
 {
     double *fp = (double *)malloc(sizeof(double) * n);
     double *fm = (double *)malloc(sizeof(double) * n);
     for (int i = 0; i < n; i++) {
-        double f = -0.5 * B * u[i] * u[i];      /* flux of Eq. 7 with U_par = 0 */
+        double f = -c * u[i] - 0.5 * B * u[i] * u[i];
         fp[i] = 0.5 * (f + alpha * u[i]);        /* Lax-Friedrichs splitting */
         fm[i] = 0.5 * (f - alpha * u[i]);
     }
@@ -268,24 +276,89 @@ static void weno_row_fluxes(const double *u, int n, double B, double alpha, doub
     free(fp); free(fm);
 }
 
-/* WENO part of b: b_k = -(F_{k+1/2} - F_{k-1/2}) / dtau, row by row. */
+/* Random velocity field of Algorithm 1 at (sigma, y_j) for every row j:
+ * U_par, U_perp and d U_perp / d y (the y-derivative of the same sum of
+ * modes, differentiated term by term).  All zero without modes. */
+void orc_medium(const orc_params *p, double sigma, double *upar, double *uperp, double *duperp)
+{
+    double dy = (p->y_max - p->y_min) / p->ny;
+    for (int j = 0; j < p->ny; j++) {
+        double rho = p->y_min + j * dy;
+        double r = sqrt(sigma * sigma + rho * rho), psi = atan2(rho, sigma);
+        double a = 0.0, b = 0.0, db = 0.0;
+        for (int n = 0; n < p->n_modes; n++) {
+            double th = p->mode_theta[n];
+            /* U~_n = |U~_n| (-sin theta_n, cos theta_n), orthogonal to K_n */
+            double u1 = -p->mode_amp[n] * sin(th), u2 = p->mode_amp[n] * cos(th);
+            double arg = p->mode_klam[n] * r * cos(th - psi) + p->mode_phase[n];
+            a += u1 * cos(arg);
+            b += u2 * cos(arg);
+            /* d(arg)/d rho = |K_n| lambda sin(theta_n) */
+            db += -u2 * sin(arg) * p->mode_klam[n] * sin(th);
+        }
+        upar[j] = a; uperp[j] = b; duperp[j] = db;
+    }
+}
+
+/* WENO part of b: b_k = -(F_{k+1/2} - F_{k-1/2}) / dtau, row by row (the
+ * tau-flux of Eq. 7), plus, with a random medium, the y-flux U_perp u by
+ * WENO5 along y, -(G_{j+1/2} - G_{j-1/2}) / dy, and the source d_y U_perp u
+ * (the rewriting of U_perp d_y u that follows Eq. 7). */
 void orc_weno_rhs(const orc_params *p, const double *u, double sigma, double *b)
 {
-    int nx = p->nx;
+    int nx = p->nx, ny = p->ny;
     double dtau = (p->tau_max - p->tau_min) / nx;
     double Bs = orc_B_of(p, sigma);
-    double alpha = Bs * p->lf_umax;
+    double *upar = calloc(ny, sizeof(double)), *uperp = calloc(ny, sizeof(double));
+    double *duperp = calloc(ny, sizeof(double));
+    if (p->n_modes > 0) orc_medium(p, sigma, upar, uperp, duperp);
     #pragma omp parallel
     {
         double *F = (double *)malloc(sizeof(double) * nx);
         #pragma omp for schedule(static)
-        for (int j = 0; j < p->ny; j++) {
+        for (int j = 0; j < ny; j++) {
             const double *ur = u + (size_t)j * nx;
-            weno_row_fluxes(ur, nx, Bs, alpha, p->weno_eps, F);
+            double c = 2.0 * M_PI * upar[j];
+            /* global LF speed of the row: |f'(u)| = |c + B u| <= |c| + B M */
+            double alpha = fabs(c) + Bs * p->lf_umax;
+            weno_row_fluxes(ur, nx, c, Bs, alpha, p->weno_eps, F);
             for (int k = 0; k < nx; k++) b[(size_t)j * nx + k] = -(F[k] - F[(k - 1 + nx) % nx]) / dtau;
         }
         free(F);
     }
+    if (p->n_modes > 0) {
+        double dy = (p->y_max - p->y_min) / ny;
+        double ay = 0.0;                      /* global LF speed along y: max |U_perp| */
+        for (int j = 0; j < ny; j++) ay = fmax(ay, fabs(uperp[j]));
+        #pragma omp parallel
+        {
+            double *col = malloc(sizeof(double) * ny), *G = malloc(sizeof(double) * ny);
+            #pragma omp for schedule(static)
+            for (int k = 0; k < nx; k++) {
+                for (int j = 0; j < ny; j++) col[j] = u[(size_t)j * nx + k];
+                /* y-flux g(u) = U_perp(y) u, split as (g +- ay u)/2 */
+                double *gp = malloc(sizeof(double) * ny), *gm = malloc(sizeof(double) * ny);
+                for (int j = 0; j < ny; j++) {
+                    double g = uperp[j] * col[j];
+                    gp[j] = 0.5 * (g + ay * col[j]);
+                    gm[j] = 0.5 * (g - ay * col[j]);
+                }
+                for (int j = 0; j < ny; j++) {
+                    double v[5], q[3], be[3], Gp, Gm;
+                    for (int s = 0; s < 5; s++) v[s] = gp[((j - 2 + s) % ny + ny) % ny];
+                    orc_weno_parts(v, p->weno_eps, q, be, &Gp);
+                    for (int s = 0; s < 5; s++) v[s] = gm[((j + 3 - s) % ny + ny) % ny];
+                    orc_weno_parts(v, p->weno_eps, q, be, &Gm);
+                    G[j] = Gp + Gm;                   /* interface j + 1/2 */
+                }
+                for (int j = 0; j < ny; j++)
+                    b[(size_t)j * nx + k] += -(G[j] - G[(j - 1 + ny) % ny]) / dy + duperp[j] * col[j];
+                free(gp); free(gm);
+            }
+            free(col); free(G);
+        }
+    }
+    free(upar); free(uperp); free(duperp);
 }
 
 /* 2-D spectrum of b(sigma, u) given u and its spectrum:                          */
@@ -584,6 +657,7 @@ static void rhs_T(const orc_params *p, const double *u, double sigma, const doub
 int orc_adjoint(const orc_params *p, const double *u0, const double *g_end, int64_t n_steps,
                 double sigma0, double *g0)
 {
+    if (p->n_modes > 0) return -2;        /* transposed medium terms: not restated here */
     size_t N = (size_t)p->nx * p->ny;
     tables_t t;
     tables_alloc(p, &t);

@@ -5,7 +5,8 @@ It produces the N-wave initial pressure profile of Sec. 4 (with the readings
 used here: ``u0 = a0 * (-tau/L)`` on ``|tau| < L`` with tanh edges of width
 ``2 dtau``, modulated in y by ``exp(-y^2/16)``, plus seeded uniform noise of
 relative amplitude 1e-2), the seeded cubic atmosphere profiles B(sigma),
-A(sigma), and the five workload configurations (sizes, step counts, seeds).
+A(sigma), the mode data of the random medium of Algorithm 1, and the
+workload configurations (sizes, step counts, seeds).
 
 Random numbers come from SplitMix64 (Steele, Lea & Flood, OOPSLA 2014):
 output i of seed s is mix64(s + (i+1) * 0x9E3779B97F4A7C15), converted to
@@ -62,6 +63,7 @@ class Workload:
     a0: float = 1.0
     name: str = ""
     meta: dict = field(default_factory=dict)
+    medium: "Medium | None" = None
 
     @property
     def dtau(self) -> float:
@@ -111,6 +113,62 @@ def cubic_profile(seed: int, sigma_end: float, spread: float = 0.2):
 def cfl_dt(dtau: float, B_max: float, umax: float, cfl: float = 0.4) -> float:
     """Step size at WENO CFL number ``cfl``: B_max * umax * dt = cfl * dtau."""
     return cfl * dtau / (B_max * umax)
+
+
+@dataclass
+class Medium:
+    """Modes of the random velocity field of Algorithm 1 (the field itself --
+    the sums over modes at each (sigma, y) -- is evaluated by the solver and by
+    the oracle).  Per mode: |K_n| lambda, theta_n (angle of K_n to the sigma
+    axis), phi_n (phase), |U~(K_n)| / c0 (amplitude normalised by the sound
+    speed)."""
+    klam: np.ndarray
+    theta: np.ndarray
+    phase: np.ndarray
+    amp: np.ndarray
+
+    @property
+    def n_modes(self) -> int:
+        return len(self.klam)
+
+    def bounds(self):
+        """Upper bounds of |U_par| and |U_perp| (sums of the mode amplitudes)."""
+        return (float(np.sum(np.abs(self.amp * np.sin(self.theta)))),
+                float(np.sum(np.abs(self.amp * np.cos(self.theta)))))
+
+
+def random_medium(seed: int, n_modes: int = 128, c0: float = 343.0, T0: float = 2e-2, sigma_u: float = 3.0,
+                  kl_range=(0.1, 9.0)) -> Medium:
+    """Mode data of Algorithm 1: phases phi_n and angles theta_n uniform in
+    [0, 2 pi) (SplitMix64 draws: the n_modes phases, then the n_modes
+    angles), wavenumbers equispaced in [K_min, K_max] = [0.1/L, 9/L] with
+    L = 4 lambda and lambda = T0 c0, amplitudes sqrt(E(K_n) / N) from the
+    Gaussian spectrum E(K) = sigma_u^2 K^3 L^4 exp(-(K L / 2)^2) / 8 (SI
+    units as printed: K in 1/m, L in m), normalised by c0."""
+    lam = T0 * c0
+    L = 4.0 * lam
+    r = uniform01(seed, 2 * n_modes)
+    phase = 2.0 * np.pi * r[:n_modes]
+    theta = 2.0 * np.pi * r[n_modes:]
+    K = np.linspace(kl_range[0] / L, kl_range[1] / L, n_modes)
+    E = 0.125 * sigma_u ** 2 * K ** 3 * L ** 4 * np.exp(-(K * L / 2.0) ** 2)
+    amp = np.sqrt(E / n_modes) / c0
+    return Medium(klam=K * lam, theta=theta, phase=phase, amp=amp)
+
+
+def medium_config(nx: int = 4096, ny: int = 2048, n_steps: int = 500, seed: int = 6,
+                  n_modes: int = 128) -> Workload:
+    """N-wave through the random medium of Algorithm 1 (homogeneous B, A).
+    The step follows the WENO CFL bound of both flux directions with the
+    paper's estimate |U_par|, |U_perp| <= 0.05 (Sec. 2):
+    dt (2 pi 0.05 + B max|u0|) <= 0.4 dtau and dt 0.05 <= 0.4 dy."""
+    u0 = nwave(nx, ny, L=1.0, a0=1.0, seed=seed)
+    umax = float(np.max(np.abs(u0)))
+    med = random_medium(seed + 500, n_modes)
+    dtau, dy = 8.0 / nx, 16.0 / ny
+    dt = min(0.4 * dtau / (2.0 * np.pi * 0.05 + 0.05 * umax), 0.4 * dy / 0.05)
+    return Workload(nx=nx, ny=ny, n_steps=n_steps, dt=dt, u0=u0, lf_umax=1.1 * umax, precision="fp64",
+                    name="medium", medium=med)
 
 
 def config(idx: int, nx: int | None = None, ny: int | None = None,
@@ -178,6 +236,9 @@ def oracle_params(w: Workload, **over):
     d = dict(nx=w.nx, ny=w.ny, dt=w.dt, tau_min=w.tau_min, tau_max=w.tau_max, y_min=w.y_min,
              y_max=w.y_max, B=w.B, A=w.A, lf_umax=w.lf_umax, B_prof=tuple(w.B_prof),
              A_prof=tuple(w.A_prof), has_profile=w.has_profile)
+    if w.medium is not None:
+        d.update(mode_klam=w.medium.klam, mode_theta=w.medium.theta, mode_phase=w.medium.phase,
+                 mode_amp=w.medium.amp)
     d.update(over)
     return d
 
