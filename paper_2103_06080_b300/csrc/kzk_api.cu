@@ -319,7 +319,7 @@ std::vector<cx<T>> staged_twiddles(int log2n, int ppt, std::vector<cx<T>>* lo = 
 template <typename T>
 RowArgs<T> row_args(const kzk_plan* p, const void* in, void* out, double sigma, double* diag_rows)
 {
-    RowArgs<T> a;
+    RowArgs<T> a{};
     a.in = (const cx<T>*)in;
     a.out = (cx<T>*)out;
     a.tw = (const cx<T>*)p->twr;
@@ -420,7 +420,7 @@ kzk_status launch_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
 template <typename T>
 ColArgs<T> col_args(const kzk_plan* p)
 {
-    ColArgs<T> a;
+    ColArgs<T> a{};
     memset(&a, 0, sizeof(a));
     a.tw = (const cx<T>*)p->twc;
     a.tw_lo = (const cx<T>*)p->twc_lo;
@@ -559,7 +559,7 @@ kzk_status advance_impl(kzk_plan* p, void* u, long long n_steps, double sigma0, 
 template <typename T>
 kzk_status build_tables(kzk_plan* p, cudaStream_t st)
 {
-    TabArgs a;
+    TabArgs a{};
     a.nx = p->nx;
     a.ny = p->ny;
     a.dt = p->dt;
@@ -640,7 +640,7 @@ kzk_status ensure_buf(void** ptr, long long* cap, long long need, size_t unit)
 template <typename T>
 AdjRowArgs<T> adj_row_args(const kzk_plan* p, const void* m, const void* u, const void* l, void* out, double sigma)
 {
-    AdjRowArgs<T> a;
+    AdjRowArgs<T> a{};
     a.m = (const cx<T>*)m;
     a.u = (const T*)u;
     a.l = (const cx<T>*)l;
@@ -663,7 +663,7 @@ AdjRowArgs<T> adj_row_args(const kzk_plan* p, const void* m, const void* u, cons
 template <typename T>
 AdjColArgs<T> adj_col_args(const kzk_plan* p)
 {
-    AdjColArgs<T> a;
+    AdjColArgs<T> a{};
     memset(&a, 0, sizeof(a));
     a.tw = (const cx<T>*)p->twc;
     a.log2ny = p->log2ny;
@@ -890,7 +890,7 @@ kzk_status batch_coefs(kzk_plan* p, long long n_steps, double sigma0, cudaStream
 template <typename T>
 kzk_status batch_launch(kzk_plan* p, long long n_steps, cudaStream_t st, bool use_graph)
 {
-    BatchArgs<T> B;
+    BatchArgs<T> B{};
     B.inst = (const BatchInst<T>*)p->binst;
     B.row_prefix = p->row_prefix;
     B.col_prefix = p->col_prefix;

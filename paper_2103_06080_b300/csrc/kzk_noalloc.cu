@@ -109,7 +109,7 @@ kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch,
     noalloc_twiddles<T><<<(nx + 255) / 256, 256, 0, st>>>(tw, nx);
     noalloc_staged_twiddles<T><<<(n + 255) / 256, 256, 0, st>>>(tws, log2nx - 1, row_ppt_of<T>());
 
-    RowArgs<T> a;
+    RowArgs<T> a{};
     a.tw = tw;
     a.tws = tws;
     a.diag_rows = nullptr;
