@@ -114,6 +114,40 @@ typedef struct kzk_plan_s kzk_plan;
 kzk_status kzk_plan_create(const kzk_grid *grid, const kzk_coeffs *coeffs, double dt,
                            int32_t batch, kzk_plan **out);
 
+/* Random inhomogeneous medium (Sec. 2, Algorithm 1): the velocity field
+ *   U(sigma, y) = sum_n U~_n cos(|K_n| lambda (sigma cos theta_n + y sin theta_n) + phi_n),
+ *   U~_n = |U~(K_n)| (-sin theta_n, cos theta_n) = (U_par, U_perp) components,
+ * enters b of Eq. 3 as 2 pi U_par d_tau V - U_perp d_y V, computed in the flux
+ * form that follows Eq. 7: WENO5 along tau of -2 pi U_par u - B u^2/2 (global
+ * Lax-Friedrichs speed per row |2 pi U_par| + B(sigma) lf_umax), WENO5 along y
+ * of U_perp u (speed max_y |U_perp|), and the source (d_y U_perp) u with the
+ * derivative of the mode sum.  The mode data (|K_n| lambda, theta_n, phi_n,
+ * |U~(K_n)| / c0, host arrays of n_modes doubles) are inputs; the caller keeps
+ * ownership (they are copied).  n_modes = 0 removes the medium. */
+#define KZK_MAX_MODES 1024
+typedef struct {
+    int32_t n_modes;
+    const double *klam;             /* |K_n| lambda                                  */
+    const double *theta;            /* theta_n: angle of K_n to the sigma axis       */
+    const double *phase;            /* phi_n                                         */
+    const double *amp;              /* |U~(K_n)| / c0                                */
+} kzk_medium;
+
+/* Attach a random medium to a (non-batched) plan.  Afterwards every step of
+ * kzk_advance / kzk_step_stages and kzk_rhs includes the medium terms; the
+ * adjoint entry points return KZK_ERR_STATE (their transposed step covers the
+ * homogeneous and stratified medium only).  Allocates a physical work array
+ * of the state's size and an [n_modes][ny] FP64 table.
+ * Errors: KZK_ERR_ARG (NULL, n_modes outside [0, KZK_MAX_MODES], NULL or
+ * non-finite arrays), KZK_ERR_STATE (batched plan), KZK_ERR_OOM, KZK_ERR_CUDA. */
+kzk_status kzk_plan_set_medium(kzk_plan *plan, const kzk_medium *medium);
+
+/* The medium's coefficients at sigma as the kernels use them: out (host,
+ * [ny][3]) = U_par, U_perp, d U_perp / dy at y_j = y_min + j dy; max_uperp
+ * (host, nullable) = max_j |U_perp|.  Synchronises the stream.
+ * Errors: KZK_ERR_ARG, KZK_ERR_STATE (no medium), KZK_ERR_CUDA. */
+kzk_status kzk_medium_eval(kzk_plan *plan, double sigma, double *out, double *max_uperp, void *stream);
+
 /* Advance u (device, [batch][ny][nx], in place, physical space) by n_steps
  * ExpRK22 steps from sigma0 (Eq. 11 / Algorithm 2).  n_steps = 0 is a no-op.
  * diag_out (host, nullable, `batch` entries): when given, the call
@@ -158,7 +192,8 @@ kzk_status kzk_get_tables(kzk_plan *plan, double *E, double *Phi1, double *Phi2)
  * transpose of the ExpRK22 step (transposed WENO5 including the derivatives
  * of the nonlinear weights, conjugated multipliers, adjoint FFTs), with a
  * checkpoint of the forward state every ckpt_every steps (>= 1) and
- * recomputation of each segment.  u0 is not modified.  g0 may alias g_end. */
+ * recomputation of each segment.  u0 is not modified.  g0 may alias g_end.
+ * KZK_ERR_STATE for a plan with a random medium (kzk_plan_set_medium). */
 kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *g0,
                        int64_t n_steps, double sigma0, int32_t ckpt_every, void *stream);
 

@@ -35,6 +35,12 @@ class KzkCoeffs(ctypes.Structure):
                 ("relax_C", ctypes.c_double * 2), ("relax_theta", ctypes.c_double * 2)]
 
 
+class KzkMedium(ctypes.Structure):
+    _fields_ = [("n_modes", ctypes.c_int32), ("klam", ctypes.POINTER(ctypes.c_double)),
+                ("theta", ctypes.POINTER(ctypes.c_double)), ("phase", ctypes.POINTER(ctypes.c_double)),
+                ("amp", ctypes.POINTER(ctypes.c_double))]
+
+
 class KzkDiag(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_double), ("energy", ctypes.c_double),
                 ("max_abs", ctypes.c_double), ("nonfinite", ctypes.c_double),
@@ -84,6 +90,9 @@ _SIGS = [
     ("kzk_batch_test_barrier", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int64]),
     ("kzk_rhs_noalloc", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs), ctypes.c_int32,
                                        _VP, _VP, ctypes.c_double, _VP]),
+    ("kzk_plan_set_medium", ctypes.c_int, [_VP, ctypes.POINTER(KzkMedium)]),
+    ("kzk_medium_eval", ctypes.c_int, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), _VP]),
 ]
 
 NOALLOC_MAX_POINTS = 1 << 18

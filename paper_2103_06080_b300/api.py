@@ -55,7 +55,34 @@ class Plan:
                   lf_umax=w.lf_umax, tau_min=w.tau_min, tau_max=w.tau_max, y_min=w.y_min, y_max=w.y_max,
                   B_prof=w.B_prof, A_prof=w.A_prof, has_profile=w.has_profile)
         kw.update(over)
-        return cls(**kw)
+        plan = cls(**kw)
+        if getattr(w, "medium", None) is not None:
+            plan.set_medium(w.medium)
+        return plan
+
+    def set_medium(self, medium) -> None:
+        """Attach the random medium of Algorithm 1 (an object with arrays klam,
+        theta, phase, amp per mode; None or zero modes removes it)."""
+        if medium is None:
+            m = L.KzkMedium(n_modes=0)
+            L.check(L.lib().kzk_plan_set_medium(self.handle, ctypes.byref(m)))
+            return
+        arrs = [np.ascontiguousarray(getattr(medium, k), dtype=np.float64) for k in ("klam", "theta", "phase", "amp")]
+        n = len(arrs[0])
+        if any(a.shape != (n,) for a in arrs):
+            raise ValueError("medium arrays must have one value per mode")
+        P = ctypes.POINTER(ctypes.c_double)
+        m = L.KzkMedium(n_modes=n, klam=arrs[0].ctypes.data_as(P), theta=arrs[1].ctypes.data_as(P),
+                        phase=arrs[2].ctypes.data_as(P), amp=arrs[3].ctypes.data_as(P))
+        L.check(L.lib().kzk_plan_set_medium(self.handle, ctypes.byref(m)))
+
+    def medium_eval(self, sigma: float, stream=None):
+        """(U_par, U_perp, dU_perp/dy) per row at sigma and max |U_perp|, as the kernels use them."""
+        out = np.zeros((self.ny, 3))
+        mx = ctypes.c_double()
+        L.check(L.lib().kzk_medium_eval(self.handle, float(sigma), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.byref(mx), _stream_ptr(stream)))
+        return out[:, 0].copy(), out[:, 1].copy(), out[:, 2].copy(), float(mx.value)
 
     # -- helpers -------------------------------------------------------------
     def _check_state(self, t: torch.Tensor, name: str) -> None:

@@ -13,6 +13,7 @@
 #include "kzk_batched.cuh"
 #include "kzk_colpipe.cuh"
 #include "kzk_kernels.cuh"
+#include "kzk_medium.cuh"
 #include "kzk_tables.cuh"
 
 using namespace kzk;
@@ -87,6 +88,13 @@ struct kzk_plan_s {
     int colp_log2tc, colp_thr, colp_by, colp_nby, colp_bt, colp_nbt, sm_count;
     size_t colp_smem1, colp_smem2;
     int* colp_flag;             // device: FLAG_TIMEOUT from a copy wait that ran out
+    // random medium of Algorithm 1 (kzk_plan_set_medium); med_n = 0: homogeneous
+    int med_n, med_nb;          // modes; CTAs of the coefficient kernel (= entries of each bmax)
+    void* med_Ty;               // device [N][ny] double2: exp(i |K_n| lambda sin(theta_n) y_j)
+    double* med_mode;           // device [5][N]: a_sig, phase, w0, w1, w2 (see kzk_medium.cuh)
+    double* med_coef;           // device [2][ny][3]: U_par, U_perp, dU_perp/dy of stages 1 and 2
+    double* med_bmax;           // device [2][med_nb]
+    void* uphys;                // device [batch][ny][nx]: physical rows of the current stage
     // adjoint workspace (allocated on first use)
     void *lam, *mu, *nu, *ls;   // spectral adjoint arrays
     void* seg;                  // segment store: physical u^n, u*^n of k steps, [(2 k)][batch][ny][nx]
@@ -245,6 +253,7 @@ kzk_status configure(kzk_plan* p)
     KZK_TRY((set_row_attr<T, ROW_RHS>(sm)));
     KZK_TRY((set_row_attr<T, ROW_FWD>(sm)));
     KZK_TRY((set_row_attr<T, ROW_INV>(sm)));
+    KZK_TRY((set_row_attr<T, ROW_RHS_MED>(sm)));
     KZK_TRY((set_col_attr<T, COL_STAGE1>(sm)));
     KZK_TRY((set_col_attr<T, COL_STAGE2>(sm)));
     KZK_TRY((set_adj_row_attr<T, ADJ_ROW_2>(sm)));
@@ -434,6 +443,51 @@ ColArgs<T> col_args(const kzk_plan* p)
     return a;
 }
 
+// Random-medium coefficients at sigma into stage buffer `stage` (0 or 1).
+kzk_status launch_medium(kzk_plan* p, double sigma, int stage, cudaStream_t st)
+{
+    MedArgs m{};
+    m.Ty = (const double2*)p->med_Ty;
+    m.a_sig = p->med_mode;
+    m.phase = p->med_mode + p->med_n;
+    m.w = p->med_mode + 2 * p->med_n;
+    m.n_modes = p->med_n;
+    m.ny = p->ny;
+    m.sigma = sigma;
+    m.coef = p->med_coef + (size_t)stage * 3 * p->ny;
+    m.bmax = p->med_bmax + (size_t)stage * p->med_nb;
+    medium_kernel<<<p->med_nb, MED_ROWS * MED_GROUPS, 0, st>>>(m);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
+// STEP 1 / STEP 3 of Algorithm 2: the row pass(es) computing the tau-spectrum
+// of b(sigma, u) from the spectral state Vin.  Homogeneous / stratified
+// medium: one pass (C2R, WENO5 along tau, R2C).  Random medium: the
+// coefficient kernel, a C2R pass to the physical rows (with the row
+// statistics), then the b pass with the y-flux and source terms.
+// diag_rows, u_out: nullable (u_out: the physical rows, homogeneous only).
+template <typename T>
+kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, double* diag_rows, void* u_out,
+                     int stage, cudaStream_t st)
+{
+    if (p->med_n > 0) {
+        KZK_TRY(launch_medium(p, sigma, stage, st));
+        RowArgs<T> ri = row_args<T>(p, Vin, p->uphys, 0.0, diag_rows);
+        KZK_TRY((launch_row<T, ROW_INV>(p, ri, st)));
+        RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, nullptr);
+        r.uphys = (const T*)p->uphys;
+        r.med_coef = p->med_coef + (size_t)stage * 3 * p->ny;
+        r.med_bmax = p->med_bmax + (size_t)stage * p->med_nb;
+        r.n_bmax = p->med_nb;
+        r.inv_dy = (T)(p->ny / (p->g.y_max - p->g.y_min));
+        return launch_row<T, ROW_RHS_MED>(p, r, st);
+    }
+    RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, diag_rows);
+    r.u_out = (T*)u_out;
+    return launch_row<T, ROW_RHS>(p, r, st);
+}
+
 // One ExpRK22 step on the spectral state p->V (Algorithm 2, STEP 1-4).
 // diag_hist_step: where C1 writes this step's diagnostics (nullable).
 // vs_out / b1_out / b2_out: destinations (default: plan workspace).
@@ -444,9 +498,7 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     // V is read-only; the result goes to V_out (default: in place).  u_n, u_s
     // (nullable): where the row passes also store the physical u^n and u*.
     if (!V_out) V_out = V;
-    RowArgs<T> r1 = row_args<T>(p, V, p->b1, sigma, diag_hist_step ? p->diag_rows : nullptr);
-    r1.u_out = (T*)u_n;
-    KZK_TRY((launch_row<T, ROW_RHS>(p, r1, st)));
+    KZK_TRY(rhs_stage<T>(p, sigma, V, p->b1, diag_hist_step ? p->diag_rows : nullptr, u_n, 0, st));
     ColArgs<T> c1 = col_args<T>(p);
     c1.a = (const cx<T>*)V;
     c1.b = (const cx<T>*)p->b1;
@@ -457,9 +509,7 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     c1.diag_rows = diag_hist_step ? p->diag_rows : nullptr;
     c1.diag_hist = diag_hist_step;
     KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
-    RowArgs<T> r2 = row_args<T>(p, vs, p->b2, sigma + p->dt, nullptr);
-    r2.u_out = (T*)u_s;
-    KZK_TRY((launch_row<T, ROW_RHS>(p, r2, st)));
+    KZK_TRY(rhs_stage<T>(p, sigma + p->dt, vs, p->b2, nullptr, u_s, 1, st));
     ColArgs<T> c2 = col_args<T>(p);
     c2.a = (const cx<T>*)p->b1;
     c2.b = (const cx<T>*)p->b2;
@@ -613,7 +663,8 @@ void plan_free(kzk_plan* p)
     void* ptrs[] = {p->V, p->b1, p->vs, p->b2, p->E, p->P1, p->P2, p->E_lo, p->twr, p->twc, p->twc_lo,
                     p->tws_row, p->twc_full,
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
-                    p->seg, p->ckpt, p->colp_flag};
+                    p->seg, p->ckpt, p->colp_flag, p->med_Ty, p->med_mode, p->med_coef, p->med_bmax,
+                    p->uphys};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1097,8 +1148,7 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
     for (long long s = 0; s < n_steps; s++) {
         const double sigma = sigma0 + (double)s * p->dt;
         KZK_CUDA(cudaEventRecord(ev[0], st));
-        RowArgs<T> r1 = row_args<T>(p, p->V, p->b1, sigma, p->diag_rows);
-        KZK_TRY((launch_row<T, ROW_RHS>(p, r1, st)));
+        KZK_TRY(rhs_stage<T>(p, sigma, p->V, p->b1, p->diag_rows, nullptr, 0, st));
         KZK_CUDA(cudaEventRecord(ev[1], st));
         ColArgs<T> c1 = col_args<T>(p);
         c1.a = (const cx<T>*)p->V;
@@ -1111,8 +1161,7 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
         c1.diag_hist = p->diag_hist + (size_t)s * p->batch * 4;
         KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
         KZK_CUDA(cudaEventRecord(ev[2], st));
-        RowArgs<T> r2 = row_args<T>(p, p->vs, p->b2, sigma + p->dt, nullptr);
-        KZK_TRY((launch_row<T, ROW_RHS>(p, r2, st)));
+        KZK_TRY(rhs_stage<T>(p, sigma + p->dt, p->vs, p->b2, nullptr, nullptr, 1, st));
         KZK_CUDA(cudaEventRecord(ev[3], st));
         ColArgs<T> c2 = col_args<T>(p);
         c2.a = (const cx<T>*)p->b1;
@@ -1263,6 +1312,81 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     return KZK_OK;
 }
 
+kzk_status kzk_plan_set_medium(kzk_plan* p, const kzk_medium* m)
+{
+    if (!p || !m) return fail(KZK_ERR_ARG, "plan or medium is NULL");
+    if (p->batched) return fail(KZK_ERR_STATE, "batched plans take no medium");
+    const int N = m->n_modes;
+    if (N < 0 || N > KZK_MAX_MODES) return fail(KZK_ERR_ARG, "n_modes = %d outside [0, %d]", N, KZK_MAX_MODES);
+    if (N > 0 && (!m->klam || !m->theta || !m->phase || !m->amp))
+        return fail(KZK_ERR_ARG, "mode arrays are NULL");
+    for (int n = 0; n < N; n++)
+        if (!std::isfinite(m->klam[n]) || !std::isfinite(m->theta[n]) || !std::isfinite(m->phase[n]) ||
+            !std::isfinite(m->amp[n]))
+            return fail(KZK_ERR_ARG, "mode %d: non-finite value", n);
+    void* old[] = {p->med_Ty, p->med_mode, p->med_coef, p->med_bmax, p->uphys};
+    for (void* q : old)
+        if (q) KZK_CUDA(cudaFree(q));
+    p->med_Ty = nullptr; p->med_mode = nullptr; p->med_coef = nullptr; p->med_bmax = nullptr; p->uphys = nullptr;
+    p->med_n = 0;
+    if (N == 0) return KZK_OK;
+    const int ny = p->ny;
+    const int nb = (ny + MED_ROWS - 1) / MED_ROWS;
+    std::vector<double> mode(5 * (size_t)N), Ty(2 * (size_t)N * ny);
+    const double dy = (p->g.y_max - p->g.y_min) / ny;
+    for (int n = 0; n < N; n++) {
+        const double st = std::sin(m->theta[n]), ct = std::cos(m->theta[n]);
+        const double c_n = m->klam[n] * st;                 // d(arg)/dy
+        mode[n] = m->klam[n] * ct;                          // d(arg)/dsigma
+        mode[N + n] = m->phase[n];
+        mode[2 * N + n] = -m->amp[n] * st;                  // U_par weight
+        mode[3 * N + n] = m->amp[n] * ct;                   // U_perp weight
+        mode[4 * N + n] = -m->amp[n] * ct * c_n;            // d U_perp / dy weight (of Im P)
+        for (int j = 0; j < ny; j++) {
+            const double y = p->g.y_min + j * dy;
+            Ty[2 * ((size_t)n * ny + j)] = std::cos(c_n * y);
+            Ty[2 * ((size_t)n * ny + j) + 1] = std::sin(c_n * y);
+        }
+    }
+    cudaError_t e = cudaMalloc(&p->med_Ty, Ty.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->med_mode, mode.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->med_coef, 2 * 3 * (size_t)ny * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->med_bmax, 2 * (size_t)nb * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p->uphys, (size_t)p->batch * p->inst_stride * p->csz);
+    if (e == cudaSuccess) e = cudaMemcpy(p->med_Ty, Ty.data(), Ty.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->med_mode, mode.data(), mode.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        void* got[] = {p->med_Ty, p->med_mode, p->med_coef, p->med_bmax, p->uphys};
+        for (void* q : got)
+            if (q) cudaFree(q);
+        p->med_Ty = nullptr; p->med_mode = nullptr; p->med_coef = nullptr; p->med_bmax = nullptr; p->uphys = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? KZK_ERR_OOM : KZK_ERR_CUDA, "medium set-up: %s",
+                    cudaGetErrorString(e));
+    }
+    p->med_n = N;
+    p->med_nb = nb;
+    p->ck_steps = 0;      // stored adjoint checkpoints belong to the old medium
+    return KZK_OK;
+}
+
+kzk_status kzk_medium_eval(kzk_plan* p, double sigma, double* out, double* max_uperp, void* stream)
+{
+    if (!p || !out) return fail(KZK_ERR_ARG, "NULL argument");
+    if (p->med_n < 1) return fail(KZK_ERR_STATE, "no medium set");
+    cudaStream_t st = (cudaStream_t)stream;
+    KZK_TRY(launch_medium(p, sigma, 0, st));
+    KZK_CUDA(cudaMemcpyAsync(out, p->med_coef, 3 * (size_t)p->ny * sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<double> bm(p->med_nb);
+    KZK_CUDA(cudaMemcpyAsync(bm.data(), p->med_bmax, bm.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KZK_CUDA(cudaStreamSynchronize(st));
+    if (max_uperp) {
+        double mx = 0.0;
+        for (double v : bm) mx = std::max(mx, v);
+        *max_uperp = mx;
+    }
+    return KZK_OK;
+}
+
 kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coeffs, const double* dts, int32_t n,
                                    int32_t flags, kzk_plan** out)
 {
@@ -1368,11 +1492,11 @@ kzk_status kzk_rhs(kzk_plan* p, const void* u, void* b, double sigma, void* stre
     cudaStream_t st = (cudaStream_t)stream;
     if (p->prec == KZK_FP64) {
         KZK_TRY(to_spectral<double>(p, u, p->V, st));
-        KZK_TRY((launch_row<double, ROW_RHS>(p, row_args<double>(p, p->V, p->b1, sigma, nullptr), st)));
+        KZK_TRY(rhs_stage<double>(p, sigma, p->V, p->b1, nullptr, nullptr, 0, st));
         return to_physical<double>(p, p->b1, b, 1.0 / p->nx, nullptr, st);
     }
     KZK_TRY(to_spectral<float>(p, u, p->V, st));
-    KZK_TRY((launch_row<float, ROW_RHS>(p, row_args<float>(p, p->V, p->b1, sigma, nullptr), st)));
+    KZK_TRY(rhs_stage<float>(p, sigma, p->V, p->b1, nullptr, nullptr, 0, st));
     return to_physical<float>(p, p->b1, b, 1.0 / p->nx, nullptr, st);
 }
 
@@ -1446,6 +1570,7 @@ kzk_status kzk_advance_checkpointed(kzk_plan* p, void* u, int64_t n_steps, doubl
 {
     if (!p || !u) return fail(KZK_ERR_ARG, "plan or u is NULL");
     if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
+    if (p->med_n > 0) return fail(KZK_ERR_STATE, "the adjoint does not cover the random-medium terms");
     if (n_steps < 1 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
     cudaStream_t st = (cudaStream_t)stream;
     p->ck_steps = 0;
@@ -1461,6 +1586,7 @@ kzk_status kzk_adjoint_checkpointed(kzk_plan* p, const void* g_end, void* g0, vo
 {
     if (!p || !g_end || !g0) return fail(KZK_ERR_ARG, "NULL argument");
     if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
+    if (p->med_n > 0) return fail(KZK_ERR_STATE, "the adjoint does not cover the random-medium terms");
     if (p->ck_steps < 1) return fail(KZK_ERR_STATE, "no checkpointed forward run stored in this plan");
     cudaStream_t st = (cudaStream_t)stream;
     return p->prec == KZK_FP64 ? reverse_sweep<double>(p, g_end, g0, st) : reverse_sweep<float>(p, g_end, g0, st);
@@ -1470,6 +1596,7 @@ kzk_status kzk_adjoint(kzk_plan* p, const void* u0, const void* g_end, void* g0,
                        int32_t ckpt_every, void* stream)
 {
     if (!p || !u0 || !g_end || !g0) return fail(KZK_ERR_ARG, "NULL argument");
+    if (p->med_n > 0) return fail(KZK_ERR_STATE, "the adjoint does not cover the random-medium terms");
     if (n_steps < 0 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 0 and ckpt_every >= 1");
     cudaStream_t st = (cudaStream_t)stream;
     if (n_steps == 0) {

@@ -72,6 +72,9 @@ def test_null_arguments_are_rejected():
     assert lib.kzk_tau_fft(None, None, None, 1, None) == L.KZK_ERR_ARG
     assert lib.kzk_adjoint(None, None, None, None, 1, 0.0, 1, None) == L.KZK_ERR_ARG
     assert lib.kzk_plan_destroy(None) == L.KZK_OK
+    m = L.KzkMedium(n_modes=0)
+    assert lib.kzk_plan_set_medium(None, ctypes.byref(m)) == L.KZK_ERR_ARG
+    assert lib.kzk_medium_eval(None, 0.0, None, None, None) == L.KZK_ERR_ARG
 
 
 def test_binding_structs_match_the_header(tmp_path):
@@ -82,7 +85,7 @@ def test_binding_structs_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"kzk_grid": L.KzkGrid, "kzk_coeffs": L.KzkCoeffs, "kzk_diag": L.KzkDiag}
+    structs = {"kzk_grid": L.KzkGrid, "kzk_coeffs": L.KzkCoeffs, "kzk_diag": L.KzkDiag, "kzk_medium": L.KzkMedium}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "kzk.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')

@@ -1,0 +1,114 @@
+"""Parity of the random-medium path (Algorithm 1; the U_par / U_perp terms of
+Eq. 2a in the flux form after Eq. 7) with the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_06080_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _api():
+    from paper_2103_06080_b300 import api
+    return api
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("ny", [16, 256, 2048])
+def test_coefficients_match_oracle(ny):
+    api = _api()
+    w = inputs.medium_config(64, ny, 10)
+    plan = api.Plan.from_workload(w)
+    p = oracle.Params(**inputs.oracle_params(w))
+    for sigma in (0.0, 1.3, 57.0):
+        a, b, c, mx = plan.medium_eval(sigma)
+        ra, rb, rc = oracle.medium(p, sigma)
+        for got, ref in ((a, ra), (b, rb), (c, rc)):
+            assert np.max(np.abs(got - ref)) < 1e-14 * max(1.0, np.max(np.abs(ref)) / 1e-2)
+        assert mx == np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 16), (512, 128), (2048, 64)])
+def test_rhs_matches_oracle(nx, ny):
+    api = _api()
+    w = inputs.medium_config(nx, ny, 10)
+    plan = api.Plan.from_workload(w)
+    sigma = 3.7
+    b = plan.rhs(_dev(w.u0), sigma=sigma).cpu().numpy()
+    ref = oracle.rhs(oracle.Params(**inputs.oracle_params(w)), w.u0, sigma=sigma)
+    assert rel_linf(b, ref) < 1e-12
+
+
+def test_run_fp64_parity():
+    api = _api()
+    w = inputs.medium_config(512, 256, 40)
+    plan = api.Plan.from_workload(w)
+    u = _dev(w.u0)
+    plan.advance(u, w.n_steps)
+    p = oracle.Params(**inputs.oracle_params(w))
+    ref = oracle.run(p, w.u0, w.n_steps, threads=True)
+    homog = oracle.run(oracle.Params(**inputs.oracle_params(w, mode_klam=None, mode_theta=None, mode_phase=None,
+                                                            mode_amp=None)), w.u0, w.n_steps, threads=True)
+    assert rel_l2(homog, ref) > 1e-3              # the medium changes the answer
+    assert rel_linf(u.cpu().numpy(), ref) < 1e-11
+
+
+def test_run_fp32_error():
+    api = _api()
+    w = inputs.medium_config(512, 256, 40)
+    plan = api.Plan.from_workload(w, precision="fp32")
+    u = _dev(w.u0, torch.float32)
+    plan.advance(u, w.n_steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    assert rel_l2(u.double().cpu().numpy(), ref) < 1e-5
+
+
+def test_batch_shares_the_medium():
+    api = _api()
+    w = inputs.medium_config(256, 64, 12)
+    u0 = np.stack([w.u0, 0.7 * w.u0[::-1]])
+    plan = api.Plan.from_workload(w, batch=2)
+    u = _dev(u0)
+    plan.advance(u, w.n_steps)
+    p = oracle.Params(**inputs.oracle_params(w))
+    for i in range(2):
+        ref = oracle.run(p, np.ascontiguousarray(u0[i]), w.n_steps)
+        assert rel_linf(u[i].cpu().numpy(), ref) < 1e-11
+
+
+def test_removing_the_medium_restores_the_homogeneous_path():
+    api = _api()
+    w = inputs.medium_config(128, 32, 5)
+    plan = api.Plan.from_workload(w)
+    plan.set_medium(None)
+    a = _dev(w.u0)
+    plan.advance(a, 5)
+    w.medium = None
+    ref_plan = api.Plan.from_workload(w)
+    b = _dev(w.u0)
+    ref_plan.advance(b, 5)
+    assert torch.equal(a, b)
+
+
+def test_adjoint_is_refused_with_a_medium():
+    api = _api()
+    w = inputs.medium_config(64, 16, 4)
+    plan = api.Plan.from_workload(w)
+    u = _dev(w.u0)
+    with pytest.raises(Exception, match="STATE"):
+        plan.adjoint(u, u.clone(), 4, ckpt_every=2)
+    with pytest.raises(Exception, match="STATE"):
+        plan.advance_checkpointed(u, 4, 0.0, 2)
