@@ -441,6 +441,29 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
                           "launch": bp.info(), "plan_create_s": t_plan,
                           "note": "one cooperative persistent kernel per call, replayed from a CUDA graph"}
         bp.close()
+    # random medium of Algorithm 1 (the paper's inhomogeneous workload) on the same grid
+    wm = inputs.medium_config(4096, 2048, 500)
+    med = {"workload": f"N-wave through the random medium of Algorithm 1 ({wm.medium.n_modes} modes), 4096x2048, "
+                       f"homogeneous B, A; dt from the paper's |U| <= 0.05",
+           "dt": wm.dt}
+    for name, dtype, k in (("fp64", torch.float64, 20), ("fp32", torch.float32, 100)):
+        pm = api.Plan.from_workload(wm, precision=name)
+        um = torch.tensor(wm.u0, dtype=dtype, device=dev)
+        pm.advance(um, 3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pm.advance(um, k)
+        e1.record()
+        torch.cuda.synchronize()
+        msm = e0.elapsed_time(e1) / k
+        ktm = pm.kernel_times(um, 5)
+        med[name] = {"value": wm.nx * wm.ny / (msm * 1e-3), "unit": UNIT, "ms_per_step": msm, "steps": k,
+                     "stage_ms": dict(zip(["rows_stage1 (coefficients + C2R + b pass)", "col_stage1",
+                                           "rows_stage2 (coefficients + C2R + b pass)", "col_stage2"], ktm))}
+        pm.close()
+        del um
+    out["random_medium"] = med
     # cuFFT comparison on the 4096 x 2048 grid
     cmp = {}
     for name, dtype, ms_ours in (("fp64", torch.float64, ms_fp64), ("fp32", torch.float32, out["fp32"]["ms_per_step"])):
