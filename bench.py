@@ -421,26 +421,32 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
     # batched persistent launch: 64 heterogeneous FP32 propagations
     if not args.no_batched:
         ws = inputs.batched_config(seed=5, count=args.batch_count, n_steps=500)
-        t0 = time.perf_counter()
-        bp = api.BatchedPlan(ws, precision="fp32", autotune=True)
-        t_plan = time.perf_counter() - t0
-        us = [torch.tensor(w.u0, dtype=torch.float32, device=dev) for w in ws]
-        bp.advance(us, 2)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        bp.advance(us, args.batch_steps)
-        e1.record()
-        torch.cuda.synchronize()
-        msb = e0.elapsed_time(e1)
         pts = sum(w.nx * w.ny for w in ws)
         out["batched"] = {"workload": f"{len(ws)} FP32 N-wave propagations, Nx in 1024..8192, Ny in 256..2048 "
                                       f"(seeded), own dsigma and profiles each; {args.batch_steps} steps per call",
-                          "value": pts * args.batch_steps / (msb * 1e-3), "unit": UNIT,
-                          "ms_per_step": msb / args.batch_steps, "points_per_step": pts,
-                          "launch": bp.info(), "plan_create_s": t_plan,
-                          "note": "one cooperative persistent kernel per call, replayed from a CUDA graph"}
-        bp.close()
+                          "unit": UNIT, "points_per_step": pts}
+        for mode in ("persistent", "streams"):
+            t0 = time.perf_counter()
+            bp = api.BatchedPlan(ws, precision="fp32", autotune=True, mode=mode)
+            t_plan = time.perf_counter() - t0
+            us = [torch.tensor(w.u0, dtype=torch.float32, device=dev) for w in ws]
+            bp.advance(us, args.batch_steps)              # captures the graph
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bp.advance(us, args.batch_steps)
+            e1.record()
+            torch.cuda.synchronize()
+            msb = e0.elapsed_time(e1)
+            out["batched"][mode] = {
+                "value": pts * args.batch_steps / (msb * 1e-3), "ms_per_step": msb / args.batch_steps,
+                "plan_create_s": t_plan, "launch": bp.info(),
+                "note": ("one cooperative persistent kernel per call (all instances, grid barriers between "
+                         "passes), replayed from a CUDA graph" if mode == "persistent" else
+                         "one CUDA graph per call: every instance's own kernels on its own captured stream, "
+                         "the instances concurrently")}
+            bp.close()
+            del us
     # random medium of Algorithm 1 (the paper's inhomogeneous workload) on the same grid
     wm = inputs.medium_config(4096, 2048, 500)
     med = {"workload": f"N-wave through the random medium of Algorithm 1 ({wm.medium.n_modes} modes), 4096x2048, "

@@ -199,6 +199,12 @@ kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *
 
 /* Flags of kzk_plan_create_batched. */
 #define KZK_BATCH_AUTOTUNE 1
+/* Instead of the persistent kernel: each kzk_advance_batched call replays a
+ * CUDA graph in which every instance runs the launches of kzk_advance (the
+ * single-plan kernels, sized for that instance) on its own captured stream,
+ * the instances concurrently.  The graph is cached per (n_steps, sigma0,
+ * state pointers). */
+#define KZK_BATCH_STREAMS 2
 
 /* Plan for n independent propagations with their own grids (same precision),
  * coefficients and steps dts[i], all advanced by one persistent cooperative
@@ -220,14 +226,15 @@ kzk_status kzk_advance_batched(kzk_plan *plan, void *const *u, int64_t n_steps, 
 
 /* Launch configuration of a batched plan: CTAs of the persistent launch,
  * log2 cap on the column-tile width (the autotuner's choice), dynamic shared
- * memory per CTA. */
+ * memory per CTA (all 0 for a KZK_BATCH_STREAMS plan). */
 kzk_status kzk_batch_info(kzk_plan *plan, int32_t *grid_ctas, int32_t *tile_cap, int64_t *smem_bytes);
 
 /* Testing hook of the bounded grid barrier: later batched launches of this
  * plan wait for extra_blocks more CTAs than they launch (extra_blocks > 0
  * makes every barrier wait run out) with a wait bound of timeout_ms; such
  * launches are not graph-captured.  extra_blocks = 0 restores normal
- * operation (the bound stays timeout_ms). */
+ * operation (the bound stays timeout_ms).  KZK_ERR_STATE for a
+ * KZK_BATCH_STREAMS plan. */
 kzk_status kzk_batch_test_barrier(kzk_plan *plan, int32_t extra_blocks, int64_t timeout_ms);
 
 /* kzk_advance that also keeps, inside the plan, the spectral state every

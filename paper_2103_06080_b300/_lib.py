@@ -97,6 +97,7 @@ _SIGS = [
 
 NOALLOC_MAX_POINTS = 1 << 18
 KZK_BATCH_AUTOTUNE = 1
+KZK_BATCH_STREAMS = 2
 
 
 def lib():

@@ -212,9 +212,14 @@ def _grid_coeffs(w, precision):
 
 class BatchedPlan:
     """Many independent propagations (own grid, coefficients and dsigma each)
-    advanced by one persistent, graph-captured launch per call."""
+    advanced by one graph launch per call: mode "persistent" -- one
+    persistent cooperative kernel for all instances; mode "streams" -- every
+    instance's own kernels on its own captured stream, concurrently."""
 
-    def __init__(self, workloads: Sequence, precision: str = "fp32", autotune: bool = True):
+    def __init__(self, workloads: Sequence, precision: str = "fp32", autotune: bool = True,
+                 mode: str = "persistent"):
+        if mode not in ("persistent", "streams"):
+            raise ValueError("mode must be 'persistent' or 'streams'")
         if precision not in ("fp64", "fp32"):
             raise ValueError("precision must be 'fp64' or 'fp32'")
         self.precision = precision
@@ -228,8 +233,9 @@ class BatchedPlan:
             gs[i], cs[i] = _grid_coeffs(w, precision)
             dts[i] = w.dt
         h = ctypes.c_void_p()
-        L.check(L.lib().kzk_plan_create_batched(gs, cs, dts, n, L.KZK_BATCH_AUTOTUNE if autotune else 0,
-                                                ctypes.byref(h)))
+        flags = (L.KZK_BATCH_AUTOTUNE if autotune else 0) | (L.KZK_BATCH_STREAMS if mode == "streams" else 0)
+        L.check(L.lib().kzk_plan_create_batched(gs, cs, dts, n, flags, ctypes.byref(h)))
+        self.mode = mode
         self._h = h
         self.n = n
 

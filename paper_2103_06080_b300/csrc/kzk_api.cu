@@ -120,6 +120,12 @@ struct kzk_plan_s {
     unsigned test_extra_blocks; // testing hook: barrier waits for this many extra CTAs
     long long timeout_ns;
     cudaStream_t cap_stream;    // capturable stream for building the graph
+    // KZK_BATCH_STREAMS: the graph advances every instance on its own stream
+    int batch_streams;
+    double graph_sigma0;
+    std::vector<void*>* graph_u;        // state pointers the cached graph was captured with
+    std::vector<cudaStream_t>* side;    // one captured stream per instance
+    std::vector<cudaEvent_t>* evs;      // fork event, then one join event per instance
 };
 
 namespace {
@@ -657,6 +663,15 @@ void plan_free(kzk_plan* p)
     }
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->side) {
+        for (cudaStream_t q : *p->side) cudaStreamDestroy(q);
+        delete p->side;
+    }
+    if (p->evs) {
+        for (cudaEvent_t q : *p->evs) cudaEventDestroy(q);
+        delete p->evs;
+    }
+    delete p->graph_u;
     void* bptrs[] = {p->binst, p->row_prefix, p->col_prefix, p->coef, p->bar};
     for (void* q : bptrs)
         if (q) cudaFree(q);
@@ -1081,6 +1096,81 @@ kzk_status advance_batched_impl(kzk_plan* p, void* const* u, long long n_steps, 
     return KZK_OK;
 }
 
+// KZK_BATCH_STREAMS: one CUDA graph per (n_steps, sigma0, state pointers) in
+// which every instance runs kzk_advance's launches on its own captured
+// stream, forked from and joined back into one origin stream, so the
+// instances' kernels run concurrently; replayed on the caller's stream.
+template <typename T>
+kzk_status advance_streams_impl(kzk_plan* p, void* const* u, long long n_steps, double sigma0, cudaStream_t st,
+                                kzk_diag* dout)
+{
+    const int n = (int)p->subs->size();
+    // every buffer the launches touch exists before capture (no allocation
+    // may happen while capturing)
+    for (kzk_plan* q : *p->subs) KZK_TRY(ensure_hist(q, std::max(1LL, n_steps)));
+    std::vector<void*> us(u, u + n);
+    const bool cached = p->graph && p->graph_steps == n_steps && p->graph_sigma0 == sigma0 && p->graph_u &&
+                        *p->graph_u == us;
+    if (!cached) {
+        if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+        if (!p->cap_stream) KZK_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        if (!p->side) {
+            p->side = new (std::nothrow) std::vector<cudaStream_t>();
+            p->evs = new (std::nothrow) std::vector<cudaEvent_t>();
+            if (!p->side || !p->evs) return fail(KZK_ERR_OOM, "host allocation failed");
+            for (int i = 0; i < n; i++) {
+                cudaStream_t q = nullptr;
+                KZK_CUDA(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+                p->side->push_back(q);
+            }
+            for (int i = 0; i <= n; i++) {
+                cudaEvent_t e = nullptr;
+                KZK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                p->evs->push_back(e);
+            }
+        }
+        cudaGraph_t g = nullptr;
+        KZK_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        kzk_status s = KZK_OK;
+        cudaError_t e = cudaEventRecord((*p->evs)[0], p->cap_stream);
+        for (int i = 0; i < n && e == cudaSuccess && s == KZK_OK; i++) {
+            cudaStream_t q = (*p->side)[i];
+            e = cudaStreamWaitEvent(q, (*p->evs)[0], 0);
+            if (e == cudaSuccess) s = advance_impl<T>((*p->subs)[i], u[i], n_steps, sigma0, q, nullptr);
+            if (e == cudaSuccess && s == KZK_OK) e = cudaEventRecord((*p->evs)[i + 1], q);
+            if (e == cudaSuccess && s == KZK_OK) e = cudaStreamWaitEvent(p->cap_stream, (*p->evs)[i + 1], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+        if (s != KZK_OK || e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (s != KZK_OK) return s;
+            return fail(KZK_ERR_CUDA, "graph capture of the batched streams: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&p->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { p->graph = nullptr; return fail(KZK_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+        p->graph_steps = n_steps;
+        p->graph_sigma0 = sigma0;
+        if (!p->graph_u) p->graph_u = new (std::nothrow) std::vector<void*>();
+        if (!p->graph_u) return fail(KZK_ERR_OOM, "host allocation failed");
+        *p->graph_u = us;
+    }
+    KZK_CUDA(cudaGraphLaunch(p->graph, st));
+    KZK_LAUNCHED();
+    for (kzk_plan* q : *p->subs) q->hist_steps = n_steps;
+    if (dout) {
+        kzk_status worst = KZK_OK;
+        for (size_t i = 0; i < p->subs->size(); i++) {
+            kzk_status s = finish_diag((*p->subs)[i], n_steps, st, &dout[i]);
+            if (s == KZK_ERR_NONFINITE || (s == KZK_ERR_CFL && worst == KZK_OK)) worst = s;
+            else if (s != KZK_OK && s != KZK_ERR_CFL && s != KZK_ERR_NONFINITE) return s;
+        }
+        return worst;
+    }
+    return KZK_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1417,6 +1507,11 @@ kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coef
     if (e == cudaSuccess) e = cudaMalloc(&p->bar, 4 * sizeof(unsigned));
     if (e != cudaSuccess) { plan_free(p); return fail(KZK_ERR_OOM, "batched plan allocation: %s", cudaGetErrorString(e)); }
     kzk_status s;
+    if (flags & KZK_BATCH_STREAMS) {
+        p->batch_streams = 1;
+        *out = p;
+        return KZK_OK;
+    }
     if (flags & KZK_BATCH_AUTOTUNE)
         s = p->prec == KZK_FP64 ? batch_autotune<double>(p, 0) : batch_autotune<float>(p, 0);
     else
@@ -1436,6 +1531,9 @@ kzk_status kzk_advance_batched(kzk_plan* p, void* const* u, int64_t n_steps, dou
         if (!u[i]) return fail(KZK_ERR_ARG, "u[%d] is NULL", i);
     if (n_steps == 0 && !diag_out) return KZK_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    if (p->batch_streams)
+        return p->prec == KZK_FP64 ? advance_streams_impl<double>(p, u, n_steps, sigma0, st, diag_out)
+                                   : advance_streams_impl<float>(p, u, n_steps, sigma0, st, diag_out);
     return p->prec == KZK_FP64 ? advance_batched_impl<double>(p, u, n_steps, sigma0, st, diag_out)
                                : advance_batched_impl<float>(p, u, n_steps, sigma0, st, diag_out);
 }
@@ -1452,6 +1550,7 @@ kzk_status kzk_batch_info(kzk_plan* p, int32_t* grid_ctas, int32_t* tile_cap, in
 kzk_status kzk_batch_test_barrier(kzk_plan* p, int32_t extra_blocks, int64_t timeout_ms)
 {
     if (!p || !p->batched) return fail(KZK_ERR_STATE, "not a batched plan");
+    if (p->batch_streams) return fail(KZK_ERR_STATE, "a KZK_BATCH_STREAMS plan has no grid barrier");
     if (extra_blocks < 0 || timeout_ms < 1 || timeout_ms > 60000) return fail(KZK_ERR_ARG, "bad barrier test values");
     p->test_extra_blocks = (unsigned)extra_blocks;
     p->timeout_ns = timeout_ms * 1000000LL;

@@ -16,12 +16,13 @@ def _small_batch(precision):
     return ws
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batched_matches_single_plans(prec):
+@pytest.mark.parametrize("prec,mode", [("fp64", "persistent"), ("fp32", "persistent"), ("fp64", "streams"),
+                                       ("fp32", "streams")])
+def test_batched_matches_single_plans(prec, mode):
     from paper_2103_06080_b300 import api
     dt = torch.float64 if prec == "fp64" else torch.float32
     ws = _small_batch(prec)
-    bp = api.BatchedPlan(ws, precision=prec, autotune=True)
+    bp = api.BatchedPlan(ws, precision=prec, autotune=True, mode=mode)
     us = [torch.tensor(w.u0, dtype=dt, device="cuda") for w in ws]
     st, diags = bp.advance(us, 20, diag=True)
     assert st == 0
