@@ -55,18 +55,19 @@ __device__ __forceinline__ void st_real(cx<T>* buf, int k, T v)
 
 // 16 (eps + beta)^2 of the left, centre and right indicators of the stencil
 // (fm1, f0, fp1) centred at c, formed as (4 eps + 4 beta)^2: the common factor
-// 16 cancels in the weights, and 4 beta = 13/3 S^2 + x^2 needs no 1/4.
-// eps4 = 4 eps.
+// 16 cancels in the weights, and 4 beta = 13/3 S^2 + x^2 needs no 1/4; the
+// shared part 13/3 S^2 + 4 eps is formed once.  eps4 = 4 eps (for a flux
+// scaled by s, pass 4 s^2 eps: the weights are unchanged).
 template <typename T>
 __device__ __forceinline__ void indicators(T fm1, T f0, T fp1, T eps4, T& tl, T& tc, T& tr)
 {
     const T S = fm1 - T(2) * f0 + fp1;
     const T D = fp1 - fm1;
-    const T P = ((T(13) / T(3)) * S) * S;
+    const T Pe = fma((T(13) / T(3)) * S, S, eps4);
     const T xl = fma(T(2), S, D), xr = fma(T(-2), S, D);
-    const T bl = eps4 + fma(xl, xl, P);
-    const T bc = eps4 + fma(D, D, P);
-    const T br = eps4 + fma(xr, xr, P);
+    const T bl = fma(xl, xl, Pe);
+    const T bc = fma(D, D, Pe);
+    const T br = fma(xr, xr, Pe);
     tl = bl * bl;
     tc = bc * bc;
     tr = br * br;
@@ -110,16 +111,19 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
                                                const WenoCoef<T>& c)
 {
     const int msk = nx - 1;
-    const T half = T(0.5);
-    const T scale = -c.inv_dtau * (T(1) / T(6));
-    const T eps4 = T(4) * c.eps;
+    // the split fluxes are carried as 4 f+- (no halves):
+    //   4 f+ = v (2 (alpha - c) - B v),   4 f- = -v (2 (alpha + c) + B v)
+    // so the reconstruction is 4 F, the indicators take 64 eps, and the 1/4
+    // joins the 1/6 of the candidate values in the final scale
+    const T scale = -c.inv_dtau * (T(1) / T(24));
+    const T eps4 = T(64) * c.eps;
+    const T ap = T(2) * (ADV ? c.alpha - c.c : c.alpha);
+    const T am = T(2) * (ADV ? c.alpha + c.c : c.alpha);
     T fp[6], fm[6];
     auto load = [&](int kk, T& p, T& m) {
         const T v = ld_real<T, PAD>(u, kk & msk);
-        T f = -half * c.B * v * v;
-        if constexpr (ADV) f = fma(-c.c, v, f);
-        p = half * fma(c.alpha, v, f);
-        m = half * fma(-c.alpha, v, f);
+        p = v * fma(-c.B, v, ap);
+        m = -v * fma(c.B, v, am);
     };
     // window slot s <-> point k - 2 + s for interface k + 1/2; start at
     // k = k0 - 1 with the indicators of centres k0 - 2 .. k0 + 0 (pre-roll)
