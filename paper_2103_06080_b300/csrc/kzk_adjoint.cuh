@@ -26,54 +26,57 @@
 
 namespace kzk {
 
-// Gradient of one reconstruction w.r.t. v_{-2..2}, scaled by w: g[j] = w dF/dv_j.
-// In FP64 all four reciprocals it needs (1/sum a and 1/(eps + beta_r)) come
-// from one division: with e_r = eps + beta_r and S = sum a_r
-// (a_r = d_r prod_{s!=r} e_s^2), r = 1 / (S e0 e1 e2) gives 1/S = r e0 e1 e2
-// and 1/e_0 = r S e1 e2, etc.  In FP32 that product can underflow, so the
-// reciprocals are taken separately.
+// Gradient of one reconstruction w.r.t. v_{-2..2}, scaled: g[j] = 6 w6 dF/dv_j
+// (callers pass w6 = w / 6).  With integer-coefficient candidates Q_r = 6 q_r
+// and E_r = 4 (eps + beta_r) = eps4 + 13/3 s_r^2 + t_r^2 (s_r, t_r the two
+// stencil combinations of beta_r), the Jiang-Shu weights are
+// omega_r = a_r / sum a with a_r = d_r prod_{s != r} E_s^2, F6 = sum omega_r Q_r,
+// and, since d ln a_r = -2 dE_r / E_r,
+//   6 dF = sum_r omega_r dQ_r - 2 sum_r omega_r (Q_r - F6) / E_r dE_r,
+//   dE_r = 26/3 s_r ds_r + 2 t_r dt_r.
+// In FP64 the four reciprocals (1/sum a, 1/E_r) come from one division,
+// r = 1 / (S E0 E1 E2); in FP32 that product can underflow, so they are taken
+// separately.
 template <typename T>
-__device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps, T w, T* g)
+__device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps4, T w6, T* g)
 {
-    const T s6 = T(1) / T(6);
-    const T q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0)) * s6;
-    const T q1 = fma(T(-1), vm1, fma(T(5), v0, T(2) * v1)) * s6;
-    const T q2 = fma(T(2), v0, fma(T(5), v1, -v2)) * s6;
-    const T c13 = T(13) / T(12);
-    const T sa = vm2 - T(2) * vm1 + v0, ta = vm2 - T(4) * vm1 + T(3) * v0;
-    const T sb = vm1 - T(2) * v0 + v1, tb = vm1 - v1;
-    const T sc = v0 - T(2) * v1 + v2, tc = T(3) * v0 - T(4) * v1 + v2;
-    const T e0 = eps + fma(c13 * sa, sa, T(0.25) * ta * ta);
-    const T e1 = eps + fma(c13 * sb, sb, T(0.25) * tb * tb);
-    const T e2 = eps + fma(c13 * sc, sc, T(0.25) * tc * tc);
-    const T t0 = e0 * e0, t1 = e1 * e1, t2 = e2 * e2;
-    const T a0 = T(0.1) * t1 * t2, a1 = T(0.6) * t0 * t2, a2 = T(0.3) * t0 * t1;
+    const T Q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0));
+    const T Q1 = fma(T(5), v0, fma(T(2), v1, -vm1));
+    const T Q2 = fma(T(2), v0, fma(T(5), v1, -v2));
+    const T sa = fma(T(-2), vm1, vm2 + v0), ta = fma(T(3), v0, fma(T(-4), vm1, vm2));
+    const T sb = fma(T(-2), v0, vm1 + v1), tb = vm1 - v1;
+    const T sc = fma(T(-2), v1, v0 + v2), tc = fma(T(3), v0, fma(T(-4), v1, v2));
+    const T k13 = T(13) / T(3);
+    const T E0 = fma(k13 * sa, sa, fma(ta, ta, eps4));
+    const T E1 = fma(k13 * sb, sb, fma(tb, tb, eps4));
+    const T E2 = fma(k13 * sc, sc, fma(tc, tc, eps4));
+    const T T0 = E0 * E0, T1 = E1 * E1, T2 = E2 * E2;
+    // linear weights 1/10, 6/10, 3/10 scaled by 10 (the factor cancels)
+    const T a0 = T1 * T2, a1 = T(6) * (T0 * T2), a2 = T(3) * (T0 * T1);
     const T S = a0 + a1 + a2;
-    T inv, ie0, ie1, ie2;                                    // 1/S, 1/e_r
+    T inv, iE0, iE1, iE2;                                    // 1/S, 1/E_r
     if constexpr (sizeof(T) == 8) {
-        const T e01 = e0 * e1;
-        const T r = T(1) / (S * e01 * e2);                   // >= eps^7: fine in FP64
-        inv = r * (e01 * e2);
+        const T e01 = E0 * E1, e012 = e01 * E2;
+        const T r = T(1) / (S * e012);                       // >= eps^7: fine in FP64
+        inv = r * e012;
         const T rS = r * S;
-        ie0 = rS * (e1 * e2); ie1 = rS * (e0 * e2); ie2 = rS * e01;
+        iE0 = rS * (E1 * E2); iE1 = rS * (E0 * E2); iE2 = rS * e01;
     } else {
-        // eps^7 underflows FP32: separate hardware reciprocals
-        inv = __frcp_rn(S); ie0 = __frcp_rn(e0); ie1 = __frcp_rn(e1); ie2 = __frcp_rn(e2);
+        inv = __frcp_rn(S); iE0 = __frcp_rn(E0); iE1 = __frcp_rn(E1); iE2 = __frcp_rn(E2);
     }
     const T o0 = a0 * inv, o1 = a1 * inv, o2 = a2 * inv;     // omega_r
-    const T F = o0 * q0 + o1 * q1 + o2 * q2;
-    // c_r = -2 omega_r (q_r - F) / e_r
-    const T c0 = T(-2) * o0 * (q0 - F) * ie0;
-    const T c1 = T(-2) * o1 * (q1 - F) * ie1;
-    const T c2 = T(-2) * o2 * (q2 - F) * ie2;
-    const T A0 = T(2) * c13 * sa * c0, B0 = T(0.5) * ta * c0;
-    const T A1 = T(2) * c13 * sb * c1, B1 = T(0.5) * tb * c1;
-    const T A2 = T(2) * c13 * sc * c2, B2 = T(0.5) * tc * c2;
-    g[0] = w * (T(2) * s6 * o0 + A0 + B0);
-    g[1] = w * (-T(7) * s6 * o0 - s6 * o1 - T(2) * A0 - T(4) * B0 + A1 + B1);
-    g[2] = w * (T(11) * s6 * o0 + T(5) * s6 * o1 + T(2) * s6 * o2 + A0 + T(3) * B0 - T(2) * A1 + A2 + T(3) * B2);
-    g[3] = w * (T(2) * s6 * o1 + T(5) * s6 * o2 + A1 - B1 - T(2) * A2 - T(4) * B2);
-    g[4] = w * (-s6 * o2 + A2 + B2);
+    const T F6 = fma(o0, Q0, fma(o1, Q1, o2 * Q2));
+    // -2 omega_r (Q_r - F6) / E_r times the dE_r coefficients 26/3 s_r and 2 t_r
+    const T C0 = o0 * (Q0 - F6) * iE0, C1 = o1 * (Q1 - F6) * iE1, C2 = o2 * (Q2 - F6) * iE2;
+    const T k52 = T(-52) / T(3);
+    const T A0 = (k52 * C0) * sa, B0 = (T(-4) * C0) * ta;
+    const T A1 = (k52 * C1) * sb, B1 = (T(-4) * C1) * tb;
+    const T A2 = (k52 * C2) * sc, B2 = (T(-4) * C2) * tc;
+    g[0] = w6 * fma(T(2), o0, A0 + B0);
+    g[1] = w6 * (fma(T(-7), o0, A1 + B1 - o1) - fma(T(2), A0, T(4) * B0));
+    g[2] = w6 * (fma(T(11), o0, fma(T(5), o1, T(2) * o2)) + fma(T(3), B0 + B2, A0 + A2) - T(2) * A1);
+    g[3] = w6 * (fma(T(2), o1, fma(T(5), o2, A1 - B1)) - fma(T(2), A2, T(4) * B2));
+    g[4] = w6 * (A2 + B2 - o2);
 }
 
 // J_WENO(u)^T mu over the points [k0, k0+Q) of one periodic row (u, mu, g:
@@ -86,6 +89,8 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
 {
     const int msk = nx - 1;
     const T half = T(0.5);
+    const T eps4 = T(4) * c.eps;
+    const T inv_dtau6 = c.inv_dtau * (T(1) / T(6));
     T fp[6], fm[6], dp[6], dm[6], acc[6];
     // window slot s <-> point k - 2 + s for interface k + 1/2, starting at k = k0
 #pragma unroll
@@ -102,11 +107,11 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
     for (int i = 0; i < Q; i++) {
         const int k = k0 + i;
         const T mk1 = ld_real<T, true>(mu, (k + 1) & msk);
-        const T psi = (mk1 - mk_) * c.inv_dtau;
+        const T psi6 = (mk1 - mk_) * inv_dtau6;
         mk_ = mk1;
         T gp[5], gm[5];
-        weno5_grad<T>(fp[0], fp[1], fp[2], fp[3], fp[4], c.eps, psi, gp);
-        weno5_grad<T>(fm[5], fm[4], fm[3], fm[2], fm[1], c.eps, psi, gm);
+        weno5_grad<T>(fp[0], fp[1], fp[2], fp[3], fp[4], eps4, psi6, gp);
+        weno5_grad<T>(fm[5], fm[4], fm[3], fm[2], fm[1], eps4, psi6, gm);
 #pragma unroll
         for (int s = 0; s < 5; s++) acc[s] = fma(gp[s], dp[s], acc[s]);
 #pragma unroll
