@@ -46,6 +46,7 @@ class _Params(ctypes.Structure):
         ("n_relax", ctypes.c_int32), ("relax_C", ctypes.c_double * 2), ("relax_theta", ctypes.c_double * 2),
         ("n_modes", ctypes.c_int32), ("mode_klam", ctypes.c_void_p), ("mode_theta", ctypes.c_void_p),
         ("mode_phase", ctypes.c_void_p), ("mode_amp", ctypes.c_void_p),
+        ("method", ctypes.c_int32),
     ]
 
 _MODE_FIELDS = ("mode_klam", "mode_theta", "mode_phase", "mode_amp")
@@ -77,6 +78,7 @@ class Params:
     mode_theta: object = None
     mode_phase: object = None
     mode_amp: object = None
+    method: int = 0              # 0: ExpRK22 (Eq. 5); 1: exponential Euler (Sec. 3.2)
 
     def c(self) -> _Params:
         p = _Params()
@@ -105,7 +107,7 @@ class Params:
                 if len(v) > 2 or len(self.relax_C) != len(self.relax_theta):
                     raise ValueError("relax_C and relax_theta: equal lengths, at most 2")
                 setattr(p, name, (ctypes.c_double * 2)(*([float(x) for x in v] + [0.0] * (2 - len(v)))))
-            elif name in ("nx", "ny", "has_profile"):
+            elif name in ("nx", "ny", "has_profile", "method"):
                 setattr(p, name, int(v))
             else:
                 setattr(p, name, float(v))
@@ -252,7 +254,8 @@ def diag(p: Params, u) -> np.ndarray:
 
 def run(p: Params, u0, n_steps: int, sigma0: float = 0.0, threads: bool = False,
         want_ustar: bool = False, want_hist: bool = False):
-    """Advance u0 by n_steps ExpRK22 steps. Returns u (and V* of the last step,
+    """Advance u0 by n_steps steps of p.method (ExpRK22 or exponential Euler).
+    Returns u (and V* of the last step,
     and the [n_steps][4] diagnostics history when asked)."""
     u = _f64(u0).reshape(p.ny, p.nx).copy()
     us = np.zeros_like(u) if want_ustar else None

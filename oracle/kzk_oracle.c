@@ -56,6 +56,7 @@ typedef struct {
     const double *mode_theta;             /* theta_n: angle between K_n and the sigma axis */
     const double *mode_phase;             /* phi_n */
     const double *mode_amp;               /* |U~(K_n)| / c0 */
+    int32_t method;                       /* 0: ExpRK22 (Eq. 5); 1: exponential Euler (Sec. 3.2) */
 } orc_params;
 
 int orc_num_threads(void)
@@ -477,6 +478,38 @@ static void exprk22_step(const orc_params *p, const tables_t *t, double *u, doub
     free(vs); free(b2r);
 }
 
+/* One exponential Euler step (Sec. 3.2): F(V^{n+1}) = E F(V^n) + dt Phi1 F(b(sigma^n, V^n)),
+ * i.e. the first stage of Eq. 5 taken as the step. */
+static void expeuler_step(const orc_params *p, const tables_t *t, double *u, double sigma, double *w)
+{
+    size_t N = (size_t)p->nx * p->ny;
+    double dt = p->dt;
+    double *ur = w, *ui = w + N, *b1r = w + 2 * N, *b1i = w + 3 * N, *sr = w + 4 * N, *si = w + 5 * N;
+    memcpy(ur, u, sizeof(double) * N);
+    memset(ui, 0, sizeof(double) * N);
+    orc_fft2d(ur, ui, p->nx, p->ny, 0);
+    rhs_hat(p, u, ur, ui, sigma, b1r, b1i);
+    for (size_t i = 0; i < N; i++) {
+        cpx E = c_mk(t->Er[i], t->Ei[i]), P1 = c_mk(t->P1r[i], t->P1i[i]);
+        cpx v = c_add(c_mul(E, c_mk(ur[i], ui[i])), c_mul(c_mk(dt * P1.re, dt * P1.im), c_mk(b1r[i], b1i[i])));
+        sr[i] = v.re; si[i] = v.im;
+    }
+    orc_fft2d(sr, si, p->nx, p->ny, 1);
+    memcpy(u, sr, sizeof(double) * N);
+}
+
+/* One step of the plan's method; u_star_out (nullable): V^{n,*} (the Euler
+ * step itself for method 1). */
+static void one_step(const orc_params *p, const tables_t *t, double *u, double sigma, double *u_star_out, double *w)
+{
+    if (p->method == 1) {
+        expeuler_step(p, t, u, sigma, w);
+        if (u_star_out) memcpy(u_star_out, u, sizeof(double) * (size_t)p->nx * p->ny);
+    } else {
+        exprk22_step(p, t, u, sigma, u_star_out, w);
+    }
+}
+
 int orc_run(const orc_params *p, double *u, int64_t n_steps, double sigma0, double *u_star, double *hist)
 {
     size_t N = (size_t)p->nx * p->ny;
@@ -485,7 +518,7 @@ int orc_run(const orc_params *p, double *u, int64_t n_steps, double sigma0, doub
     double *w = malloc(sizeof(double) * 7 * N);
     for (int64_t n = 0; n < n_steps; n++) {
         double sigma = sigma0 + (double)n * p->dt;
-        exprk22_step(p, &t, u, sigma, u_star, w);
+        one_step(p, &t, u, sigma, u_star, w);
         if (hist) orc_diag(p, u, hist + 4 * n);
     }
     free(w);
@@ -506,7 +539,7 @@ int orc_run_timed(const orc_params *p, double *u, int64_t n_steps, double sigma0
     for (int64_t n = 0; n < n_steps; n++) {
         struct timespec a, b;
         clock_gettime(CLOCK_MONOTONIC, &a);
-        exprk22_step(p, &t, u, sigma0 + (double)n * p->dt, NULL, w);
+        one_step(p, &t, u, sigma0 + (double)n * p->dt, NULL, w);
         clock_gettime(CLOCK_MONOTONIC, &b);
         step_seconds[n] = (double)(b.tv_sec - a.tv_sec) + 1e-9 * (double)(b.tv_nsec - a.tv_nsec);
     }
@@ -667,7 +700,7 @@ int orc_adjoint(const orc_params *p, const double *u0, const double *g_end, int6
     memcpy(us, u0, sizeof(double) * N);
     for (int64_t n = 0; n < n_steps; n++) {
         memcpy(us + (size_t)(n + 1) * N, us + (size_t)n * N, sizeof(double) * N);
-        exprk22_step(p, &t, us + (size_t)(n + 1) * N, sigma0 + n * p->dt, uss + (size_t)n * N, w);
+        one_step(p, &t, us + (size_t)(n + 1) * N, sigma0 + n * p->dt, uss + (size_t)n * N, w);
     }
     double *lam = malloc(sizeof(double) * N), *mu2 = malloc(sizeof(double) * N);
     double *lst = malloc(sizeof(double) * N), *tmp = malloc(sizeof(double) * N);
@@ -676,6 +709,14 @@ int orc_adjoint(const orc_params *p, const double *u0, const double *g_end, int6
     for (int64_t n = n_steps - 1; n >= 0; n--) {
         double sigma = sigma0 + n * p->dt;
         const double *un = us + (size_t)n * N, *ust = uss + (size_t)n * N;
+        if (p->method == 1) {
+            /* transpose of u' = P_E u + P_{dt Phi1} G_n(u) */
+            apply_mult(p, lam, t.P1r, t.P1i, p->dt, 1, nu1);
+            apply_mult(p, lam, t.Er, t.Ei, 1.0, 1, lst);
+            rhs_T(p, un, sigma, nu1, tmp);
+            for (size_t i = 0; i < N; i++) lam[i] = lst[i] + tmp[i];
+            continue;
+        }
         apply_mult(p, lam, t.P2r, t.P2i, p->dt, 1, mu2);             /* mu2 */
         rhs_T(p, ust, sigma + p->dt, mu2, tmp);                        /* J_{G_{n+1}}(u*)^T mu2 */
         for (size_t i = 0; i < N; i++) lst[i] = lam[i] + tmp[i];       /* lam* */
