@@ -90,7 +90,13 @@ typedef struct {
     int32_t n_relax;                /* relaxation processes, 0 .. KZK_MAX_RELAX      */
     double relax_C[KZK_MAX_RELAX];  /* strengths C_r >= 0                            */
     double relax_theta[KZK_MAX_RELAX]; /* relaxation times theta_r > 0 (tau units)   */
+    int32_t method;                 /* KZK_EXPRK22 (0, Eq. 5) or KZK_EXPEULER (1: the
+                                       exponential Euler scheme of Sec. 3.2, first order:
+                                       the first stage of Eq. 5 taken as the step) */
 } kzk_coeffs;
+
+#define KZK_EXPRK22 0
+#define KZK_EXPEULER 1
 
 /* Diagnostics (FP64): of the state after the last step, and over the run. */
 typedef struct {
@@ -109,7 +115,8 @@ typedef struct kzk_plan_s kzk_plan;
  * Eq. 11 on the device (rounded once to float for KZK_FP32), the twiddle
  * tables, and the workspace (4 spectral arrays per instance).
  * Errors: KZK_ERR_ARG (null, dt <= 0, B <= 0, A < 0, lf_umax <= 0, batch < 1,
- * n_relax outside [0, KZK_MAX_RELAX], some C_r < 0 or theta_r <= 0),
+ * n_relax outside [0, KZK_MAX_RELAX], some C_r < 0 or theta_r <= 0, unknown
+ * method),
  * KZK_ERR_SIZE, KZK_ERR_OOM, KZK_ERR_CUDA.  *out is NULL on failure. */
 kzk_status kzk_plan_create(const kzk_grid *grid, const kzk_coeffs *coeffs, double dt,
                            int32_t batch, kzk_plan **out);
@@ -170,7 +177,8 @@ kzk_status kzk_diag_history(kzk_plan *plan, double *hist, int64_t n, void *strea
 kzk_status kzk_rhs(kzk_plan *plan, const void *u, void *b, double sigma, void *stream);
 
 /* One step from u (device) into u_next (device) that also returns the first
- * stage V^{n,*} of Eq. 5 (device, physical).  u_next may alias u. */
+ * stage V^{n,*} of Eq. 5 (device, physical; for KZK_EXPEULER the step itself,
+ * u_star = u_next).  u_next may alias u. */
 kzk_status kzk_step_stages(kzk_plan *plan, const void *u, void *u_star, void *u_next,
                            double sigma0, void *stream);
 
@@ -267,7 +275,9 @@ int64_t kzk_launch_count(void);
  * recorded on `stream` around every kernel of the step, and returns in ms[4]
  * the mean device duration of one launch of each kernel: ms[0] row pass of
  * stage 1, ms[1] column pass of stage 1, ms[2] row pass of stage 2, ms[3]
- * column pass of stage 2.  Synchronises the stream. */
+ * column pass of stage 2 (0 for KZK_EXPEULER; with a random medium a "row
+ * pass" is its coefficient, C2R and b launches together).  Synchronises the
+ * stream. */
 kzk_status kzk_kernel_times(kzk_plan *plan, void *u, int64_t n_steps, double sigma0, void *stream,
                             double *ms);
 

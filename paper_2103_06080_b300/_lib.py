@@ -32,7 +32,8 @@ class KzkCoeffs(ctypes.Structure):
                 ("weno_eps", ctypes.c_double), ("lf_umax", ctypes.c_double),
                 ("B_prof", ctypes.c_double * 4), ("A_prof", ctypes.c_double * 4),
                 ("has_profile", ctypes.c_int32), ("n_relax", ctypes.c_int32),
-                ("relax_C", ctypes.c_double * 2), ("relax_theta", ctypes.c_double * 2)]
+                ("relax_C", ctypes.c_double * 2), ("relax_theta", ctypes.c_double * 2),
+                ("method", ctypes.c_int32)]
 
 
 class KzkMedium(ctypes.Structure):
@@ -98,6 +99,8 @@ _SIGS = [
 NOALLOC_MAX_POINTS = 1 << 18
 KZK_BATCH_AUTOTUNE = 1
 KZK_BATCH_STREAMS = 2
+KZK_EXPRK22 = 0
+KZK_EXPEULER = 1
 
 
 def lib():

@@ -29,7 +29,10 @@ class Plan:
                  tau_min: float = -4.0, tau_max: float = 4.0, y_min: float = -8.0, y_max: float = 8.0,
                  B_prof: Sequence[float] = (1.0, 0.0, 0.0, 0.0), A_prof: Sequence[float] = (1.0, 0.0, 0.0, 0.0),
                  has_profile: bool = False, diffraction: float = 0.0, reg_eps: float = 0.0,
-                 weno_eps: float = 0.0, relax_C: Sequence[float] = (), relax_theta: Sequence[float] = ()):
+                 weno_eps: float = 0.0, relax_C: Sequence[float] = (), relax_theta: Sequence[float] = (),
+                 method: str = "exprk22"):
+        if method not in ("exprk22", "expeuler"):
+            raise ValueError("method must be 'exprk22' or 'expeuler'")
         if precision not in ("fp64", "fp32"):
             raise ValueError("precision must be 'fp64' or 'fp32'")
         self.nx, self.ny, self.dt, self.batch = int(nx), int(ny), float(dt), int(batch)
@@ -43,7 +46,8 @@ class Plan:
         c = L.KzkCoeffs(B=B, A=A, diffraction=diffraction, reg_eps=reg_eps, weno_eps=weno_eps, lf_umax=lf_umax,
                         B_prof=(ctypes.c_double * 4)(*B_prof), A_prof=(ctypes.c_double * 4)(*A_prof),
                         has_profile=int(bool(has_profile)), n_relax=len(relax_C), relax_C=pad(relax_C),
-                        relax_theta=pad(relax_theta))
+                        relax_theta=pad(relax_theta),
+                        method=L.KZK_EXPEULER if method == "expeuler" else L.KZK_EXPRK22)
         self._grid, self._coeffs = g, c
         h = ctypes.c_void_p()
         L.check(L.lib().kzk_plan_create(ctypes.byref(g), ctypes.byref(c), self.dt, self.batch, ctypes.byref(h)))

@@ -504,17 +504,21 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     // V is read-only; the result goes to V_out (default: in place).  u_n, u_s
     // (nullable): where the row passes also store the physical u^n and u*.
     if (!V_out) V_out = V;
+    const bool euler = p->c.method == KZK_EXPEULER;
     KZK_TRY(rhs_stage<T>(p, sigma, V, p->b1, diag_hist_step ? p->diag_rows : nullptr, u_n, 0, st));
     ColArgs<T> c1 = col_args<T>(p);
     c1.a = (const cx<T>*)V;
     c1.b = (const cx<T>*)p->b1;
-    c1.out = (cx<T>*)vs;
+    // exponential Euler: the first stage is the step (every column tile is
+    // read whole before it is written, so V_out may alias V)
+    c1.out = (cx<T>*)(euler ? V_out : vs);
     c1.Ta = (const cx<T>*)p->E;
     c1.Ta_lo = (const cx<T>*)p->E_lo;
     c1.Tb = (const cx<T>*)p->P1;
     c1.diag_rows = diag_hist_step ? p->diag_rows : nullptr;
     c1.diag_hist = diag_hist_step;
     KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
+    if (euler) return KZK_OK;
     KZK_TRY(rhs_stage<T>(p, sigma + p->dt, vs, p->b2, nullptr, u_s, 1, st));
     ColArgs<T> c2 = col_args<T>(p);
     c2.a = (const cx<T>*)p->b1;
@@ -747,6 +751,28 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* u
     const dim3 cgrid(p->n >> p->log2tc, p->batch), rgrid(p->ny, p->batch);
     const size_t rsm = adj_row_smem<T>(p);
     const int rthr = p->adj_row_thr;
+    if (p->c.method == KZK_EXPEULER) {
+        // transpose of u' = P_E u + P_{ds Phi1} G_n(u): with mu2 = 0 the
+        // stage-1 column pass gives lam_lin = P_{conj E} lam', nu1 =
+        // P_{conj(ds Phi1)} lam', then lam = lam_lin + J_{G_n}(u)^T nu1
+        const size_t arr = (size_t)p->batch * p->inst_stride * p->csz;
+        KZK_CUDA(cudaMemsetAsync(p->mu, 0, arr, st));
+        AdjColArgs<T> c1 = adj_col_args<T>(p);
+        c1.a = (const cx<T>*)p->lam;
+        c1.b = (const cx<T>*)p->mu;
+        c1.out = (cx<T>*)p->ls;
+        c1.out2 = (cx<T>*)p->nu;
+        c1.Ta = (const cx<T>*)p->E;
+        c1.sa = (T)1;
+        c1.Tb = (const cx<T>*)p->P1;
+        c1.sb = (T)p->nx;
+        adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
+        KZK_LAUNCHED();
+        AdjRowArgs<T> r1 = adj_row_args<T>(p, p->nu, un, p->ls, p->lam, sigma);
+        adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_1><<<rgrid, rthr, rsm, st>>>(r1);
+        KZK_LAUNCHED();
+        return KZK_OK;
+    }
     // mu2 = P_{conj(ds Phi2)} lam'
     AdjColArgs<T> c2 = adj_col_args<T>(p);
     c2.a = (const cx<T>*)p->lam;
@@ -1241,9 +1267,10 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
         KZK_TRY(rhs_stage<T>(p, sigma, p->V, p->b1, p->diag_rows, nullptr, 0, st));
         KZK_CUDA(cudaEventRecord(ev[1], st));
         ColArgs<T> c1 = col_args<T>(p);
+        const bool euler = p->c.method == KZK_EXPEULER;
         c1.a = (const cx<T>*)p->V;
         c1.b = (const cx<T>*)p->b1;
-        c1.out = (cx<T>*)p->vs;
+        c1.out = (cx<T>*)(euler ? p->V : p->vs);
         c1.Ta = (const cx<T>*)p->E;
         c1.Ta_lo = (const cx<T>*)p->E_lo;
         c1.Tb = (const cx<T>*)p->P1;
@@ -1251,6 +1278,18 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
         c1.diag_hist = p->diag_hist + (size_t)s * p->batch * 4;
         KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
         KZK_CUDA(cudaEventRecord(ev[2], st));
+        if (euler) {
+            // exponential Euler: no second stage
+            KZK_CUDA(cudaEventRecord(ev[3], st));
+            KZK_CUDA(cudaEventRecord(ev[4], st));
+            KZK_CUDA(cudaEventSynchronize(ev[4]));
+            for (int k = 0; k < 4; k++) {
+                float t = 0;
+                KZK_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+                acc[k] += t;
+            }
+            continue;
+        }
         KZK_TRY(rhs_stage<T>(p, sigma + p->dt, p->vs, p->b2, nullptr, nullptr, 1, st));
         KZK_CUDA(cudaEventRecord(ev[3], st));
         ColArgs<T> c2 = col_args<T>(p);
@@ -1335,6 +1374,8 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     if (!(dt > 0) || !std::isfinite(dt)) return fail(KZK_ERR_ARG, "dt must be positive and finite");
     if (!(coeffs->B > 0) || !(coeffs->A >= 0) || !(coeffs->lf_umax > 0))
         return fail(KZK_ERR_ARG, "need B > 0, A >= 0, lf_umax > 0");
+    if (coeffs->method != KZK_EXPRK22 && coeffs->method != KZK_EXPEULER)
+        return fail(KZK_ERR_ARG, "unknown method %d", coeffs->method);
     if (coeffs->n_relax < 0 || coeffs->n_relax > KZK_MAX_RELAX)
         return fail(KZK_ERR_ARG, "n_relax = %d outside [0, %d]", coeffs->n_relax, KZK_MAX_RELAX);
     for (int r = 0; r < coeffs->n_relax; r++)
@@ -1603,15 +1644,17 @@ kzk_status kzk_step_stages(kzk_plan* p, const void* u, void* u_star, void* u_nex
 {
     if (!p || !u || !u_star || !u_next) return fail(KZK_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
+    // exponential Euler: the step is its first stage, u_star = u_next
+    const bool euler = p->c.method == KZK_EXPEULER;
     if (p->prec == KZK_FP64) {
         KZK_TRY(to_spectral<double>(p, u, p->V, st));
         KZK_TRY(step<double>(p, sigma0, st, nullptr, p->V, p->vs));
-        KZK_TRY(to_physical<double>(p, p->vs, u_star, 1.0, nullptr, st));
+        KZK_TRY(to_physical<double>(p, euler ? p->V : p->vs, u_star, 1.0, nullptr, st));
         return to_physical<double>(p, p->V, u_next, 1.0, nullptr, st);
     }
     KZK_TRY(to_spectral<float>(p, u, p->V, st));
     KZK_TRY(step<float>(p, sigma0, st, nullptr, p->V, p->vs));
-    KZK_TRY(to_physical<float>(p, p->vs, u_star, 1.0, nullptr, st));
+    KZK_TRY(to_physical<float>(p, euler ? p->V : p->vs, u_star, 1.0, nullptr, st));
     return to_physical<float>(p, p->V, u_next, 1.0, nullptr, st);
 }
 

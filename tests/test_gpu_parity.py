@@ -300,3 +300,36 @@ def test_adjoint_finite_differences_fp64():
         # |v| = 1 bounds the directional derivative by |g0|; FD in FP64 with
         # h = 1e-6 carries ~1e-8 |g0| of rounding noise
         assert abs(ad - fd) <= 1e-6 * float(g0.norm()), (ad, fd)
+
+
+# exponential Euler (Sec. 3.2): plan option method="expeuler"
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_expeuler_run_matches_oracle(prec):
+    api = _api()
+    w = inputs.config(2, nx=512, ny=128, n_steps=30)
+    plan = api.Plan.from_workload(w, precision=prec, method="expeuler")
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = _dev(w.u0, dt)
+    plan.advance(u, w.n_steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w, method=1)), w.u0, w.n_steps, threads=True)
+    rk = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    assert rel_l2(rk, ref) > 1e-4                 # a different scheme
+    got = u.double().cpu().numpy()
+    if prec == "fp64":
+        assert rel_linf(got, ref) < 1e-11
+    else:
+        assert rel_l2(got, ref) < 1e-5
+
+
+def test_expeuler_stages_and_adjoint():
+    api = _api()
+    w = inputs.config(2, nx=128, ny=32, n_steps=8)
+    plan = api.Plan.from_workload(w, method="expeuler")
+    p = oracle.Params(**inputs.oracle_params(w, method=1))
+    us, un = plan.step_stages(_dev(w.u0))
+    ref = oracle.run(p, w.u0, 1)
+    assert rel_linf(un.cpu().numpy(), ref) < 1e-12 and torch.equal(us, un)
+    g_end = 2 * w.dtau * oracle.run(p, w.u0, w.n_steps)
+    g_ref = oracle.adjoint(p, w.u0, g_end, w.n_steps)
+    g0 = plan.adjoint(_dev(w.u0), _dev(g_end), w.n_steps, ckpt_every=3)
+    assert rel_linf(g0.cpu().numpy(), g_ref) < 1e-10
