@@ -95,6 +95,7 @@ struct kzk_plan_s {
     double* med_coef;           // device [2][ny][3]: U_par, U_perp, dU_perp/dy of stages 1 and 2
     double* med_bmax;           // device [2][med_nb]
     void* uphys;                // device [batch][ny][nx]: physical rows of the current stage
+    void* by;                   // device [batch][ny][nx]: y-flux difference + source of the current stage
     // adjoint workspace (allocated on first use)
     void *lam, *mu, *nu, *ls;   // spectral adjoint arrays
     void* seg;                  // segment store: physical u^n, u*^n of k steps, [(2 k)][batch][ny][nx]
@@ -260,6 +261,7 @@ kzk_status configure(kzk_plan* p)
     KZK_TRY((set_row_attr<T, ROW_FWD>(sm)));
     KZK_TRY((set_row_attr<T, ROW_INV>(sm)));
     KZK_TRY((set_row_attr<T, ROW_RHS_MED>(sm)));
+    KZK_CUDA(cudaFuncSetAttribute(ysweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     KZK_TRY((set_col_attr<T, COL_STAGE1>(sm)));
     KZK_TRY((set_col_attr<T, COL_STAGE2>(sm)));
     KZK_TRY((set_adj_row_attr<T, ADJ_ROW_2>(sm)));
@@ -481,12 +483,25 @@ kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, dou
         KZK_TRY(launch_medium(p, sigma, stage, st));
         RowArgs<T> ri = row_args<T>(p, Vin, p->uphys, 0.0, diag_rows);
         KZK_TRY((launch_row<T, ROW_INV>(p, ri, st)));
+        YSweepArgs<T> y{};
+        y.u = (const T*)p->uphys;
+        y.by = (T*)p->by;
+        y.coef = p->med_coef + (size_t)stage * 3 * p->ny;
+        y.bmax = p->med_bmax + (size_t)stage * p->med_nb;
+        y.n_bmax = p->med_nb;
+        y.nx = p->nx;
+        y.ny = p->ny;
+        y.Q = std::min(p->ny, 64);
+        y.inst_elems = (long long)p->nx * p->ny;
+        y.eps = (T)p->c.weno_eps;
+        y.inv_dy = (T)(p->ny / (p->g.y_max - p->g.y_min));
+        const dim3 yg((p->nx + YSWEEP_THREADS - 1) / YSWEEP_THREADS, (p->ny + y.Q - 1) / y.Q, p->batch);
+        ysweep_kernel<T><<<yg, YSWEEP_THREADS, ysweep_smem<T>(y.Q), st>>>(y);
+        KZK_LAUNCHED();
         RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, nullptr);
         r.uphys = (const T*)p->uphys;
+        r.by = (const T*)p->by;
         r.med_coef = p->med_coef + (size_t)stage * 3 * p->ny;
-        r.med_bmax = p->med_bmax + (size_t)stage * p->med_nb;
-        r.n_bmax = p->med_nb;
-        r.inv_dy = (T)(p->ny / (p->g.y_max - p->g.y_min));
         return launch_row<T, ROW_RHS_MED>(p, r, st);
     }
     RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, diag_rows);
@@ -683,7 +698,7 @@ void plan_free(kzk_plan* p)
                     p->tws_row, p->twc_full,
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
                     p->seg, p->ckpt, p->colp_flag, p->med_Ty, p->med_mode, p->med_coef, p->med_bmax,
-                    p->uphys};
+                    p->uphys, p->by};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1455,10 +1470,11 @@ kzk_status kzk_plan_set_medium(kzk_plan* p, const kzk_medium* m)
         if (!std::isfinite(m->klam[n]) || !std::isfinite(m->theta[n]) || !std::isfinite(m->phase[n]) ||
             !std::isfinite(m->amp[n]))
             return fail(KZK_ERR_ARG, "mode %d: non-finite value", n);
-    void* old[] = {p->med_Ty, p->med_mode, p->med_coef, p->med_bmax, p->uphys};
+    void* old[] = {p->med_Ty, p->med_mode, p->med_coef, p->med_bmax, p->uphys, p->by};
     for (void* q : old)
         if (q) KZK_CUDA(cudaFree(q));
     p->med_Ty = nullptr; p->med_mode = nullptr; p->med_coef = nullptr; p->med_bmax = nullptr; p->uphys = nullptr;
+    p->by = nullptr;
     p->med_n = 0;
     if (N == 0) return KZK_OK;
     const int ny = p->ny;
@@ -1484,13 +1500,15 @@ kzk_status kzk_plan_set_medium(kzk_plan* p, const kzk_medium* m)
     if (e == cudaSuccess) e = cudaMalloc((void**)&p->med_coef, 2 * 3 * (size_t)ny * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&p->med_bmax, 2 * (size_t)nb * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->uphys, (size_t)p->batch * p->inst_stride * p->csz);
+    if (e == cudaSuccess) e = cudaMalloc(&p->by, (size_t)p->batch * p->inst_stride * p->csz);
     if (e == cudaSuccess) e = cudaMemcpy(p->med_Ty, Ty.data(), Ty.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->med_mode, mode.data(), mode.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        void* got[] = {p->med_Ty, p->med_mode, p->med_coef, p->med_bmax, p->uphys};
+        void* got[] = {p->med_Ty, p->med_mode, p->med_coef, p->med_bmax, p->uphys, p->by};
         for (void* q : got)
             if (q) cudaFree(q);
         p->med_Ty = nullptr; p->med_mode = nullptr; p->med_coef = nullptr; p->med_bmax = nullptr; p->uphys = nullptr;
+        p->by = nullptr;
         return fail(e == cudaErrorMemoryAllocation ? KZK_ERR_OOM : KZK_ERR_CUDA, "medium set-up: %s",
                     cudaGetErrorString(e));
     }

@@ -42,51 +42,12 @@ struct RowArgs {
     T out_scale;            // ROW_FWD: 1/nx; ROW_INV: scale of the result
     T* u_out;               // ROW_RHS: also store the physical row here ([batch][ny][nx]; nullable)
     // ROW_RHS_MED (random medium): b from the physical rows, with the tau-flux
-    // -2 pi U_par u - B u^2/2, the y-flux U_perp u (WENO5 along y) and the
-    // source d_y U_perp u (Eq. 7 and the text after it)
+    // -2 pi U_par u - B u^2/2, plus the y-flux difference and the source
+    // d_y U_perp u computed by ysweep_kernel (Eq. 7 and the text after it)
     const T* uphys;         // physical rows [batch][ny][nx]
+    const T* by;            // the y-flux difference and source of every point [batch][ny][nx] (ysweep_kernel)
     const double* med_coef; // [ny][3]: U_par, U_perp, d U_perp / dy at this sigma
-    const double* med_bmax; // [n_bmax] partial maxima of |U_perp| (their max is the LF speed along y)
-    int n_bmax;
-    T inv_dy;
 };
-
-// Random medium: adds -(G_{j+1/2} - G_{j-1/2}) / dy + (d_y U_perp) u to the
-// tau part of b already in Y, for every point of row `row` (X: the physical
-// row).  Consecutive threads take consecutive points, so the loads of the
-// neighbouring rows j-3 .. j+3 are coalesced (they come mostly from L2).
-template <typename T>
-__device__ __forceinline__ void med_y_terms(const RowArgs<T>& a, int row, int inst, const cx<T>* X, cx<T>* Y,
-                                            int tid, int nthr)
-{
-    const int nx = 1 << a.log2nx, ny = a.ny;
-    double ay = 0.0;
-    for (int i = 0; i < a.n_bmax; i++) ay = fmax(ay, __ldg(a.med_bmax + i));
-    const T alpha_y = (T)ay;
-    T up[7];
-    long long roff[7];
-#pragma unroll
-    for (int s = 0; s < 7; s++) {
-        const int r = ((row - 3 + s) % ny + ny) % ny;
-        up[s] = (T)__ldg(a.med_coef + 3 * r + 1);
-        roff[s] = (long long)r * nx;
-    }
-    const T dperp = (T)__ldg(a.med_coef + 3 * row + 2);
-    const T* ub = a.uphys + 2 * (long long)inst * a.inst_stride;
-    const T eps4 = T(4) * a.wc.eps, sc = -a.inv_dy * (T(1) / T(6));
-    for (int k = tid; k < nx; k += nthr) {
-        T gp[7], gm[7];
-#pragma unroll
-        for (int s = 0; s < 7; s++) {
-            const T v = __ldcg(ub + roff[s] + k);
-            const T g = up[s] * v;
-            gp[s] = T(0.5) * fma(alpha_y, v, g);
-            gm[s] = T(0.5) * fma(-alpha_y, v, g);
-        }
-        const T d6 = weno_y_diff6<T>(gp, gm, eps4);
-        st_real<T, true>(Y, k, ld_real<T, true>(Y, k) + fma(d6, sc, dperp * ld_real<T, true>(X, k)));
-    }
-}
 
 // Block reduction of the four diagnostics (FP64 across threads, fixed
 // order: deterministic).  blockDim.x must be a power of two; red holds
@@ -305,7 +266,9 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
             }
             __syncthreads();
             if constexpr (MODE == ROW_RHS_MED) {
-                med_y_terms<T>(a, row, inst, X, Y, tid, nthr);
+                // plus the y-flux difference and source of this row
+                const T* byrow = a.by + 2 * base;
+                for (int k = tid; k < nx; k += nthr) st_real<T, true>(Y, k, ld_real<T, true>(Y, k) + __ldcg(byrow + k));
                 __syncthreads();
             }
             fft_batched<T, ROW_PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);

@@ -13,6 +13,7 @@
 // All in FP64 (the coefficients feed both plan precisions).
 #pragma once
 #include "kzk_common.cuh"
+#include "kzk_weno.cuh"
 
 namespace kzk {
 
@@ -77,6 +78,120 @@ __global__ void __launch_bounds__(MED_ROWS * MED_GROUPS) medium_kernel(MedArgs a
         double m = 0.0;
         for (int q = 0; q < MED_ROWS; q++) m = fmax(m, mx[q]);
         a.bmax[blockIdx.x] = m;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y-flux of the random medium: b_y = -(G_{j+1/2} - G_{j-1/2}) / dy + (d_y U_perp) u
+// with G the WENO5 reconstruction of g = U_perp(y) u split by the global
+// Lax-Friedrichs speed alpha_y = max_j |U_perp| (Eq. 7 and the text after it).
+// One thread per (column k, chunk of Q rows): a sliding window down the
+// column, as the tau sweep of weno_row_chunk slides along a row, so every
+// interface is reconstructed once; consecutive threads take consecutive
+// columns (coalesced row loads).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct YSweepArgs {
+    const T* u;              // physical rows [batch][ny][nx]
+    T* by;                   // out: b_y [batch][ny][nx]
+    const double* coef;      // [ny][3]: U_par, U_perp, d U_perp / dy
+    const double* bmax;      // [n_bmax] partial maxima of |U_perp|
+    int n_bmax, nx, ny, Q;
+    long long inst_elems;    // nx * ny
+    T eps, inv_dy;
+};
+
+constexpr int YSWEEP_THREADS = 128;
+
+// shared memory of one sweep CTA: Q + 7 rows of YSWEEP_THREADS columns, and
+// the split-flux factors and source coefficient of those rows
+template <typename T>
+__host__ __device__ constexpr size_t ysweep_smem(int Q)
+{
+    return (size_t)(Q + 7) * (YSWEEP_THREADS + 3) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(YSWEEP_THREADS) ysweep_kernel(YSweepArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char ys_smem[];
+    const int tid = threadIdx.x;
+    const int k0 = blockIdx.x * YSWEEP_THREADS, k = k0 + tid;
+    const int j0 = blockIdx.y * a.Q;
+    const int ny = a.ny, nx = a.nx;
+    const int Q = min(a.Q, ny - j0);
+    const int R = Q + 7;                       // rows j0 - 4 .. j0 + Q + 2
+    T* tile = reinterpret_cast<T*>(ys_smem);   // [R][YSWEEP_THREADS]
+    T* cp = tile + (size_t)R * YSWEEP_THREADS; // [R]: 2 (U_perp + alpha_y)
+    T* cm = cp + R;                            // [R]: 2 (U_perp - alpha_y)
+    T* dp = cm + R;                            // [R]: d U_perp / dy
+    double ay = 0.0;
+    for (int i = 0; i < a.n_bmax; i++) ay = fmax(ay, __ldg(a.bmax + i));
+    const T* u = a.u + (long long)blockIdx.z * a.inst_elems;
+    // the CTA's rows (periodic in y), every load in flight at once
+    for (int idx = tid; idx < R * YSWEEP_THREADS; idx += YSWEEP_THREADS) {
+        const int r = idx / YSWEEP_THREADS, c = idx % YSWEEP_THREADS;
+        const int row = (((j0 - 4 + r) % ny) + ny) % ny;
+        tile[idx] = (k0 + c < nx) ? __ldg(u + (long long)row * nx + k0 + c) : T(0);
+    }
+    for (int r = tid; r < R; r += YSWEEP_THREADS) {
+        const int row = (((j0 - 4 + r) % ny) + ny) % ny;
+        const double up = __ldg(a.coef + 3 * row + 1);
+        cp[r] = (T)(2.0 * (up + ay));
+        cm[r] = (T)(2.0 * (up - ay));
+        dp[r] = (T)__ldg(a.coef + 3 * row + 2);
+    }
+    __syncthreads();
+    if (k >= nx) return;
+    T* by = a.by + (long long)blockIdx.z * a.inst_elems + k;
+    // the split fluxes are carried as 4 g+- = 2 (U_perp +- alpha_y) u
+    // (indicators with 64 eps, final scale 1/24: see weno_row_chunk)
+    const T scale = -a.inv_dy * (T(1) / T(24));
+    const T eps4 = T(64) * a.eps;
+    auto load = [&](int jj, T& p, T& m) {
+        const int r = jj - (j0 - 4);
+        const T v = tile[r * YSWEEP_THREADS + tid];
+        p = v * cp[r];
+        m = v * cm[r];
+    };
+    T fp[6], fm[6];
+    // window slot s <-> row j - 2 + s for interface j + 1/2; pre-roll as in
+    // weno_row_chunk (interfaces j0 - 1/2 and on)
+    int j = j0 - 1;
+#pragma unroll
+    for (int s = 0; s < 5; s++) load(j - 3 + s, fp[s + 1], fm[s + 1]);
+    T tLp3, tLp2, tLp1, tCp2, tCp1, tRp1, tLm2, tLm1, tCm1, tx;
+    indicators<T>(fp[2], fp[3], fp[4], eps4, tLp2, tx, tx);
+    indicators<T>(fm[2], fm[3], fm[4], eps4, tx, tx, tx);
+    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tx);
+    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tx, tx);
+    tLp3 = tLp2; tLp2 = tLp1; tCp2 = tCp1;
+    tLm2 = tLm1;
+#pragma unroll
+    for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
+    load(j0 + 1, fp[5], fm[5]);
+    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tRp1);
+    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tCm1, tx);
+    T Fprev = 0;
+    for (; j < j0 + Q; j++) {
+#pragma unroll
+        for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
+        load(j + 3, fp[5], fm[5]);
+        T tLpN, tCpN, tRpN, tLmN, tCmN, tRmN;
+        indicators<T>(fp[3], fp[4], fp[5], eps4, tLpN, tCpN, tRpN);
+        indicators<T>(fm[3], fm[4], fm[5], eps4, tLmN, tCmN, tRmN);
+        const T F = flux6<T>(fp, fm, tLp3, tCp2, tRp1, tLm2, tCm1, tRmN);
+        if (j >= j0) {
+            // row j: the flux difference plus the source (d_y U_perp) u
+            const int r = j - (j0 - 4);
+            by[(long long)j * nx] = fma(F - Fprev, scale, dp[r] * tile[r * YSWEEP_THREADS + tid]);
+        }
+        Fprev = F;
+        tLp3 = tLp2; tLp2 = tLp1; tLp1 = tLpN;
+        tCp2 = tCp1; tCp1 = tCpN;
+        tRp1 = tRpN;
+        tLm2 = tLm1; tLm1 = tLmN;
+        tCm1 = tCmN;
     }
 }
 

@@ -172,28 +172,6 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
     }
 }
 
-// 6 (G_{j+1/2} - G_{j-1/2}) at one point of row j from the split fluxes at
-// rows j-3 .. j+3 (gp[s], gm[s]: row j - 3 + s): the reconstructions of the
-// tau sweep applied along y (random medium, the y-flux U_perp u of Eq. 7),
-// each centre's indicators computed once for both interfaces.
-template <typename T>
-__device__ __forceinline__ T weno_y_diff6(const T* gp, const T* gm, T eps4)
-{
-    // g+ indicators at centres j-2 .. j+1 (index i: centre j - 2 + i), g- at
-    // centres j-1 .. j+2 (index i: centre j - 1 + i)
-    T pl[4], pc[4], pr[4], ml[4], mc[4], mr[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        indicators<T>(gp[i], gp[i + 1], gp[i + 2], eps4, pl[i], pc[i], pr[i]);
-        indicators<T>(gm[i + 1], gm[i + 2], gm[i + 3], eps4, ml[i], mc[i], mr[i]);
-    }
-    // interface j + 1/2: + side rows j-2 .. j+2, - side rows j+3 .. j-1
-    const T up = flux6<T>(gp + 1, gm + 1, pl[1], pc[2], pr[3], ml[1], mc[2], mr[3]);
-    // interface j - 1/2: + side rows j-3 .. j+1, - side rows j+2 .. j-2
-    const T dn = flux6<T>(gp, gm, pl[0], pc[1], pr[2], ml[0], mc[1], mr[2]);
-    return up - dn;
-}
-
 // sum u, sum u^2, max|u| and non-finite count of the points [k0, k0 + Q).
 template <typename T, bool PAD>
 __device__ __forceinline__ void row_stats(const cx<T>* u, int k0, int Q, T& s1, T& s2, T& mx, int& nf)
