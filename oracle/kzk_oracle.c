@@ -608,23 +608,28 @@ void orc_weno_grad(const double *v, double eps, double *g)
 /* J_WENO(u)^T mu, physical space, row by row. */
 void orc_weno_rhs_T(const orc_params *p, const double *u, double sigma, const double *mu, double *out)
 {
-    int nx = p->nx;
+    int nx = p->nx, ny = p->ny;
     double dtau = (p->tau_max - p->tau_min) / nx;
     double Bs = orc_B_of(p, sigma);
-    double alpha = Bs * p->lf_umax;
+    double *upar = calloc(ny, sizeof(double)), *uperp = calloc(ny, sizeof(double));
+    double *duperp = calloc(ny, sizeof(double));
+    if (p->n_modes > 0) orc_medium(p, sigma, upar, uperp, duperp);
     #pragma omp parallel
     {
         double *fp = malloc(sizeof(double) * nx), *fm = malloc(sizeof(double) * nx);
         double *dfp = malloc(sizeof(double) * nx), *dfm = malloc(sizeof(double) * nx);
         #pragma omp for schedule(static)
-        for (int j = 0; j < p->ny; j++) {
+        for (int j = 0; j < ny; j++) {
             const double *ur = u + (size_t)j * nx;
             const double *mr = mu + (size_t)j * nx;
             double *o = out + (size_t)j * nx;
+            /* tau-flux f = -c u - B u^2 / 2 (c = 2 pi U_par of the row), LF speed |c| + B M */
+            double c = 2.0 * M_PI * upar[j];
+            double alpha = fabs(c) + Bs * p->lf_umax;
             for (int i = 0; i < nx; i++) {
-                double f = -0.5 * Bs * ur[i] * ur[i];
+                double f = -c * ur[i] - 0.5 * Bs * ur[i] * ur[i];
                 fp[i] = 0.5 * (f + alpha * ur[i]);  fm[i] = 0.5 * (f - alpha * ur[i]);
-                dfp[i] = 0.5 * (-Bs * ur[i] + alpha); dfm[i] = 0.5 * (-Bs * ur[i] - alpha);
+                dfp[i] = 0.5 * (-c - Bs * ur[i] + alpha); dfm[i] = 0.5 * (-c - Bs * ur[i] - alpha);
                 o[i] = 0.0;
             }
             for (int k = 0; k < nx; k++) {
@@ -642,6 +647,45 @@ void orc_weno_rhs_T(const orc_params *p, const double *u, double sigma, const do
         }
         free(fp); free(fm); free(dfp); free(dfm);
     }
+    if (p->n_modes > 0) {
+        /* y-flux g = U_perp u split by ay = max |U_perp| (dg+-/du = (U_perp +- ay)/2,
+         * constant in u), transposed column by column, plus the source d_y U_perp */
+        double dy = (p->y_max - p->y_min) / ny;
+        double ay = 0.0;
+        for (int j = 0; j < ny; j++) ay = fmax(ay, fabs(uperp[j]));
+        #pragma omp parallel
+        {
+            double *gp = malloc(sizeof(double) * ny), *gm = malloc(sizeof(double) * ny);
+            #pragma omp for schedule(static)
+            for (int k = 0; k < nx; k++) {
+                for (int j = 0; j < ny; j++) {
+                    double uu = u[(size_t)j * nx + k], g = uperp[j] * uu;
+                    gp[j] = 0.5 * (g + ay * uu);
+                    gm[j] = 0.5 * (g - ay * uu);
+                }
+                for (int j = 0; j < ny; j++) {
+                    double psi = (mu[(size_t)((j + 1) % ny) * nx + k] - mu[(size_t)j * nx + k]) / dy;
+                    double v[5], g[5];
+                    for (int s = 0; s < 5; s++) v[s] = gp[((j - 2 + s) % ny + ny) % ny];
+                    orc_weno_grad(v, p->weno_eps, g);
+                    for (int s = 0; s < 5; s++) {
+                        int i = ((j - 2 + s) % ny + ny) % ny;
+                        out[(size_t)i * nx + k] += psi * g[s] * 0.5 * (uperp[i] + ay);
+                    }
+                    for (int s = 0; s < 5; s++) v[s] = gm[((j + 3 - s) % ny + ny) % ny];
+                    orc_weno_grad(v, p->weno_eps, g);
+                    for (int s = 0; s < 5; s++) {
+                        int i = ((j + 3 - s) % ny + ny) % ny;
+                        out[(size_t)i * nx + k] += psi * g[s] * 0.5 * (uperp[i] - ay);
+                    }
+                }
+            }
+            free(gp); free(gm);
+        }
+        for (int j = 0; j < ny; j++)
+            for (int k = 0; k < nx; k++) out[(size_t)j * nx + k] += duperp[j] * mu[(size_t)j * nx + k];
+    }
+    free(upar); free(uperp); free(duperp);
 }
 
 /* out = Re F^{-1}( M o F(x) ), M given as re/im arrays, conj selects conj(M). */
@@ -690,7 +734,6 @@ static void rhs_T(const orc_params *p, const double *u, double sigma, const doub
 int orc_adjoint(const orc_params *p, const double *u0, const double *g_end, int64_t n_steps,
                 double sigma0, double *g0)
 {
-    if (p->n_modes > 0) return -2;        /* transposed medium terms: not restated here */
     size_t N = (size_t)p->nx * p->ny;
     tables_t t;
     tables_alloc(p, &t);

@@ -126,8 +126,38 @@ def test_flux_form_with_variable_uperp():
     assert _order(errs, ns) > 4.0
 
 
-def test_adjoint_is_refused_with_a_medium():
-    med = _one_mode(0.5, 1.0, 0.0, 0.01)
-    p = _params(16, 8, med)
-    with pytest.raises(ValueError):
-        oracle.adjoint(p, np.zeros((8, 16)), np.zeros((8, 16)), 1)
+def test_transpose_is_adjoint_of_linearisation():
+    """<J^T mu, v> = <mu, J v> with J v from central differences of the
+    medium's b (the transposed tau- and y-fluxes and the source)."""
+    w = inputs.medium_config(64, 32, 4)
+    p = oracle.Params(**inputs.oracle_params(w))
+    rng = np.random.default_rng(21)
+    u = w.u0
+    sigma = 5.3
+    for _ in range(3):
+        mu = rng.standard_normal(u.shape)
+        v = rng.standard_normal(u.shape)
+        h = 1e-6
+        jv = (oracle.weno_rhs(p, u + h * v, sigma) - oracle.weno_rhs(p, u - h * v, sigma)) / (2 * h)
+        jtmu = oracle.weno_rhs_T(p, u, mu, sigma)
+        lhs, rhs = np.sum(jtmu * v), np.sum(mu * jv)
+        assert abs(lhs - rhs) < 1e-7 * (np.linalg.norm(jtmu) * np.linalg.norm(v)), (lhs, rhs)
+
+
+def test_adjoint_matches_finite_differences():
+    w = inputs.medium_config(32, 16, 5)
+    p = oracle.Params(**inputs.oracle_params(w))
+    n, dtau = 5, w.dtau
+
+    def loss(u0):
+        u = oracle.run(p, u0, n)
+        return np.sum(u * u) * dtau
+
+    g0 = oracle.adjoint(p, w.u0, 2 * dtau * oracle.run(p, w.u0, n), n)
+    rng = np.random.default_rng(22)
+    for _ in range(3):
+        v = rng.standard_normal(w.u0.shape)
+        v /= np.linalg.norm(v)
+        h = 3e-6
+        fd = (loss(w.u0 + h * v) - loss(w.u0 - h * v)) / (2 * h)
+        assert abs(np.sum(g0 * v) - fd) < 1e-8 * np.linalg.norm(g0), (np.sum(g0 * v), fd)
