@@ -141,10 +141,11 @@ typedef struct {
 } kzk_medium;
 
 /* Attach a random medium to a (non-batched) plan.  Afterwards every step of
- * kzk_advance / kzk_step_stages and kzk_rhs includes the medium terms; the
- * adjoint entry points return KZK_ERR_STATE (their transposed step covers the
- * homogeneous and stratified medium only).  Allocates a physical work array
- * of the state's size and an [n_modes][ny] FP64 table.
+ * kzk_advance / kzk_step_stages and kzk_rhs includes the medium terms, and
+ * the adjoint entry points transpose them (the tau-flux with 2 pi U_par, the
+ * y-WENO5 -- its weights differentiated like the tau ones -- and the source).
+ * Allocates two physical work arrays of the state's size and an
+ * [n_modes][ny] FP64 table.
  * Errors: KZK_ERR_ARG (NULL, n_modes outside [0, KZK_MAX_MODES], NULL or
  * non-finite arrays), KZK_ERR_STATE (batched plan), KZK_ERR_OOM, KZK_ERR_CUDA. */
 kzk_status kzk_plan_set_medium(kzk_plan *plan, const kzk_medium *medium);
@@ -200,8 +201,7 @@ kzk_status kzk_get_tables(kzk_plan *plan, double *E, double *Phi1, double *Phi2)
  * transpose of the ExpRK22 step (transposed WENO5 including the derivatives
  * of the nonlinear weights, conjugated multipliers, adjoint FFTs), with a
  * checkpoint of the forward state every ckpt_every steps (>= 1) and
- * recomputation of each segment.  u0 is not modified.  g0 may alias g_end.
- * KZK_ERR_STATE for a plan with a random medium (kzk_plan_set_medium). */
+ * recomputation of each segment.  u0 is not modified.  g0 may alias g_end. */
 kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *g0,
                        int64_t n_steps, double sigma0, int32_t ckpt_every, void *stream);
 

@@ -96,11 +96,11 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
 #pragma unroll
     for (int s = 0; s < 6; s++) {
         const T v = ld_real<T, true>(u, (k0 - 2 + s) & msk);
-        const T f = -half * c.B * v * v;
+        const T f = fma(-c.c, v, -half * c.B * v * v);
         fp[s] = half * fma(c.alpha, v, f);
         fm[s] = half * fma(-c.alpha, v, f);
-        dp[s] = half * (c.alpha - c.B * v);
-        dm[s] = half * (-c.alpha - c.B * v);
+        dp[s] = half * ((c.alpha - c.c) - c.B * v);
+        dm[s] = half * ((-c.alpha - c.c) - c.B * v);
         acc[s] = T(0);
     }
     T mk_ = ld_real<T, true>(mu, k0 & msk);
@@ -125,11 +125,11 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
             fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; dp[s] = dp[s + 1]; dm[s] = dm[s + 1]; acc[s] = acc[s + 1];
         }
         const T v = ld_real<T, true>(u, (k + 4) & msk);
-        const T f = -half * c.B * v * v;
+        const T f = fma(-c.c, v, -half * c.B * v * v);
         fp[5] = half * fma(c.alpha, v, f);
         fm[5] = half * fma(-c.alpha, v, f);
-        dp[5] = half * (c.alpha - c.B * v);
-        dm[5] = half * (-c.alpha - c.B * v);
+        dp[5] = half * ((c.alpha - c.c) - c.B * v);
+        dm[5] = half * ((-c.alpha - c.c) - c.B * v);
         acc[5] = T(0);
     }
     // remaining points k0+Q-2 .. k0+Q+2 in acc[0..4]
@@ -155,6 +155,10 @@ struct AdjRowArgs {
     T dA;                   // A(sigma) - A
     T kscale;
     T inv_nx;
+    // random medium (nullable): this stage's coefficients (the row's c = 2 pi
+    // U_par enters the tau-flux) and the transposed y part, added before the R2C
+    const double* med_coef; // [ny][3]
+    const T* yT;            // [batch][ny][nx] physical
 };
 
 enum AdjRowMode { ADJ_ROW_2 = 0, ADJ_ROW_1 = 1 };
@@ -193,7 +197,13 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS) adj_row_kernel(AdjRowArgs<T> 
     const int Q = nx / nthr >= 4 ? nx / nthr : 4;
     const int nact = nx / Q;
     const int k0 = tid * Q;
-    if (tid < nact) weno_row_chunk_T<T>(U, M, G, spl + 2 * tid, spr + 3 * tid, nx, k0, Q, a.wc);
+    WenoCoef<T> wc = a.wc;
+    if (a.med_coef) {
+        const double cj = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * row);
+        wc.c = (T)cj;
+        wc.alpha = (T)(fabs(cj) + (double)a.wc.alpha);
+    }
+    if (tid < nact) weno_row_chunk_T<T>(U, M, G, spl + 2 * tid, spr + 3 * tid, nx, k0, Q, wc);
     __syncthreads();
     if (tid < nact) {
         const int left = (tid + nact - 1) % nact, right = (tid + 1) % nact;
@@ -204,6 +214,11 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS) adj_row_kernel(AdjRowArgs<T> 
         st_real<T, true>(G, k0 + Q - 1, ld_real<T, true>(G, k0 + Q - 1) + spl[2 * right + 1]);
     }
     __syncthreads();
+    if (a.yT) {
+        const T* yrow = a.yT + 2 * base;
+        for (int k = tid; k < nx; k += nthr) st_real<T, true>(G, k, ld_real<T, true>(G, k) + __ldcg(yrow + k));
+        __syncthreads();
+    }
     fft_batched<T, PPT, false, false, true>(G, log2n, 0, 1, 0, tw, tid, nthr);
     for (int k = tid; k <= n / 2; k += nthr) {
         cx<T> xk, xnk;

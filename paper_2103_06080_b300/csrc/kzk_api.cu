@@ -262,6 +262,7 @@ kzk_status configure(kzk_plan* p)
     KZK_TRY((set_row_attr<T, ROW_INV>(sm)));
     KZK_TRY((set_row_attr<T, ROW_RHS_MED>(sm)));
     KZK_CUDA(cudaFuncSetAttribute(ysweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    KZK_CUDA(cudaFuncSetAttribute(ysweepT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     KZK_TRY((set_col_attr<T, COL_STAGE1>(sm)));
     KZK_TRY((set_col_attr<T, COL_STAGE2>(sm)));
     KZK_TRY((set_adj_row_attr<T, ADJ_ROW_2>(sm)));
@@ -474,17 +475,19 @@ kzk_status launch_medium(kzk_plan* p, double sigma, int stage, cudaStream_t st)
 // medium: one pass (C2R, WENO5 along tau, R2C).  Random medium: the
 // coefficient kernel, a C2R pass to the physical rows (with the row
 // statistics), then the b pass with the y-flux and source terms.
-// diag_rows, u_out: nullable (u_out: the physical rows, homogeneous only).
+// diag_rows, u_out: nullable (u_out: where the physical rows are kept).
 template <typename T>
 kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, double* diag_rows, void* u_out,
                      int stage, cudaStream_t st)
 {
     if (p->med_n > 0) {
+        // the physical stage state: into u_out when the adjoint sweep keeps it
+        void* phys = u_out ? u_out : p->uphys;
         KZK_TRY(launch_medium(p, sigma, stage, st));
-        RowArgs<T> ri = row_args<T>(p, Vin, p->uphys, 0.0, diag_rows);
+        RowArgs<T> ri = row_args<T>(p, Vin, phys, 0.0, diag_rows);
         KZK_TRY((launch_row<T, ROW_INV>(p, ri, st)));
         YSweepArgs<T> y{};
-        y.u = (const T*)p->uphys;
+        y.u = (const T*)phys;
         y.by = (T*)p->by;
         y.coef = p->med_coef + (size_t)stage * 3 * p->ny;
         y.bmax = p->med_bmax + (size_t)stage * p->med_nb;
@@ -499,7 +502,7 @@ kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, dou
         ysweep_kernel<T><<<yg, YSWEEP_THREADS, ysweep_smem<T>(y.Q), st>>>(y);
         KZK_LAUNCHED();
         RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, nullptr);
-        r.uphys = (const T*)p->uphys;
+        r.uphys = (const T*)phys;
         r.by = (const T*)p->by;
         r.med_coef = p->med_coef + (size_t)stage * 3 * p->ny;
         return launch_row<T, ROW_RHS_MED>(p, r, st);
@@ -760,12 +763,47 @@ AdjColArgs<T> adj_col_args(const kzk_plan* p)
 
 // Transposed step on the plan's cotangent p->lam (packed spectral), given the
 // step's stage states V^n and V* (packed spectral).
+// One transposed row pass: out = l + F(J_{G_sigma}(u)^T C2R(m)) / nx, u the
+// physical stage state.  With a random medium: the coefficients at sigma, the
+// cotangent in physical space (p->uphys) and the transposed y part (p->by)
+// first.
+template <typename T, int MODE>
+kzk_status adj_row_stage(kzk_plan* p, const void* m, const void* u, const void* l, void* out, double sigma,
+                         int slot, cudaStream_t st)
+{
+    AdjRowArgs<T> r = adj_row_args<T>(p, m, u, l, out, sigma);
+    if (p->med_n > 0) {
+        KZK_TRY(launch_medium(p, sigma, slot, st));
+        KZK_TRY(to_physical<T>(p, m, p->uphys, 1.0, nullptr, st));
+        YSweepTArgs<T> y{};
+        y.u = (const T*)u;
+        y.mu = (const T*)p->uphys;
+        y.yT = (T*)p->by;
+        y.coef = p->med_coef + (size_t)slot * 3 * p->ny;
+        y.bmax = p->med_bmax + (size_t)slot * p->med_nb;
+        y.n_bmax = p->med_nb;
+        y.nx = p->nx;
+        y.ny = p->ny;
+        y.Q = std::min(p->ny, 32);
+        y.inst_elems = (long long)p->nx * p->ny;
+        y.eps = (T)p->c.weno_eps;
+        y.inv_dy = (T)(p->ny / (p->g.y_max - p->g.y_min));
+        const dim3 yg((p->nx + YSWEEP_THREADS - 1) / YSWEEP_THREADS, (p->ny + y.Q - 1) / y.Q, p->batch);
+        ysweepT_kernel<T><<<yg, YSWEEP_THREADS, ysweepT_smem<T>(y.Q), st>>>(y);
+        KZK_LAUNCHED();
+        r.med_coef = y.coef;
+        r.yT = (const T*)p->by;
+    }
+    const dim3 rgrid(p->ny, p->batch);
+    adj_row_kernel<T, row_ppt<T>(), MODE><<<rgrid, p->adj_row_thr, adj_row_smem<T>(p), st>>>(r);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
 template <typename T>
 kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* us, cudaStream_t st)
 {
-    const dim3 cgrid(p->n >> p->log2tc, p->batch), rgrid(p->ny, p->batch);
-    const size_t rsm = adj_row_smem<T>(p);
-    const int rthr = p->adj_row_thr;
+    const dim3 cgrid(p->n >> p->log2tc, p->batch);
     if (p->c.method == KZK_EXPEULER) {
         // transpose of u' = P_E u + P_{ds Phi1} G_n(u): with mu2 = 0 the
         // stage-1 column pass gives lam_lin = P_{conj E} lam', nu1 =
@@ -783,10 +821,7 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* u
         c1.sb = (T)p->nx;
         adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
         KZK_LAUNCHED();
-        AdjRowArgs<T> r1 = adj_row_args<T>(p, p->nu, un, p->ls, p->lam, sigma);
-        adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_1><<<rgrid, rthr, rsm, st>>>(r1);
-        KZK_LAUNCHED();
-        return KZK_OK;
+        return adj_row_stage<T, ADJ_ROW_1>(p, p->nu, un, p->ls, p->lam, sigma, 0, st);
     }
     // mu2 = P_{conj(ds Phi2)} lam'
     AdjColArgs<T> c2 = adj_col_args<T>(p);
@@ -797,9 +832,7 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* u
     adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_2><<<cgrid, p->col_thr, p->col_smem, st>>>(c2);
     KZK_LAUNCHED();
     // lam* = lam' + J_{G_{n+1}}(u*)^T mu2
-    AdjRowArgs<T> r2 = adj_row_args<T>(p, p->mu, us, p->lam, p->ls, sigma + p->dt);
-    adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_2><<<rgrid, rthr, rsm, st>>>(r2);
-    KZK_LAUNCHED();
+    KZK_TRY((adj_row_stage<T, ADJ_ROW_2>(p, p->mu, us, p->lam, p->ls, sigma + p->dt, 1, st)));
     // lam_lin = P_{conj E} lam*,  nu1 = P_{conj(ds Phi1)} lam* - mu2
     AdjColArgs<T> c1 = adj_col_args<T>(p);
     c1.a = (const cx<T>*)p->ls;
@@ -813,10 +846,7 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* u
     adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
     KZK_LAUNCHED();
     // lam = lam_lin + J_{G_n}(u)^T nu1
-    AdjRowArgs<T> r1 = adj_row_args<T>(p, p->nu, un, p->ls, p->lam, sigma);
-    adj_row_kernel<T, row_ppt<T>(), ADJ_ROW_1><<<rgrid, rthr, rsm, st>>>(r1);
-    KZK_LAUNCHED();
-    return KZK_OK;
+    return adj_row_stage<T, ADJ_ROW_1>(p, p->nu, un, p->ls, p->lam, sigma, 0, st);
 }
 
 template <typename T>
@@ -1730,7 +1760,6 @@ kzk_status kzk_advance_checkpointed(kzk_plan* p, void* u, int64_t n_steps, doubl
 {
     if (!p || !u) return fail(KZK_ERR_ARG, "plan or u is NULL");
     if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
-    if (p->med_n > 0) return fail(KZK_ERR_STATE, "the adjoint does not cover the random-medium terms");
     if (n_steps < 1 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
     cudaStream_t st = (cudaStream_t)stream;
     p->ck_steps = 0;
@@ -1746,7 +1775,6 @@ kzk_status kzk_adjoint_checkpointed(kzk_plan* p, const void* g_end, void* g0, vo
 {
     if (!p || !g_end || !g0) return fail(KZK_ERR_ARG, "NULL argument");
     if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
-    if (p->med_n > 0) return fail(KZK_ERR_STATE, "the adjoint does not cover the random-medium terms");
     if (p->ck_steps < 1) return fail(KZK_ERR_STATE, "no checkpointed forward run stored in this plan");
     cudaStream_t st = (cudaStream_t)stream;
     return p->prec == KZK_FP64 ? reverse_sweep<double>(p, g_end, g0, st) : reverse_sweep<float>(p, g_end, g0, st);
@@ -1756,7 +1784,6 @@ kzk_status kzk_adjoint(kzk_plan* p, const void* u0, const void* g_end, void* g0,
                        int32_t ckpt_every, void* stream)
 {
     if (!p || !u0 || !g_end || !g0) return fail(KZK_ERR_ARG, "NULL argument");
-    if (p->med_n > 0) return fail(KZK_ERR_STATE, "the adjoint does not cover the random-medium terms");
     if (n_steps < 0 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 0 and ckpt_every >= 1");
     cudaStream_t st = (cudaStream_t)stream;
     if (n_steps == 0) {

@@ -14,6 +14,7 @@
 #pragma once
 #include "kzk_common.cuh"
 #include "kzk_weno.cuh"
+#include "kzk_adjoint.cuh"
 
 namespace kzk {
 
@@ -192,6 +193,119 @@ __global__ void __launch_bounds__(YSWEEP_THREADS) ysweep_kernel(YSweepArgs<T> a)
         tRp1 = tRpN;
         tLm2 = tLm1; tLm1 = tLmN;
         tCm1 = tCmN;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Transpose of the y part for the adjoint: yT = J_y(u)^T mu + (d_y U_perp) mu,
+// J_y the derivative of -(G_{j+1/2} - G_{j-1/2}) / dy.  For each interface
+// j' + 1/2 with psi = (mu_{j'+1} - mu_{j'}) / dy the gradients of its two
+// reconstructions (weno5_grad) are scattered to rows j'-2 .. j'+3 times
+// dg+-/du = (U_perp +- alpha_y) / 2 (alpha_y does not depend on u) through an
+// accumulation window that slides down the column; a row is complete once the
+// last interface touching it (j' = row + 2) is done.  A thread covers the
+// interfaces j0 - 3 .. j0 + Q + 1 of its rows [j0, j0 + Q).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct YSweepTArgs {
+    const T* u;              // stage state, physical [batch][ny][nx]
+    const T* mu;             // cotangent of b, physical [batch][ny][nx]
+    T* yT;                   // out [batch][ny][nx]
+    const double* coef;      // [ny][3]: U_par, U_perp, d U_perp / dy
+    const double* bmax;      // [n_bmax]
+    int n_bmax, nx, ny, Q;
+    long long inst_elems;
+    T eps, inv_dy;
+};
+
+template <typename T>
+__host__ __device__ constexpr size_t ysweepT_smem(int Q)
+{
+    // u rows j0-5 .. j0+Q+4, mu rows j0-3 .. j0+Q+2, per-row factors of the u rows
+    return ((size_t)(Q + 10) * (YSWEEP_THREADS + 3) + (size_t)(Q + 6) * YSWEEP_THREADS) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(YSWEEP_THREADS) ysweepT_kernel(YSweepTArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char yt_smem[];
+    const int tid = threadIdx.x;
+    const int k0 = blockIdx.x * YSWEEP_THREADS, k = k0 + tid;
+    const int j0 = blockIdx.y * a.Q;
+    const int ny = a.ny, nx = a.nx;
+    const int Q = min(a.Q, ny - j0);
+    const int Ru = Q + 10, Rm = Q + 6;
+    T* tu = reinterpret_cast<T*>(yt_smem);      // [Ru][128]: rows j0-5 ..
+    T* tm = tu + (size_t)Ru * YSWEEP_THREADS;   // [Rm][128]: rows j0-3 ..
+    T* dgp = tm + (size_t)Rm * YSWEEP_THREADS;  // [Ru]: (U_perp + alpha_y) / 2
+    T* dgm = dgp + Ru;                          // [Ru]: (U_perp - alpha_y) / 2
+    T* dpr = dgm + Ru;                          // [Ru]: d U_perp / dy
+    double ay = 0.0;
+    for (int i = 0; i < a.n_bmax; i++) ay = fmax(ay, __ldg(a.bmax + i));
+    const T* u = a.u + (long long)blockIdx.z * a.inst_elems;
+    const T* mu = a.mu + (long long)blockIdx.z * a.inst_elems;
+    for (int idx = tid; idx < Ru * YSWEEP_THREADS; idx += YSWEEP_THREADS) {
+        const int r = idx / YSWEEP_THREADS, c = idx % YSWEEP_THREADS;
+        const int row = (((j0 - 5 + r) % ny) + ny) % ny;
+        tu[idx] = (k0 + c < nx) ? __ldg(u + (long long)row * nx + k0 + c) : T(0);
+    }
+    for (int idx = tid; idx < Rm * YSWEEP_THREADS; idx += YSWEEP_THREADS) {
+        const int r = idx / YSWEEP_THREADS, c = idx % YSWEEP_THREADS;
+        const int row = (((j0 - 3 + r) % ny) + ny) % ny;
+        tm[idx] = (k0 + c < nx) ? __ldg(mu + (long long)row * nx + k0 + c) : T(0);
+    }
+    for (int r = tid; r < Ru; r += YSWEEP_THREADS) {
+        const int row = (((j0 - 5 + r) % ny) + ny) % ny;
+        const double up = __ldg(a.coef + 3 * row + 1);
+        dgp[r] = (T)(0.5 * (up + ay));
+        dgm[r] = (T)(0.5 * (up - ay));
+        dpr[r] = (T)__ldg(a.coef + 3 * row + 2);
+    }
+    __syncthreads();
+    if (k >= nx) return;
+    T* out = a.yT + (long long)blockIdx.z * a.inst_elems + k;
+    const T eps4 = T(4) * a.eps;
+    const T inv_dy6 = a.inv_dy * (T(1) / T(6));
+    auto U = [&](int row) { return tu[(row - (j0 - 5)) * YSWEEP_THREADS + tid]; };
+    auto M = [&](int row) { return tm[(row - (j0 - 3)) * YSWEEP_THREADS + tid]; };
+    // window slot s <-> row j' - 2 + s for interface j' + 1/2
+    T gp[6], gm[6], fp[6], fm[6], acc[6];
+    int jp = j0 - 3;
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const int r = jp - 2 + s - (j0 - 5);
+        const T v = U(jp - 2 + s);
+        fp[s] = dgp[r];
+        fm[s] = dgm[r];
+        gp[s] = fp[s] * v;
+        gm[s] = fm[s] * v;
+        acc[s] = T(0);
+    }
+    for (; jp <= j0 + Q + 1; jp++) {
+        const T psi6 = (M(jp + 1) - M(jp)) * inv_dy6;
+        T gP[5], gM[5];
+        weno5_grad<T>(gp[0], gp[1], gp[2], gp[3], gp[4], eps4, psi6, gP);
+        weno5_grad<T>(gm[5], gm[4], gm[3], gm[2], gm[1], eps4, psi6, gM);
+#pragma unroll
+        for (int s = 0; s < 5; s++) acc[s] = fma(gP[s], fp[s], acc[s]);
+#pragma unroll
+        for (int s = 0; s < 5; s++) acc[5 - s] = fma(gM[s], fm[5 - s], acc[5 - s]);
+        const int done = jp - 2;                       // its last interface
+        if (done >= j0 && done < j0 + Q)
+            out[(long long)done * nx] = fma(dpr[done - (j0 - 5)], M(done), acc[0]);
+#pragma unroll
+        for (int s = 0; s < 5; s++) {
+            gp[s] = gp[s + 1]; gm[s] = gm[s + 1]; fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; acc[s] = acc[s + 1];
+        }
+        if (jp + 4 <= j0 + Q + 4) {
+            const int r = jp + 4 - (j0 - 5);
+            const T v = U(jp + 4);
+            fp[5] = dgp[r];
+            fm[5] = dgm[r];
+            gp[5] = fp[5] * v;
+            gm[5] = fm[5] * v;
+        }
+        acc[5] = T(0);
     }
 }
 

@@ -103,12 +103,38 @@ def test_removing_the_medium_restores_the_homogeneous_path():
     assert torch.equal(a, b)
 
 
-def test_adjoint_is_refused_with_a_medium():
+@pytest.mark.parametrize("prec,tol,method", [("fp64", 1e-10, "exprk22"), ("fp32", 3e-3, "exprk22"),
+                                             ("fp64", 1e-10, "expeuler")])
+def test_adjoint_matches_oracle(prec, tol, method):
     api = _api()
-    w = inputs.medium_config(64, 16, 4)
+    w = inputs.medium_config(128, 64, 8)
+    plan = api.Plan.from_workload(w, precision=prec, method=method)
+    p = oracle.Params(**inputs.oracle_params(w, method=1 if method == "expeuler" else 0))
+    g_end = 2 * w.dtau * oracle.run(p, w.u0, w.n_steps)
+    ref = oracle.adjoint(p, w.u0, g_end, w.n_steps)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    g0 = plan.adjoint(_dev(w.u0, dt), _dev(g_end, dt), w.n_steps, ckpt_every=3)
+    assert rel_linf(g0.double().cpu().numpy(), ref) < tol
+
+
+def test_adjoint_finite_differences():
+    api = _api()
+    w = inputs.medium_config(64, 32, 6)
     plan = api.Plan.from_workload(w)
-    u = _dev(w.u0)
-    with pytest.raises(Exception, match="STATE"):
-        plan.adjoint(u, u.clone(), 4, ckpt_every=2)
-    with pytest.raises(Exception, match="STATE"):
-        plan.advance_checkpointed(u, 4, 0.0, 2)
+    u0 = _dev(w.u0)
+
+    def loss(u):
+        v = u.clone()
+        plan.advance(v, w.n_steps)
+        return float((v * v).sum()) * w.dtau
+
+    y = u0.clone()
+    plan.advance(y, w.n_steps)
+    g0 = plan.adjoint(u0, 2 * w.dtau * y, w.n_steps, ckpt_every=4).cpu().numpy()
+    rng = np.random.default_rng(31)
+    for _ in range(3):
+        v = rng.standard_normal(w.u0.shape)
+        v /= np.linalg.norm(v)
+        h = 1e-6
+        fd = (loss(u0 + h * _dev(v)) - loss(u0 - h * _dev(v))) / (2 * h)
+        assert abs(np.sum(g0 * v) - fd) < 1e-6 * np.linalg.norm(g0)
