@@ -168,7 +168,7 @@ def cpu_oracle_rate(w, n_steps: int, threads: bool = True, budget_s: float = 0.0
     one untimed first step (it pays the first touch of the oracle's work
     arrays), then m timed steps, each timed inside the oracle (table set-up
     excluded).  With budget_s > 0, m is the number of steps that fit in about
-    budget_s seconds judged from the first step (at most n_steps)."""
+    budget_s seconds estimated from the first step (at most n_steps)."""
     import oracle
     p = oracle.Params(**inputs.oracle_params(w))
     m = max(1, n_steps)
