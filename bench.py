@@ -45,6 +45,38 @@ def _peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def source_hash() -> str:
+    """First 12 hex digits of the SHA-256 of the CUDA sources (csrc/, sorted)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2103_06080_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(kernel: str, prec: str):
+    """DRAM bytes (read + write) of one launch of `kernel` from the ncu summaries
+    under profiles/ (lines 'traffic <kernel> <prec> <bytes> src <hash>'), or
+    None when no capture matches the current sources."""
+    d = os.path.join(ROOT, "profiles")
+    want = source_hash()
+    try:
+        names = sorted(os.listdir(d))
+    except OSError:
+        return None
+    for f in names:
+        if not f.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(d, f)):
+            t = line.strip().strip("`").split()
+            if len(t) == 6 and t[0] == "traffic" and t[1] == kernel and t[2] == prec and t[4] == "src" and t[5] == want:
+                return float(t[3])
+    return None
+
+
 # --------------------------------------------------------------------------
 # algorithmic work per launch (also stated in the design notes)
 # --------------------------------------------------------------------------
@@ -259,12 +291,13 @@ def run_ours(args, rank, world, local_rank):
         hbm = peaks["hbm_gbs"] * 1e9
         roof = {"bound": "hbm", "kernel": names[dom], "achieved": by[dom] / (kt[dom] * 1e-3) / 1e9,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": by[dom] / (kt[dom] * 1e-3) / hbm,
-                "traffic": None, "peak_source": f"{peak_src} HBM copy bandwidth", "kernel_ms": dict(zip(names, kt))}
+                "traffic": measured_traffic(names[dom], "fp32"), "peak_source": f"{peak_src} HBM copy bandwidth",
+                "kernel_ms": dict(zip(names, kt))}
     else:
         fp64_peak = api.alu_peak("fp64")
         roof = {"bound": "alu", "kernel": names[dom], "achieved": fl[dom] / (kt[dom] * 1e-3) / 1e12,
                 "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                "frac": fl[dom] / (kt[dom] * 1e-3) / fp64_peak, "traffic": None,
+                "frac": fl[dom] / (kt[dom] * 1e-3) / fp64_peak, "traffic": measured_traffic(names[dom], "fp64"),
                 "peak_source": "measured FP64 FMA throughput (kzk_alu_peak) on this GPU",
                 "kernel_ms": dict(zip(names, kt)),
                 "hbm_frac_of_measured": by[dom] / (kt[dom] * 1e-3) / (peaks["hbm_gbs"] * 1e9)}
@@ -371,7 +404,7 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
         "dtype": "f32 (FP64-generated tables rounded once; FP64 diagnostics)",
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": by3[dom] / (kt3[dom] * 1e-3) / 1e9,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": by3[dom] / (kt3[dom] * 1e-3) / hbm,
-                     "traffic": None, "kernel_ms": dict(zip(names, kt3)),
+                     "traffic": measured_traffic(names[dom], "fp32"), "kernel_ms": dict(zip(names, kt3)),
                      "step_frac": sum(by3) / (sum(kt3) * 1e-3) / hbm},
     }
     p3.close()
