@@ -69,11 +69,69 @@ int orc_num_threads(void)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Mixed-radix FFT for lengths that are not powers of two (the paper's grids   */
+/* have 7 * 2^k points in tau and 1250 * 2^k = 2^(k+1) * 5^4 in y, Table 1).    */
+/* Recursive Cooley-Tukey decimation in time: with p the smallest prime factor */
+/* of n and m = n / p, the p interleaved subsequences x_{p j + r} are          */
+/* transformed (length m) and combined as                                      */
+/*     X_k = sum_r exp(sgn 2 pi i r k / n) Y_r[k mod m];                        */
+/* a prime length is the direct sum.  Unnormalised.                            */
+/* ------------------------------------------------------------------------ */
+static void fft_mixed(const double *xr, const double *xi, int stride, int n, double sgn, double *yr, double *yi)
+{
+    if (n == 1) { yr[0] = xr[0]; yi[0] = xi[0]; return; }
+    int p = 2;
+    while (n % p) p++;
+    if (p == n) {
+        for (int k = 0; k < n; k++) {
+            double sr = 0.0, si = 0.0;
+            for (int j = 0; j < n; j++) {
+                /* exp(sgn 2 pi i j k / n), argument reduced modulo n */
+                double ang = sgn * 2.0 * M_PI * (double)((long long)j * k % n) / (double)n;
+                double wr = cos(ang), wi = sin(ang);
+                sr += xr[(size_t)j * stride] * wr - xi[(size_t)j * stride] * wi;
+                si += xr[(size_t)j * stride] * wi + xi[(size_t)j * stride] * wr;
+            }
+            yr[k] = sr; yi[k] = si;
+        }
+        return;
+    }
+    const int m = n / p;
+    double *tr = (double *)malloc(sizeof(double) * n), *ti = (double *)malloc(sizeof(double) * n);
+    for (int r = 0; r < p; r++)
+        fft_mixed(xr + (size_t)r * stride, xi + (size_t)r * stride, stride * p, m, sgn, tr + (size_t)r * m,
+                  ti + (size_t)r * m);
+    for (int k = 0; k < n; k++) {
+        double sr = 0.0, si = 0.0;
+        for (int r = 0; r < p; r++) {
+            double ang = sgn * 2.0 * M_PI * (double)((long long)r * k % n) / (double)n;
+            double wr = cos(ang), wi = sin(ang);
+            double ar = tr[(size_t)r * m + k % m], ai = ti[(size_t)r * m + k % m];
+            sr += ar * wr - ai * wi;
+            si += ar * wi + ai * wr;
+        }
+        yr[k] = sr; yi[k] = si;
+    }
+    free(tr); free(ti);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Radix-2 FFT (textbook iterative Cooley-Tukey, bit reversal + butterflies).  */
 /* Forward: X_k = sum_n x_n exp(-2 pi i k n / N).  Inverse includes 1/N.       */
+/* Other lengths: the mixed-radix transform above.                             */
 /* ------------------------------------------------------------------------ */
 void orc_fft1d(double *re, double *im, int n, int inverse)
 {
+    if (n & (n - 1)) {
+        double *yr = (double *)malloc(sizeof(double) * n), *yi = (double *)malloc(sizeof(double) * n);
+        fft_mixed(re, im, 1, n, inverse ? 1.0 : -1.0, yr, yi);
+        for (int i = 0; i < n; i++) {
+            re[i] = inverse ? yr[i] / n : yr[i];
+            im[i] = inverse ? yi[i] / n : yi[i];
+        }
+        free(yr); free(yi);
+        return;
+    }
     /* bit-reversal permutation */
     for (int i = 1, j = 0; i < n; i++) {
         int bit = n >> 1;
