@@ -45,24 +45,36 @@ def _peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-def source_hash() -> str:
-    """First 12 hex digits of the SHA-256 of the CUDA sources (csrc/, sorted)."""
+# the headers that hold the device code of each timed pass (kernel bodies and
+# everything they include); a change to any of them voids a stored capture
+_ROW_SRC = ("kzk_common.cuh", "kzk_fft.cuh", "kzk_weno.cuh", "kzk_kernels.cuh")
+KERNEL_SOURCES = {
+    ("row_stage1", "fp64"): _ROW_SRC, ("row_stage2", "fp64"): _ROW_SRC,
+    ("row_stage1", "fp32"): _ROW_SRC, ("row_stage2", "fp32"): _ROW_SRC,
+    ("col_stage1", "fp64"): _ROW_SRC, ("col_stage2", "fp64"): _ROW_SRC,
+    ("col_stage1", "fp32"): _ROW_SRC + ("kzk_colpipe.cuh",), ("col_stage2", "fp32"): _ROW_SRC + ("kzk_colpipe.cuh",),
+}
+
+
+def source_hash(files) -> str:
+    """First 12 hex digits of the SHA-256 of the named csrc/ files, in order."""
     import hashlib
     d = os.path.join(ROOT, "paper_2103_06080_b300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+    for f in files:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:12]
 
 
 def measured_traffic(kernel: str, prec: str):
-    """DRAM bytes (read + write) of one launch of `kernel` from the ncu summaries
-    under profiles/ (lines 'traffic <kernel> <prec> <bytes> src <hash>'), or
-    None when no capture matches the current sources."""
+    """DRAM bytes (read + write) of one launch of the pass `kernel` from the
+    ncu summaries under profiles/ (lines 'traffic <kernel> <prec> <bytes> src
+    <hash>'), or None when no capture matches the current device code."""
     d = os.path.join(ROOT, "profiles")
-    want = source_hash()
+    if (kernel, prec) not in KERNEL_SOURCES:
+        return None
+    want = source_hash(KERNEL_SOURCES[(kernel, prec)])
     try:
         names = sorted(os.listdir(d))
     except OSError:
