@@ -48,7 +48,7 @@ extern "C" {
 typedef enum {
     KZK_OK = 0,
     KZK_ERR_ARG = 1,        /* null pointer, bad enum, non-positive extent, bad dt      */
-    KZK_ERR_SIZE = 2,       /* nx, ny not powers of two or outside [8, 8192] x [2, 4096] */
+    KZK_ERR_SIZE = 2,       /* grid size not supported (see kzk_grid)                   */
     KZK_ERR_CFL = 3,        /* max|u| exceeded lf_umax (LF splitting no longer upwind)  */
     KZK_ERR_NONFINITE = 4,  /* a NaN or Inf appeared in the state                       */
     KZK_ERR_CUDA = 5,       /* a CUDA runtime call failed                                */
@@ -61,7 +61,13 @@ typedef enum { KZK_FP64 = 0, KZK_FP32 = 1 } kzk_precision;
 
 /* Grid of Sec. 3.3: tau_k = tau_min + k (tau_max - tau_min)/nx, y_j likewise. */
 typedef struct {
-    int32_t nx, ny;                 /* powers of two; nx: tau (contiguous), ny: y */
+    int32_t nx, ny;                 /* nx: tau points (contiguous), ny: y points; either
+                                       powers of two in [8, 8192] x [2, 4096], or even
+                                       sizes in [8, 16384] x [2, 32768] with nx/2 and ny
+                                       free of prime factors above 7 (the paper's
+                                       7*2^k x 1250*2^k grids, Table 1: mixed-radix
+                                       transforms; KZK_MIXED=1 in the environment selects
+                                       them for power-of-two grids too) */
     double tau_min, tau_max, y_min, y_max;
     int32_t prec;                   /* kzk_precision of state and bulk arithmetic */
 } kzk_grid;
@@ -117,7 +123,9 @@ typedef struct kzk_plan_s kzk_plan;
  * Errors: KZK_ERR_ARG (null, dt <= 0, B <= 0, A < 0, lf_umax <= 0, batch < 1,
  * n_relax outside [0, KZK_MAX_RELAX], some C_r < 0 or theta_r <= 0, unknown
  * method),
- * KZK_ERR_SIZE, KZK_ERR_OOM, KZK_ERR_CUDA.  *out is NULL on failure. */
+ * KZK_ERR_SIZE (see kzk_grid; also a grid whose column or row does not fit
+ * the device's shared memory), KZK_ERR_OOM, KZK_ERR_CUDA.  *out is NULL on
+ * failure. */
 kzk_status kzk_plan_create(const kzk_grid *grid, const kzk_coeffs *coeffs, double dt,
                            int32_t batch, kzk_plan **out);
 
@@ -201,7 +209,9 @@ kzk_status kzk_get_tables(kzk_plan *plan, double *E, double *Phi1, double *Phi2)
  * transpose of the ExpRK22 step (transposed WENO5 including the derivatives
  * of the nonlinear weights, conjugated multipliers, adjoint FFTs), with a
  * checkpoint of the forward state every ckpt_every steps (>= 1) and
- * recomputation of each segment.  u0 is not modified.  g0 may alias g_end. */
+ * recomputation of each segment.  u0 is not modified.  g0 may alias g_end.
+ * KZK_ERR_SIZE on a mixed-radix plan (the adjoint kernels are power-of-two
+ * only; so is kzk_advance_checkpointed). */
 kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *g0,
                        int64_t n_steps, double sigma0, int32_t ckpt_every, void *stream);
 
@@ -222,7 +232,7 @@ kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *
  * for the column passes, the same computation as kzk_advance -- separated by
  * grid barriers whose waits are bounded (KZK_ERR_TIMEOUT).  With
  * KZK_BATCH_AUTOTUNE the column-tile width is chosen by timing two steps of
- * each candidate at creation.  Each nx must be <= 8192. */
+ * each candidate at creation.  Each grid must be a power of two, nx <= 8192. */
 kzk_status kzk_plan_create_batched(const kzk_grid *grids, const kzk_coeffs *coeffs, const double *dts,
                                    int32_t n, int32_t flags, kzk_plan **out);
 

@@ -14,6 +14,7 @@
 #include "kzk_colpipe.cuh"
 #include "kzk_kernels.cuh"
 #include "kzk_medium.cuh"
+#include "kzk_mixed.cuh"
 #include "kzk_tables.cuh"
 
 using namespace kzk;
@@ -127,6 +128,14 @@ struct kzk_plan_s {
     std::vector<void*>* graph_u;        // state pointers the cached graph was captured with
     std::vector<cudaStream_t>* side;    // one captured stream per instance
     std::vector<cudaEvent_t>* evs;      // fork event, then one join event per instance
+    // grids whose sizes are not powers of two (kzk_mixed.cuh)
+    int mixed;
+    MixFFT mrow, mcol;          // radix schedules of the tau (length nx/2) and y transforms
+    int *mpos_row, *mpos_col;   // device: position of each frequency after the forward passes
+    int* mipos_col;             // device: frequency at each position (y)
+    void* wsc;                  // device [batch][ny][nx/2]: P1' FFT_y(b1) between the two C1 launches
+    int mrow_thr, mcol_lc;
+    size_t mrow_smem, mcol_smem;
 };
 
 namespace {
@@ -236,9 +245,42 @@ void colp_configure(kzk_plan* p, int optin)
     }
 }
 
+// Mixed-radix plans: one row per CTA; column tiles of the widest power of two
+// (at most 16) dividing nx/2 whose tile fits 96 KB (two CTAs per SM), else
+// single columns up to the device's shared-memory limit.
+template <typename T>
+kzk_status configure_mixed(kzk_plan* p)
+{
+    if (!mix_plan(p->n, 2, &p->mrow) || !mix_plan(p->ny, 1, &p->mcol))
+        return fail(KZK_ERR_SIZE, "nx/2 = %d and ny = %d must have no prime factor above 7", p->n, p->ny);
+    int dev = 0, optin = 0;
+    KZK_CUDA(cudaGetDevice(&dev));
+    KZK_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    KZK_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    p->mrow_thr = mix_row_threads(p->nx);
+    p->mrow_smem = mix_row_smem<T>(p->nx, p->mrow_thr);
+    int lc = 0;
+    while (lc < 4 && p->n % (2 << lc) == 0 && (size_t)p->ny * (2 << lc) * sizeof(cx<T>) <= 96 * 1024) lc++;
+    p->mcol_lc = lc;
+    p->mcol_smem = std::max(((size_t)p->ny << lc) * sizeof(cx<T>), 4 * (size_t)MIX_COL_THREADS * sizeof(double));
+    if (p->mrow_smem > (size_t)optin || p->mcol_smem > (size_t)optin)
+        return fail(KZK_ERR_SIZE, "grid %d x %d needs more shared memory than the device offers", p->nx, p->ny);
+    p->colp_log2tc = -1;
+    KZK_CUDA(cudaFuncSetAttribute(mix_row_kernel<T, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_row_kernel<T, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_row_kernel<T, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_row_kernel<T, ROW_RHS_MED>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C1B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C1V>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(ysweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    return KZK_OK;
+}
+
 template <typename T>
 kzk_status configure(kzk_plan* p)
 {
+    if (p->mixed) return configure_mixed<T>(p);
     p->row_thr = row_threads<T>(p->nx);
     if (p->row_thr > ROW_MAX_THREADS) return fail(KZK_ERR_SIZE, "nx = %d too large for one row per CTA", p->nx);
     p->row_smem = row_smem_bytes<T>(p->nx);
@@ -361,6 +403,16 @@ RowArgs<T> row_args(const kzk_plan* p, const void* in, void* out, double sigma, 
 template <typename T, int MODE>
 kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st)
 {
+    if (p->mixed) {
+        MixRowArgs<T> m{};
+        m.r = a;
+        m.nx = p->nx;
+        m.f = p->mrow;
+        m.pos = p->mpos_row;
+        mix_row_kernel<T, MODE><<<dim3(p->ny, p->batch), p->mrow_thr, p->mrow_smem, st>>>(m);
+        KZK_LAUNCHED();
+        return KZK_OK;
+    }
     row_kernel<T, MODE><<<dim3(p->ny, p->batch), p->row_thr, p->row_smem, st>>>(a);
     KZK_LAUNCHED();
     return KZK_OK;
@@ -426,9 +478,39 @@ kzk_status launch_colp(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
     return KZK_OK;
 }
 
+// Mixed-radix plans: STAGE1 as two launches (P1' FFT_y(b1) into the scratch
+// array, then the state's transform, propagator and inverse), STAGE2 as one.
+template <typename T, int MODE>
+kzk_status launch_mix_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
+{
+    MixColArgs<T> m{};
+    m.c = a;
+    m.c.tw = (const cx<T>*)p->twc;
+    m.c.tw_lo = (const cx<T>*)p->twc_lo;
+    m.w = (cx<T>*)p->wsc;
+    m.ny = p->ny;
+    m.n = p->n;
+    m.lc = p->mcol_lc;
+    m.f = p->mcol;
+    m.pos = p->mpos_col;
+    m.ipos = p->mipos_col;
+    const dim3 grid(p->n >> p->mcol_lc, p->batch);
+    if (MODE == COL_STAGE1) {
+        mix_col_kernel<T, MIX_C1B><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+        KZK_LAUNCHED();
+        mix_col_kernel<T, MIX_C1V><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+        KZK_LAUNCHED();
+    } else {
+        mix_col_kernel<T, MIX_C2><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+        KZK_LAUNCHED();
+    }
+    return KZK_OK;
+}
+
 template <typename T, int MODE>
 kzk_status launch_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
 {
+    if (p->mixed) return launch_mix_col<T, MODE>(p, a, st);
     if (p->colp_log2tc >= 0) return launch_colp<T, MODE>(p, a, st);
     col_kernel<T, MODE><<<dim3(p->n >> p->log2tc, p->batch), p->col_thr, p->col_smem, st>>>(a);
     KZK_LAUNCHED();
@@ -660,6 +742,27 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
     KZK_LAUNCHED();
     auto tr = twiddles<T>(p->nx);
     auto tcf = twiddles<T>(p->ny);
+    if (p->mixed) {
+        // full y table (hi and, FP32, lo) and the digit-reversal positions
+        std::vector<cx<T>> tcl;
+        auto tch = twiddles<T>(p->ny, &tcl);
+        std::vector<int> pr(p->n), pc(p->ny), ipc(p->ny);
+        for (int k = 0; k < p->n; k++) pr[k] = mix_position(p->mrow, k);
+        for (int l = 0; l < p->ny; l++) {
+            pc[l] = mix_position(p->mcol, l);
+            ipc[pc[l]] = l;
+        }
+        KZK_CUDA(cudaMemcpy(p->twr, tr.data(), tr.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+        KZK_CUDA(cudaMemcpy(p->twc_full, tcf.data(), tcf.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+        KZK_CUDA(cudaMemcpy(p->twc, tch.data(), tch.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+        if (p->twc_lo)
+            KZK_CUDA(cudaMemcpy(p->twc_lo, tcl.data(), tcl.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+        KZK_CUDA(cudaMemcpy(p->mpos_row, pr.data(), pr.size() * sizeof(int), cudaMemcpyHostToDevice));
+        KZK_CUDA(cudaMemcpy(p->mpos_col, pc.data(), pc.size() * sizeof(int), cudaMemcpyHostToDevice));
+        KZK_CUDA(cudaMemcpy(p->mipos_col, ipc.data(), ipc.size() * sizeof(int), cudaMemcpyHostToDevice));
+        KZK_CUDA(cudaStreamSynchronize(st));
+        return KZK_OK;
+    }
     auto trs = staged_twiddles<T>(p->log2nx - 1, row_ppt_of<T>());
     std::vector<cx<T>> tcl;
     auto tcs = staged_twiddles<T>(p->log2ny, col_ppt_of<T>(), &tcl);
@@ -701,7 +804,7 @@ void plan_free(kzk_plan* p)
                     p->tws_row, p->twc_full,
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
                     p->seg, p->ckpt, p->colp_flag, p->med_Ty, p->med_mode, p->med_coef, p->med_bmax,
-                    p->uphys, p->by};
+                    p->uphys, p->by, p->mpos_row, p->mpos_col, p->mipos_col, p->wsc};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1410,9 +1513,17 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     *out = nullptr;
     if (!grid || !coeffs) return fail(KZK_ERR_ARG, "grid or coeffs is NULL");
     if (grid->prec != KZK_FP64 && grid->prec != KZK_FP32) return fail(KZK_ERR_ARG, "bad precision %d", grid->prec);
-    if (!is_pow2(grid->nx) || !is_pow2(grid->ny) || grid->nx < 8 || grid->nx > 8192 || grid->ny < 2 ||
-        grid->ny > 4096)
+    // powers of two: the radix-8/16 kernels; other even sizes with no prime
+    // factor above 7 (the paper's 7 * 2^k x 1250 * 2^k grids): the mixed-radix
+    // kernels (KZK_MIXED=1 in the environment selects them for every grid)
+    const char* menv = getenv("KZK_MIXED");
+    const bool mixed = !(is_pow2(grid->nx) && is_pow2(grid->ny)) || (menv && menv[0] == '1');
+    if (!mixed && (grid->nx < 8 || grid->nx > 8192 || grid->ny < 2 || grid->ny > 4096))
         return fail(KZK_ERR_SIZE, "nx = %d, ny = %d: powers of two in [8, 8192] x [2, 4096] required",
+                    grid->nx, grid->ny);
+    if (mixed && (grid->nx < 8 || grid->nx > 16384 || (grid->nx & 1) || grid->ny < 2 || grid->ny > 32768 ||
+                  (grid->ny & 1)))
+        return fail(KZK_ERR_SIZE, "nx = %d, ny = %d: even sizes in [8, 16384] x [2, 32768] required",
                     grid->nx, grid->ny);
     if (!(grid->tau_max > grid->tau_min) || !(grid->y_max > grid->y_min))
         return fail(KZK_ERR_ARG, "empty domain");
@@ -1454,6 +1565,7 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     p->log2ny = ilog2(grid->ny);
     p->csz = p->prec == KZK_FP64 ? sizeof(double2) : sizeof(float2);
     p->inst_stride = (long long)p->ny * p->n;
+    p->mixed = mixed ? 1 : 0;
 
     kzk_status s = p->prec == KZK_FP64 ? configure<double>(p) : configure<float>(p);
     if (s != KZK_OK) { plan_free(p); return s; }
@@ -1477,6 +1589,12 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     if (e == cudaSuccess) e = cudaMalloc(&p->diag_final, (size_t)batch * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->colp_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->colp_flag, 0, sizeof(int));
+    if (p->mixed) {
+        if (e == cudaSuccess) e = cudaMalloc(&p->mpos_row, (size_t)p->n * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&p->mpos_col, (size_t)p->ny * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&p->mipos_col, (size_t)p->ny * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&p->wsc, arr);
+    }
     if (e != cudaSuccess) {
         plan_free(p);
         return fail(e == cudaErrorMemoryAllocation ? KZK_ERR_OOM : KZK_ERR_CUDA, "plan allocation: %s",
@@ -1589,6 +1707,7 @@ kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coef
         if (s != KZK_OK) { plan_free(p); return s; }
         p->subs->push_back(q);
         if (q->nx > 8192) { plan_free(p); return fail(KZK_ERR_SIZE, "instance %d too large", i); }
+        if (q->mixed) { plan_free(p); return fail(KZK_ERR_SIZE, "instance %d: batched plans need power-of-two grids", i); }
     }
     cudaError_t e = cudaMalloc(&p->binst, (size_t)n * std::max(sizeof(BatchInst<float>), sizeof(BatchInst<double>)));
     if (e == cudaSuccess) e = cudaMalloc(&p->row_prefix, (n + 1) * sizeof(int));
@@ -1761,6 +1880,7 @@ kzk_status kzk_advance_checkpointed(kzk_plan* p, void* u, int64_t n_steps, doubl
     if (!p || !u) return fail(KZK_ERR_ARG, "plan or u is NULL");
     if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
     if (n_steps < 1 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
+    if (p->mixed) return fail(KZK_ERR_SIZE, "the adjoint kernels need a power-of-two grid");
     cudaStream_t st = (cudaStream_t)stream;
     p->ck_steps = 0;
     if (p->prec == KZK_FP64) {
@@ -1785,6 +1905,7 @@ kzk_status kzk_adjoint(kzk_plan* p, const void* u0, const void* g_end, void* g0,
 {
     if (!p || !u0 || !g_end || !g0) return fail(KZK_ERR_ARG, "NULL argument");
     if (n_steps < 0 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 0 and ckpt_every >= 1");
+    if (p->mixed) return fail(KZK_ERR_SIZE, "the adjoint kernels need a power-of-two grid");
     cudaStream_t st = (cudaStream_t)stream;
     if (n_steps == 0) {
         if (g0 != g_end)

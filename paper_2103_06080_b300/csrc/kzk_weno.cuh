@@ -105,12 +105,14 @@ __device__ __forceinline__ T flux6(const T* fp, const T* fm, T tLp, T tCp, T tRp
 
 // b over the points [k0, k0 + Q) of one periodic row u[0..nx) (shared
 // memory, PAD layout), written to out at the same points.  ADV: the flux of
-// the random medium, f(u) = -c u - B u^2 / 2 (Eq. 7).
-template <typename T, bool PAD, bool ADV = false>
+// the random medium, f(u) = -c u - B u^2 / 2 (Eq. 7).  POW2: nx is a power of
+// two (the periodic wrap is a mask); otherwise any nx >= 8.
+template <typename T, bool PAD, bool ADV = false, bool POW2 = true>
 __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int nx, int k0, int Q,
                                                const WenoCoef<T>& c)
 {
     const int msk = nx - 1;
+    auto wrap = [&](int kk) { return POW2 ? (kk & msk) : (kk < 0 ? kk + nx : (kk >= nx ? kk - nx : kk)); };
     // the split fluxes are carried as 4 f+- (no halves):
     //   4 f+ = v (2 (alpha - c) - B v),   4 f- = -v (2 (alpha + c) + B v)
     // so the reconstruction is 4 F, the indicators take 64 eps, and the 1/4
@@ -121,7 +123,7 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
     const T am = T(2) * (ADV ? c.alpha + c.c : c.alpha);
     T fp[6], fm[6];
     auto load = [&](int kk, T& p, T& m) {
-        const T v = ld_real<T, PAD>(u, kk & msk);
+        const T v = ld_real<T, PAD>(u, wrap(kk));
         p = v * fma(-c.B, v, ap);
         m = -v * fma(c.B, v, am);
     };

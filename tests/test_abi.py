@@ -47,8 +47,10 @@ def _create(nx=64, ny=32, prec=0, dt=0.01, B=0.05, A=7e-6, M=1.0, batch=1, relax
 
 
 @pytest.mark.parametrize("kw,code", [
-    (dict(nx=48), L.KZK_ERR_SIZE), (dict(nx=4), L.KZK_ERR_SIZE), (dict(nx=16384), L.KZK_ERR_SIZE),
-    (dict(ny=1), L.KZK_ERR_SIZE), (dict(ny=3000), L.KZK_ERR_SIZE), (dict(ny=8192), L.KZK_ERR_SIZE),
+    (dict(nx=44), L.KZK_ERR_SIZE), (dict(nx=4), L.KZK_ERR_SIZE), (dict(nx=16384), L.KZK_ERR_SIZE),
+    (dict(ny=1), L.KZK_ERR_SIZE), (dict(ny=3002), L.KZK_ERR_SIZE), (dict(ny=8192), L.KZK_ERR_SIZE),
+    (dict(nx=45), L.KZK_ERR_SIZE), (dict(ny=25), L.KZK_ERR_SIZE), (dict(nx=7 * 2 ** 12), L.KZK_ERR_SIZE),
+    (dict(nx=2 * 13, ny=50), L.KZK_ERR_SIZE), (dict(nx=56, ny=2 * 11), L.KZK_ERR_SIZE),
     (dict(prec=7), L.KZK_ERR_ARG), (dict(dt=0.0), L.KZK_ERR_ARG), (dict(dt=float("nan")), L.KZK_ERR_ARG),
     (dict(B=0.0), L.KZK_ERR_ARG), (dict(A=-1.0), L.KZK_ERR_ARG), (dict(M=0.0), L.KZK_ERR_ARG),
     (dict(batch=0), L.KZK_ERR_ARG),

@@ -1,0 +1,190 @@
+"""Parity of the mixed-radix path (grids whose sizes are not powers of two,
+such as the 7 * 2^k x 1250 * 2^k grids of Table 1) with the FP64 oracle,
+through the C ABI.
+
+The same bars as the power-of-two path: FP64 relative L-infinity within 1e-11
+after whole runs (tighter for single operations), FP32 relative l2 within
+1e-5.  Sizes include single and several column tiles, odd half lengths
+(nx / 2 odd), every radix (2, 3, 4, 5, 7, 8), the random medium, exponential
+Euler and batches; the paper's largest grid (3584 x 10000) is checked against
+the closed form of a propagating Fourier mode, which holds at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_06080_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _api():
+    from paper_2103_06080_b300 import api
+    return api
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("nx,ny", [(14, 6), (56, 50), (448, 10), (30, 18), (3584, 4), (210, 42)])
+def test_tau_fft_matches_dft(nx, ny):
+    api = _api()
+    rng = np.random.default_rng(nx + ny)
+    u = rng.standard_normal((ny, nx))
+    plan = api.Plan(nx=nx, ny=ny, dt=0.01)
+    V = plan.tau_fft(_dev(u), -1).cpu().numpy()
+    ref = np.stack([oracle.fft1d(u[j]) for j in range(ny)]) / nx
+    got = V[..., 0] + 1j * V[..., 1]
+    assert np.max(np.abs(got[:, 1:] - ref[:, 1:nx // 2])) < 1e-14 * np.max(np.abs(ref)) + 1e-15
+    assert np.max(np.abs(got[:, 0].real - ref[:, 0].real)) < 1e-14
+    assert np.max(np.abs(got[:, 0].imag - ref[:, nx // 2].real)) < 1e-14
+    back = plan.tau_fft(torch.tensor(V, device="cuda"), +1).cpu().numpy()
+    assert np.max(np.abs(back - u)) < 1e-13 * np.max(np.abs(u))
+
+
+@pytest.mark.parametrize("nx,ny", [(56, 50), (448, 250), (30, 42)])
+def test_rhs_matches_oracle(nx, ny):
+    api = _api()
+    w = inputs.config(2, nx=nx, ny=ny, n_steps=10)
+    plan = api.Plan.from_workload(w)
+    b = plan.rhs(_dev(w.u0), sigma=0.7).cpu().numpy()
+    ref = oracle.rhs(oracle.Params(**inputs.oracle_params(w)), w.u0, sigma=0.7)
+    assert rel_linf(b, ref) < 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(56, 50, 40), (448, 250, 30), (210, 1250, 6), (14, 6, 20)])
+def test_run_fp64_parity(nx, ny, steps):
+    api = _api()
+    w = inputs.config(2, nx=nx, ny=ny, n_steps=steps)
+    plan = api.Plan.from_workload(w)
+    u = _dev(w.u0)
+    st, d = plan.advance(u, w.n_steps, diag=True)
+    assert st == 0
+    p = oracle.Params(**inputs.oracle_params(w))
+    ref, hist = oracle.run(p, w.u0, w.n_steps, threads=True, want_hist=True)
+    assert rel_linf(u.cpu().numpy(), ref) < 1e-11
+    gh = plan.diag_history(w.n_steps)[:, 0, :]
+    assert np.allclose(gh[1:, 1], hist[:-1, 1], rtol=1e-11)
+    assert abs(d[0]["energy"] - hist[-1, 1]) < 1e-11 * hist[-1, 1]
+    assert np.max(np.abs(gh[:, 0] - gh[0, 0])) < 1e-14
+
+
+def test_one_step_stages_match_oracle():
+    api = _api()
+    w = inputs.config(2, nx=448, ny=50, n_steps=5)
+    plan = api.Plan.from_workload(w)
+    s0 = 2 * w.dt
+    us, un = plan.step_stages(_dev(w.u0), sigma0=s0)
+    ref_un, ref_us = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, 1, sigma0=s0, want_ustar=True)
+    assert rel_linf(us.cpu().numpy(), ref_us) < 1e-13
+    assert rel_linf(un.cpu().numpy(), ref_un) < 1e-13
+
+
+def test_fp32_error_against_fp64_oracle():
+    api = _api()
+    w = inputs.config(3, nx=448, ny=250, n_steps=100)
+    plan = api.Plan.from_workload(w, precision="fp32")
+    u = _dev(w.u0, torch.float32)
+    plan.advance(u, w.n_steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    got = u.double().cpu().numpy()
+    assert rel_l2(got, ref) < 1e-5
+    assert rel_linf(got, ref) < 1e-4
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_random_medium_run(prec, tol):
+    api = _api()
+    w = inputs.medium_config(448, 250, 12)
+    plan = api.Plan.from_workload(w, precision=prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    u = _dev(w.u0, dt)
+    plan.advance(u, w.n_steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    got = u.double().cpu().numpy()
+    assert (rel_linf if prec == "fp64" else rel_l2)(got, ref) < tol
+
+
+def test_expeuler_and_relaxation_run():
+    api = _api()
+    w = inputs.config(2, nx=56, ny=50, n_steps=15)
+    kw = dict(relax_C=(1e-3,), relax_theta=(0.05,))
+    plan = api.Plan.from_workload(w, method="expeuler", **kw)
+    u = _dev(w.u0)
+    plan.advance(u, w.n_steps)
+    p = oracle.Params(**inputs.oracle_params(w, method=1, relax_C=(1e-3,), relax_theta=(0.05,)))
+    assert rel_linf(u.cpu().numpy(), oracle.run(p, w.u0, w.n_steps)) < 1e-11
+
+
+def test_batch_instances_are_independent():
+    api = _api()
+    w = inputs.config(2, nx=112, ny=250, n_steps=8)
+    u0 = np.stack([w.u0, -0.5 * w.u0[::-1]])
+    plan = api.Plan.from_workload(w, batch=2)
+    u = _dev(u0)
+    plan.advance(u, w.n_steps)
+    p = oracle.Params(**inputs.oracle_params(w))
+    for i in range(2):
+        assert rel_linf(u[i].cpu().numpy(), oracle.run(p, np.ascontiguousarray(u0[i]), w.n_steps)) < 1e-11
+
+
+def test_mixed_kernels_on_a_power_of_two_grid(monkeypatch):
+    """KZK_MIXED=1 runs the mixed-radix kernels on a power-of-two grid: the
+    result agrees with the radix-8/16 kernels and with the oracle."""
+    api = _api()
+    w = inputs.config(2, nx=512, ny=128, n_steps=30)
+    a = _dev(w.u0)
+    api.Plan.from_workload(w).advance(a, w.n_steps)
+    monkeypatch.setenv("KZK_MIXED", "1")
+    b = _dev(w.u0)
+    api.Plan.from_workload(w).advance(b, w.n_steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    assert rel_linf(b.cpu().numpy(), ref) < 1e-11
+    assert rel_linf(b.cpu().numpy(), a.cpu().numpy()) < 1e-11
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_paper_grid_single_mode_closed_form(prec, tol):
+    """Set 4 of Table 1 (N_theta = 7 * 512 = 3584, N_rho = 10000), B = 0: a
+    Fourier mode follows exp(lambda sigma) exactly (Eq. 2a), so every point of
+    the full grid is checked against the closed form."""
+    api = _api()
+    nx, ny, dt, n = 3584, 10000, 0.05, 6
+    A = 7e-4
+    mt, my = 5, 3
+    kt, ky = 2 * np.pi * mt / 8.0, 2 * np.pi * my / 16.0
+    plan = api.Plan(nx=nx, ny=ny, dt=dt, precision=prec, B=1e-300, A=A, lf_umax=1.0)
+    tau = torch.arange(nx, dtype=torch.float64, device="cuda") * (8.0 / nx) - 4.0
+    y = torch.arange(ny, dtype=torch.float64, device="cuda") * (16.0 / ny) - 8.0
+    phase = kt * tau[None, :] + ky * y[:, None]
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    u = torch.cos(phase).to(dtype).contiguous()
+    plan.advance(u, n)
+    lam = (1 / (4 * np.pi)) * (-ky ** 2) / (1j * kt) - A * kt ** 2
+    z = np.exp(lam * n * dt)
+    exact = z.real * torch.cos(phase) - z.imag * torch.sin(phase)
+    err = float((u.double() - exact).abs().max())
+    assert err < tol
+
+
+def test_unsupported_sizes_and_features_are_refused():
+    api = _api()
+    for nx, ny in ((22, 16), (15, 10), (64, 26), (56, 13)):   # prime factor 11 or 13, odd sizes
+        with pytest.raises(Exception):
+            api.Plan(nx=nx, ny=ny, dt=0.01)
+    w = inputs.config(2, nx=56, ny=50, n_steps=4)
+    plan = api.Plan.from_workload(w)
+    with pytest.raises(Exception):
+        plan.adjoint(_dev(w.u0), _dev(w.u0), 4, ckpt_every=2)
+    with pytest.raises(Exception):
+        api.BatchedPlan([w], precision="fp64")
