@@ -388,6 +388,44 @@ def cufft_transforms_ms(torch, dev, nx, ny, dtype, reps=20):
     return e0.elapsed_time(e1) / reps
 
 
+# The paper's four grids (Table 1: N_theta = 7 * 2^(5+s) tau points, N_rho =
+# 1250 * 2^(s-1) transverse points, N_sigma = 300 * 2^(s-1) steps) and its
+# measured totals on a Titan V (Table 3), as pt-steps/s = N_sigma N_rho
+# N_theta / time: context for the same method family on other hardware.
+PAPER_SETS = {1: (448, 1250, 300), 2: (896, 2500, 600), 3: (1792, 5000, 1200), 4: (3584, 10000, 2400)}
+PAPER_TITANV_S = {"fp64": {1: 1.165, 2: 8.343, 3: 65.13, 4: 851.7}, "fp32": {1: 0.5564, 2: 3.788, 3: 28.31, 4: 392.7}}
+
+
+def paper_grid_reports(api, torch, dev):
+    """The random-medium step on the paper's mixed-radix grids, FP64 and FP32."""
+    rep = {"workload": "N-wave through the random medium of Algorithm 1 on the grids of Table 1 "
+                       "(tau x y = 7*2^(5+s) x 1250*2^(s-1)); timed steps per set below, pt-steps/s",
+           "paper_titan_v": "pt-steps/s from the paper's total times (Table 3; Titan V, its own timing scope)"}
+    for s, (nx, ny, nsig) in PAPER_SETS.items():
+        w = inputs.medium_config(nx, ny, 50)
+        row = {"grid": f"{nx}x{ny}", "paper_steps": nsig}
+        for name, dtype in (("fp64", torch.float64), ("fp32", torch.float32)):
+            pm = api.Plan.from_workload(w, precision=name)
+            u = torch.tensor(w.u0, dtype=dtype, device=dev)
+            pm.advance(u, 3)
+            k = max(10, min(200, int(2e9 / (nx * ny * (8 if name == "fp64" else 1)))))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pm.advance(u, k)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            ref = nsig * nx * ny / PAPER_TITANV_S[name][s]
+            row[name] = {"value": nx * ny / (ms * 1e-3), "ms_per_step": ms, "steps": k,
+                         "stage_ms": pm.kernel_times(u, 3), "paper_titan_v": ref,
+                         "ratio_to_paper": nx * ny / (ms * 1e-3) / ref}
+            pm.close()
+            del u
+        rep[f"set{s}"] = row
+    return rep
+
+
 def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
     """FP32 throughput + error, the adjoint/forward cost ratio, the batched
     launch and the cuFFT comparison."""
@@ -515,6 +553,7 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
         pm.close()
         del um
     out["random_medium"] = med
+    out["paper_grids"] = paper_grid_reports(api, torch, dev)
     # cuFFT comparison on the 4096 x 2048 grid
     cmp = {}
     for name, dtype, ms_ours in (("fp64", torch.float64, ms_fp64), ("fp32", torch.float32, out["fp32"]["ms_per_step"])):
