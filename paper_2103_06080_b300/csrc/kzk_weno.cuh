@@ -22,8 +22,9 @@
 //    and denominator by prod (eps + beta_r)^2, so a_r -> d_r prod_{s != r} t_s;
 //  * the 1/6 of the candidate values q_r is folded into 1/dtau, and common
 //    factors of the weights (16 in (eps + beta)^2, 10 in d_r) are dropped;
-//  * FP64: both halves F+ and F- share one division; FP32: two hardware
-//    reciprocals (the product of the two denominators could underflow).
+//  * FP64: both halves F+ and F- and two neighbouring interfaces share one
+//    division; FP32: two hardware reciprocals per interface (the product of
+//    the denominators could underflow).
 #pragma once
 #include "kzk_common.cuh"
 #include "kzk_fft.cuh"
@@ -89,7 +90,7 @@ __device__ __forceinline__ void rec_parts(T vm2, T vm1, T v0, T v1, T v2, T t0, 
     num6 = fma(a0, q0, fma(a1, q1, a2 * q2));
 }
 
-// 6 * F_{k+1/2} (both halves) from the window state.
+// 6 * F_{k+1/2} (both halves) from the window state (one interface).
 template <typename T>
 __device__ __forceinline__ T flux6(const T* fp, const T* fm, T tLp, T tCp, T tRp, T tLm, T tCm, T tRm)
 {
@@ -148,29 +149,59 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
     // centre k0 (slots 3, 4, 5)
     indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tRp1);
     indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tCm1, tx);
-    // loop invariant at the top of iteration k: tX1 = centre k+1, tX2 = centre
-    // k, tLp3 = centre k-1; the body adds centre k+2
-    T Fprev = 0;
-#pragma unroll 2
-    for (; k < k0 + Q; k++) {
+    // invariant at the top of interface k: tX1 = centre k+1, tX2 = centre k,
+    // tLp3 = centre k-1; each interface adds centre k+2.  parts(): slide the
+    // window by one point and return 6 x the numerator and the denominator of
+    // both halves of F_{k+1/2}.
+    auto parts = [&](int kk, T& np, T& dp, T& nm, T& dm) {
 #pragma unroll
         for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
-        load(k + 3, fp[5], fm[5]);
+        load(kk + 3, fp[5], fm[5]);
         T tLpN, tCpN, tRpN, tLmN, tCmN, tRmN;
         indicators<T>(fp[3], fp[4], fp[5], eps4, tLpN, tCpN, tRpN);
         indicators<T>(fm[3], fm[4], fm[5], eps4, tLmN, tCmN, tRmN);
-        // at this point tX1 refer to centre k+1, tX2 to centre k, tLp3 to k-1.
-        // interface k+1/2: + side left(k-1), centre(k), right(k+1);
-        //                  - side right(k+2), centre(k+1), left(k)
-        const T F = flux6<T>(fp, fm, tLp3, tCp2, tRp1, tLm2, tCm1, tRmN);
-        if (k >= k0) st_real<T, PAD>(out, k, (F - Fprev) * scale);
-        Fprev = F;
-        // ages for interface k+3/2
+        // + side: left(k-1), centre(k), right(k+1); - side: right(k+2), centre(k+1), left(k)
+        rec_parts<T>(fp[0], fp[1], fp[2], fp[3], fp[4], tLp3, tCp2, tRp1, np, dp);
+        rec_parts<T>(fm[5], fm[4], fm[3], fm[2], fm[1], tRmN, tCm1, tLm2, nm, dm);
         tLp3 = tLp2; tLp2 = tLp1; tLp1 = tLpN;
         tCp2 = tCp1; tCp1 = tCpN;
         tRp1 = tRpN;
         tLm2 = tLm1; tLm1 = tLmN;
         tCm1 = tCmN;
+    };
+    T np, dp, nm, dm;
+    parts(k, np, dp, nm, dm);
+    if constexpr (sizeof(T) == 8) {
+        // F = N / D with N = np dm + nm dp, D = dp dm; two interfaces share one
+        // division: 1 / (D1 D2) gives both quotients
+        T Fprev = fma(np, dm, nm * dp) / (dp * dm);
+#pragma unroll 1
+        for (k = k0; k + 1 < k0 + Q; k += 2) {
+            parts(k, np, dp, nm, dm);
+            const T N1 = fma(np, dm, nm * dp), D1 = dp * dm;
+            parts(k + 1, np, dp, nm, dm);
+            const T N2 = fma(np, dm, nm * dp), D2 = dp * dm;
+            const T inv = T(1) / (D1 * D2);
+            const T F1 = N1 * D2 * inv, F2 = N2 * D1 * inv;
+            st_real<T, PAD>(out, k, (F1 - Fprev) * scale);
+            st_real<T, PAD>(out, k + 1, (F2 - F1) * scale);
+            Fprev = F2;
+        }
+        if (k < k0 + Q) {
+            parts(k, np, dp, nm, dm);
+            st_real<T, PAD>(out, k, (fma(np, dm, nm * dp) / (dp * dm) - Fprev) * scale);
+        }
+    } else {
+        // FP32: two hardware reciprocals (the product of the two denominators
+        // could underflow)
+        T Fprev = __fdividef(np, dp) + __fdividef(nm, dm);
+#pragma unroll 2
+        for (k = k0; k < k0 + Q; k++) {
+            parts(k, np, dp, nm, dm);
+            const T F = __fdividef(np, dp) + __fdividef(nm, dm);
+            st_real<T, PAD>(out, k, (F - Fprev) * scale);
+            Fprev = F;
+        }
     }
 }
 
