@@ -396,19 +396,41 @@ PAPER_SETS = {1: (448, 1250, 300), 2: (896, 2500, 600), 3: (1792, 5000, 1200), 4
 PAPER_TITANV_S = {"fp64": {1: 1.165, 2: 8.343, 3: 65.13, 4: 851.7}, "fp32": {1: 0.5564, 2: 3.788, 3: 28.31, 4: 392.7}}
 
 
-def paper_grid_reports(api, torch, dev):
-    """The random-medium step on the paper's mixed-radix grids, FP64 and FP32."""
+def medium_step_work(nx, ny, w):
+    """Algorithmic FLOPs and bytes of one random-medium step on the mixed-radix
+    path: per stage the coefficient kernel (negligible), the C2R row pass
+    (FFT; V in, u out), the y-sweep (y-WENO5 + source; u in, b_y out) and the
+    b row pass (tau-WENO5 + FFT; u, b_y in, b out); then the three column
+    launches (C1 split in two through the scratch W, C2).  Bytes in units of
+    N w (N = nx ny); FP32 adds the lo part of E' (half a unit)."""
+    lg = np.log2(nx // 2)
+    fft_pt = 2.5 * lg + 4
+    stage_flops = nx * ny * (fft_pt + (166 + 3) + (2 * fft_pt + 166 + 3 + 3))
+    flops = 2 * stage_flops + col_flops(nx, ny, 1) + col_flops(nx, ny, 2)
+    units = 2 * (2 + 2 + 3) + 2.5 + (4.0 if w == 4 else 3.5) + 4.5
+    return flops, units * nx * ny * w
+
+
+def paper_grid_reports(api, torch, dev, sets=None, precisions=("fp64", "fp32"), steps=None, warmup=3):
+    """The random-medium step on the paper's mixed-radix grids."""
+    peaks, peak_src = _peaks()
+    fp64_peak = api.alu_peak("fp64")
     rep = {"workload": "N-wave through the random medium of Algorithm 1 on the grids of Table 1 "
                        "(tau x y = 7*2^(5+s) x 1250*2^(s-1)); timed steps per set below, pt-steps/s",
-           "paper_titan_v": "pt-steps/s from the paper's total times (Table 3; Titan V, its own timing scope)"}
+           "paper_titan_v": "pt-steps/s from the paper's total times (Table 3; Titan V, its own timing scope)",
+           "step_roofline": "whole step: algorithmic FLOPs / time against the measured FP64 FMA peak (fp64), "
+                            "algorithmic bytes / time against the measured HBM copy bandwidth (fp32)"}
     for s, (nx, ny, nsig) in PAPER_SETS.items():
+        if sets and s not in sets:
+            continue
         w = inputs.medium_config(nx, ny, 50)
         row = {"grid": f"{nx}x{ny}", "paper_steps": nsig}
-        for name, dtype in (("fp64", torch.float64), ("fp32", torch.float32)):
+        for name in precisions:
+            dtype = torch.float64 if name == "fp64" else torch.float32
             pm = api.Plan.from_workload(w, precision=name)
             u = torch.tensor(w.u0, dtype=dtype, device=dev)
-            pm.advance(u, 3)
-            k = max(10, min(200, int(2e9 / (nx * ny * (8 if name == "fp64" else 1)))))
+            pm.advance(u, warmup)
+            k = steps or max(10, min(200, int(2e9 / (nx * ny * (8 if name == "fp64" else 1)))))
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -417,8 +439,13 @@ def paper_grid_reports(api, torch, dev):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / k
             ref = nsig * nx * ny / PAPER_TITANV_S[name][s]
+            fl, by = medium_step_work(nx, ny, 8 if name == "fp64" else 4)
+            roof = ({"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": fp64_peak / 1e12,
+                     "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / fp64_peak} if name == "fp64" else
+                    {"bound": "hbm", "achieved": by / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": by / (ms * 1e-3) / (peaks["hbm_gbs"] * 1e9)})
             row[name] = {"value": nx * ny / (ms * 1e-3), "ms_per_step": ms, "steps": k,
-                         "stage_ms": pm.kernel_times(u, 3), "paper_titan_v": ref,
+                         "stage_ms": pm.kernel_times(u, 3), "step_roofline": roof, "paper_titan_v": ref,
                          "ratio_to_paper": nx * ny / (ms * 1e-3) / ref}
             pm.close()
             del u
@@ -586,9 +613,19 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--paper-set", type=int, choices=[1, 2, 3, 4], default=None,
+                    help="instead of the headline: the random-medium step on Set S of the paper's Table 1 "
+                         "(mixed-radix grid), --steps timed steps at --precision; prints that report")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.paper_set and args.impl == "ours":
+        import torch
+        from paper_2103_06080_b300 import api
+        rep = paper_grid_reports(api, torch, torch.device("cuda", 0), sets=[args.paper_set],
+                                 precisions=(args.precision,), steps=args.steps, warmup=args.warmup)
+        print(json.dumps(rep), flush=True)
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -155,45 +155,13 @@ __global__ void __launch_bounds__(YSWEEP_THREADS) ysweep_kernel(YSweepArgs<T> a)
         p = v * cp[r];
         m = v * cm[r];
     };
-    T fp[6], fm[6];
-    // window slot s <-> row j - 2 + s for interface j + 1/2; pre-roll as in
-    // weno_row_chunk (interfaces j0 - 1/2 and on)
-    int j = j0 - 1;
-#pragma unroll
-    for (int s = 0; s < 5; s++) load(j - 3 + s, fp[s + 1], fm[s + 1]);
-    T tLp3, tLp2, tLp1, tCp2, tCp1, tRp1, tLm2, tLm1, tCm1, tx;
-    indicators<T>(fp[2], fp[3], fp[4], eps4, tLp2, tx, tx);
-    indicators<T>(fm[2], fm[3], fm[4], eps4, tx, tx, tx);
-    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tx);
-    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tx, tx);
-    tLp3 = tLp2; tLp2 = tLp1; tCp2 = tCp1;
-    tLm2 = tLm1;
-#pragma unroll
-    for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
-    load(j0 + 1, fp[5], fm[5]);
-    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tRp1);
-    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tCm1, tx);
-    T Fprev = 0;
-    for (; j < j0 + Q; j++) {
-#pragma unroll
-        for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
-        load(j + 3, fp[5], fm[5]);
-        T tLpN, tCpN, tRpN, tLmN, tCmN, tRmN;
-        indicators<T>(fp[3], fp[4], fp[5], eps4, tLpN, tCpN, tRpN);
-        indicators<T>(fm[3], fm[4], fm[5], eps4, tLmN, tCmN, tRmN);
-        const T F = flux6<T>(fp, fm, tLp3, tCp2, tRp1, tLm2, tCm1, tRmN);
-        if (j >= j0) {
-            // row j: the flux difference plus the source (d_y U_perp) u
-            const int r = j - (j0 - 4);
-            by[(long long)j * nx] = fma(F - Fprev, scale, dp[r] * tile[r * YSWEEP_THREADS + tid]);
-        }
-        Fprev = F;
-        tLp3 = tLp2; tLp2 = tLp1; tLp1 = tLpN;
-        tCp2 = tCp1; tCp1 = tCpN;
-        tRp1 = tRpN;
-        tLm2 = tLm1; tLm1 = tLmN;
-        tCm1 = tCmN;
-    }
+    // interfaces j0 - 1/2 .. j0 + Q - 1/2; row j gets the flux difference
+    // plus the source (d_y U_perp) u
+    auto store = [&](int jj, T d) {
+        const int r = jj - (j0 - 4);
+        by[(long long)jj * nx] = fma(d, scale, dp[r] * tile[r * YSWEEP_THREADS + tid]);
+    };
+    weno_sweep<T>(j0, Q, eps4, load, store);
 }
 
 // ---------------------------------------------------------------------------

@@ -90,44 +90,16 @@ __device__ __forceinline__ void rec_parts(T vm2, T vm1, T v0, T v1, T v2, T t0, 
     num6 = fma(a0, q0, fma(a1, q1, a2 * q2));
 }
 
-// 6 * F_{k+1/2} (both halves) from the window state (one interface).
-template <typename T>
-__device__ __forceinline__ T flux6(const T* fp, const T* fm, T tLp, T tCp, T tRp, T tLm, T tCm, T tRm)
+// Sliding WENO5 sweep over the interfaces k0 - 1/2 .. k0 + Q - 1/2 of a
+// periodic line.  load(kk, p, m) gives the split fluxes (scaled: 4 f+ and
+// 4 f-) at point kk; store(k, d) receives d = 24 (F_{k+1/2} - F_{k-1/2}) for
+// k in [k0, k0 + Q) in order.  eps4: the Jiang-Shu epsilon for that scaling
+// (64 eps).  Every smoothness indicator is computed once per stencil centre
+// and every interface once.
+template <typename T, typename Load, typename Store>
+__device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Store store)
 {
-    T np, dp, nm, dm;
-    rec_parts<T>(fp[0], fp[1], fp[2], fp[3], fp[4], tLp, tCp, tRp, np, dp);
-    rec_parts<T>(fm[5], fm[4], fm[3], fm[2], fm[1], tRm, tCm, tLm, nm, dm);
-    if constexpr (sizeof(T) == 8) {
-        return fma(np, dm, nm * dp) / (dp * dm);
-    } else {
-        return __fdividef(np, dp) + __fdividef(nm, dm);
-    }
-}
-
-// b over the points [k0, k0 + Q) of one periodic row u[0..nx) (shared
-// memory, PAD layout), written to out at the same points.  ADV: the flux of
-// the random medium, f(u) = -c u - B u^2 / 2 (Eq. 7).  POW2: nx is a power of
-// two (the periodic wrap is a mask); otherwise any nx >= 8.
-template <typename T, bool PAD, bool ADV = false, bool POW2 = true>
-__device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int nx, int k0, int Q,
-                                               const WenoCoef<T>& c)
-{
-    const int msk = nx - 1;
-    auto wrap = [&](int kk) { return POW2 ? (kk & msk) : (kk < 0 ? kk + nx : (kk >= nx ? kk - nx : kk)); };
-    // the split fluxes are carried as 4 f+- (no halves):
-    //   4 f+ = v (2 (alpha - c) - B v),   4 f- = -v (2 (alpha + c) + B v)
-    // so the reconstruction is 4 F, the indicators take 64 eps, and the 1/4
-    // joins the 1/6 of the candidate values in the final scale
-    const T scale = -c.inv_dtau * (T(1) / T(24));
-    const T eps4 = T(64) * c.eps;
-    const T ap = T(2) * (ADV ? c.alpha - c.c : c.alpha);
-    const T am = T(2) * (ADV ? c.alpha + c.c : c.alpha);
     T fp[6], fm[6];
-    auto load = [&](int kk, T& p, T& m) {
-        const T v = ld_real<T, PAD>(u, wrap(kk));
-        p = v * fma(-c.B, v, ap);
-        m = -v * fma(c.B, v, am);
-    };
     // window slot s <-> point k - 2 + s for interface k + 1/2; start at
     // k = k0 - 1 with the indicators of centres k0 - 2 .. k0 + 0 (pre-roll)
     int k = k0 - 1;
@@ -183,13 +155,13 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
             const T N2 = fma(np, dm, nm * dp), D2 = dp * dm;
             const T inv = T(1) / (D1 * D2);
             const T F1 = N1 * D2 * inv, F2 = N2 * D1 * inv;
-            st_real<T, PAD>(out, k, (F1 - Fprev) * scale);
-            st_real<T, PAD>(out, k + 1, (F2 - F1) * scale);
+            store(k, F1 - Fprev);
+            store(k + 1, F2 - F1);
             Fprev = F2;
         }
         if (k < k0 + Q) {
             parts(k, np, dp, nm, dm);
-            st_real<T, PAD>(out, k, (fma(np, dm, nm * dp) / (dp * dm) - Fprev) * scale);
+            store(k, fma(np, dm, nm * dp) / (dp * dm) - Fprev);
         }
     } else {
         // FP32: two hardware reciprocals (the product of the two denominators
@@ -199,10 +171,36 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
         for (k = k0; k < k0 + Q; k++) {
             parts(k, np, dp, nm, dm);
             const T F = __fdividef(np, dp) + __fdividef(nm, dm);
-            st_real<T, PAD>(out, k, (F - Fprev) * scale);
+            store(k, F - Fprev);
             Fprev = F;
         }
     }
+}
+
+// b over the points [k0, k0 + Q) of one periodic row u[0..nx) (shared
+// memory, PAD layout), written to out at the same points.  ADV: the flux of
+// the random medium, f(u) = -c u - B u^2 / 2 (Eq. 7).  POW2: nx is a power of
+// two (the periodic wrap is a mask); otherwise any nx >= 8.
+template <typename T, bool PAD, bool ADV = false, bool POW2 = true>
+__device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int nx, int k0, int Q,
+                                               const WenoCoef<T>& c)
+{
+    const int msk = nx - 1;
+    auto wrap = [&](int kk) { return POW2 ? (kk & msk) : (kk < 0 ? kk + nx : (kk >= nx ? kk - nx : kk)); };
+    // the split fluxes are carried as 4 f+- (no halves):
+    //   4 f+ = v (2 (alpha - c) - B v),   4 f- = -v (2 (alpha + c) + B v)
+    // so the reconstruction is 4 F, the indicators take 64 eps, and the 1/4
+    // joins the 1/6 of the candidate values in the final scale
+    const T scale = -c.inv_dtau * (T(1) / T(24));
+    const T ap = T(2) * (ADV ? c.alpha - c.c : c.alpha);
+    const T am = T(2) * (ADV ? c.alpha + c.c : c.alpha);
+    auto load = [&](int kk, T& p, T& m) {
+        const T v = ld_real<T, PAD>(u, wrap(kk));
+        p = v * fma(-c.B, v, ap);
+        m = -v * fma(c.B, v, am);
+    };
+    auto store = [&](int k, T d) { st_real<T, PAD>(out, k, d * scale); };
+    weno_sweep<T>(k0, Q, T(64) * c.eps, load, store);
 }
 
 // sum u, sum u^2, max|u| and non-finite count of the points [k0, k0 + Q).
