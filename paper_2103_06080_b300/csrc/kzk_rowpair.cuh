@@ -1,0 +1,232 @@
+// kzk_rowpair.cuh -- FP32 row passes on two grid rows at once, in the packed
+// FP32 arithmetic of sm_100+ (one FADD2 / FMUL2 / FFMA2 instruction carries
+// one operation for each of two rows).
+//
+// The FP32 row pass is bound by instruction issue, not by memory or by the
+// FMA pipe: about three hundred warp instructions per grid point for the two
+// real FFTs and the WENO5 sweep.  Rows j and j + 1 of one instance follow
+// exactly the same sequence of operations (same sigma, same tables, same
+// stencils), so they are carried as the two lanes of one 64-bit value `f2`,
+// and a complex value of the pair as `c2` = {(re_j, re_j+1), (im_j, im_j+1)}.
+// The generic row code (c2r_pre, fft_batched, weno_row_chunk, r2c_post_pair)
+// is instantiated on f2 unchanged; only the global loads and stores, the row
+// statistics and the per-row random-medium speeds are written for the pair.
+// The arithmetic of every lane is the FP32 arithmetic of the single-row kernel
+// (FMAs may be contracted differently, so the two agree to rounding, not bit
+// for bit); KZK_ROWPAIR=0 in the environment selects the single-row kernel.
+#pragma once
+#include "kzk_kernels.cuh"
+
+namespace kzk {
+
+// Two FP32 values, lane 0 for row j and lane 1 for row j + 1.
+struct f2 {
+    float2 v;
+    f2() = default;
+    __host__ __device__ constexpr f2(float a, float b) : v{a, b} {}
+    __host__ __device__ constexpr f2(float a) : v{a, a} {}
+    __host__ __device__ constexpr f2(double a) : v{(float)a, (float)a} {}
+    __host__ __device__ constexpr f2(int a) : v{(float)a, (float)a} {}
+    __host__ __device__ constexpr explicit f2(float2 a) : v(a) {}
+};
+
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b)
+{
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a.v, 8);
+    memcpy(&rb, &b.v, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return f2(d);
+}
+// compile-time constants only (the generic code divides literals)
+__host__ __device__ constexpr f2 operator/(f2 a, f2 b) { return f2(a.v.x / b.v.x, a.v.y / b.v.y); }
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ f2 fast_div(f2 a, f2 b)
+{
+    return f2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
+}
+
+struct __align__(16) c2 {
+    f2 x, y;
+};
+template <> struct cplx_of<f2> { using type = c2; };
+
+// Twiddle tables of the pair kernels: each FP32 entry (wr, wi) stored as
+// ((wr, wr), (wi, wi)), so that a twiddle multiplies both rows with no
+// register moves.
+struct RowPairArgs {
+    RowArgs<float> r;       // the single-row arguments (tw / tws unused here)
+    const c2* tw2;          // exp(-2 pi i k / nx), k in [0, nx), as pairs
+    const c2* tws2;         // staged twiddles of the length-nx/2 FFT, as pairs
+};
+
+__device__ __forceinline__ c2 pack2(float2 a, float2 b) { return c2{f2(a.x, b.x), f2(a.y, b.y)}; }
+__device__ __forceinline__ float2 lane0(c2 z) { return make_float2(z.x.v.x, z.y.v.x); }
+__device__ __forceinline__ float2 lane1(c2 z) { return make_float2(z.x.v.y, z.y.v.y); }
+
+// statistics of both rows (FP32, as row_stats): sum, sum of squares, max |u|
+// and non-finite count of the points [k0, k0 + Q)
+__device__ __forceinline__ void pair_stats(const c2* u, int k0, int Q, float& sa1, float& sa2, float& mxa, int& nfa,
+                                           float& sb1, float& sb2, float& mxb, int& nfb)
+{
+    for (int k = k0; k < k0 + Q; k++) {
+        const f2 w = ld_real<f2, true>(u, k);
+        const float v0 = w.v.x, v1 = w.v.y;
+        if (isfinite(v0)) { sa1 += v0; sa2 = fmaf(v0, v0, sa2); mxa = fmaxf(mxa, fabsf(v0)); } else { nfa += 1; }
+        if (isfinite(v1)) { sb1 += v1; sb2 = fmaf(v1, v1, sb2); mxb = fmaxf(mxb, fabsf(v1)); } else { nfb += 1; }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const RowArgs<float>& a = P.r;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int row = 2 * blockIdx.x, inst = blockIdx.y;
+    const int nx = 1 << a.log2nx, n = nx >> 1, log2n = a.log2nx - 1;
+    c2* X = reinterpret_cast<c2*>(smem_raw);
+    c2* Y = X + row_buf_len(n);
+    double* red = reinterpret_cast<double*>(Y + row_buf_len(n));
+    const long long base = (long long)inst * a.inst_stride + (long long)row * n;   // row j; row j + 1 at + n
+    const Tw<f2> tw{P.tws2, nullptr, -1};
+    constexpr int PPT = 8;
+    const float2* in = reinterpret_cast<const float2*>(a.in);
+    float2* out = reinterpret_cast<float2*>(a.out);
+
+    if constexpr (MODE == ROW_FWD) {
+        for (int i = tid; i < n; i += nthr) Y[padx(i)] = pack2(__ldcg(in + base + i), __ldcg(in + base + n + i));
+        __syncthreads();
+        fft_batched<f2, PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
+        const float s = a.out_scale;
+        for (int k = tid; k <= n / 2; k += nthr) {
+            c2 xk, xnk;
+            r2c_post_pair<f2, true>(Y, n, k, P.tw2, xk, xnk);
+            float2 p0 = lane0(xk), p1 = lane1(xk);
+            out[base + k] = make_float2(p0.x * s, p0.y * s);
+            out[base + n + k] = make_float2(p1.x * s, p1.y * s);
+            if (k != 0 && 2 * k != n) {
+                p0 = lane0(xnk);
+                p1 = lane1(xnk);
+                out[base + n - k] = make_float2(p0.x * s, p0.y * s);
+                out[base + 2 * n - k] = make_float2(p1.x * s, p1.y * s);
+            }
+        }
+        return;
+    }
+    if constexpr (MODE == ROW_RHS_MED) {
+        const float* u0 = a.uphys + 2 * base;
+        for (int i = tid; i < nx; i += nthr) st_real<f2, true>(X, i, f2(__ldcg(u0 + i), __ldcg(u0 + nx + i)));
+        __syncthreads();
+    } else {
+        for (int i = tid; i < n; i += nthr) X[padx(i)] = pack2(__ldcg(in + base + i), __ldcg(in + base + n + i));
+        __syncthreads();
+        c2r_pre<f2, true>(X, n, P.tw2, tid, nthr);
+        __syncthreads();
+        fft_batched<f2, PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
+    }
+
+    float sa1 = 0, sa2 = 0, mxa = 0, sb1 = 0, sb2 = 0, mxb = 0;
+    int nfa = 0, nfb = 0;
+    if constexpr (MODE == ROW_INV) {
+        float* d0 = reinterpret_cast<float*>(out + base);
+        for (int i = tid; i < nx; i += nthr) {
+            const f2 w = ld_real<f2, true>(X, i);
+            const float v0 = w.v.x * a.out_scale, v1 = w.v.y * a.out_scale;
+            d0[i] = v0;
+            d0[nx + i] = v1;
+            if (isfinite(v0)) { sa1 += v0; sa2 = fmaf(v0, v0, sa2); mxa = fmaxf(mxa, fabsf(v0)); } else { nfa++; }
+            if (isfinite(v1)) { sb1 += v1; sb2 = fmaf(v1, v1, sb2); mxb = fmaxf(mxb, fabsf(v1)); } else { nfb++; }
+        }
+    } else {
+        if (MODE == ROW_RHS && a.u_out) {
+            float* d0 = a.u_out + 2 * base;
+            for (int i = tid; i < nx; i += nthr) {
+                const f2 w = ld_real<f2, true>(X, i);
+                d0[i] = w.v.x;
+                d0[nx + i] = w.v.y;
+            }
+        }
+        const int Q = nx / nthr >= 16 ? nx / nthr : (nx >= 16 ? 16 : nx);
+        const int k0 = tid * Q;
+        if (k0 < nx) {
+            WenoCoef<f2> wc;
+            wc.B = f2(a.wc.B);
+            wc.alpha = f2(a.wc.alpha);
+            wc.eps = f2(a.wc.eps);
+            wc.inv_dtau = f2(a.wc.inv_dtau);
+            wc.c = f2(0.0f);
+            if constexpr (MODE == ROW_RHS_MED) {
+                // each row's advection speed c = 2 pi U_par and LF speed |c| + B M
+                const double c0 = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * row);
+                const double c1 = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * (row + 1));
+                wc.c = f2((float)c0, (float)c1);
+                wc.alpha = f2((float)(fabs(c0) + (double)a.wc.alpha), (float)(fabs(c1) + (double)a.wc.alpha));
+                weno_row_chunk<f2, true, true>(X, Y, nx, k0, Q, wc);
+            } else {
+                weno_row_chunk<f2, true>(X, Y, nx, k0, Q, wc);
+            }
+            if (a.diag_rows) pair_stats(X, k0, Q, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
+        }
+        __syncthreads();
+        if constexpr (MODE == ROW_RHS_MED) {
+            const float* by0 = a.by + 2 * base;
+            for (int k = tid; k < nx; k += nthr)
+                st_real<f2, true>(Y, k, ld_real<f2, true>(Y, k) + f2(__ldcg(by0 + k), __ldcg(by0 + nx + k)));
+            __syncthreads();
+        }
+        fft_batched<f2, PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
+        for (int k = tid; k <= n / 2; k += nthr) {
+            c2 xk, xnk;
+            r2c_post_pair<f2, true>(Y, n, k, P.tw2, xk, xnk);
+            float2 k0a = lane0(xk), k0b = lane1(xk), kna = lane0(xnk), knb = lane1(xnk);
+            if (a.cA != 0.0f) {
+                // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx), each row
+                const float2* va = in + base;
+                const float2* vb = in + base + n;
+                if (k == 0) {
+                    const float kN = a.kscale * (float)n, f = a.cA * kN * kN;
+                    k0a.y -= f * __ldcg(va).y;
+                    k0b.y -= f * __ldcg(vb).y;
+                } else {
+                    const float kt = a.kscale * (float)k, f = a.cA * kt * kt;
+                    const float2 v0 = __ldcg(va + k), v1 = __ldcg(vb + k);
+                    k0a.x -= f * v0.x; k0a.y -= f * v0.y;
+                    k0b.x -= f * v1.x; k0b.y -= f * v1.y;
+                    if (2 * k != n) {
+                        const float kt2 = a.kscale * (float)(n - k), g = a.cA * kt2 * kt2;
+                        const float2 w0 = __ldcg(va + n - k), w1 = __ldcg(vb + n - k);
+                        kna.x -= g * w0.x; kna.y -= g * w0.y;
+                        knb.x -= g * w1.x; knb.y -= g * w1.y;
+                    }
+                }
+            }
+            out[base + k] = k0a;
+            out[base + n + k] = k0b;
+            if (k != 0 && 2 * k != n) {
+                out[base + n - k] = kna;
+                out[base + 2 * n - k] = knb;
+            }
+        }
+    }
+    if (a.diag_rows) {
+        double* dst = a.diag_rows + ((long long)inst * a.ny + row) * 4;
+        block_diag_t<float>(red, sa1, sa2, mxa, nfa, dst);
+        __syncthreads();
+        block_diag_t<float>(red, sb1, sb2, mxb, nfb, dst + 4);
+    }
+}
+
+// threads and shared memory of one pair CTA: as the FP32 single-row kernel,
+// with 16-byte elements
+__host__ __forceinline__ size_t rowpair_smem_bytes(int nx)
+{
+    return 2 * (size_t)row_buf_len(nx / 2) * sizeof(c2) + 4 * (size_t)row_threads<float>(nx) * sizeof(double);
+}
+
+}  // namespace kzk

@@ -28,8 +28,12 @@
 #pragma once
 #include "kzk_common.cuh"
 #include "kzk_fft.cuh"
+#include <type_traits>
 
 namespace kzk {
+
+// quotient a / b to about 2 ulp (the FP32 sweep's hardware reciprocal)
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 
 template <typename T>
 struct WenoCoef {
@@ -143,7 +147,7 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
     };
     T np, dp, nm, dm;
     parts(k, np, dp, nm, dm);
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, double>::value) {
         // F = N / D with N = np dm + nm dp, D = dp dm; two interfaces share one
         // division: 1 / (D1 D2) gives both quotients
         T Fprev = fma(np, dm, nm * dp) / (dp * dm);
@@ -166,11 +170,11 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
     } else {
         // FP32: two hardware reciprocals (the product of the two denominators
         // could underflow)
-        T Fprev = __fdividef(np, dp) + __fdividef(nm, dm);
+        T Fprev = fast_div(np, dp) + fast_div(nm, dm);
 #pragma unroll 2
         for (k = k0; k < k0 + Q; k++) {
             parts(k, np, dp, nm, dm);
-            const T F = __fdividef(np, dp) + __fdividef(nm, dm);
+            const T F = fast_div(np, dp) + fast_div(nm, dm);
             store(k, F - Fprev);
             Fprev = F;
         }

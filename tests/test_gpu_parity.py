@@ -333,3 +333,33 @@ def test_expeuler_stages_and_adjoint():
     g_ref = oracle.adjoint(p, w.u0, g_end, w.n_steps)
     g0 = plan.adjoint(_dev(w.u0), _dev(g_end), w.n_steps, ckpt_every=3)
     assert rel_linf(g0.cpu().numpy(), g_ref) < 1e-10
+
+
+# FP32 row passes: row pairs in packed FP32 (default) and single rows
+# (KZK_ROWPAIR=0); both against the oracle, and against each other.
+@pytest.mark.parametrize("nx,ny,batch,medium", [(512, 256, 1, False), (64, 2, 3, False), (8192, 4, 1, False),
+                                                (256, 64, 2, True)])
+def test_fp32_row_pair_and_single_row(nx, ny, batch, medium, monkeypatch):
+    api = _api()
+    if medium:
+        w = inputs.medium_config(nx, ny, 20)
+    else:
+        w = inputs.config(3, nx=nx, ny=ny, n_steps=40)
+    u0 = np.stack([w.u0 * (1.0 - 0.1 * i) for i in range(batch)])
+    ref = np.stack([oracle.run(oracle.Params(**inputs.oracle_params(w)), np.ascontiguousarray(x), w.n_steps,
+                               threads=True) for x in u0])
+    got = {}
+    for env in ("1", "0"):
+        monkeypatch.setenv("KZK_ROWPAIR", env)
+        plan = api.Plan.from_workload(w, precision="fp32", batch=batch)
+        u = _dev(u0, torch.float32)
+        st, d = plan.advance(u, w.n_steps, diag=True)
+        assert st == 0
+        got[env] = (u.double().cpu().numpy(), plan.diag_history(w.n_steps))
+        plan.close()
+    for env in ("1", "0"):
+        assert rel_l2(got[env][0], ref) < 1e-5
+    assert rel_l2(got["1"][0], got["0"][0]) < 2e-6
+    # per-step FP64 diagnostics of every row pair agree with the single rows
+    assert np.allclose(got["1"][1][:, :, 1], got["0"][1][:, :, 1], rtol=1e-5)
+
