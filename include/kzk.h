@@ -69,7 +69,17 @@ typedef struct {
                                        transforms; KZK_MIXED=1 in the environment selects
                                        them for power-of-two grids too) */
     double tau_min, tau_max, y_min, y_max;
-    int32_t prec;                   /* kzk_precision of state and bulk arithmetic */
+    int32_t prec;                   /* kzk_precision of state and bulk arithmetic.
+                                       KZK_FP32 plans keep the spectral state as a
+                                       compensated pair hi + lo of FP32 values: the
+                                       column passes transform only the increment of a
+                                       stage ((E - 1) V + dsigma Phi1 b1 of Eq. 11) and add
+                                       it to hi + lo exactly (TwoSum), so the rounding of
+                                       a full-state transform pair does not accumulate
+                                       over thousands of steps (KZK_COMPSTATE=0 in the
+                                       environment: a plain FP32 state).  KZK_FP32 row
+                                       passes run on row pairs in packed FP32
+                                       (KZK_ROWPAIR=0: single rows). */
 } kzk_grid;
 
 #define KZK_MAX_RELAX 2

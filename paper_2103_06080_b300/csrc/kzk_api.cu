@@ -137,6 +137,11 @@ struct kzk_plan_s {
     void* wsc;                  // device [batch][ny][nx/2]: P1' FFT_y(b1) between the two C1 launches
     int mrow_thr, mcol_lc;
     size_t mrow_smem, mcol_smem;
+    // FP32 plans: compensated state (the spectral state as hi + lo; the column
+    // passes transform increments, with the table (E - 1)/ny)
+    int comp;
+    void *Vlo, *vslo;           // lo parts of V and V*
+    void* Em1;                  // (E - 1)/ny, folded as E'
     // FP32 plans: row passes on row pairs in packed FP32 (kzk_rowpair.cuh)
     int rowpair;
     size_t rowpair_smem;
@@ -331,8 +336,10 @@ kzk_status configure(kzk_plan* p)
     }
     colp_configure<T>(p, optin);
     if (p->colp_log2tc >= 0) {
-        KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-        KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     }
     return KZK_OK;
 }
@@ -501,7 +508,9 @@ kzk_status launch_colp(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
     P.timeout_ns = 2000000000LL;
     P.ahead = 2 * p->sm_count;   // two CTAs per SM: one wave ahead
     const int grid = P.total;
-    colp_kernel<T, MODE><<<grid, p->colp_thr, MODE == COL_STAGE1 ? p->colp_smem1 : p->colp_smem2, st>>>(P);
+    const size_t smem = MODE == COL_STAGE1 ? p->colp_smem1 : p->colp_smem2;
+    if (p->comp) colp_kernel<T, MODE, true><<<grid, p->colp_thr, smem, st>>>(P);
+    else colp_kernel<T, MODE, false><<<grid, p->colp_thr, smem, st>>>(P);
     KZK_LAUNCHED();
     return KZK_OK;
 }
@@ -622,6 +631,33 @@ kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, dou
     return launch_row<T, ROW_RHS>(p, r, st);
 }
 
+// Stage-1 table and state pointers: the plain state takes E' (+ E'_lo in
+// FP32); the compensated state (FP32 plans) takes (E - 1)/ny and the lo
+// arrays, V* = V + increment (exponential Euler: V' in place of V).
+template <typename T>
+void stage1_tables(const kzk_plan* p, ColArgs<T>& c1, bool euler)
+{
+    if (p->comp) {
+        c1.Ta = (const cx<T>*)p->Em1;
+        c1.Ta_lo = nullptr;
+        c1.lo_in = (const cx<T>*)p->Vlo;
+        c1.lo_out = (cx<T>*)(euler ? p->Vlo : p->vslo);
+    } else {
+        c1.Ta = (const cx<T>*)p->E;
+        c1.Ta_lo = (const cx<T>*)p->E_lo;
+    }
+}
+template <typename T>
+void stage2_lo(const kzk_plan* p, ColArgs<T>& c2)
+{
+    if (p->comp) {
+        c2.lo_in = (const cx<T>*)p->vslo;
+        c2.lo_out = (cx<T>*)p->Vlo;
+    }
+}
+
+kzk_status reset_lo(kzk_plan* p, cudaStream_t st);
+
 // One ExpRK22 step on the spectral state p->V (Algorithm 2, STEP 1-4).
 // diag_hist_step: where C1 writes this step's diagnostics (nullable).
 // vs_out / b1_out / b2_out: destinations (default: plan workspace).
@@ -640,8 +676,7 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     // exponential Euler: the first stage is the step (every column tile is
     // read whole before it is written, so V_out may alias V)
     c1.out = (cx<T>*)(euler ? V_out : vs);
-    c1.Ta = (const cx<T>*)p->E;
-    c1.Ta_lo = (const cx<T>*)p->E_lo;
+    stage1_tables<T>(p, c1, euler);
     c1.Tb = (const cx<T>*)p->P1;
     c1.diag_rows = diag_hist_step ? p->diag_rows : nullptr;
     c1.diag_hist = diag_hist_step;
@@ -654,7 +689,16 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     c2.c = (const cx<T>*)vs;
     c2.out = (cx<T>*)V_out;
     c2.Ta = (const cx<T>*)p->P2;
+    stage2_lo<T>(p, c2);
     KZK_TRY((launch_col<T, COL_STAGE2>(p, c2, st)));
+    return KZK_OK;
+}
+
+// zero lo part after a state is (re)loaded into p->V in spectral form
+kzk_status reset_lo(kzk_plan* p, cudaStream_t st)
+{
+    if (p->comp)
+        KZK_CUDA(cudaMemsetAsync(p->Vlo, 0, (size_t)p->batch * p->inst_stride * p->csz, st));
     return KZK_OK;
 }
 
@@ -663,7 +707,9 @@ kzk_status to_spectral(kzk_plan* p, const void* u, void* V, cudaStream_t st)
 {
     RowArgs<T> a = row_args<T>(p, u, V, 0.0, nullptr);
     a.out_scale = (T)(1.0 / p->nx);
-    return launch_row<T, ROW_FWD>(p, a, st);
+    KZK_TRY((launch_row<T, ROW_FWD>(p, a, st)));
+    // a state loaded into the plan's state array starts with a zero lo part
+    return V == p->V ? reset_lo(p, st) : KZK_OK;
 }
 
 template <typename T>
@@ -760,6 +806,7 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
     a.P1 = p->P1;
     a.P2 = p->P2;
     a.E_lo = p->E_lo;
+    a.Em1 = p->Em1;
     a.n_relax = p->c.n_relax;
     for (int r = 0; r < 2; r++) {
         a.relax_C[r] = r < p->c.n_relax ? p->c.relax_C[r] : 0.0;
@@ -844,7 +891,8 @@ void plan_free(kzk_plan* p)
                     p->tws_row, p->twc_full,
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
                     p->seg, p->ckpt, p->colp_flag, p->med_Ty, p->med_mode, p->med_coef, p->med_bmax,
-                    p->uphys, p->by, p->mpos_row, p->mpos_col, p->mipos_col, p->wsc, p->twr2, p->tws2};
+                    p->uphys, p->by, p->mpos_row, p->mpos_col, p->mipos_col, p->wsc, p->twr2, p->tws2,
+                    p->Vlo, p->vslo, p->Em1};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1047,6 +1095,7 @@ kzk_status reverse_sweep(kzk_plan* p, const void* g_end, void* g0, cudaStream_t 
         for (long long s = s0; s < s1; s++) {
             const long long i = s - s0;
             void* Vn = i == 0 ? arr_at(p->ckpt, c) : p->V;
+            if (i == 0) KZK_TRY(reset_lo(p, st));     // checkpoints keep the hi part
             KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, Vn, p->vs, p->V, arr_at(p->seg, 2 * i),
                             arr_at(p->seg, 2 * i + 1)));
         }
@@ -1460,8 +1509,7 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
         c1.a = (const cx<T>*)p->V;
         c1.b = (const cx<T>*)p->b1;
         c1.out = (cx<T>*)(euler ? p->V : p->vs);
-        c1.Ta = (const cx<T>*)p->E;
-        c1.Ta_lo = (const cx<T>*)p->E_lo;
+        stage1_tables<T>(p, c1, euler);
         c1.Tb = (const cx<T>*)p->P1;
         c1.diag_rows = p->diag_rows;
         c1.diag_hist = p->diag_hist + (size_t)s * p->batch * 4;
@@ -1487,6 +1535,7 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
         c2.c = (const cx<T>*)p->vs;
         c2.out = (cx<T>*)p->V;
         c2.Ta = (const cx<T>*)p->P2;
+        stage2_lo<T>(p, c2);
         KZK_TRY((launch_col<T, COL_STAGE2>(p, c2, st)));
         KZK_CUDA(cudaEventRecord(ev[4], st));
         KZK_CUDA(cudaEventSynchronize(ev[4]));
@@ -1607,6 +1656,9 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     p->csz = p->prec == KZK_FP64 ? sizeof(double2) : sizeof(float2);
     p->inst_stride = (long long)p->ny * p->n;
     p->mixed = mixed ? 1 : 0;
+    // FP32: compensated spectral state unless KZK_COMPSTATE=0 in the environment
+    const char* cenv = getenv("KZK_COMPSTATE");
+    p->comp = (p->prec == KZK_FP32 && !(cenv && cenv[0] == '0')) ? 1 : 0;
 
     kzk_status s = p->prec == KZK_FP64 ? configure<double>(p) : configure<float>(p);
     if (s != KZK_OK) { plan_free(p); return s; }
@@ -1630,6 +1682,11 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     if (e == cudaSuccess) e = cudaMalloc(&p->diag_final, (size_t)batch * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&p->colp_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->colp_flag, 0, sizeof(int));
+    if (p->comp) {
+        if (e == cudaSuccess) e = cudaMalloc(&p->Vlo, arr);
+        if (e == cudaSuccess) e = cudaMalloc(&p->vslo, arr);
+        if (e == cudaSuccess) e = cudaMalloc(&p->Em1, tab);
+    }
     if (p->rowpair) {
         if (e == cudaSuccess) e = cudaMalloc(&p->twr2, (size_t)p->nx * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc(&p->tws2, (size_t)p->n * sizeof(float4));

@@ -170,22 +170,34 @@ struct Mul2St {
 };
 
 // last inverse pass: results straight to HBM (STAGE2: plus V* from staging)
-template <typename T, bool ADD>
+template <typename T, bool ADD, bool COMP = false>
 struct OutSt {
     cx<T>* out;
     const cx<T>* C;
     long long ibase;
     int log2tc, log2n, m0;
+    // COMP (compensated state): out = hi + v with hi from C (ADD) or from
+    // hi_g (the state the stage started from), lo in lo_in / lo_out
+    const cx<T>* hi_g;
+    const cx<T>* lo_in;
+    cx<T>* lo_out;
     template <int R>
     __device__ __forceinline__ void st(int i0, int s, const cx<T>* v) const
     {
         const int c = i0 & ((1 << log2tc) - 1);
-        cx<T>* o = out + ibase + m0 + c;
+        const long long o0 = ibase + m0 + c;
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int i = i0 + r * s;
-            const long long g = (long long)(i >> log2tc) << log2n;
-            o[g] = ADD ? add<T>(C[i], v[r]) : v[r];
+            const long long g = o0 + ((long long)(i >> log2tc) << log2n);
+            if constexpr (COMP) {
+                cx<T> h, l;
+                comp_add<T>(ADD ? C[i] : __ldcg(hi_g + g), __ldcg(lo_in + g), v[r], h, l);
+                out[g] = h;
+                lo_out[g] = l;
+            } else {
+                out[g] = ADD ? add<T>(C[i], v[r]) : v[r];
+            }
         }
     }
 };
@@ -586,7 +598,7 @@ __device__ __noinline__ void colp_packed(const ColArgs<T>& a, unsigned char* sme
             const cx<T> zv = WA[e], zvm = WA[em], zb = WB[e], zbm = WB[em];
             cx<T> r = mult_entry<T>(E, zv, zvm, true);
             cx<T> rm = mult_entry<T>(E, zvm, zv, true);
-            if constexpr (ACC) {
+            if (ACC && a.Ta_lo) {
                 const cx<T> El = __ldg(a.Ta_lo + ti);
                 r = add<T>(r, mult_entry<T>(El, zv, zvm, true));
                 rm = add<T>(rm, mult_entry<T>(El, zvm, zv, true));
@@ -605,13 +617,14 @@ __device__ __noinline__ void colp_packed(const ColArgs<T>& a, unsigned char* sme
     __syncthreads();
 }
 
-// One column tile (CTA q = tile q)
-template <typename T, int MODE>
+// One column tile (CTA q = tile q).  COMP: the compensated FP32 state (the
+// transforms carry increments only, so their constants need no lo parts).
+template <typename T, int MODE, bool COMP = false>
 __global__ void __launch_bounds__(COLP_THREADS, 2) colp_kernel(const __grid_constant__ ColPipeArgs<T> P)
 {
     extern __shared__ __align__(128) unsigned char colp_smem[];
     unsigned char* smem = colp_smem;
-    constexpr bool ACC = sizeof(T) == 4;
+    constexpr bool ACC = sizeof(T) == 4 && !COMP;
     const ColArgs<T>& a = P.c;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int log2ny = a.log2ny, log2tc = a.log2tc, ny = 1 << log2ny;
@@ -669,13 +682,13 @@ __global__ void __launch_bounds__(COLP_THREADS, 2) colp_kernel(const __grid_cons
         tile_first<T, true, ACC>(log2ny, log2tc, twa, tid, nthr, PadIO<T>{WA}, WA);
         tile_middle<T, true, ACC>(log2ny, log2tc, twa, tid, nthr, WA);
         tile_last<T, true, ACC>(log2ny, log2tc, twa, tid, nthr, WA,
-                                OutSt<T, false>{a.out, nullptr, ibase, log2tc, a.log2n, m0});
+                                OutSt<T, false, COMP>{a.out, nullptr, ibase, log2tc, a.log2n, m0, a.a, a.lo_in, a.lo_out});
     } else {
         tile_first<T, true, false>(log2ny, log2tc, twp, tid, nthr, PadIO<T>{WA}, WA);
         tile_middle<T, true, false>(log2ny, log2tc, twp, tid, nthr, WA);
         if (!colp_wait(smem, 1, 0u, P.timeout_ns, P.flag)) return;
         tile_last<T, true, false>(log2ny, log2tc, twp, tid, nthr, WA,
-                                  OutSt<T, true>{a.out, WB, ibase, log2tc, a.log2n, m0});
+                                  OutSt<T, true, COMP>{a.out, WB, ibase, log2tc, a.log2n, m0, nullptr, a.lo_in, a.lo_out});
     }
 }
 

@@ -35,6 +35,24 @@ template <typename T> __device__ __forceinline__ cx<T> fma_c(cx<T> a, cx<T> b, c
     return mk<T>(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
 }
 
+// Compensated state update: the value hi + lo plus an increment d, returned as
+// a new pair (s_hi, s_lo) with s_hi + s_lo = hi + fl(lo + d) exactly (Knuth's
+// TwoSum on each component; no reassociation, no FMA involved).
+template <typename T>
+__device__ __forceinline__ void comp_add(cx<T> hi, cx<T> lo, cx<T> d, cx<T>& s_hi, cx<T>& s_lo)
+{
+    auto two_sum = [](T h, T t, T& s, T& e) {
+        s = h + t;
+        const T bb = s - h;
+        e = (h - (s - bb)) + (t - bb);
+    };
+    T sx, ex, sy, ey;
+    two_sum(hi.x, lo.x + d.x, sx, ex);
+    two_sum(hi.y, lo.y + d.y, sy, ey);
+    s_hi = mk<T>(sx, sy);
+    s_lo = mk<T>(ex, ey);
+}
+
 __host__ __device__ __forceinline__ int ilog2(unsigned v)
 {
     int r = 0;

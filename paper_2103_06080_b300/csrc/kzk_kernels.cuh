@@ -340,6 +340,12 @@ struct ColArgs {
     const double* diag_rows;  // [batch][ny][4] or nullptr
     double* diag_hist;        // [batch][4] for this step
     double inv_count, cell;   // 1/(nx ny), dtau dy
+    // compensated state (FP32 plans): the state is the pair hi + lo; STAGE1
+    // takes lo of V (hi: a) and writes lo of V* (hi: out), with Ta = (E - 1)/ny
+    // so that the transforms carry only the increment; STAGE2 takes lo of V*
+    // (hi: c) and writes lo of V' (hi: out).  nullptr: plain state.
+    const cx<T>* lo_in;
+    cx<T>* lo_out;
 };
 
 // Table entry at (l, m) applied to a column-FFT'd value z (zm: the value at
@@ -461,7 +467,9 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
             const long long ti = (long long)lf * n + m;
             const cx<T> zv = SA[padx(e)], zb = SB[padx(e)];
             cx<T> r = mul<T>(a.Ta[ti], zv);
-            if constexpr (ACC) r = fma_c<T>(a.Ta_lo[ti], zv, r);
+            if constexpr (ACC) {
+                if (a.Ta_lo) r = fma_c<T>(a.Ta_lo[ti], zv, r);
+            }
             SA[padx(e)] = fma_c<T>(a.Tb[ti], zb, r);
         }
         if (m0 == 0) {
@@ -472,7 +480,7 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
                 const cx<T> zv = SA[e], zvm = SA[em], zb = SB[e], zbm = SB[em];
                 cx<T> r = mult_entry<T>(a.Ta[ti], zv, zvm, true);
                 cx<T> rm = mult_entry<T>(a.Ta[ti], zvm, zv, true);
-                if constexpr (ACC) {
+                if (ACC && a.Ta_lo) {
                     r = add<T>(r, mult_entry<T>(a.Ta_lo[ti], zv, zvm, true));
                     rm = add<T>(rm, mult_entry<T>(a.Ta_lo[ti], zvm, zv, true));
                 }
@@ -484,7 +492,18 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
         }
         __syncthreads();
         fft_batched<T, COL_PPT, true, true, true, ACC>(SA, a.log2ny, a.log2tc, TC, 1, twa, tid, nthr);
-        for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = SA[padx(e)];
+        if (a.lo_out) {
+            // the transforms carried the increment: V* = V + increment, compensated
+            for (int e = tid; e < total; e += nthr) {
+                const long long g = gidx(e);
+                cx<T> h, l;
+                comp_add<T>(__ldcg(a.a + g), __ldcg(a.lo_in + g), SA[padx(e)], h, l);
+                a.out[g] = h;
+                a.lo_out[g] = l;
+            }
+        } else {
+            for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = SA[padx(e)];
+        }
     } else {
         {
             int e = tid;
@@ -520,7 +539,15 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
         }
         __syncthreads();
         fft_batched<T, COL_PPT, true, true, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
-        {
+        if (a.lo_out) {
+            for (int e = tid; e < total; e += nthr) {
+                const long long g = gidx(e);
+                cx<T> h, l;
+                comp_add<T>(__ldcg(a.c + g), __ldcg(a.lo_in + g), SA[padx(e)], h, l);
+                a.out[g] = h;
+                a.lo_out[g] = l;
+            }
+        } else {
             int e = tid;
             for (; e + 3 * nthr < total; e += 4 * nthr) {
                 cx<T> vc[4];

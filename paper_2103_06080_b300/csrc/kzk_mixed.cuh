@@ -488,7 +488,9 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
             A.w[gidx(e)] = mul<T>(__ldg(a.Tb + ti), z);
         } else if constexpr (MODE == MIX_C1V) {
             cx<T> r = mul<T>(__ldg(a.Ta + ti), z);
-            if constexpr (ACC) r = fma_c<T>(__ldg(a.Ta_lo + ti), z, r);
+            if constexpr (ACC) {
+                if (a.Ta_lo) r = fma_c<T>(__ldg(a.Ta_lo + ti), z, r);
+            }
             S[e] = add<T>(r, __ldcg(A.w + gidx(e)));
         } else {
             S[e] = mul<T>(__ldg(a.Ta + ti), z);
@@ -507,7 +509,7 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
             } else if constexpr (MODE == MIX_C1V) {
                 const cx<T> M = __ldg(a.Ta + ti);
                 cx<T> r = mult_entry<T>(M, z, zm, true), rm = mult_entry<T>(M, zm, z, true);
-                if constexpr (ACC) {
+                if (ACC && a.Ta_lo) {
                     const cx<T> Ml = __ldg(a.Ta_lo + ti);
                     r = add<T>(r, mult_entry<T>(Ml, z, zm, true));
                     rm = add<T>(rm, mult_entry<T>(Ml, zm, z, true));
@@ -526,7 +528,15 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
     mix_inverse<T, ACC>(S, A.f, lc, a.tw, a.tw_lo, tid, nthr);
     for (int e = tid; e < total; e += nthr) {
         const long long g = gidx(e);
-        a.out[g] = MODE == MIX_C1V ? S[e] : add<T>(__ldcg(a.c + g), S[e]);
+        if (a.lo_out) {
+            // compensated state: the transforms carried the increment
+            cx<T> h, l;
+            comp_add<T>(__ldcg((MODE == MIX_C1V ? a.a : a.c) + g), __ldcg(a.lo_in + g), S[e], h, l);
+            a.out[g] = h;
+            a.lo_out[g] = l;
+        } else {
+            a.out[g] = MODE == MIX_C1V ? S[e] : add<T>(__ldcg(a.c + g), S[e]);
+        }
     }
 }
 

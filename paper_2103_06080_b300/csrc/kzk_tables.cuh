@@ -26,6 +26,7 @@ struct TabArgs {
     void* P1;
     void* P2;
     void* E_lo;      // float plans: E' - (float)E' (nullptr for double)
+    void* Em1;       // compensated-state plans: (E - 1)/ny = z Phi1 / ny (nullptr otherwise)
 };
 
 // phi-functions at z.  |z| < 1/2: Phi2 from its Taylor series
@@ -127,6 +128,22 @@ __global__ void tables_kernel(TabArgs a)
     }
     reinterpret_cast<cx<T>*>(a.P1)[idx] = oP1;
     reinterpret_cast<cx<T>*>(a.P2)[idx] = oP2;
+    if (a.Em1) {
+        // E - 1 = z Phi1, without the cancellation of forming E first
+        cx<T> o;
+        if (m == 0) {
+            double2 E0, P10, P20, EN, P1N, P2N;
+            const double2 z0 = z_of(a, 0.0, ky, false);
+            const double2 zN = z_of(a, a.kts * n, ky, true);
+            phi_eval(z0.x, z0.y, E0, P10, P20);
+            phi_eval(zN.x, zN.y, EN, P1N, P2N);
+            o = mk<T>((T)((z0.x * P10.x - z0.y * P10.y) * sE), (T)((zN.x * P1N.x - zN.y * P1N.y) * sE));
+        } else {
+            const double2 z = z_of(a, a.kts * m, ky, false);
+            o = mk<T>((T)((z.x * P1.x - z.y * P1.y) * sE), (T)((z.x * P1.y + z.y * P1.x) * sE));
+        }
+        reinterpret_cast<cx<T>*>(a.Em1)[idx] = o;
+    }
 }
 
 }  // namespace kzk

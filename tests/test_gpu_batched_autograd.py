@@ -21,11 +21,12 @@ def _small_batch(precision):
 def test_batched_matches_single_plans(prec, mode, monkeypatch):
     from paper_2103_06080_b300 import api
     if mode == "persistent":
-        # the persistent kernel runs the per-tile column bodies and the
-        # single-row bodies: compare with single plans on the same kernels,
-        # bit for bit
+        # the persistent kernel runs the per-tile column bodies, the
+        # single-row bodies and the plain (uncompensated) FP32 state: compare
+        # with single plans on the same kernels, bit for bit
         monkeypatch.setenv("KZK_COLPIPE", "0")
         monkeypatch.setenv("KZK_ROWPAIR", "0")
+        monkeypatch.setenv("KZK_COMPSTATE", "0")
     dt = torch.float64 if prec == "fp64" else torch.float32
     ws = _small_batch(prec)
     bp = api.BatchedPlan(ws, precision=prec, autotune=True, mode=mode)

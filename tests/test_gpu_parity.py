@@ -363,3 +363,42 @@ def test_fp32_row_pair_and_single_row(nx, ny, batch, medium, monkeypatch):
     # per-step FP64 diagnostics of every row pair agree with the single rows
     assert np.allclose(got["1"][1][:, :, 1], got["0"][1][:, :, 1], rtol=1e-5)
 
+
+# FP32 state: compensated (default: the spectral state as hi + lo, the column
+# passes transforming increments) and plain (KZK_COMPSTATE=0).  Over the
+# 2000 steps of the precision workload the compensated state keeps the FP32
+# error within the 1e-5 goal, where the plain state accumulates the rounding
+# of a full-state transform pair every step.
+def test_fp32_compensated_state_2000_steps(monkeypatch):
+    # the precision workload as specified: 1024 x 512, 2000 steps, FP64 oracle
+    api = _api()
+    w = inputs.config(3, nx=1024, ny=512, n_steps=2000)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    err = {}
+    for env in ("1", "0"):
+        monkeypatch.setenv("KZK_COMPSTATE", env)
+        plan = api.Plan.from_workload(w, precision="fp32")
+        u = _dev(w.u0, torch.float32)
+        plan.advance(u, w.n_steps)
+        err[env] = rel_l2(u.double().cpu().numpy(), ref)
+        plan.close()
+    assert err["1"] < 1e-5, err
+    assert err["1"] < err["0"], err
+
+
+@pytest.mark.parametrize("method", ["exprk22", "expeuler"])
+def test_fp32_compensated_state_short_runs(method, monkeypatch):
+    api = _api()
+    w = inputs.config(2, nx=256, ny=64, n_steps=30)
+    p = oracle.Params(**inputs.oracle_params(w, method=1 if method == "expeuler" else 0))
+    ref = oracle.run(p, w.u0, w.n_steps)
+    for env in ("1", "0"):
+        monkeypatch.setenv("KZK_COMPSTATE", env)
+        for pipe in ("1", "0"):
+            monkeypatch.setenv("KZK_COLPIPE", pipe)
+            plan = api.Plan.from_workload(w, precision="fp32", method=method)
+            u = _dev(w.u0, torch.float32)
+            plan.advance(u, w.n_steps)
+            assert rel_l2(u.double().cpu().numpy(), ref) < 1e-5, (env, pipe)
+            plan.close()
+
