@@ -71,7 +71,7 @@ typedef struct {
     double tau_min, tau_max, y_min, y_max;
     int32_t prec;                   /* kzk_precision of state and bulk arithmetic.
                                        KZK_FP32 plans keep the spectral state as a
-                                       compensated pair hi + lo of FP32 values: the
+                                       compensated pair hi + lo (FP32 hi, bf16 lo): the
                                        column passes transform only the increment of a
                                        stage ((E - 1) V + dsigma Phi1 b1 of Eq. 11) and add
                                        it to hi + lo exactly (TwoSum), so the rounding of

@@ -640,8 +640,8 @@ void stage1_tables(const kzk_plan* p, ColArgs<T>& c1, bool euler)
     if (p->comp) {
         c1.Ta = (const cx<T>*)p->Em1;
         c1.Ta_lo = nullptr;
-        c1.lo_in = (const cx<T>*)p->Vlo;
-        c1.lo_out = (cx<T>*)(euler ? p->Vlo : p->vslo);
+        c1.lo_in = (const lo_t<T>*)p->Vlo;
+        c1.lo_out = (lo_t<T>*)(euler ? p->Vlo : p->vslo);
     } else {
         c1.Ta = (const cx<T>*)p->E;
         c1.Ta_lo = (const cx<T>*)p->E_lo;
@@ -651,8 +651,8 @@ template <typename T>
 void stage2_lo(const kzk_plan* p, ColArgs<T>& c2)
 {
     if (p->comp) {
-        c2.lo_in = (const cx<T>*)p->vslo;
-        c2.lo_out = (cx<T>*)p->Vlo;
+        c2.lo_in = (const lo_t<T>*)p->vslo;
+        c2.lo_out = (lo_t<T>*)p->Vlo;
     }
 }
 
@@ -698,7 +698,7 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
 kzk_status reset_lo(kzk_plan* p, cudaStream_t st)
 {
     if (p->comp)
-        KZK_CUDA(cudaMemsetAsync(p->Vlo, 0, (size_t)p->batch * p->inst_stride * p->csz, st));
+        KZK_CUDA(cudaMemsetAsync(p->Vlo, 0, (size_t)p->batch * p->inst_stride * sizeof(__nv_bfloat162), st));
     return KZK_OK;
 }
 
@@ -1683,8 +1683,10 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     if (e == cudaSuccess) e = cudaMalloc(&p->colp_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->colp_flag, 0, sizeof(int));
     if (p->comp) {
-        if (e == cudaSuccess) e = cudaMalloc(&p->Vlo, arr);
-        if (e == cudaSuccess) e = cudaMalloc(&p->vslo, arr);
+        // lo parts: one bf16 pair per complex value
+        const size_t lo_arr = (size_t)batch * p->inst_stride * sizeof(__nv_bfloat162);
+        if (e == cudaSuccess) e = cudaMalloc(&p->Vlo, lo_arr);
+        if (e == cudaSuccess) e = cudaMalloc(&p->vslo, lo_arr);
         if (e == cudaSuccess) e = cudaMalloc(&p->Em1, tab);
     }
     if (p->rowpair) {

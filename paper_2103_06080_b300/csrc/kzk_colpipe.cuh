@@ -179,8 +179,8 @@ struct OutSt {
     // COMP (compensated state): out = hi + v with hi from C (ADD) or from
     // hi_g (the state the stage started from), lo in lo_in / lo_out
     const cx<T>* hi_g;
-    const cx<T>* lo_in;
-    cx<T>* lo_out;
+    const lo_t<T>* lo_in;
+    lo_t<T>* lo_out;
     template <int R>
     __device__ __forceinline__ void st(int i0, int s, const cx<T>* v) const
     {
@@ -192,9 +192,9 @@ struct OutSt {
             const long long g = o0 + ((long long)(i >> log2tc) << log2n);
             if constexpr (COMP) {
                 cx<T> h, l;
-                comp_add<T>(ADD ? C[i] : __ldcg(hi_g + g), __ldcg(lo_in + g), v[r], h, l);
+                comp_add<T>(ADD ? C[i] : __ldcg(hi_g + g), lo_load<T>(lo_in + g), v[r], h, l);
                 out[g] = h;
-                lo_out[g] = l;
+                lo_store<T>(lo_out + g, l);
             } else {
                 out[g] = ADD ? add<T>(C[i], v[r]) : v[r];
             }

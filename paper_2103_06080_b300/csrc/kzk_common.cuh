@@ -1,5 +1,6 @@
 // kzk_common.cuh -- complex arithmetic and small helpers shared by the kernels.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -51,6 +52,32 @@ __device__ __forceinline__ void comp_add(cx<T> hi, cx<T> lo, cx<T> d, cx<T>& s_h
     two_sum(hi.y, lo.y + d.y, sy, ey);
     s_hi = mk<T>(sx, sy);
     s_lo = mk<T>(ex, ey);
+}
+
+// Storage of the lo part of a compensated state: for FP32 one bf16 pair per
+// complex value (8 significant bits below the 24 of the hi part: the pair
+// carries about 33 bits, 2^-33 relative per update), else the value type.
+template <typename T> struct lo_of { using type = cx<T>; };
+template <> struct lo_of<float> { using type = __nv_bfloat162; };
+template <typename T> using lo_t = typename lo_of<T>::type;
+
+template <typename T>
+__device__ __forceinline__ cx<T> lo_load(const lo_t<T>* p)
+{
+    if constexpr (sizeof(lo_t<T>) == 4) {
+        const unsigned w = __ldcg(reinterpret_cast<const unsigned*>(p));
+        __nv_bfloat162 b;
+        memcpy(&b, &w, 4);
+        return __bfloat1622float2(b);
+    } else {
+        return __ldcg(p);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void lo_store(lo_t<T>* p, cx<T> v)
+{
+    if constexpr (sizeof(lo_t<T>) == 4) *p = __float22bfloat162_rn(v);
+    else *p = v;
 }
 
 __host__ __device__ __forceinline__ int ilog2(unsigned v)

@@ -344,8 +344,8 @@ struct ColArgs {
     // takes lo of V (hi: a) and writes lo of V* (hi: out), with Ta = (E - 1)/ny
     // so that the transforms carry only the increment; STAGE2 takes lo of V*
     // (hi: c) and writes lo of V' (hi: out).  nullptr: plain state.
-    const cx<T>* lo_in;
-    cx<T>* lo_out;
+    const lo_t<T>* lo_in;
+    lo_t<T>* lo_out;
 };
 
 // Table entry at (l, m) applied to a column-FFT'd value z (zm: the value at
@@ -497,9 +497,9 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
             for (int e = tid; e < total; e += nthr) {
                 const long long g = gidx(e);
                 cx<T> h, l;
-                comp_add<T>(__ldcg(a.a + g), __ldcg(a.lo_in + g), SA[padx(e)], h, l);
+                comp_add<T>(__ldcg(a.a + g), lo_load<T>(a.lo_in + g), SA[padx(e)], h, l);
                 a.out[g] = h;
-                a.lo_out[g] = l;
+                lo_store<T>(a.lo_out + g, l);
             }
         } else {
             for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = SA[padx(e)];
@@ -543,9 +543,9 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
             for (int e = tid; e < total; e += nthr) {
                 const long long g = gidx(e);
                 cx<T> h, l;
-                comp_add<T>(__ldcg(a.c + g), __ldcg(a.lo_in + g), SA[padx(e)], h, l);
+                comp_add<T>(__ldcg(a.c + g), lo_load<T>(a.lo_in + g), SA[padx(e)], h, l);
                 a.out[g] = h;
-                a.lo_out[g] = l;
+                lo_store<T>(a.lo_out + g, l);
             }
         } else {
             int e = tid;

@@ -531,9 +531,9 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
         if (a.lo_out) {
             // compensated state: the transforms carried the increment
             cx<T> h, l;
-            comp_add<T>(__ldcg((MODE == MIX_C1V ? a.a : a.c) + g), __ldcg(a.lo_in + g), S[e], h, l);
+            comp_add<T>(__ldcg((MODE == MIX_C1V ? a.a : a.c) + g), lo_load<T>(a.lo_in + g), S[e], h, l);
             a.out[g] = h;
-            a.lo_out[g] = l;
+            lo_store<T>(a.lo_out + g, l);
         } else {
             a.out[g] = MODE == MIX_C1V ? S[e] : add<T>(__ldcg(a.c + g), S[e]);
         }
