@@ -50,7 +50,7 @@ def _peaks():
 _ROW_SRC = ("kzk_common.cuh", "kzk_fft.cuh", "kzk_weno.cuh", "kzk_kernels.cuh")
 KERNEL_SOURCES = {
     ("row_stage1", "fp64"): _ROW_SRC, ("row_stage2", "fp64"): _ROW_SRC,
-    ("row_stage1", "fp32"): _ROW_SRC, ("row_stage2", "fp32"): _ROW_SRC,
+    ("row_stage1", "fp32"): _ROW_SRC + ("kzk_rowpair.cuh",), ("row_stage2", "fp32"): _ROW_SRC + ("kzk_rowpair.cuh",),
     ("col_stage1", "fp64"): _ROW_SRC, ("col_stage2", "fp64"): _ROW_SRC,
     ("col_stage1", "fp32"): _ROW_SRC + ("kzk_colpipe.cuh",), ("col_stage2", "fp32"): _ROW_SRC + ("kzk_colpipe.cuh",),
 }
