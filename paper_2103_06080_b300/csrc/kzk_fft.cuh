@@ -9,8 +9,8 @@
 // points with stride n/R into registers, applies the inter-stage twiddles,
 // runs an in-register DFT of size R and writes the results to their sorted
 // positions, so the output is in natural order with no bit reversal.
-// Twiddles come from a plan-time table tw[k] = exp(-2 pi i k / Ntw)
-// (Ntw = 2^tw_log2 >= n), built in FP64 on the host.
+// Twiddles come from a plan-time staged table (see Tw), built in long double
+// on the host.
 //
 // ACC (float only): every multiplication by a fixed constant -- table
 // twiddles and the DFT's own roots of unity -- uses a two-float (hi + lo)
@@ -115,11 +115,10 @@ template <typename T, int R, int S, bool ACC> struct RegDFT {
 };
 
 // Twiddle tables: hi part and, for ACC, the lo correction (lo == nullptr
-// otherwise).  log2 >= 0: one table exp(-2 pi i k / 2^log2) indexed
-// (r k) << shift.  log2 < 0: a per-pass ("staged") table for this transform
-// length and radix schedule: pass p with Ns_p, R_p occupies
-// (R_p - 1) * Ns_p entries, entry (r - 1) * Ns_p + k = exp(-2 pi i r k / (Ns_p R_p)),
-// so the lanes of a warp (consecutive k) read consecutive entries.
+// otherwise), as a per-pass ("staged") table for the transform length and
+// radix schedule: pass p with Ns_p, R_p occupies (R_p - 1) * Ns_p entries,
+// entry (r - 1) * Ns_p + k = exp(-2 pi i r k / (Ns_p R_p)), so the lanes of a
+// warp (consecutive k) read consecutive entries.  (log2 is unused: -1.)
 template <typename T>
 struct Tw {
     const cx<T>* __restrict__ hi;
@@ -141,7 +140,6 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
     const int log2nbf = log2n - LR;                 // butterflies per transform = n / R
     const int total = 1 << (log2nb + log2nbf);
     const int Ns = 1 << log2Ns;
-    const int twsh = tw.log2 - log2Ns - LR;         // table index = r * k << twsh
     cx<T> v[NB][R];
     int obase[NB];
 #pragma unroll
@@ -167,7 +165,7 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
             if (log2Ns > 0) {
 #pragma unroll
                 for (int r = 1; r < R; r++) {
-                    const int ti = tw.log2 >= 0 ? (r * k) << twsh : stage_off + (r - 1) * Ns + k;
+                    const int ti = stage_off + (r - 1) * Ns + k;
                     const cx<T> w = tw.hi[ti];
                     if constexpr (ACC && sizeof(T) == 4) {
                         const cx<T> wl = tw.lo[ti];
@@ -246,15 +244,6 @@ __host__ __device__ inline int fft_schedule(int log2n, int ppt, int* lr, int* ln
         p++;
     }
     return p;
-}
-
-// Older call form (no padding, single-precision constants).
-template <typename T, int PPT, bool COLS, bool INV>
-__device__ __forceinline__ void fft_batched(cx<T>* buf, int log2n, int log2nb, int si, int sb,
-                                            const cx<T>* __restrict__ tw, int tw_log2, int tid, int nthr)
-{
-    Tw<T> t{tw, nullptr, tw_log2};
-    fft_batched<T, PPT, COLS, INV, false, false>(buf, log2n, log2nb, si, sb, t, tid, nthr);
 }
 
 }  // namespace kzk
