@@ -220,8 +220,8 @@ kzk_status kzk_get_tables(kzk_plan *plan, double *E, double *Phi1, double *Phi2)
  * of the nonlinear weights, conjugated multipliers, adjoint FFTs), with a
  * checkpoint of the forward state every ckpt_every steps (>= 1) and
  * recomputation of each segment.  u0 is not modified.  g0 may alias g_end.
- * KZK_ERR_SIZE on a mixed-radix plan (the adjoint kernels are power-of-two
- * only; so is kzk_advance_checkpointed). */
+ * Mixed-radix plans: KZK_ERR_SIZE when nx has no divisor in [4, 16] with
+ * nx / divisor <= 512 (the transposed row pass's chunks). */
 kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *g0,
                        int64_t n_steps, double sigma0, int32_t ckpt_every, void *stream);
 

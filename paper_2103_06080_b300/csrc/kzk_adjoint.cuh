@@ -80,14 +80,16 @@ __device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps
 }
 
 // J_WENO(u)^T mu over the points [k0, k0+Q) of one periodic row (u, mu, g:
-// padded row buffers of nx reals): own-point sums go to g, the two
+// row buffers of nx reals, PAD layout): own-point sums go to g, the two
 // contributions left of k0 to spl[0..1] and the three right of k0+Q-1 to
-// spr[0..2] (added by the neighbours afterwards).
-template <typename T>
+// spr[0..2] (added by the neighbours afterwards).  POW2: nx a power of two
+// (the periodic wrap is a mask); otherwise any nx >= 8.
+template <typename T, bool PAD = true, bool POW2 = true>
 __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu, cx<T>* g, T* spl, T* spr,
                                                  int nx, int k0, int Q, const WenoCoef<T>& c)
 {
     const int msk = nx - 1;
+    auto wrap = [&](int kk) { return POW2 ? (kk & msk) : (kk < 0 ? kk + nx : (kk >= nx ? kk - nx : kk)); };
     const T half = T(0.5);
     const T eps4 = T(4) * c.eps;
     const T inv_dtau6 = c.inv_dtau * (T(1) / T(6));
@@ -95,7 +97,7 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
     // window slot s <-> point k - 2 + s for interface k + 1/2, starting at k = k0
 #pragma unroll
     for (int s = 0; s < 6; s++) {
-        const T v = ld_real<T, true>(u, (k0 - 2 + s) & msk);
+        const T v = ld_real<T, PAD>(u, wrap(k0 - 2 + s));
         const T f = fma(-c.c, v, -half * c.B * v * v);
         fp[s] = half * fma(c.alpha, v, f);
         fm[s] = half * fma(-c.alpha, v, f);
@@ -103,10 +105,10 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
         dm[s] = half * ((-c.alpha - c.c) - c.B * v);
         acc[s] = T(0);
     }
-    T mk_ = ld_real<T, true>(mu, k0 & msk);
+    T mk_ = ld_real<T, PAD>(mu, wrap(k0));
     for (int i = 0; i < Q; i++) {
         const int k = k0 + i;
-        const T mk1 = ld_real<T, true>(mu, (k + 1) & msk);
+        const T mk1 = ld_real<T, PAD>(mu, wrap(k + 1));
         const T psi6 = (mk1 - mk_) * inv_dtau6;
         mk_ = mk1;
         T gp[5], gm[5];
@@ -119,12 +121,12 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
         // point k - 2 is complete
         const int pt = k - 2;
         if (pt < k0) spl[pt - (k0 - 2)] = acc[0];
-        else st_real<T, true>(g, pt, acc[0]);
+        else st_real<T, PAD>(g, pt, acc[0]);
 #pragma unroll
         for (int s = 0; s < 5; s++) {
             fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; dp[s] = dp[s + 1]; dm[s] = dm[s + 1]; acc[s] = acc[s + 1];
         }
-        const T v = ld_real<T, true>(u, (k + 4) & msk);
+        const T v = ld_real<T, PAD>(u, wrap(k + 4));
         const T f = fma(-c.c, v, -half * c.B * v * v);
         fp[5] = half * fma(c.alpha, v, f);
         fm[5] = half * fma(-c.alpha, v, f);
@@ -136,7 +138,7 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
 #pragma unroll
     for (int s = 0; s < 5; s++) {
         const int pt = k0 + Q - 2 + s;
-        if (pt < k0 + Q) st_real<T, true>(g, pt, acc[s]);
+        if (pt < k0 + Q) st_real<T, PAD>(g, pt, acc[s]);
         else spr[pt - (k0 + Q)] = acc[s];
     }
 }

@@ -137,6 +137,8 @@ struct kzk_plan_s {
     void* wsc;                  // device [batch][ny][nx/2]: P1' FFT_y(b1) between the two C1 launches
     int mrow_thr, mcol_lc;
     size_t mrow_smem, mcol_smem;
+    int madj_thr, madj_Q;       // transposed row pass: threads, WENO chunk length (0: not available)
+    size_t madj_smem;
     // FP32 plans: compensated state (the spectral state as hi + lo; the column
     // passes transform increments, with the table (E - 1)/ny)
     int comp;
@@ -276,6 +278,22 @@ kzk_status configure_mixed(kzk_plan* p)
     if (p->mrow_smem > (size_t)optin || p->mcol_smem > (size_t)optin)
         return fail(KZK_ERR_SIZE, "grid %d x %d needs more shared memory than the device offers", p->nx, p->ny);
     p->colp_log2tc = -1;
+    // transposed row pass: chunks of Q points (the largest divisor of nx in
+    // [4, 16]), one thread per chunk
+    p->madj_Q = 0;
+    for (int q = 16; q >= 4; q--)
+        if (p->nx % q == 0 && p->nx / q <= MIX_ROW_MAX_THREADS) { p->madj_Q = q; break; }
+    if (p->madj_Q) {
+        p->madj_thr = std::max(64, (p->nx / p->madj_Q + 31) / 32 * 32);
+        p->madj_smem = mix_adj_row_smem<T>(p->nx, p->madj_thr);
+        if (p->madj_smem > (size_t)optin) p->madj_Q = 0;
+    }
+    KZK_CUDA(cudaFuncSetAttribute(mix_adj_row_kernel<T, ADJ_ROW_1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_adj_row_kernel<T, ADJ_ROW_2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_adj_col_kernel<T, MIX_ADJ_C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_adj_col_kernel<T, MIX_ADJ_C1A>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_adj_col_kernel<T, MIX_ADJ_C1B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(ysweepT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(mix_row_kernel<T, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(mix_row_kernel<T, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(mix_row_kernel<T, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -986,7 +1004,52 @@ kzk_status adj_row_stage(kzk_plan* p, const void* m, const void* u, const void* 
         r.yT = (const T*)p->by;
     }
     const dim3 rgrid(p->ny, p->batch);
+    if (p->mixed) {
+        MixAdjRowArgs<T> m{};
+        m.r = r;
+        m.nx = p->nx;
+        m.Q = p->madj_Q;
+        m.f = p->mrow;
+        m.pos = p->mpos_row;
+        mix_adj_row_kernel<T, MODE><<<rgrid, p->madj_thr, p->madj_smem, st>>>(m);
+        KZK_LAUNCHED();
+        return KZK_OK;
+    }
     adj_row_kernel<T, row_ppt<T>(), MODE><<<rgrid, p->adj_row_thr, adj_row_smem<T>(p), st>>>(r);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
+// Transposed column pass (adj_col_kernel, or on mixed-radix grids the
+// mix_adj_col_kernel launches: ADJ_COL_1 as two, through the scratch array).
+template <typename T, int MODE>
+kzk_status launch_adj_col(const kzk_plan* p, const AdjColArgs<T>& c, cudaStream_t st)
+{
+    if (p->mixed) {
+        MixAdjColArgs<T> m{};
+        m.c = c;
+        m.c.tw = (const cx<T>*)p->twc;
+        m.w = (cx<T>*)p->wsc;
+        m.ny = p->ny;
+        m.n = p->n;
+        m.lc = p->mcol_lc;
+        m.f = p->mcol;
+        m.pos = p->mpos_col;
+        m.ipos = p->mipos_col;
+        const dim3 grid(p->n >> p->mcol_lc, p->batch);
+        if (MODE == ADJ_COL_2) {
+            mix_adj_col_kernel<T, MIX_ADJ_C2><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+            KZK_LAUNCHED();
+        } else {
+            mix_adj_col_kernel<T, MIX_ADJ_C1A><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+            KZK_LAUNCHED();
+            mix_adj_col_kernel<T, MIX_ADJ_C1B><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+            KZK_LAUNCHED();
+        }
+        return KZK_OK;
+    }
+    const dim3 cgrid(p->n >> p->log2tc, p->batch);
+    adj_col_kernel<T, col_ppt_of<T>(), MODE><<<cgrid, p->col_thr, p->col_smem, st>>>(c);
     KZK_LAUNCHED();
     return KZK_OK;
 }
@@ -994,7 +1057,6 @@ kzk_status adj_row_stage(kzk_plan* p, const void* m, const void* u, const void* 
 template <typename T>
 kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* us, cudaStream_t st)
 {
-    const dim3 cgrid(p->n >> p->log2tc, p->batch);
     if (p->c.method == KZK_EXPEULER) {
         // transpose of u' = P_E u + P_{ds Phi1} G_n(u): with mu2 = 0 the
         // stage-1 column pass gives lam_lin = P_{conj E} lam', nu1 =
@@ -1010,8 +1072,7 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* u
         c1.sa = (T)1;
         c1.Tb = (const cx<T>*)p->P1;
         c1.sb = (T)p->nx;
-        adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
-        KZK_LAUNCHED();
+        KZK_TRY((launch_adj_col<T, ADJ_COL_1>(p, c1, st)));
         return adj_row_stage<T, ADJ_ROW_1>(p, p->nu, un, p->ls, p->lam, sigma, 0, st);
     }
     // mu2 = P_{conj(ds Phi2)} lam'
@@ -1020,8 +1081,7 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* u
     c2.out = (cx<T>*)p->mu;
     c2.Ta = (const cx<T>*)p->P2;
     c2.sa = (T)p->nx;
-    adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_2><<<cgrid, p->col_thr, p->col_smem, st>>>(c2);
-    KZK_LAUNCHED();
+    KZK_TRY((launch_adj_col<T, ADJ_COL_2>(p, c2, st)));
     // lam* = lam' + J_{G_{n+1}}(u*)^T mu2
     KZK_TRY((adj_row_stage<T, ADJ_ROW_2>(p, p->mu, us, p->lam, p->ls, sigma + p->dt, 1, st)));
     // lam_lin = P_{conj E} lam*,  nu1 = P_{conj(ds Phi1)} lam* - mu2
@@ -1034,8 +1094,7 @@ kzk_status adjoint_step(kzk_plan* p, double sigma, const void* un, const void* u
     c1.sa = (T)1;
     c1.Tb = (const cx<T>*)p->P1;
     c1.sb = (T)p->nx;
-    adj_col_kernel<T, col_ppt_of<T>(), ADJ_COL_1><<<cgrid, p->col_thr, p->col_smem, st>>>(c1);
-    KZK_LAUNCHED();
+    KZK_TRY((launch_adj_col<T, ADJ_COL_1>(p, c1, st)));
     // lam = lam_lin + J_{G_n}(u)^T nu1
     return adj_row_stage<T, ADJ_ROW_1>(p, p->nu, un, p->ls, p->lam, sigma, 0, st);
 }
@@ -1984,7 +2043,7 @@ kzk_status kzk_advance_checkpointed(kzk_plan* p, void* u, int64_t n_steps, doubl
     if (!p || !u) return fail(KZK_ERR_ARG, "plan or u is NULL");
     if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
     if (n_steps < 1 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 1 and ckpt_every >= 1");
-    if (p->mixed) return fail(KZK_ERR_SIZE, "the adjoint kernels need a power-of-two grid");
+    if (p->mixed && !p->madj_Q) return fail(KZK_ERR_SIZE, "nx = %d: no transposed row pass for this length", p->nx);
     cudaStream_t st = (cudaStream_t)stream;
     p->ck_steps = 0;
     if (p->prec == KZK_FP64) {
@@ -2009,7 +2068,7 @@ kzk_status kzk_adjoint(kzk_plan* p, const void* u0, const void* g_end, void* g0,
 {
     if (!p || !u0 || !g_end || !g0) return fail(KZK_ERR_ARG, "NULL argument");
     if (n_steps < 0 || ckpt_every < 1) return fail(KZK_ERR_ARG, "need n_steps >= 0 and ckpt_every >= 1");
-    if (p->mixed) return fail(KZK_ERR_SIZE, "the adjoint kernels need a power-of-two grid");
+    if (p->mixed && !p->madj_Q) return fail(KZK_ERR_SIZE, "nx = %d: no transposed row pass for this length", p->nx);
     cudaStream_t st = (cudaStream_t)stream;
     if (n_steps == 0) {
         if (g0 != g_end)

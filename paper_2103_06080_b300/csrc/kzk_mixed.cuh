@@ -25,7 +25,11 @@
 //   MIX_C1V: V* = IFFT_y(E' FFT_y(V) + W)
 // and the second column pass is unchanged:
 //   MIX_C2:  V' = V* + IFFT_y(P2' FFT_y(b2 - b1)).
+// The transposed step (the adjoint) has its row pass (mix_adj_row_kernel)
+// and column passes (mix_adj_col_kernel) on the same transforms; its
+// two-output column pass is split the same way, through the same scratch.
 #pragma once
+#include "kzk_adjoint.cuh"
 #include "kzk_kernels.cuh"
 
 namespace kzk {
@@ -537,6 +541,175 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
         } else {
             a.out[g] = MODE == MIX_C1V ? S[e] : add<T>(__ldcg(a.c + g), S[e]);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Transposed step (adjoint) on mixed-radix grids: the row pass of
+// adj_row_kernel and the column passes of adj_col_kernel.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct MixAdjRowArgs {
+    AdjRowArgs<T> r;        // as for power-of-two rows (log2nx and tws unused)
+    int nx, Q;              // row length; points per WENO chunk (Q divides nx)
+    MixFFT f;               // length nx / 2 on r.tw (stride 2)
+    const int* pos;         // [nx / 2]
+};
+
+template <typename T>
+__host__ __forceinline__ size_t mix_adj_row_smem(int nx, int nthr)
+{
+    return 3 * (size_t)(nx / 2) * sizeof(cx<T>) + 5 * (size_t)nthr * sizeof(T);
+}
+
+// One row of J_G^T (see adj_row_kernel): the physical state row, the C2R of
+// the cotangent row, the WENO5 transpose over chunks of Q points (chunk
+// boundaries exchange their spilled sums), the transposed y part, R2C.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(MIX_ROW_MAX_THREADS) mix_adj_row_kernel(MixAdjRowArgs<T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const AdjRowArgs<T>& a = A.r;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nx = A.nx, n = nx >> 1;
+    const int row = blockIdx.x, inst = blockIdx.y;
+    cx<T>* U = reinterpret_cast<cx<T>*>(smem_raw);
+    cx<T>* M = U + n;
+    cx<T>* G = M + n;
+    T* spl = reinterpret_cast<T*>(G + n);
+    T* spr = spl + 2 * nthr;
+    const long long base = (long long)inst * a.inst_stride + (long long)row * n;
+    const int* pos = A.pos;
+
+    const T* urow = a.u + 2 * base;
+    for (int i = tid; i < nx; i += nthr) st_real<T, false>(U, i, __ldcg(urow + i));
+    for (int k = tid; k <= n / 2; k += nthr) {
+        const int kn = k == 0 ? 0 : n - k;
+        cx<T> zk, znk;
+        c2r_vals<T>(__ldcg(a.m + base + k), __ldcg(a.m + base + kn), __ldg(a.tw + k), k, n, zk, znk);
+        M[__ldg(pos + k)] = zk;
+        if (k != 0 && 2 * k != n) M[__ldg(pos + kn)] = znk;
+    }
+    __syncthreads();
+    mix_inverse<T, false>(M, A.f, 0, a.tw, nullptr, tid, nthr);
+
+    const int Q = A.Q, nact = nx / Q, k0 = tid * Q;
+    WenoCoef<T> wc = a.wc;
+    if (a.med_coef) {
+        const double cj = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * row);
+        wc.c = (T)cj;
+        wc.alpha = (T)(fabs(cj) + (double)a.wc.alpha);
+    }
+    if (tid < nact) weno_row_chunk_T<T, false, false>(U, M, G, spl + 2 * tid, spr + 3 * tid, nx, k0, Q, wc);
+    __syncthreads();
+    if (tid < nact) {
+        const int left = (tid + nact - 1) % nact, right = (tid + 1) % nact;
+        for (int s = 0; s < 3; s++) st_real<T, false>(G, k0 + s, ld_real<T, false>(G, k0 + s) + spr[3 * left + s]);
+        st_real<T, false>(G, k0 + Q - 2, ld_real<T, false>(G, k0 + Q - 2) + spl[2 * right + 0]);
+        st_real<T, false>(G, k0 + Q - 1, ld_real<T, false>(G, k0 + Q - 1) + spl[2 * right + 1]);
+    }
+    __syncthreads();
+    if (a.yT) {
+        const T* yrow = a.yT + 2 * base;
+        for (int k = tid; k < nx; k += nthr) st_real<T, false>(G, k, ld_real<T, false>(G, k) + __ldcg(yrow + k));
+        __syncthreads();
+    }
+    mix_forward<T, false>(G, A.f, 0, a.tw, nullptr, tid, nthr);
+    for (int k = tid; k <= n / 2; k += nthr) {
+        const int kn = k == 0 ? 0 : n - k;
+        cx<T> xk, xnk;
+        r2c_vals<T>(G[__ldg(pos + k)], G[__ldg(pos + kn)], __ldg(a.tw + k), k, n, xk, xnk);
+        xk = scale<T>(xk, a.inv_nx);
+        xnk = scale<T>(xnk, a.inv_nx);
+        const cx<T> mk0 = __ldcg(a.m + base + k);
+        const cx<T> lk = __ldcg(a.l + base + k);
+        if (k == 0) {
+            const T kN = a.kscale * T(n);
+            xk.y -= a.dA * kN * kN * mk0.y;
+            a.out[base] = add<T>(lk, xk);
+        } else {
+            const T kt = a.kscale * T(k);
+            xk.x -= a.dA * kt * kt * mk0.x;
+            xk.y -= a.dA * kt * kt * mk0.y;
+            a.out[base + k] = add<T>(lk, xk);
+            if (2 * k != n) {
+                const T kt2 = a.kscale * T(n - k);
+                const cx<T> mk2 = __ldcg(a.m + base + n - k);
+                xnk.x -= a.dA * kt2 * kt2 * mk2.x;
+                xnk.y -= a.dA * kt2 * kt2 * mk2.y;
+                a.out[base + n - k] = add<T>(__ldcg(a.l + base + n - k), xnk);
+            }
+        }
+    }
+}
+
+// Transposed column passes: MIX_ADJ_C2: out = IFFT(sa conj(Ta) FFT(a));
+// MIX_ADJ_C1A: z = FFT(a) (kept in the scratch w, transformed order),
+// out = IFFT(sa conj(Ta) z); MIX_ADJ_C1B: out2 = IFFT(sb conj(Tb) z) - b.
+// (out may alias a: z is saved before out is written.)
+enum MixAdjColMode { MIX_ADJ_C2 = 0, MIX_ADJ_C1A = 1, MIX_ADJ_C1B = 2 };
+
+template <typename T>
+struct MixAdjColArgs {
+    AdjColArgs<T> c;        // a, b, out, out2, Ta, Tb, sa, sb, inst_stride (tw: full y table)
+    cx<T>* w;               // scratch [batch][ny][nx/2]
+    int ny, n, lc;
+    MixFFT f;
+    const int* pos;
+    const int* ipos;
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(MIX_COL_THREADS) mix_adj_col_kernel(MixAdjColArgs<T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T>* S = reinterpret_cast<cx<T>*>(smem_raw);
+    const AdjColArgs<T>& a = A.c;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ny = A.ny, n = A.n, lc = A.lc, TC = 1 << lc;
+    const int m0 = blockIdx.x * TC, inst = blockIdx.y;
+    const long long ibase = (long long)inst * a.inst_stride;
+    const int total = ny << lc;
+    auto gidx = [&](int e) -> long long { return ibase + (long long)(e >> lc) * n + m0 + (e & (TC - 1)); };
+
+    if constexpr (MODE == MIX_ADJ_C1B) {
+        for (int e = tid; e < total; e += nthr) S[e] = __ldcg(A.w + gidx(e));
+        __syncthreads();
+    } else {
+        for (int e = tid; e < total; e += nthr) S[e] = __ldcg(a.a + gidx(e));
+        __syncthreads();
+        mix_forward<T, false>(S, A.f, lc, a.tw, nullptr, tid, nthr);
+        if constexpr (MODE == MIX_ADJ_C1A) {
+            for (int e = tid; e < total; e += nthr) A.w[gidx(e)] = S[e];
+            __syncthreads();    // the packed column's pairs are rewritten below
+        }
+    }
+    const cx<T>* Tm = MODE == MIX_ADJ_C1B ? a.Tb : a.Ta;
+    const T sm = MODE == MIX_ADJ_C1B ? a.sb : a.sa;
+    for (int e = tid; e < total; e += nthr) {
+        const int c = e & (TC - 1), m = m0 + c;
+        if (m == 0) continue;
+        const int l = __ldg(A.ipos + (e >> lc));
+        const int lf = l <= (ny >> 1) ? l : ny - l;
+        S[e] = mulc<T>(S[e], scale<T>(__ldg(Tm + (long long)lf * n + m), sm));
+    }
+    if (m0 == 0) {
+        for (int l = tid; l <= (ny >> 1); l += nthr) {
+            const int lm = l == 0 ? 0 : ny - l;
+            const int e = __ldg(A.pos + l) << lc, em = __ldg(A.pos + lm) << lc;
+            const cx<T> M = scale<T>(__ldg(Tm + (long long)l * n), sm);
+            const cx<T> z = S[e], zm = S[em];
+            S[e] = conj_mult_entry<T>(M, z, zm, true);
+            if (lm != l) S[em] = conj_mult_entry<T>(M, zm, z, true);
+        }
+    }
+    __syncthreads();
+    mix_inverse<T, false>(S, A.f, lc, a.tw, nullptr, tid, nthr);
+    for (int e = tid; e < total; e += nthr) {
+        const long long g = gidx(e);
+        if constexpr (MODE == MIX_ADJ_C1B) a.out2[g] = sub<T>(S[e], __ldcg(a.b + g));
+        else a.out[g] = S[e];
     }
 }
 

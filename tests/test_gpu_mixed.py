@@ -6,8 +6,10 @@ The same bars as the power-of-two path: FP64 relative L-infinity within 1e-11
 after whole runs (tighter for single operations), FP32 relative l2 within
 1e-5.  Sizes include single and several column tiles, odd half lengths
 (nx / 2 odd), every radix (2, 3, 4, 5, 7, 8), the random medium, exponential
-Euler and batches; the paper's largest grid (3584 x 10000) is checked against
-the closed form of a propagating Fourier mode, which holds at any size.
+Euler, batches and the adjoint (against the oracle's transposed step and
+finite differences); the paper's largest grid (3584 x 10000) is checked
+against the closed form of a propagating Fourier mode, which holds at any
+size.
 """
 import numpy as np
 import pytest
@@ -183,8 +185,46 @@ def test_unsupported_sizes_and_features_are_refused():
         with pytest.raises(Exception):
             api.Plan(nx=nx, ny=ny, dt=0.01)
     w = inputs.config(2, nx=56, ny=50, n_steps=4)
-    plan = api.Plan.from_workload(w)
-    with pytest.raises(Exception):
-        plan.adjoint(_dev(w.u0), _dev(w.u0), 4, ckpt_every=2)
     with pytest.raises(Exception):
         api.BatchedPlan([w], precision="fp64")
+
+
+@pytest.mark.parametrize("nx,ny,prec,tol,method,medium", [
+    (56, 50, "fp64", 1e-10, "exprk22", False), (448, 250, "fp64", 1e-10, "exprk22", False),
+    (30, 18, "fp64", 1e-10, "expeuler", False), (112, 50, "fp64", 1e-10, "exprk22", True),
+    (448, 250, "fp32", 3e-3, "exprk22", False)])
+def test_adjoint_matches_oracle(nx, ny, prec, tol, method, medium):
+    api = _api()
+    n = 8
+    w = inputs.medium_config(nx, ny, n) if medium else inputs.config(2, nx=nx, ny=ny, n_steps=n)
+    plan = api.Plan.from_workload(w, precision=prec, method=method)
+    p = oracle.Params(**inputs.oracle_params(w, method=1 if method == "expeuler" else 0))
+    g_end = 2 * w.dtau * oracle.run(p, w.u0, n)
+    ref = oracle.adjoint(p, w.u0, g_end, n)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    g0 = plan.adjoint(_dev(w.u0, dt), _dev(g_end, dt), n, ckpt_every=3)
+    assert rel_linf(g0.double().cpu().numpy(), ref) < tol
+
+
+def test_adjoint_finite_differences_on_a_paper_grid_shape():
+    # Set 1 of Table 1 (448 x 1250), a few steps: <g0, v> against central differences
+    api = _api()
+    w = inputs.config(2, nx=448, ny=1250, n_steps=4)
+    plan = api.Plan.from_workload(w)
+    u0 = _dev(w.u0)
+
+    def loss(u):
+        v = u.clone()
+        plan.advance(v, w.n_steps)
+        return float((v * v).sum()) * w.dtau
+
+    y = u0.clone()
+    plan.advance(y, w.n_steps)
+    g0 = plan.adjoint(u0, 2 * w.dtau * y, w.n_steps, ckpt_every=2).cpu().numpy()
+    rng = np.random.default_rng(41)
+    for _ in range(2):
+        v = rng.standard_normal(w.u0.shape)
+        v /= np.linalg.norm(v)
+        h = 1e-6
+        fd = (loss(u0 + h * _dev(v)) - loss(u0 - h * _dev(v))) / (2 * h)
+        assert abs(np.sum(g0 * v) - fd) < 1e-6 * np.linalg.norm(g0)
