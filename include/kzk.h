@@ -242,7 +242,8 @@ kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *
  * for the column passes, the same computation as kzk_advance -- separated by
  * grid barriers whose waits are bounded (KZK_ERR_TIMEOUT).  With
  * KZK_BATCH_AUTOTUNE the column-tile width is chosen by timing two steps of
- * each candidate at creation.  Each grid must be a power of two, nx <= 8192. */
+ * each candidate at creation.  Each grid must be a power of two, nx <= 8192
+ * (with KZK_BATCH_STREAMS any grid kzk_plan_create accepts). */
 kzk_status kzk_plan_create_batched(const kzk_grid *grids, const kzk_coeffs *coeffs, const double *dts,
                                    int32_t n, int32_t flags, kzk_plan **out);
 

@@ -1870,7 +1870,10 @@ kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coef
         if (s != KZK_OK) { plan_free(p); return s; }
         p->subs->push_back(q);
         if (q->nx > 8192) { plan_free(p); return fail(KZK_ERR_SIZE, "instance %d too large", i); }
-        if (q->mixed) { plan_free(p); return fail(KZK_ERR_SIZE, "instance %d: batched plans need power-of-two grids", i); }
+        if (q->mixed && !(flags & KZK_BATCH_STREAMS)) {
+            plan_free(p);
+            return fail(KZK_ERR_SIZE, "instance %d: the persistent batched kernel needs power-of-two grids", i);
+        }
     }
     cudaError_t e = cudaMalloc(&p->binst, (size_t)n * std::max(sizeof(BatchInst<float>), sizeof(BatchInst<double>)));
     if (e == cudaSuccess) e = cudaMalloc(&p->row_prefix, (n + 1) * sizeof(int));

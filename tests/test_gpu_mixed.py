@@ -186,7 +186,30 @@ def test_unsupported_sizes_and_features_are_refused():
             api.Plan(nx=nx, ny=ny, dt=0.01)
     w = inputs.config(2, nx=56, ny=50, n_steps=4)
     with pytest.raises(Exception):
-        api.BatchedPlan([w], precision="fp64")
+        api.BatchedPlan([w], precision="fp64", mode="persistent")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_streams_with_mixed_and_power_of_two_instances(prec):
+    """One graph launch advancing instances of the paper's grid shapes next to
+    power-of-two ones: every instance equals its own plan, bit for bit."""
+    api = _api()
+    ws = [inputs.config(2, nx=448, ny=250, n_steps=6), inputs.config(2, nx=512, ny=128, n_steps=6),
+          inputs.config(2, nx=56, ny=50, n_steps=6)]
+    for w in ws:
+        w.precision = prec
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    bp = api.BatchedPlan(ws, precision=prec, mode="streams")
+    us = [_dev(w.u0, dt) for w in ws]
+    st, _ = bp.advance(us, 6, diag=True)
+    assert st == 0
+    for w, u in zip(ws, us):
+        p = api.Plan.from_workload(w, precision=prec)
+        v = _dev(w.u0, dt)
+        p.advance(v, 6)
+        assert torch.equal(u, v), (w.nx, w.ny)
+        p.close()
+    bp.close()
 
 
 @pytest.mark.parametrize("nx,ny,prec,tol,method,medium", [
