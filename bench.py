@@ -97,12 +97,15 @@ def row_bytes(nx, ny, w):
     return 2 * nx * ny * w
 
 
-def col_bytes(nx, ny, w, stage):
-    """Column pass: stage 1 reads V, b1 and the folded E', P1' (half an array
-    each) and writes V*; stage 2 reads b1, b2, V*, folded P2' and writes V'."""
+def col_bytes(nx, ny, w, stage, comp=False):
+    """Column pass: stage 1 reads V, b1 and the folded E' (or (E - 1)'), P1'
+    (half an array each) and writes V*; stage 2 reads b1, b2, V*, folded P2'
+    and writes V'.  comp (the compensated FP32 state): each stage also reads
+    and writes the lo part (a bf16 pair per complex value: half an array)."""
     unit = nx * ny * w
     tab = (ny // 2 + 1) * (nx // 2) * 2 * w
-    return (3 * unit + 2 * tab) if stage == 1 else (4 * unit + tab)
+    lo = unit if comp else 0                        # lo in + lo out, half an array each
+    return (3 * unit + 2 * tab + lo) if stage == 1 else (4 * unit + tab + lo)
 
 
 def row_flops(nx, ny, profile=True):
@@ -295,8 +298,9 @@ def run_ours(args, rank, world, local_rank):
     kt = plan.kernel_times(u, min(args.steps, 20), sigma0=0.0)
     names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
     fl = [row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 1), row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 2)]
-    by = [row_bytes(w.nx, w.ny, wsz), col_bytes(w.nx, w.ny, wsz, 1), row_bytes(w.nx, w.ny, wsz),
-          col_bytes(w.nx, w.ny, wsz, 2)]
+    comp = fp32 and os.environ.get("KZK_COMPSTATE", "1") != "0"
+    by = [row_bytes(w.nx, w.ny, wsz), col_bytes(w.nx, w.ny, wsz, 1, comp), row_bytes(w.nx, w.ny, wsz),
+          col_bytes(w.nx, w.ny, wsz, 2, comp)]
     dom = int(np.argmax(kt))
     peaks, peak_src = _peaks()
     if fp32:
@@ -353,6 +357,12 @@ def run_ours(args, rank, world, local_rank):
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{m} step(s) of the full 4096x2048 FP64 grid ({dt:.1f} s), "
                                           f"OpenMP oracle, first step untimed, then per-step timing inside the oracle"}
+        if not args.quick:
+            # the sequential build of the same oracle (the paper's "sequential" column)
+            r1, dt1, _, m1 = cpu_oracle_rate(w2, 1, threads=False)
+            line["cpu_baseline"]["single_core"] = {
+                "value": r1, "unit": UNIT, "cores": 1,
+                "sample": f"{m1} step of the full 4096x2048 FP64 grid ({dt1:.1f} s), sequential oracle build"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -473,8 +483,9 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
     torch.cuda.synchronize()
     ms3 = e0.elapsed_time(e1)
     kt3 = p3.kernel_times(u3, 20)
-    by3 = [row_bytes(4096, 2048, 4), col_bytes(4096, 2048, 4, 1), row_bytes(4096, 2048, 4),
-           col_bytes(4096, 2048, 4, 2)]
+    comp3 = os.environ.get("KZK_COMPSTATE", "1") != "0"
+    by3 = [row_bytes(4096, 2048, 4), col_bytes(4096, 2048, 4, 1, comp3), row_bytes(4096, 2048, 4),
+           col_bytes(4096, 2048, 4, 2, comp3)]
     names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
     dom = int(np.argmax(kt3))
     hbm = peaks["hbm_gbs"] * 1e9
