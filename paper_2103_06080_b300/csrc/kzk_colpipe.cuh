@@ -10,9 +10,10 @@
 //   STAGE2: b1, b2 and the P2' slice, then V* once b2 has been consumed.
 // The first forward pass reads the dense tiles and writes the padded work
 // tiles over them; the phi-multiply is applied while the last forward pass
-// stores (STAGE1 reads E', E'_lo, P1' from L2: the multiply needs each table
-// entry twice, for rows l and ny - l); the last inverse pass writes HBM
-// directly.  The CTA also prefetches into L2 the copies of the tile a CTA one
+// stores (STAGE1 reads E', E'_lo, P1' from L2 -- with the compensated FP32
+// state (E - 1)' and P1' -- the multiply needs each table entry twice, for rows
+// l and ny - l); the last inverse pass writes HBM directly (with the
+// compensated state: adds the increment to hi + lo by TwoSum).  The CTA also prefetches into L2 the copies of the tile a CTA one
 // wave later will take.  Arithmetic and rounding are those of col_body
 // (kzk_kernels.cuh): the same passes, twiddles and products in the same order.
 //
@@ -285,7 +286,7 @@ __device__ __forceinline__ void tile_last(int log2n, int log2tc, const Tw<T>& tw
 
 // ---------------------------------------------------------------------------
 // Paired passes (STAGE1 forward): the state tile A (two-float constants in
-// FP32) and the b1 tile B go through the same butterflies between one pair of
+// FP32 with the plain state) and the b1 tile B go through the same butterflies between one pair of
 // barriers, so a thread holds both spectra at the same positions when the last
 // pass stores -- the multiply then reads b1_hat from registers.
 // ---------------------------------------------------------------------------
@@ -301,7 +302,8 @@ struct PadIO2 {
     }
 };
 
-// V*_hat = E' V_hat (+ E'_lo V_hat in FP32) + P1' b1_hat, tables read from
+// V*_hat = E' V_hat (+ E'_lo V_hat in FP32; the compensated state passes
+// (E - 1)' and no lo part) + P1' b1_hat, tables read from
 // global memory (L2); the packed column m = 0 keeps both spectra untouched for
 // the row-pair combination
 template <typename T, bool ACC>

@@ -385,7 +385,9 @@ constexpr int COL_MAX_THREADS = 1024;
 //  STAGE1 (STEP 2): shared memory holds two tiles [ny][2 TC]: columns [0, TC)
 //    the state V, [TC, 2 TC) b1.  FFT both along y (the state's transform
 //    with two-float constants in FP32), combine E' V + P1' b1 into the state
-//    half, inverse FFT it (two-float again) and store V*.
+//    half, inverse FFT it (two-float again) and store V*.  Compensated FP32
+//    state (lo_out set): Ta = (E - 1)', and the result is the increment,
+//    added to V = a + lo_in by TwoSum into V* = out + lo_out.
 //  STAGE2 (STEP 4): one tile of b2 - b1, FFT, times P2', inverse FFT, plus V*.
 // Body of one column-tile task (tile index `tile`), run by all nthr =
 // blockDim.x threads of a CTA (nthr * PPT >= ny * TC).
