@@ -79,6 +79,76 @@ __device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps
     g[4] = w6 * (A2 + B2 - o2);
 }
 
+// The sliding form of weno5_grad for the row sweep.  Every 3-point stencil
+// centre c contributes S = f_{c-1} - 2 f_c + f_{c+1}, D = f_{c+1} - f_{c-1}
+// and Pe = 13/3 S^2 + eps4 once; a reconstruction takes its three stencils'
+// (s_r, t_r, E_r = t_r^2 + Pe) from the centres it spans, the t_r being the
+// combinations D + 2S, -D, 2S - D of weno5_grad's (s, t) pairs (mirrored for
+// the downwind side).
+template <typename T>
+struct GradCentre {
+    T S, D, Pe;
+};
+template <typename T>
+__device__ __forceinline__ GradCentre<T> grad_centre(T fm1, T f0, T fp1, T eps4)
+{
+    GradCentre<T> c;
+    c.S = fma(T(-2), f0, fm1 + fp1);
+    c.D = fp1 - fm1;
+    c.Pe = fma((T(13) / T(3)) * c.S, c.S, eps4);
+    return c;
+}
+template <typename T>
+struct GradPart {
+    T Q0, Q1, Q2, s0, t0, s1, t1, s2, t2, E0, E1, E2, a0, a1, a2, Ssum, e01, e012;
+};
+// candidates, weights and X = S E0 E1 E2 of one reconstruction from v_{-2..2}
+// and its stencils' (s, t, Pe)
+template <typename T>
+__device__ __forceinline__ void grad_prep(GradPart<T>& q, T vm2, T vm1, T v0, T v1, T v2, T s0, T t0, T Pe0, T s1,
+                                          T t1, T Pe1, T s2, T t2, T Pe2)
+{
+    q.Q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0));
+    q.Q1 = fma(T(5), v0, fma(T(2), v1, -vm1));
+    q.Q2 = fma(T(2), v0, fma(T(5), v1, -v2));
+    q.s0 = s0; q.t0 = t0; q.s1 = s1; q.t1 = t1; q.s2 = s2; q.t2 = t2;
+    q.E0 = fma(t0, t0, Pe0);
+    q.E1 = fma(t1, t1, Pe1);
+    q.E2 = fma(t2, t2, Pe2);
+    const T T0 = q.E0 * q.E0, T1 = q.E1 * q.E1, T2 = q.E2 * q.E2;
+    q.a0 = T1 * T2;
+    q.a1 = T(6) * (T0 * T2);
+    q.a2 = T(3) * (T0 * T1);
+    q.Ssum = q.a0 + q.a1 + q.a2;
+    q.e01 = q.E0 * q.E1;
+    q.e012 = q.e01 * q.E2;
+}
+// g[j] = 6 w6 dF/dv_j (as weno5_grad), given r = 1 / (S E0 E1 E2) (FP64)
+template <typename T>
+__device__ __forceinline__ void grad_finish(const GradPart<T>& q, T r, T w6, T* g)
+{
+    T inv, iE0, iE1, iE2;
+    if constexpr (sizeof(T) == 8) {
+        inv = r * q.e012;
+        const T rS = r * q.Ssum;
+        iE0 = rS * (q.E1 * q.E2); iE1 = rS * (q.E0 * q.E2); iE2 = rS * q.e01;
+    } else {
+        inv = __frcp_rn(q.Ssum); iE0 = __frcp_rn(q.E0); iE1 = __frcp_rn(q.E1); iE2 = __frcp_rn(q.E2);
+    }
+    const T o0 = q.a0 * inv, o1 = q.a1 * inv, o2 = q.a2 * inv;
+    const T F6 = fma(o0, q.Q0, fma(o1, q.Q1, o2 * q.Q2));
+    const T C0 = o0 * (q.Q0 - F6) * iE0, C1 = o1 * (q.Q1 - F6) * iE1, C2 = o2 * (q.Q2 - F6) * iE2;
+    const T k52 = T(-52) / T(3);
+    const T A0 = (k52 * C0) * q.s0, B0 = (T(-4) * C0) * q.t0;
+    const T A1 = (k52 * C1) * q.s1, B1 = (T(-4) * C1) * q.t1;
+    const T A2 = (k52 * C2) * q.s2, B2 = (T(-4) * C2) * q.t2;
+    g[0] = w6 * fma(T(2), o0, A0 + B0);
+    g[1] = w6 * (fma(T(-7), o0, A1 + B1 - o1) - fma(T(2), A0, T(4) * B0));
+    g[2] = w6 * (fma(T(11), o0, fma(T(5), o1, T(2) * o2)) + fma(T(3), B0 + B2, A0 + A2) - T(2) * A1);
+    g[3] = w6 * (fma(T(2), o1, fma(T(5), o2, A1 - B1)) - fma(T(2), A2, T(4) * B2));
+    g[4] = w6 * (A2 + B2 - o2);
+}
+
 // J_WENO(u)^T mu over the points [k0, k0+Q) of one periodic row (u, mu, g:
 // row buffers of nx reals, PAD layout): own-point sums go to g, the two
 // contributions left of k0 to spl[0..1] and the three right of k0+Q-1 to
@@ -106,14 +176,36 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
         acc[s] = T(0);
     }
     T mk_ = ld_real<T, PAD>(mu, wrap(k0));
+    // stencil centres: + side k0 - 1, k0 (points fp[0..3]); - side k0, k0 + 1 (fm[1..4])
+    GradCentre<T> cpA = grad_centre<T>(fp[0], fp[1], fp[2], eps4);   // + side, centre k - 1
+    GradCentre<T> cpB = grad_centre<T>(fp[1], fp[2], fp[3], eps4);   // + side, centre k
+    GradCentre<T> cmA = grad_centre<T>(fm[1], fm[2], fm[3], eps4);   // - side, centre k
+    GradCentre<T> cmB = grad_centre<T>(fm[2], fm[3], fm[4], eps4);   // - side, centre k + 1
     for (int i = 0; i < Q; i++) {
         const int k = k0 + i;
         const T mk1 = ld_real<T, PAD>(mu, wrap(k + 1));
         const T psi6 = (mk1 - mk_) * inv_dtau6;
         mk_ = mk1;
+        const GradCentre<T> cpC = grad_centre<T>(fp[2], fp[3], fp[4], eps4);   // + side, centre k + 1
+        const GradCentre<T> cmC = grad_centre<T>(fm[3], fm[4], fm[5], eps4);   // - side, centre k + 2
         T gp[5], gm[5];
-        weno5_grad<T>(fp[0], fp[1], fp[2], fp[3], fp[4], eps4, psi6, gp);
-        weno5_grad<T>(fm[5], fm[4], fm[3], fm[2], fm[1], eps4, psi6, gm);
+        {
+            GradPart<T> q;
+            grad_prep<T>(q, fp[0], fp[1], fp[2], fp[3], fp[4],
+                         cpA.S, fma(T(2), cpA.S, cpA.D), cpA.Pe, cpB.S, -cpB.D, cpB.Pe,
+                         cpC.S, fma(T(2), cpC.S, -cpC.D), cpC.Pe);
+            // X = S E0 E1 E2 >= eps^7: one FP64 division gives 1/S and the 1/E_r
+            grad_finish<T>(q, sizeof(T) == 8 ? T(1) / (q.Ssum * q.e012) : T(0), psi6, gp);
+        }
+        {
+            GradPart<T> q;
+            grad_prep<T>(q, fm[5], fm[4], fm[3], fm[2], fm[1],
+                         cmC.S, fma(T(2), cmC.S, -cmC.D), cmC.Pe, cmB.S, cmB.D, cmB.Pe,
+                         cmA.S, fma(T(2), cmA.S, cmA.D), cmA.Pe);
+            grad_finish<T>(q, sizeof(T) == 8 ? T(1) / (q.Ssum * q.e012) : T(0), psi6, gm);
+        }
+        cpA = cpB; cpB = cpC;
+        cmA = cmB; cmB = cmC;
 #pragma unroll
         for (int s = 0; s < 5; s++) acc[s] = fma(gp[s], dp[s], acc[s]);
 #pragma unroll
