@@ -79,7 +79,11 @@ typedef struct {
                                        over thousands of steps (KZK_COMPSTATE=0 in the
                                        environment: a plain FP32 state).  KZK_FP32 row
                                        passes run on row pairs in packed FP32
-                                       (KZK_ROWPAIR=0: single rows). */
+                                       (KZK_ROWPAIR=0: single rows); their column passes
+                                       stage tiles with the tensor memory accelerator
+                                       (KZK_COLPIPE=0: per-tile kernels with plain loads;
+                                       KZK_COLPIPE=2: the TMA kernels for KZK_FP64 too).
+                                       The environment is read at plan creation. */
 } kzk_grid;
 
 #define KZK_MAX_RELAX 2
