@@ -17,6 +17,9 @@
 #include "kzk_mixed.cuh"
 #include "kzk_rowpair.cuh"
 #include "kzk_tables.cuh"
+// after the FP64 headers: the pair type's overloads (kzk_rowpair.cuh) would hide
+// the scalar math functions they call inside namespace kzk
+#include "kzk_colpair.cuh"
 
 using namespace kzk;
 
@@ -148,6 +151,12 @@ struct kzk_plan_s {
     int rowpair;
     size_t rowpair_smem;
     void *twr2, *tws2;          // the tau twiddle tables with every entry as a lane pair
+    // FP32 plans with the compensated state: column passes on column pairs
+    // (kzk_colpair.cuh); colpair = 0: not used
+    int colpair, cpair_by, cpair_nby;
+    size_t cpair_smem1, cpair_smem2;
+    void *Em1p, *P1p, *P2p;     // (E - 1)', P1', P2' as pair tables [nx/4][pair_tab_rows(ny)]
+    void* twcp;                 // twiddles of the pair schedule, as lane pairs
 };
 
 namespace {
@@ -257,6 +266,46 @@ void colp_configure(kzk_plan* p, int optin)
     }
 }
 
+// Column-pair kernels (kzk_colpair.cuh): FP32 plans with the compensated
+// state, 256 <= ny <= 4096, unless KZK_COLPAIR=0 (then the TMA Stockham tile
+// kernels) or KZK_COLPIPE=0 (the per-tile kernels) in the environment.
+template <int L>
+kzk_status cpair_attr(kzk_plan* p, int optin)
+{
+    const size_t s1 = pair_layout<L, COL_STAGE1>().total;
+    const size_t s2 = pair_layout<L, COL_STAGE2>().total;
+    if (std::max(s1, s2) > (size_t)optin) return KZK_OK;
+    KZK_CUDA(cudaFuncSetAttribute(colpair_kernel<L, COL_STAGE1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(colpair_kernel<L, COL_STAGE2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    int per_sm = 0;
+    KZK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, colpair_kernel<L, COL_STAGE1>, PairSched<L>::T,
+                                                           s1));
+    if (per_sm < 1) return KZK_OK;
+    p->cpair_smem1 = s1;
+    p->cpair_smem2 = s2;
+    p->colpair = 1;
+    return KZK_OK;
+}
+template <typename T>
+kzk_status cpair_configure(kzk_plan* p, int optin)
+{
+    p->colpair = 0;
+    const char* env = getenv("KZK_COLPAIR");
+    const char* penv = getenv("KZK_COLPIPE");
+    if (sizeof(T) != 4 || !p->comp || p->mixed || (env && env[0] == '0') || (penv && penv[0] == '0'))
+        return KZK_OK;
+    if (p->log2ny < 8 || p->log2ny > 12 || p->n < 2 || !encode_tiled()) return KZK_OK;
+    p->cpair_by = std::min(p->ny, 256);
+    p->cpair_nby = p->ny / p->cpair_by;
+    switch (p->log2ny) {
+    case 8: return cpair_attr<8>(p, optin);
+    case 9: return cpair_attr<9>(p, optin);
+    case 10: return cpair_attr<10>(p, optin);
+    case 11: return cpair_attr<11>(p, optin);
+    default: return cpair_attr<12>(p, optin);
+    }
+}
+
 // Mixed-radix plans: one row per CTA; column tiles of the widest power of two
 // (at most 16) dividing nx/2 whose tile fits 96 KB (two CTAs per SM), else
 // single columns up to the device's shared-memory limit.
@@ -353,6 +402,7 @@ kzk_status configure(kzk_plan* p)
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_RHS_MED>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     }
     colp_configure<T>(p, optin);
+    KZK_TRY(cpair_configure<T>(p, optin));
     if (p->colp_log2tc >= 0) {
         KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -533,6 +583,50 @@ kzk_status launch_colp(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
     return KZK_OK;
 }
 
+// Column-pair kernels: state tiles {2 n, ny, batch} floats in boxes {4, by, 1};
+// pair tables by bulk copies; the lo parts of the state pair-major.
+template <int L, int MODE>
+kzk_status launch_colpair_l(const kzk_plan* p, const ColArgs<float>& a, cudaStream_t st)
+{
+    ColPairArgs P;
+    memset(&P, 0, sizeof(P));
+    P.c = a;
+    const cuuint64_t sdims[3] = {2ull * p->n, (cuuint64_t)p->ny, (cuuint64_t)p->batch};
+    const cuuint64_t sstr[2] = {2ull * p->n * sizeof(float), 2ull * p->n * p->ny * sizeof(float)};
+    const cuuint32_t sbox[3] = {4u, (cuuint32_t)p->cpair_by, 1u};
+    KZK_TRY(encode_map<float>(&P.ma, 3, a.a, sdims, sstr, sbox));
+    KZK_TRY(encode_map<float>(&P.mb, 3, a.b, sdims, sstr, sbox));
+    if (MODE == COL_STAGE1) {
+        P.tab0 = (const c2*)p->Em1p;
+        P.tab1 = (const c2*)p->P1p;
+    } else {
+        KZK_TRY(encode_map<float>(&P.mc, 3, a.c, sdims, sstr, sbox));
+        P.tab0 = (const c2*)p->P2p;
+    }
+    P.tw = (const c2*)p->twcp;
+    P.by = p->cpair_by;
+    P.nby = p->cpair_nby;
+    P.n_tiles = p->n / 2;
+    P.total = P.n_tiles * p->batch;
+    P.flag = p->colp_flag;
+    P.timeout_ns = 2000000000LL;
+    const size_t smem = MODE == COL_STAGE1 ? p->cpair_smem1 : p->cpair_smem2;
+    colpair_kernel<L, MODE><<<P.total, PairSched<L>::T, smem, st>>>(P);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+template <int MODE>
+kzk_status launch_colpair(const kzk_plan* p, const ColArgs<float>& a, cudaStream_t st)
+{
+    switch (p->log2ny) {
+    case 8: return launch_colpair_l<8, MODE>(p, a, st);
+    case 9: return launch_colpair_l<9, MODE>(p, a, st);
+    case 10: return launch_colpair_l<10, MODE>(p, a, st);
+    case 11: return launch_colpair_l<11, MODE>(p, a, st);
+    default: return launch_colpair_l<12, MODE>(p, a, st);
+    }
+}
+
 // Mixed-radix plans: STAGE1 as two launches (P1' FFT_y(b1) into the scratch
 // array, then the state's transform, propagator and inverse), STAGE2 as one.
 template <typename T, int MODE>
@@ -566,6 +660,8 @@ template <typename T, int MODE>
 kzk_status launch_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
 {
     if (p->mixed) return launch_mix_col<T, MODE>(p, a, st);
+    if constexpr (std::is_same<T, float>::value)
+        if (p->colpair) return launch_colpair<MODE>(p, a, st);
     if (p->colp_log2tc >= 0) return launch_colp<T, MODE>(p, a, st);
     col_kernel<T, MODE><<<dim3(p->n >> p->log2tc, p->batch), p->col_thr, p->col_smem, st>>>(a);
     KZK_LAUNCHED();
@@ -808,6 +904,35 @@ kzk_status advance_impl(kzk_plan* p, void* u, long long n_steps, double sigma0, 
     return KZK_OK;
 }
 
+// Pair tables and twiddles of the column-pair kernels, from the folded FP32
+// tables and the full y twiddle table w (exp(-2 pi i k / ny)).
+template <int L, typename W>
+kzk_status build_pair_tables(kzk_plan* p, const std::vector<W>& w, cudaStream_t st)
+{
+    using S = PairSched<L>;
+    const size_t ptab = (size_t)pair_tab_rows(p->ny) * p->n * sizeof(float2);
+    const void* src[3] = {p->Em1, p->P1, p->P2};
+    void* dst[3] = {p->Em1p, p->P1p, p->P2p};
+    const long long count = (long long)(p->ny / 2 + 1) * (p->n / 2);
+    for (int i = 0; i < 3; i++) {
+        KZK_CUDA(cudaMemsetAsync(dst[i], 0, ptab, st));
+        pair_table_kernel<L><<<(unsigned)((count + 255) / 256), 256, 0, st>>>((const float2*)src[i], (c2*)dst[i],
+                                                                            p->n);
+        KZK_LAUNCHED();
+    }
+    std::vector<float4> t(S::TW > 0 ? S::TW : 1);
+    for (int i = 0; i < S::NP - 1; i++) {
+        const int R = S::radix(i), s = S::stride(i), step = S::N / (R * s);
+        for (int r = 1; r < R; r++)
+            for (int q = 0; q < s; q++) {
+                const W z = w[(size_t)((long long)q * r * step % S::N)];
+                t[S::tw_off(i) + (r - 1) * s + q] = make_float4((float)z.x, (float)z.x, (float)z.y, (float)z.y);
+            }
+    }
+    KZK_CUDA(cudaMemcpy(p->twcp, t.data(), t.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    return KZK_OK;
+}
+
 template <typename T>
 kzk_status build_tables(kzk_plan* p, cudaStream_t st)
 {
@@ -879,6 +1004,15 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
         KZK_CUDA(cudaMemcpy(p->twr2, r2.data(), r2.size() * sizeof(float4), cudaMemcpyHostToDevice));
         KZK_CUDA(cudaMemcpy(p->tws2, s2.data(), s2.size() * sizeof(float4), cudaMemcpyHostToDevice));
     }
+    if (p->colpair) {
+        switch (p->log2ny) {
+        case 8: KZK_TRY(build_pair_tables<8>(p, tcf, st)); break;
+        case 9: KZK_TRY(build_pair_tables<9>(p, tcf, st)); break;
+        case 10: KZK_TRY(build_pair_tables<10>(p, tcf, st)); break;
+        case 11: KZK_TRY(build_pair_tables<11>(p, tcf, st)); break;
+        default: KZK_TRY(build_pair_tables<12>(p, tcf, st)); break;
+        }
+    }
     KZK_CUDA(cudaStreamSynchronize(st));
     return KZK_OK;
 }
@@ -910,7 +1044,7 @@ void plan_free(kzk_plan* p)
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
                     p->seg, p->ckpt, p->colp_flag, p->med_Ty, p->med_mode, p->med_coef, p->med_bmax,
                     p->uphys, p->by, p->mpos_row, p->mpos_col, p->mipos_col, p->wsc, p->twr2, p->tws2,
-                    p->Vlo, p->vslo, p->Em1};
+                    p->Vlo, p->vslo, p->Em1, p->Em1p, p->P1p, p->P2p, p->twcp};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1747,6 +1881,13 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
         if (e == cudaSuccess) e = cudaMalloc(&p->Vlo, lo_arr);
         if (e == cudaSuccess) e = cudaMalloc(&p->vslo, lo_arr);
         if (e == cudaSuccess) e = cudaMalloc(&p->Em1, tab);
+    }
+    if (p->colpair) {
+        const size_t ptab = (size_t)pair_tab_rows(p->ny) * p->n * sizeof(float2);
+        void** ptabs[] = {&p->Em1p, &p->P1p, &p->P2p};
+        for (void** t : ptabs)
+            if (e == cudaSuccess) e = cudaMalloc(t, ptab);
+        if (e == cudaSuccess) e = cudaMalloc(&p->twcp, (size_t)p->ny * sizeof(float4));
     }
     if (p->rowpair) {
         if (e == cudaSuccess) e = cudaMalloc(&p->twr2, (size_t)p->nx * sizeof(float4));

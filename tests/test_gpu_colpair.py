@@ -1,0 +1,105 @@
+"""The FP32 column passes on column pairs (kzk_colpair.cuh): every
+supported length ny = 256 .. 4096, batches, both stages of the step, the
+packed column 0, the exponential Euler step (output over its input), the
+random medium, and agreement with the Stockham tile kernels they replace
+(KZK_COLPAIR=0).  FP32 against the FP64 oracle: relative l2 within 1e-5."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_06080_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _api():
+    from paper_2103_06080_b300 import api
+    return api
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _run32(w, u0, steps, batch=1, **kw):
+    api = _api()
+    plan = api.Plan.from_workload(w, precision="fp32", batch=batch, **kw)
+    u = torch.tensor(np.ascontiguousarray(u0), dtype=torch.float32, device="cuda")
+    plan.advance(u, steps)
+    out = u.double().cpu().numpy()
+    plan.close()
+    return out
+
+
+@pytest.mark.parametrize("nx,ny,steps", [(64, 256, 20), (32, 512, 20), (64, 1024, 16), (16, 2048, 12),
+                                         (8, 4096, 8), (256, 256, 30)])
+def test_colpair_runs_match_oracle(nx, ny, steps):
+    w = inputs.config(2, nx=nx, ny=ny, n_steps=steps)
+    got = _run32(w, w.u0, steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, steps, threads=True)
+    assert rel_l2(got, ref) < 1e-5
+
+
+def test_colpair_batch_of_two():
+    w = inputs.config(2, nx=64, ny=512, n_steps=15)
+    u0 = np.stack([w.u0, 0.7 * w.u0[::-1]])
+    got = _run32(w, u0, 15, batch=2)
+    p = oracle.Params(**inputs.oracle_params(w))
+    for i in range(2):
+        assert rel_l2(got[i], oracle.run(p, np.ascontiguousarray(u0[i]), 15, threads=True)) < 1e-5, i
+
+
+@pytest.mark.parametrize("ny", [256, 2048])
+def test_colpair_agrees_with_stockham_kernels(ny, monkeypatch):
+    w = inputs.config(2, nx=128, ny=ny, n_steps=20)
+    a = _run32(w, w.u0, 20)
+    monkeypatch.setenv("KZK_COLPAIR", "0")
+    b = _run32(w, w.u0, 20)
+    assert rel_l2(a, b) < 1e-6
+    assert np.max(np.abs(a - b)) > 0   # different kernels: the switch took effect
+
+
+def test_colpair_one_step_stages():
+    api = _api()
+    w = inputs.config(2, nx=128, ny=512, n_steps=1)
+    plan = api.Plan.from_workload(w, precision="fp32")
+    s0 = 3 * w.dt
+    us, un = plan.step_stages(torch.tensor(w.u0, dtype=torch.float32, device="cuda"), sigma0=s0)
+    ref_un, ref_us = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, 1, sigma0=s0, want_ustar=True)
+    assert rel_l2(us.double().cpu().numpy(), ref_us) < 1e-6
+    assert rel_l2(un.double().cpu().numpy(), ref_un) < 1e-6
+
+
+def test_colpair_exponential_euler():
+    w = inputs.config(2, nx=64, ny=256, n_steps=25)
+    got = _run32(w, w.u0, 25, method="expeuler")
+    p = oracle.Params(**inputs.oracle_params(w, method=1))
+    assert rel_l2(got, oracle.run(p, w.u0, 25, threads=True)) < 1e-5
+
+
+def test_colpair_random_medium():
+    api = _api()
+    w = inputs.medium_config(128, 256, 10)
+    plan = api.Plan.from_workload(w, precision="fp32")
+    u = torch.tensor(w.u0, dtype=torch.float32, device="cuda")
+    plan.advance(u, w.n_steps)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    assert rel_l2(u.double().cpu().numpy(), ref) < 1e-5
+
+
+def test_colpair_diagnostics():
+    """The per-step diagnostics reduced by the first column pair of each
+    instance agree with the FP64 plan's."""
+    api = _api()
+    w = inputs.config(2, nx=64, ny=1024, n_steps=6)
+    d = {}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        plan = api.Plan.from_workload(w, precision=prec)
+        u = torch.tensor(w.u0, dtype=dt, device="cuda")
+        plan.advance(u, w.n_steps, diag=True)
+        d[prec] = plan.diag_history(w.n_steps)
+        plan.close()
+    assert np.all(np.isfinite(d["fp32"]))
+    e32, e64 = d["fp32"][:, 0, 1], d["fp64"][:, 0, 1]
+    assert np.max(np.abs(e32 - e64) / np.abs(e64)) < 1e-5

@@ -132,9 +132,10 @@ def test_fp32_error_against_fp64_oracle():
     assert rel_linf(got, ref) < 1e-4
 
 
-# Column kernels: the TMA-staged ones (default for FP32 plans, KZK_COLPIPE=2
-# for FP64) and the per-tile ones (KZK_COLPIPE=0, and every plan the staged
-# ones do not fit: ny = 4096 in FP32 needs 1024 threads per tile).
+# Column kernels: the TMA-staged Stockham ones (FP32 plans the column-pair
+# kernels do not take, KZK_COLPIPE=2 for FP64) and the per-tile ones
+# (KZK_COLPIPE=0, and every plan the staged ones do not fit: ny = 4096 in FP32
+# needs 1024 threads per tile).
 @pytest.mark.parametrize("prec,mode,nx,ny,batch,steps", [
     ("fp32", "1", 1024, 512, 1, 30),
     ("fp32", "0", 1024, 512, 1, 30),
@@ -145,6 +146,7 @@ def test_fp32_error_against_fp64_oracle():
 ])
 def test_column_kernel_variants(prec, mode, nx, ny, batch, steps, monkeypatch):
     monkeypatch.setenv("KZK_COLPIPE", mode)
+    monkeypatch.setenv("KZK_COLPAIR", "0")   # the column-pair kernels: test_gpu_colpair.py
     api = _api()
     w = inputs.config(2, nx=nx, ny=ny, n_steps=steps)
     u0 = np.stack([w.u0, 0.8 * w.u0[::-1]][:batch])
