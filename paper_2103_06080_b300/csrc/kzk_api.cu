@@ -596,6 +596,7 @@ kzk_status launch_colpair_l(const kzk_plan* p, const ColArgs<float>& a, cudaStre
     const cuuint32_t sbox[3] = {4u, (cuuint32_t)p->cpair_by, 1u};
     KZK_TRY(encode_map<float>(&P.ma, 3, a.a, sdims, sstr, sbox));
     KZK_TRY(encode_map<float>(&P.mb, 3, a.b, sdims, sstr, sbox));
+    KZK_TRY(encode_map<float>(&P.mo, 3, a.out, sdims, sstr, sbox));
     if (MODE == COL_STAGE1) {
         P.tab0 = (const c2*)p->Em1p;
         P.tab1 = (const c2*)p->P1p;

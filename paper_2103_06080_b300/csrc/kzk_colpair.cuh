@@ -140,6 +140,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
 struct ColPairArgs {
     ColArgs<float> c;          // pointers and sizes, as for col_kernel (tables unused; lo pair-major)
     CUtensorMap ma, mb, mc;    // state arrays {2 n, ny, batch} floats, box {4, by, 1}
+    CUtensorMap mo;            // the output state array, same shape and box
     const c2* tab0;            // pair tables [n/2][pair_tab_rows]: STAGE1 (E - 1)', STAGE2 P2'
     const c2* tab1;            // STAGE1 P1'
     const c2* tw;              // twiddles of the schedule as lane pairs
@@ -153,7 +154,8 @@ struct PairLayout {
     unsigned red, ra, rb, t0, t1, total, tile_bytes, table_bytes;
 };
 
-// mbarriers (128 B); diagnostics scratch; region A: dense tile (V | b1), then
+// mbarriers (128 B: STAGE1 b1 | V and tables | V again; STAGE2 inputs | V*);
+// diagnostics scratch; region A: dense tile (V | b1), then
 // the work tile; region B: dense tile (b1 | b2), then (STAGE1) the b1 work
 // tile or (STAGE2) the dense V* tile; the table slice(s).
 template <int L, int MODE>
@@ -356,8 +358,10 @@ __device__ __noinline__ void pair_fixup(c2* A, const c2* B, const c2* T0, const 
     }
 }
 
-// Copies of CTA q: table slice(s) (one contiguous run each), state tiles
-// into A and B (barrier 0).
+// Copies of CTA q.  STAGE1: the b1 tile into B (barrier 0), then the table
+// slices (one contiguous run each) and the V tile into A (barrier 1), so the
+// transform of b1 runs while the rest arrives.  STAGE2: the table slice and
+// both tiles (barrier 0).
 template <int MODE>
 __device__ __forceinline__ void pair_issue_in(const ColPairArgs& P, unsigned char* smem, const PairLayout& y, int q)
 {
@@ -365,79 +369,113 @@ __device__ __forceinline__ void pair_issue_in(const ColPairArgs& P, unsigned cha
     const int inst = q / P.n_tiles, m = q - inst * P.n_tiles, x = 4 * m;
     const unsigned box = y.tile_bytes / P.nby;
     const long long toff = (long long)m * (y.table_bytes / 16);
-    mbar_expect(bar, 2 * y.tile_bytes + (MODE == COL_STAGE1 ? 2u : 1u) * y.table_bytes);
-    bulk_load(smem + y.t0, P.tab0 + toff, y.table_bytes, bar);
-    if (MODE == COL_STAGE1) bulk_load(smem + y.t1, P.tab1 + toff, y.table_bytes, bar);
-    for (int k = 0; k < P.nby; k++) {
-        tma_load_3d(smem + y.ra + k * box, &P.ma, x, k * P.by, inst, bar);
-        tma_load_3d(smem + y.rb + k * box, &P.mb, x, k * P.by, inst, bar);
+    if (MODE == COL_STAGE1) {
+        mbar_expect(bar, y.tile_bytes);
+        for (int k = 0; k < P.nby; k++) tma_load_3d(smem + y.rb + k * box, &P.mb, x, k * P.by, inst, bar);
+        mbar_expect(bar + 1, y.tile_bytes + 2 * y.table_bytes);
+        bulk_load(smem + y.t0, P.tab0 + toff, y.table_bytes, bar + 1);
+        bulk_load(smem + y.t1, P.tab1 + toff, y.table_bytes, bar + 1);
+        for (int k = 0; k < P.nby; k++) tma_load_3d(smem + y.ra + k * box, &P.ma, x, k * P.by, inst, bar + 1);
+    } else {
+        mbar_expect(bar, 2 * y.tile_bytes + y.table_bytes);
+        bulk_load(smem + y.t0, P.tab0 + toff, y.table_bytes, bar);
+        for (int k = 0; k < P.nby; k++) {
+            tma_load_3d(smem + y.ra + k * box, &P.ma, x, k * P.by, inst, bar);
+            tma_load_3d(smem + y.rb + k * box, &P.mb, x, k * P.by, inst, bar);
+        }
     }
 }
-// STAGE2: V* into B (barrier 1), once b2 has been consumed
+// The state hi the increment is added to, into B once B is free (STAGE1: V
+// on barrier 2; STAGE2: V* on barrier 1)
+template <int MODE>
 __device__ __forceinline__ void pair_issue_c(const ColPairArgs& P, unsigned char* smem, const PairLayout& y, int q)
 {
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem) + 1;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem) + (MODE == COL_STAGE1 ? 2 : 1);
+    const CUtensorMap* m = MODE == COL_STAGE1 ? &P.ma : &P.mc;
     const int inst = q / P.n_tiles, x = 4 * (q - inst * P.n_tiles);
     const unsigned box = y.tile_bytes / P.nby;
     mbar_expect(bar, y.tile_bytes);
-    for (int k = 0; k < P.nby; k++) tma_load_3d(smem + y.rb + k * box, &P.mc, x, k * P.by, inst, bar);
+    for (int k = 0; k < P.nby; k++) tma_load_3d(smem + y.rb + k * box, m, x, k * P.by, inst, bar);
 }
-// Last inverse pass (pass 0) straight to HBM: the increment v is added to the
-// state hi + lo by TwoSum (STAGE1: hi = V from HBM; STAGE2: hi = V* from the
-// copy in B).  The global loads are issued before the barrier that precedes
-// the pass (STAGE2: before the wait for the V* copy, which is that barrier).
-template <int L, int MODE>
-__device__ __forceinline__ bool pair_last(const ColPairArgs& P, unsigned char* smem, const c2* A, const c2* B,
-                                          long long gbase, long long lbase, int tid)
+
+// tensor store of a shared-memory box, its bulk group, and the wait for its
+// reads of shared memory
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* m, const void* src, int x, int y, int z)
 {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<unsigned long long>(m)),
+                 "r"(smem_addr(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Last inverse pass (pass 0): the increment v is added to the state hi + lo
+// by TwoSum, hi from the copy in B (STAGE1: V, STAGE2: V*), lo from HBM
+// (loaded before the wait for that copy, which is also the barrier the pass
+// needs); the lo rows (pair-major: coalesced) are stored directly.  STAGE1
+// writes the new hi rows over A in row order and sends them by a tensor store
+// (C1 then loads 3 tiles and stores 1 through the tensor engine); STAGE2,
+// whose engine already takes 3 tiles in, stores its rows from the threads.
+template <int L, int MODE>
+__device__ __forceinline__ bool pair_last(const ColPairArgs& P, unsigned char* smem, c2* A, const c2* B,
+                                          long long gbase, long long lbase, int inst, int m, int tid)
+{
+    constexpr bool TOUT = MODE == COL_STAGE1;
     using S = PairSched<L>;
     constexpr int R = S::radix(0), s = S::stride(0), G = 8 / R, off = S::tw_off(0);
     const ColArgs<float>& a = P.c;
-    const int log2n = a.log2n;
     int bs[G], qs[G];
     uint2 lo[G][R];
-    float4 hi[G][R];
 #pragma unroll
     for (int u = 0; u < G; u++) {
         pair_group<L, 0>(tid, u, bs[u], qs[u]);
 #pragma unroll
-        for (int j = 0; j < R; j++) {
-            const int row = bs[u] + s * j;
-            lo[u][j] = __ldcg(reinterpret_cast<const uint2*>(a.lo_in + lbase + 2 * row));
-            if constexpr (MODE == COL_STAGE1)
-                hi[u][j] = __ldcg(reinterpret_cast<const float4*>(a.a + gbase + ((long long)row << log2n)));
-        }
+        for (int j = 0; j < R; j++)
+            lo[u][j] = __ldcg(reinterpret_cast<const uint2*>(a.lo_in + lbase + 2 * (bs[u] + s * j)));
     }
-    if constexpr (MODE == COL_STAGE1) __syncthreads();
-    else if (!colp_wait(smem, 1, 0u, P.timeout_ns, P.flag)) return false;
+    if (!colp_wait(smem, MODE == COL_STAGE1 ? 2 : 1, 0u, P.timeout_ns, P.flag)) return false;
+    c2 v[G][R];
 #pragma unroll
     for (int u = 0; u < G; u++) {
-        c2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; r++) v[r] = A[psw(bs[u] + s * r)];
+        for (int r = 0; r < R; r++) v[u][r] = A[psw(bs[u] + s * r)];
         if constexpr (s > 1) {
 #pragma unroll
-            for (int r = 1; r < R; r++) v[r] = mulc<f2>(v[r], P.tw[off + (r - 1) * s + qs[u]]);
+            for (int r = 1; r < R; r++) v[u][r] = mulc<f2>(v[u][r], P.tw[off + (r - 1) * s + qs[u]]);
         }
-        RegDFT<f2, R, 1, false>::run(v);
+        RegDFT<f2, R, 1, false>::run(v[u]);
+    }
+    if constexpr (TOUT) __syncwarp();   // row e's slot held element psw(e), read above by a lane of this warp
+    float4* out = reinterpret_cast<float4*>(A);
+#pragma unroll
+    for (int u = 0; u < G; u++)
 #pragma unroll
         for (int j = 0; j < R; j++) {
             const int row = bs[u] + s * j;
-            const long long g = gbase + ((long long)row << log2n);
-            const c2 h = MODE == COL_STAGE1 ? pair_of(hi[u][j]) : pair_of(reinterpret_cast<const float4*>(B)[row]);
             __nv_bfloat162 l0, l1;
             memcpy(&l0, &lo[u][j].x, 4);
             memcpy(&l1, &lo[u][j].y, 4);
             const c2 lc = pack2(__bfloat1622float2(l0), __bfloat1622float2(l1));
             c2 sh, sl;
-            comp_add<f2>(h, lc, v[j], sh, sl);
-            *reinterpret_cast<float4*>(a.out + g) = row_of(sh);
+            comp_add<f2>(pair_of(reinterpret_cast<const float4*>(B)[row]), lc, v[u][j], sh, sl);
+            if constexpr (TOUT) out[row] = row_of(sh);
+            else *reinterpret_cast<float4*>(a.out + gbase + ((long long)row << a.log2n)) = row_of(sh);
             const __nv_bfloat162 o0 = __float22bfloat162_rn(lane0(sl)), o1 = __float22bfloat162_rn(lane1(sl));
             uint2 w;
             memcpy(&w.x, &o0, 4);
             memcpy(&w.y, &o1, 4);
             *reinterpret_cast<uint2*>(a.lo_out + lbase + 2 * row) = w;
         }
+    if constexpr (!TOUT) return true;
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned box = S::N * 16u / P.nby;
+        for (int k = 0; k < P.nby; k++)
+            tma_store_3d(&P.mo, reinterpret_cast<const unsigned char*>(A) + k * box, 4 * m, k * P.by, inst);
+        bulk_commit();
+        bulk_wait_read();
     }
     return true;
 }
@@ -464,6 +502,7 @@ __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpai
         unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem);
         mbar_init(bar, 1);
         mbar_init(bar + 1, 1);
+        mbar_init(bar + 2, 1);
         mbar_fence_init();
         pair_issue_in<MODE>(P, smem, y, q);
     }
@@ -482,6 +521,7 @@ __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpai
     if constexpr (MODE == COL_STAGE1) {
         pair_forward_head<L>(B, DenseIn{B}, tw, tid);
         pair_pass<L, S::NP - 1, true>(tw, tid, SwzIO{B}, SwzIO{B});   // b1_hat, read back by the same lane
+        if (!colp_wait(smem, 1, 0u, P.timeout_ns, P.flag)) return;
         pair_forward_head<L>(A, DenseIn{A}, tw, tid);
     } else {
         pair_forward_head<L>(A, DiffIn{A, B}, tw, tid);
@@ -490,7 +530,7 @@ __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpai
     // block-wide barrier follows pass 0 when it spans warps; one warp otherwise)
     if constexpr (MODE == COL_STAGE2) {
         if constexpr (S::NBP == 0) __syncthreads();
-        if (tid == 0) pair_issue_c(P, smem, y, q);
+        if (tid == 0) pair_issue_c<MODE>(P, smem, y, q);
     }
     if (m0 != 0) {
         pair_fused<L, MODE>(A, B, T0, T1, tid);
@@ -500,6 +540,11 @@ __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpai
         pair_fixup<L, MODE>(A, B, T0, T1);
         __syncthreads();
         pair_pass<L, S::NP - 1, false>(tw, tid, ia, ia);
+    }
+    // STAGE1: b1_hat consumed by every warp; bring V into B for the last pass
+    if constexpr (MODE == COL_STAGE1) {
+        __syncthreads();
+        if (tid == 0) pair_issue_c<MODE>(P, smem, y, q);
     }
     __syncwarp();
     // inverse: the remaining warp passes, then the block passes; pass 0 to HBM
@@ -515,8 +560,8 @@ __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpai
         __syncthreads();
         pair_pass<L, 1, false>(tw, tid, ia, ia);
     }
-    const long long gbase = (long long)inst * a.inst_stride + m0;
-    pair_last<L, MODE>(P, smem, A, B, gbase, gbase - m0 + (long long)m0 * N, tid);
+    pair_last<L, MODE>(P, smem, A, B, (long long)inst * a.inst_stride + m0,
+                       (long long)inst * a.inst_stride + (long long)m0 * N, inst, m0 / 2, tid);
 }
 
 }  // namespace kzk
