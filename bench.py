@@ -498,6 +498,15 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
                      "traffic": measured_traffic(names[dom], "fp32"), "kernel_ms": dict(zip(names, kt3)),
                      "step_frac": sum(by3) / (sum(kt3) * 1e-3) / hbm},
     }
+    # the FP32 passes are bound by instruction issue and latency, not by HBM:
+    # the dominant one's algorithmic FLOPs against the measured FP32 FMA peak
+    # (the faster of scalar FFMA and packed FFMA2 chains)
+    fl3 = [row_flops(4096, 2048), col_flops(4096, 2048, 1), row_flops(4096, 2048), col_flops(4096, 2048, 2)]
+    fp32_peak = api.alu_peak("fp32")
+    out["fp32"]["roofline"]["alu"] = {
+        "achieved": fl3[dom] / (kt3[dom] * 1e-3) / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+        "frac": fl3[dom] / (kt3[dom] * 1e-3) / fp32_peak,
+        "peak_source": "measured FP32 FMA throughput (kzk_alu_peak: max of FFMA and FFMA2 chains) on this GPU"}
     p3.close()
     del u3
     # FP32 error of the precision workload (1024 x 512, 2000 steps, and the full

@@ -79,10 +79,14 @@ typedef struct {
                                        over thousands of steps (KZK_COMPSTATE=0 in the
                                        environment: a plain FP32 state).  KZK_FP32 row
                                        passes run on row pairs in packed FP32
-                                       (KZK_ROWPAIR=0: single rows); their column passes
-                                       stage tiles with the tensor memory accelerator
-                                       (KZK_COLPIPE=0: per-tile kernels with plain loads;
-                                       KZK_COLPIPE=2: the TMA kernels for KZK_FP64 too).
+                                       (KZK_ROWPAIR=0: single rows); with the compensated
+                                       state and 256 <= ny <= 4096 their column passes run
+                                       on column pairs in packed FP32 with in-place
+                                       transforms (KZK_COLPAIR=0: Stockham tiles staged by
+                                       the tensor memory accelerator, the column passes of
+                                       the other KZK_FP32 plans; KZK_COLPIPE=0: per-tile
+                                       kernels with plain loads; KZK_COLPIPE=2: the TMA
+                                       Stockham kernels for KZK_FP64 too).
                                        The environment is read at plan creation. */
 } kzk_grid;
 
@@ -309,7 +313,8 @@ kzk_status kzk_kernel_times(kzk_plan *plan, void *u, int64_t n_steps, double sig
 /* Measurement helper (no counterpart in the paper): sustained fused
  * multiply-add throughput of the device in FLOP/s (2 per FMA) for the given
  * precision, from a kernel of independent FMA chains on every SM timed with
- * CUDA events.  Synchronises the stream. */
+ * CUDA events (KZK_FP32: the faster of scalar and packed-pair FMA chains).
+ * Synchronises the stream. */
 kzk_status kzk_alu_peak(int32_t prec, void *stream, double *flops_per_s);
 
 /* Largest batch * nx * ny accepted by kzk_rhs_noalloc. */
