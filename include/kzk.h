@@ -247,7 +247,9 @@ kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *
  * kernel launch per kzk_advance_batched call (captured once in a CUDA graph
  * and replayed).  The launch runs every pass of every step for all instances
  * -- rows of all instances for the row passes, column tiles of all instances
- * for the column passes, the same computation as kzk_advance -- separated by
+ * for the column passes, the same computation as kzk_advance (KZK_FP32: with
+ * the plans' compensated state, on the single-row and per-tile column bodies,
+ * as KZK_ROWPAIR=0 KZK_COLPIPE=0 plans compute it) -- separated by
  * grid barriers whose waits are bounded (KZK_ERR_TIMEOUT).  With
  * KZK_BATCH_AUTOTUNE the column-tile width is chosen by timing two steps of
  * each candidate at creation.  Each grid must be a power of two, nx <= 8192

@@ -1357,6 +1357,12 @@ kzk_status batch_upload(kzk_plan* p, void* const* u, int tile_cap, size_t* smem_
         I.u = u ? (cx<T>*)u[i] : nullptr;
         I.E = (const cx<T>*)q->E; I.E_lo = (const cx<T>*)q->E_lo;
         I.P1 = (const cx<T>*)q->P1; I.P2 = (const cx<T>*)q->P2;
+        if (q->comp) {
+            I.Em1 = (const cx<T>*)q->Em1;
+            I.Vlo = (lo_t<T>*)q->Vlo;
+            I.vslo = (lo_t<T>*)q->vslo;
+            if (!I.Em1 || !I.Vlo || !I.vslo) return fail(KZK_ERR_STATE, "instance %d: missing lo arrays", i);
+        }
         I.diag_rows = q->diag_rows; I.diag_hist = q->diag_hist; I.diag_final = q->diag_final;
         I.ny = q->ny;
         I.n_tiles = q->n >> l2tc;
@@ -1429,6 +1435,12 @@ kzk_status batch_launch(kzk_plan* p, long long n_steps, cudaStream_t st, bool us
     auto enqueue = [&](cudaStream_t on) -> cudaError_t {
         cudaError_t e = cudaMemsetAsync(p->bar, 0, 4 * sizeof(unsigned), on);
         if (e != cudaSuccess) return e;
+        // every launch loads its states afresh: the compensated lo parts start at zero
+        for (kzk_plan* q : *p->subs)
+            if (q->comp) {
+                e = cudaMemsetAsync(q->Vlo, 0, (size_t)q->batch * q->inst_stride * sizeof(__nv_bfloat162), on);
+                if (e != cudaSuccess) return e;
+            }
         return cudaLaunchCooperativeKernel((const void*)batched_kernel<T>, dim3(p->grid_ctas), dim3(BATCH_THREADS),
                                            args, p->batch_smem, on);
     };

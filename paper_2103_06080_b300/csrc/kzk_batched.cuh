@@ -6,6 +6,9 @@
 //   FWD (physical -> spectral), then per step R1, C1, R2, C2
 //   (Algorithm 2, STEP 1-4), then INV (spectral -> physical) and the final
 //   diagnostics.
+// FP32 instances carry the compensated state of their plans (the column
+// bodies transform increments and add them to hi + lo; the lo parts start at
+// zero with every launch).
 // Each pass is a list of tasks -- rows of every instance for the row passes,
 // column tiles of every instance for the column passes -- handed out round
 // robin over the CTAs; a grid barrier separates the passes.  The barrier's
@@ -29,6 +32,11 @@ struct BatchInst {
     const cx<T>* E_lo;
     const cx<T>* P1;
     const cx<T>* P2;
+    // FP32 plans with the compensated state (hi + lo, lo in row layout here):
+    // (E - 1)', and the lo parts of V and V*; nullptr for the plain state
+    const cx<T>* Em1;
+    lo_t<T>* Vlo;
+    lo_t<T>* vslo;
     double* diag_rows;       // [ny][4]
     double* diag_hist;       // [hist_cap][4]
     double* diag_final;      // [4]
@@ -150,10 +158,12 @@ __device__ __forceinline__ void batched_cols(const BatchArgs<T>& B, int s, unsig
             a.Ta = I.E; a.Ta_lo = I.E_lo; a.Tb = I.P1;
             a.diag_rows = I.diag_rows;
             a.diag_hist = I.diag_hist + (size_t)s * 4;
+            if (I.Vlo) { a.Ta = I.Em1; a.Ta_lo = nullptr; a.lo_in = I.Vlo; a.lo_out = I.vslo; }
         } else {
             a.a = I.b1; a.b = I.b2; a.c = I.vs; a.out = I.V;
             a.Ta = I.P2;
             a.diag_rows = nullptr;
+            if (I.Vlo) { a.lo_in = I.vslo; a.lo_out = I.Vlo; }
         }
         targs->col = a;
         }

@@ -16,17 +16,20 @@ def _small_batch(precision):
     return ws
 
 
-@pytest.mark.parametrize("prec,mode", [("fp64", "persistent"), ("fp32", "persistent"), ("fp64", "streams"),
-                                       ("fp32", "streams")])
+@pytest.mark.parametrize("prec,mode", [("fp64", "persistent"), ("fp32", "persistent"), ("fp32", "persistent-plain"),
+                                       ("fp64", "streams"), ("fp32", "streams")])
 def test_batched_matches_single_plans(prec, mode, monkeypatch):
     from paper_2103_06080_b300 import api
-    if mode == "persistent":
-        # the persistent kernel runs the per-tile column bodies, the
-        # single-row bodies and the plain (uncompensated) FP32 state: compare
-        # with single plans on the same kernels, bit for bit
+    if mode.startswith("persistent"):
+        # the persistent kernel runs the per-tile column bodies and the
+        # single-row bodies (FP32: with the compensated state unless
+        # KZK_COMPSTATE=0): compare with single plans on the same kernels,
+        # bit for bit
         monkeypatch.setenv("KZK_COLPIPE", "0")
         monkeypatch.setenv("KZK_ROWPAIR", "0")
-        monkeypatch.setenv("KZK_COMPSTATE", "0")
+        if mode == "persistent-plain":
+            monkeypatch.setenv("KZK_COMPSTATE", "0")
+        mode = "persistent"
     dt = torch.float64 if prec == "fp64" else torch.float32
     ws = _small_batch(prec)
     bp = api.BatchedPlan(ws, precision=prec, autotune=True, mode=mode)
@@ -42,6 +45,22 @@ def test_batched_matches_single_plans(prec, mode, monkeypatch):
         p.close()
     # a second call replays the captured graph
     bp.advance(us, 20, sigma0=20 * ws[0].dt)
+    bp.close()
+
+
+def test_batched_fp32_persistent_accuracy():
+    """The persistent launch carries the compensated FP32 state: against the
+    FP64 oracle after 200 steps, relative l2 within 1e-5."""
+    from paper_2103_06080_b300 import api
+    # workloads whose atmosphere profiles span the 200 steps
+    ws = inputs.batched_config(seed=5, count=4, n_steps=200, scale=8)[:2]
+    bp = api.BatchedPlan(ws, precision="fp32", autotune=False)
+    us = [torch.tensor(w.u0, dtype=torch.float32, device="cuda") for w in ws]
+    bp.advance(us, 200)
+    for w, u in zip(ws, us):
+        ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, 200, threads=True)
+        got = u.double().cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5, (w.nx, w.ny)
     bp.close()
 
 
