@@ -87,7 +87,7 @@ struct PairSched {
 };
 
 // work-tile slot of element i (16-byte slots)
-__device__ __forceinline__ int psw(int i) { return i ^ ((i >> 3) & 7); }
+__host__ __device__ __forceinline__ int psw(int i) { return i ^ ((i >> 3) & 7); }
 
 // Shared-memory row of folded table row r: r with its low three bits XORed by
 // three bits of r >> 3, chosen per length so that the rows a warp reads in the
@@ -182,7 +182,7 @@ __host__ __device__ constexpr PairLayout pair_layout()
 
 // Group u of thread tid in pass I: base element and q (offset within the stride).
 template <int L, int I>
-__device__ __forceinline__ void pair_group(int tid, int u, int& base, int& qq)
+__host__ __device__ __forceinline__ void pair_group(int tid, int u, int& base, int& qq)
 {
     using S = PairSched<L>;
     constexpr int R = S::radix(I), s = S::stride(I);
