@@ -103,3 +103,31 @@ def test_colpair_diagnostics():
     assert np.all(np.isfinite(d["fp32"]))
     e32, e64 = d["fp32"][:, 0, 1], d["fp64"][:, 0, 1]
     assert np.max(np.abs(e32 - e64) / np.abs(e64)) < 1e-5
+
+
+def test_colpair_with_relaxation():
+    """Two relaxation processes change the tables only; the pair tables are
+    built from them."""
+    relax = dict(relax_C=(2e-4, 6e-4), relax_theta=(0.02, 0.1))
+    w = inputs.config(2, nx=64, ny=512, n_steps=20)
+    got = _run32(w, w.u0, 20, **relax)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w, **relax)), w.u0, 20, threads=True)
+    plain = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, 20, threads=True)
+    assert rel_l2(plain, ref) > 1e-4
+    assert rel_l2(got, ref) < 1e-5
+
+
+def test_colpair_in_the_adjoint_recompute():
+    """The FP32 adjoint recomputes each checkpoint segment with the forward
+    step (column pairs at ny = 256); the gradient against the oracle's
+    adjoint within the FP32 adjoint tolerance of the other grids (3e-3)."""
+    api = _api()
+    w = inputs.config(2, nx=64, ny=256, n_steps=8)
+    plan = api.Plan.from_workload(w, precision="fp32")
+    p = oracle.Params(**inputs.oracle_params(w))
+    g_end = 2 * w.dtau * oracle.run(p, w.u0, w.n_steps)
+    ref = oracle.adjoint(p, w.u0, g_end, w.n_steps)
+    g0 = plan.adjoint(torch.tensor(w.u0, dtype=torch.float32, device="cuda"),
+                      torch.tensor(g_end, dtype=torch.float32, device="cuda"), w.n_steps, ckpt_every=3)
+    got = g0.double().cpu().numpy()
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 3e-3
