@@ -154,6 +154,7 @@ struct kzk_plan_s {
     // FP32 plans with the compensated state: column passes on column pairs
     // (kzk_colpair.cuh); colpair = 0: not used
     int colpair, cpair_by, cpair_nby;
+    int cpair_diff;             // row pairs store b2 - b1 for the column-pair STAGE2 (both kernels in use)
     size_t cpair_smem1, cpair_smem2;
     void *Em1p, *P1p, *P2p;     // (E - 1)', P1', P2' as pair tables [nx/4][pair_tab_rows(ny)]
     void* twcp;                 // twiddles of the pair schedule, as lane pairs
@@ -277,6 +278,8 @@ kzk_status cpair_attr(kzk_plan* p, int optin)
     if (std::max(s1, s2) > (size_t)optin) return KZK_OK;
     KZK_CUDA(cudaFuncSetAttribute(colpair_kernel<L, COL_STAGE1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(colpair_kernel<L, COL_STAGE2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(colpair_kernel<L, COL_STAGE2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin));
     int per_sm = 0;
     KZK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, colpair_kernel<L, COL_STAGE1>, PairSched<L>::T,
                                                            s1));
@@ -400,9 +403,13 @@ kzk_status configure(kzk_plan* p)
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_RHS_MED>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_RHS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_RHS_MED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      optin));
     }
     colp_configure<T>(p, optin);
     KZK_TRY(cpair_configure<T>(p, optin));
+    p->cpair_diff = p->colpair && p->rowpair;
     if (p->colp_log2tc >= 0) {
         KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -492,8 +499,9 @@ RowArgs<T> row_args(const kzk_plan* p, const void* in, void* out, double sigma, 
     return a;
 }
 
+// sub (nullable, row pairs only): spectral rows subtracted from the result
 template <typename T, int MODE>
-kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st)
+kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st, const void* sub = nullptr)
 {
     if constexpr (std::is_same<T, float>::value) {
         if (p->rowpair) {
@@ -501,6 +509,14 @@ kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st)
             P.r = a;
             P.tw2 = (const c2*)p->twr2;
             P.tws2 = (const c2*)p->tws2;
+            P.sub = (const float2*)sub;
+            if constexpr (MODE == ROW_RHS || MODE == ROW_RHS_MED) {
+                if (sub) {
+                    rowpair_kernel<MODE, true><<<dim3(p->ny / 2, p->batch), p->row_thr, p->rowpair_smem, st>>>(P);
+                    KZK_LAUNCHED();
+                    return KZK_OK;
+                }
+            }
             rowpair_kernel<MODE><<<dim3(p->ny / 2, p->batch), p->row_thr, p->rowpair_smem, st>>>(P);
             KZK_LAUNCHED();
             return KZK_OK;
@@ -612,7 +628,8 @@ kzk_status launch_colpair_l(const kzk_plan* p, const ColArgs<float>& a, cudaStre
     P.flag = p->colp_flag;
     P.timeout_ns = 2000000000LL;
     const size_t smem = MODE == COL_STAGE1 ? p->cpair_smem1 : p->cpair_smem2;
-    colpair_kernel<L, MODE><<<P.total, PairSched<L>::T, smem, st>>>(P);
+    if (MODE == COL_STAGE2 && p->cpair_diff) colpair_kernel<L, MODE, true><<<P.total, PairSched<L>::T, smem, st>>>(P);
+    else colpair_kernel<L, MODE><<<P.total, PairSched<L>::T, smem, st>>>(P);
     KZK_LAUNCHED();
     return KZK_OK;
 }
@@ -739,11 +756,13 @@ kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, dou
         r.uphys = (const T*)phys;
         r.by = (const T*)p->by;
         r.med_coef = p->med_coef + (size_t)stage * 3 * p->ny;
-        return launch_row<T, ROW_RHS_MED>(p, r, st);
+        return launch_row<T, ROW_RHS_MED>(p, r, st, stage == 1 && p->cpair_diff ? p->b1 : nullptr);
     }
     RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, diag_rows);
     r.u_out = (T*)u_out;
-    return launch_row<T, ROW_RHS>(p, r, st);
+    // column-pair plans on row pairs: the second stage stores b2 - b1 (C2's
+    // input), the subtraction done once per element in the row pass
+    return launch_row<T, ROW_RHS>(p, r, st, stage == 1 && p->cpair_diff ? p->b1 : nullptr);
 }
 
 // Stage-1 table and state pointers: the plain state takes E' (+ E'_lo in

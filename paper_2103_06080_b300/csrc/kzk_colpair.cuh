@@ -361,8 +361,9 @@ __device__ __noinline__ void pair_fixup(c2* A, const c2* B, const c2* T0, const 
 // Copies of CTA q.  STAGE1: the b1 tile into B (barrier 0), then the table
 // slices (one contiguous run each) and the V tile into A (barrier 1), so the
 // transform of b1 runs while the rest arrives.  STAGE2: the table slice and
-// both tiles (barrier 0).
-template <int MODE>
+// both tiles (barrier 0); D2 (the row pass stored b2 - b1): that tile into A
+// and the table (barrier 0), V* into B at once (barrier 1).
+template <int MODE, bool D2>
 __device__ __forceinline__ void pair_issue_in(const ColPairArgs& P, unsigned char* smem, const PairLayout& y, int q)
 {
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem);
@@ -376,6 +377,12 @@ __device__ __forceinline__ void pair_issue_in(const ColPairArgs& P, unsigned cha
         bulk_load(smem + y.t0, P.tab0 + toff, y.table_bytes, bar + 1);
         bulk_load(smem + y.t1, P.tab1 + toff, y.table_bytes, bar + 1);
         for (int k = 0; k < P.nby; k++) tma_load_3d(smem + y.ra + k * box, &P.ma, x, k * P.by, inst, bar + 1);
+    } else if (D2) {
+        mbar_expect(bar, y.tile_bytes + y.table_bytes);
+        for (int k = 0; k < P.nby; k++) tma_load_3d(smem + y.ra + k * box, &P.mb, x, k * P.by, inst, bar);
+        bulk_load(smem + y.t0, P.tab0 + toff, y.table_bytes, bar);
+        mbar_expect(bar + 1, y.tile_bytes);
+        for (int k = 0; k < P.nby; k++) tma_load_3d(smem + y.rb + k * box, &P.mc, x, k * P.by, inst, bar + 1);
     } else {
         mbar_expect(bar, 2 * y.tile_bytes + y.table_bytes);
         bulk_load(smem + y.t0, P.tab0 + toff, y.table_bytes, bar);
@@ -480,8 +487,9 @@ __device__ __forceinline__ bool pair_last(const ColPairArgs& P, unsigned char* s
     return true;
 }
 
-// One column pair (CTA q = pair q), compensated FP32 state.
-template <int L, int MODE>
+// One column pair (CTA q = pair q), compensated FP32 state.  D2 (STAGE2): the
+// input array b holds b2 - b1 (written so by the row-pair pass).
+template <int L, int MODE, bool D2 = false>
 __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpair_kernel(
     const __grid_constant__ ColPairArgs P)
 {
@@ -504,7 +512,7 @@ __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpai
         mbar_init(bar + 1, 1);
         mbar_init(bar + 2, 1);
         mbar_fence_init();
-        pair_issue_in<MODE>(P, smem, y, q);
+        pair_issue_in<MODE, D2>(P, smem, y, q);
     }
     const int inst = q / P.n_tiles, m0 = 2 * (q - inst * P.n_tiles);
     if (MODE == COL_STAGE1 && m0 == 0 && a.diag_rows && a.diag_hist)
@@ -523,12 +531,14 @@ __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpai
         pair_pass<L, S::NP - 1, true>(tw, tid, SwzIO{B}, SwzIO{B});   // b1_hat, read back by the same lane
         if (!colp_wait(smem, 1, 0u, P.timeout_ns, P.flag)) return;
         pair_forward_head<L>(A, DenseIn{A}, tw, tid);
+    } else if constexpr (D2) {
+        pair_forward_head<L>(A, DenseIn{A}, tw, tid);
     } else {
         pair_forward_head<L>(A, DiffIn{A, B}, tw, tid);
     }
     // STAGE2: b2 is consumed once every warp has passed its first pass (a
     // block-wide barrier follows pass 0 when it spans warps; one warp otherwise)
-    if constexpr (MODE == COL_STAGE2) {
+    if constexpr (MODE == COL_STAGE2 && !D2) {
         if constexpr (S::NBP == 0) __syncthreads();
         if (tid == 0) pair_issue_c<MODE>(P, smem, y, q);
     }

@@ -63,6 +63,8 @@ struct RowPairArgs {
     RowArgs<float> r;       // the single-row arguments (tw / tws unused here)
     const c2* tw2;          // exp(-2 pi i k / nx), k in [0, nx), as pairs
     const c2* tws2;         // staged twiddles of the length-nx/2 FFT, as pairs
+    const float2* sub;      // ROW_RHS / ROW_RHS_MED (nullable): spectral rows subtracted from the result
+                            // (the second stage of column-pair plans stores b2 - b1 for C2)
 };
 
 __device__ __forceinline__ c2 pack2(float2 a, float2 b) { return c2{f2(a.x, b.x), f2(a.y, b.y)}; }
@@ -82,7 +84,8 @@ __device__ __forceinline__ void pair_stats(const c2* u, int k0, int Q, float& sa
     }
 }
 
-template <int MODE>
+// SUB: subtract the rows P.sub from the result (ROW_RHS / ROW_RHS_MED)
+template <int MODE, bool SUB = false>
 __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -174,6 +177,15 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             if (a.diag_rows) pair_stats(X, k0, Q, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
         }
         __syncthreads();
+        // the rows to subtract (both rows: 2n float2, contiguous) into X, free
+        // from here on, while the forward transform runs
+        if constexpr (SUB) {
+            const unsigned xs = (unsigned)__cvta_generic_to_shared(X);
+            for (int i = tid; i < n; i += nthr)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(xs + 16u * i),
+                             "l"(P.sub + base + 2 * i)
+                             : "memory");
+        }
         if constexpr (MODE == ROW_RHS_MED) {
             const float* by0 = a.by + 2 * base;
             for (int k = tid; k < nx; k += nthr)
@@ -181,6 +193,11 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             __syncthreads();
         }
         fft_batched<f2, PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
+        if constexpr (SUB) {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncthreads();
+        }
+        const float2* Xs = reinterpret_cast<const float2*>(X);
         for (int k = tid; k <= n / 2; k += nthr) {
             c2 xk, xnk;
             r2c_post_pair<f2, true>(Y, n, k, P.tw2, xk, xnk);
@@ -204,6 +221,16 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
                         kna.x -= g * w0.x; kna.y -= g * w0.y;
                         knb.x -= g * w1.x; knb.y -= g * w1.y;
                     }
+                }
+            }
+            if constexpr (SUB) {
+                const float2 s0 = Xs[k], s1 = Xs[n + k];
+                k0a.x -= s0.x; k0a.y -= s0.y;
+                k0b.x -= s1.x; k0b.y -= s1.y;
+                if (k != 0 && 2 * k != n) {
+                    const float2 t0 = Xs[n - k], t1 = Xs[2 * n - k];
+                    kna.x -= t0.x; kna.y -= t0.y;
+                    knb.x -= t1.x; knb.y -= t1.y;
                 }
             }
             out[base + k] = k0a;
