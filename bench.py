@@ -529,10 +529,8 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
                                   "rel_linf": float(d.abs().max() / res["fp64"].abs().max())}
         out["fp32"]["error_vs_fp64"] = {**errs, "case": f"{args.err_steps} steps of the seeded precision "
                                                       "workload; reference: the FP64 path (oracle parity 1e-11)"}
-    # adjoint / forward on the adjoint workload (2048 x 1024, FP64, checkpoint every 32)
+    # adjoint / forward on the adjoint workload (2048 x 1024, checkpoint every 32), FP64 and FP32
     w4 = inputs.config(4, n_steps=args.adj_steps)
-    p4 = api.Plan.from_workload(w4, precision="fp64")
-    u4 = torch.tensor(w4.u0, dtype=torch.float64, device=dev)
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -541,22 +539,28 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
         torch.cuda.synchronize()
         return time.perf_counter() - t, r
 
-    y = u4.clone()
-    p4.advance(y, 4)                                            # warm-up
-    t_fwd, _ = timed(lambda: p4.advance(y, w4.n_steps))
-    y = u4.clone()
-    t_fwd_ck, _ = timed(lambda: p4.advance_checkpointed(y, w4.n_steps, 0.0, 32))
-    g_end = 2 * w4.dtau * y
-    t_bwd, _ = timed(lambda: p4.adjoint_checkpointed(g_end))
-    t_full, _ = timed(lambda: p4.adjoint(u4, g_end, w4.n_steps, ckpt_every=32))
+    def adjoint_cost(prec):
+        p4 = api.Plan.from_workload(w4, precision=prec)
+        u4 = torch.tensor(w4.u0, dtype=torch.float64 if prec == "fp64" else torch.float32, device=dev)
+        y = u4.clone()
+        p4.advance(y, 4)                                            # warm-up
+        t_fwd, _ = timed(lambda: p4.advance(y, w4.n_steps))
+        y = u4.clone()
+        t_fwd_ck, _ = timed(lambda: p4.advance_checkpointed(y, w4.n_steps, 0.0, 32))
+        g_end = 2 * w4.dtau * y
+        t_bwd, _ = timed(lambda: p4.adjoint_checkpointed(g_end))
+        t_full, _ = timed(lambda: p4.adjoint(u4, g_end, w4.n_steps, ckpt_every=32))
+        p4.close()
+        return {"forward_s": t_fwd, "forward_with_checkpoints_s": t_fwd_ck, "backward_s": t_bwd,
+                "backward_over_forward": t_bwd / t_fwd,
+                "full_gradient_s": t_full, "full_gradient_over_forward": t_full / t_fwd}
+
     out["adjoint"] = {"workload": f"fp64 2048x1024, {w4.n_steps} steps, checkpoint every 32",
-                      "forward_s": t_fwd, "forward_with_checkpoints_s": t_fwd_ck, "backward_s": t_bwd,
-                      "backward_over_forward": t_bwd / t_fwd,
-                      "full_gradient_s": t_full, "full_gradient_over_forward": t_full / t_fwd,
+                      **adjoint_cost("fp64"),
                       "note": "backward = per-segment recompute from stored checkpoints + reverse sweep "
                               "(the autograd backward); full gradient = kzk_adjoint from u0 (forward sweep "
                               "with checkpoints + backward)"}
-    p4.close()
+    out["adjoint"]["fp32"] = adjoint_cost("fp32")
     # batched persistent launch: 64 heterogeneous FP32 propagations
     if not args.no_batched:
         ws = inputs.batched_config(seed=5, count=args.batch_count, n_steps=500)
