@@ -93,20 +93,23 @@ def measured_traffic(kernel: str, prec: str):
 # --------------------------------------------------------------------------
 # algorithmic work per launch (also stated in the design notes)
 # --------------------------------------------------------------------------
-def row_bytes(nx, ny, w):
-    """Row pass: read one packed spectral array, write one (N * w bytes each)."""
-    return 2 * nx * ny * w
+def row_bytes(nx, ny, w, sub=False):
+    """Row pass: read one packed spectral array, write one (N * w bytes each);
+    sub (the second stage of FP32 plans on row and column pairs): also reads
+    b1, to store b2 - b1."""
+    return (3 if sub else 2) * nx * ny * w
 
 
-def col_bytes(nx, ny, w, stage, comp=False):
+def col_bytes(nx, ny, w, stage, comp=False, diff=False):
     """Column pass: stage 1 reads V, b1 and the folded E' (or (E - 1)'), P1'
-    (half an array each) and writes V*; stage 2 reads b1, b2, V*, folded P2'
-    and writes V'.  comp (the compensated FP32 state): each stage also reads
-    and writes the lo part (a bf16 pair per complex value: half an array)."""
+    (half an array each) and writes V*; stage 2 reads b1, b2 (diff: the one
+    array b2 - b1), V*, folded P2' and writes V'.  comp (the compensated FP32
+    state): each stage also reads and writes the lo part (a bf16 pair per
+    complex value: half an array)."""
     unit = nx * ny * w
     tab = (ny // 2 + 1) * (nx // 2) * 2 * w
     lo = unit if comp else 0                        # lo in + lo out, half an array each
-    return (3 * unit + 2 * tab + lo) if stage == 1 else (4 * unit + tab + lo)
+    return (3 * unit + 2 * tab + lo) if stage == 1 else ((3 if diff else 4) * unit + tab + lo)
 
 
 def row_flops(nx, ny, profile=True):
@@ -300,8 +303,10 @@ def run_ours(args, rank, world, local_rank):
     names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
     fl = [row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 1), row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 2)]
     comp = fp32 and os.environ.get("KZK_COMPSTATE", "1") != "0"
-    by = [row_bytes(w.nx, w.ny, wsz), col_bytes(w.nx, w.ny, wsz, 1, comp), row_bytes(w.nx, w.ny, wsz),
-          col_bytes(w.nx, w.ny, wsz, 2, comp)]
+    diff = comp and 256 <= w.ny <= 4096 and all(os.environ.get(v, "1") != "0"
+                                                for v in ("KZK_ROWPAIR", "KZK_COLPAIR", "KZK_COLPIPE"))
+    by = [row_bytes(w.nx, w.ny, wsz), col_bytes(w.nx, w.ny, wsz, 1, comp), row_bytes(w.nx, w.ny, wsz, diff),
+          col_bytes(w.nx, w.ny, wsz, 2, comp, diff)]
     dom = int(np.argmax(kt))
     peaks, peak_src = _peaks()
     if fp32:
@@ -485,8 +490,10 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
     ms3 = e0.elapsed_time(e1)
     kt3 = p3.kernel_times(u3, 20)
     comp3 = os.environ.get("KZK_COMPSTATE", "1") != "0"
-    by3 = [row_bytes(4096, 2048, 4), col_bytes(4096, 2048, 4, 1, comp3), row_bytes(4096, 2048, 4),
-           col_bytes(4096, 2048, 4, 2, comp3)]
+    # row and column pairs both in use: the stage-2 row pass stores b2 - b1
+    diff3 = comp3 and all(os.environ.get(v, "1") != "0" for v in ("KZK_ROWPAIR", "KZK_COLPAIR", "KZK_COLPIPE"))
+    by3 = [row_bytes(4096, 2048, 4), col_bytes(4096, 2048, 4, 1, comp3), row_bytes(4096, 2048, 4, diff3),
+           col_bytes(4096, 2048, 4, 2, comp3, diff3)]
     names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
     dom = int(np.argmax(kt3))
     hbm = peaks["hbm_gbs"] * 1e9
