@@ -85,6 +85,38 @@ __device__ __forceinline__ void pair_stats(const c2* u, int k0, int Q, float& sa
 }
 
 // SUB: subtract the rows P.sub from the result (ROW_RHS / ROW_RHS_MED)
+// The two rows' statistics reduced as block_diag_t reduces one row's (FP32
+// shuffles within warps, FP64 sums over the warps in warp order), split at the
+// barrier that follows the WENO sweep: before it, lane 0 of every warp stores
+// its 8 partials; after it, thread c < 8 sums partial c over the warps.
+__device__ __forceinline__ void pair_diag_partial(double* red, float sa1, float sa2, float mxa, int nfa, float sb1,
+                                                  float sb2, float mxb, int nfb)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sa1 += __shfl_xor_sync(0xffffffffu, sa1, o);
+        sa2 += __shfl_xor_sync(0xffffffffu, sa2, o);
+        mxa = fmax(mxa, __shfl_xor_sync(0xffffffffu, mxa, o));
+        nfa += __shfl_xor_sync(0xffffffffu, nfa, o);
+        sb1 += __shfl_xor_sync(0xffffffffu, sb1, o);
+        sb2 += __shfl_xor_sync(0xffffffffu, sb2, o);
+        mxb = fmax(mxb, __shfl_xor_sync(0xffffffffu, mxb, o));
+        nfb += __shfl_xor_sync(0xffffffffu, nfb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        double* r = red + 8 * (threadIdx.x >> 5);
+        r[0] = (double)sa1; r[1] = (double)sa2; r[2] = (double)mxa; r[3] = (double)nfa;
+        r[4] = (double)sb1; r[5] = (double)sb2; r[6] = (double)mxb; r[7] = (double)nfb;
+    }
+}
+__device__ __forceinline__ void pair_diag_final(const double* red, double* dst)
+{
+    const int c = threadIdx.x, nw = (blockDim.x + 31) >> 5;
+    double v = 0;
+    for (int w = 0; w < nw; w++) v = (c & 3) == 2 ? fmax(v, red[8 * w + c]) : v + red[8 * w + c];
+    dst[c] = v;   // row j: dst[0..3], row j + 1: dst[4..7]
+}
+
 template <int MODE, bool SUB = false>
 __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs P)
 {
@@ -176,7 +208,9 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             }
             if (a.diag_rows) pair_stats(X, k0, Q, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
         }
+        if (a.diag_rows) pair_diag_partial(red, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
         __syncthreads();
+        if (a.diag_rows && tid < 8) pair_diag_final(red, a.diag_rows + ((long long)inst * a.ny + row) * 4);
         // the rows to subtract (both rows: 2n float2, contiguous) into X, free
         // from here on, while the forward transform runs
         if constexpr (SUB) {
@@ -241,7 +275,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             }
         }
     }
-    if (a.diag_rows) {
+    if (MODE == ROW_INV && a.diag_rows) {
         double* dst = a.diag_rows + ((long long)inst * a.ny + row) * 4;
         block_diag_t<float>(red, sa1, sa2, mxa, nfa, dst);
         __syncthreads();
