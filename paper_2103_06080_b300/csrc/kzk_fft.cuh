@@ -130,9 +130,11 @@ struct Tw {
 // (PPT / R butterflies per pass).  COLS: consecutive threads take consecutive
 // transforms (column tiles, transform index fastest in memory); otherwise
 // consecutive threads take consecutive butterflies of one transform.
-template <typename T, int R, int PPT, bool COLS, bool INV, bool PAD, bool ACC>
-__device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int si, int sb, int log2Ns,
-                                         const Tw<T>& tw, int stage_off, int tid, int nthr)
+// In place (src == dst, OOP false): a barrier between the loads and the
+// stores; out of place (OOP): none.  Both end with a __syncthreads().
+template <typename T, int R, int PPT, bool COLS, bool INV, bool PAD, bool ACC, bool OOP = false>
+__device__ __forceinline__ void fft_pass(const cx<T>* src, cx<T>* dst, int log2n, int log2nb, int si, int sb,
+                                         int log2Ns, const Tw<T>& tw, int stage_off, int tid, int nthr)
 {
     constexpr int NB = PPT / R;
     constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
@@ -157,10 +159,10 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
                 // padded index of ib + r * stride is padx(ib) + r * padded stride
                 const int pb = sidx<PAD>(ib), ps = PAD ? stride + (stride >> 4) : stride;
 #pragma unroll
-                for (int r = 0; r < R; r++) v[q][r] = buf[pb + r * ps];
+                for (int r = 0; r < R; r++) v[q][r] = src[pb + r * ps];
             } else {
 #pragma unroll
-                for (int r = 0; r < R; r++) v[q][r] = buf[sidx<PAD>(ib + r * stride)];
+                for (int r = 0; r < R; r++) v[q][r] = src[sidx<PAD>(ib + r * stride)];
             }
             if (log2Ns > 0) {
 #pragma unroll
@@ -180,7 +182,7 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
             obase[q] = b * sb + (((j - k) << LR) + k) * si;
         }
     }
-    __syncthreads();
+    if constexpr (!OOP) __syncthreads();
     const int ostride = Ns * si;
 #pragma unroll
     for (int q = 0; q < NB; q++) {
@@ -188,14 +190,20 @@ __device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int 
             if (!PAD || (ostride & 15) == 0) {
                 const int pb = sidx<PAD>(obase[q]), ps = PAD ? ostride + (ostride >> 4) : ostride;
 #pragma unroll
-                for (int r = 0; r < R; r++) buf[pb + r * ps] = v[q][r];
+                for (int r = 0; r < R; r++) dst[pb + r * ps] = v[q][r];
             } else {
 #pragma unroll
-                for (int r = 0; r < R; r++) buf[sidx<PAD>(obase[q] + r * ostride)] = v[q][r];
+                for (int r = 0; r < R; r++) dst[sidx<PAD>(obase[q] + r * ostride)] = v[q][r];
             }
         }
     }
     __syncthreads();
+}
+template <typename T, int R, int PPT, bool COLS, bool INV, bool PAD, bool ACC>
+__device__ __forceinline__ void fft_pass(cx<T>* buf, int log2n, int log2nb, int si, int sb, int log2Ns,
+                                         const Tw<T>& tw, int stage_off, int tid, int nthr)
+{
+    fft_pass<T, R, PPT, COLS, INV, PAD, ACC, false>(buf, buf, log2n, log2nb, si, sb, log2Ns, tw, stage_off, tid, nthr);
 }
 
 // Full transform: radix-16 passes while possible, then one smaller pass.
@@ -225,6 +233,44 @@ __device__ __forceinline__ void fft_batched(cx<T>* buf, int log2n, int log2nb, i
             done += 1;
         }
     }
+}
+
+// The same schedule out of place, passes alternating between buffers a (the
+// input) and b; returns the buffer holding the result.  One barrier per pass.
+template <typename T, int PPT, bool COLS, bool INV, bool PAD = false, bool ACC = false>
+__device__ __forceinline__ cx<T>* fft_batched_pp(cx<T>* a, cx<T>* b, int log2n, int log2nb, int si, int sb,
+                                                 const Tw<T>& tw, int tid, int nthr)
+{
+    int done = 0, off = 0;
+    cx<T>* s = a;
+    cx<T>* d = b;
+    while (done < log2n) {
+        const int rem = log2n - done;
+        if (PPT >= 16 && rem >= 4) {
+            fft_pass<T, (PPT >= 16 ? 16 : 2), PPT, COLS, INV, PAD, ACC, true>(s, d, log2n, log2nb, si, sb, done, tw,
+                                                                             off, tid, nthr);
+            off += (done > 0 ? ((PPT >= 16 ? 16 : 2) - 1) << done : 0);
+            done += (PPT >= 16 ? 4 : 1);
+        } else if (PPT >= 8 && rem >= 3) {
+            fft_pass<T, (PPT >= 8 ? 8 : 2), PPT, COLS, INV, PAD, ACC, true>(s, d, log2n, log2nb, si, sb, done, tw,
+                                                                           off, tid, nthr);
+            off += (done > 0 ? ((PPT >= 8 ? 8 : 2) - 1) << done : 0);
+            done += (PPT >= 8 ? 3 : 1);
+        } else if (PPT >= 4 && rem >= 2) {
+            fft_pass<T, (PPT >= 4 ? 4 : 2), PPT, COLS, INV, PAD, ACC, true>(s, d, log2n, log2nb, si, sb, done, tw,
+                                                                           off, tid, nthr);
+            off += (done > 0 ? ((PPT >= 4 ? 4 : 2) - 1) << done : 0);
+            done += (PPT >= 4 ? 2 : 1);
+        } else {
+            fft_pass<T, 2, PPT, COLS, INV, PAD, ACC, true>(s, d, log2n, log2nb, si, sb, done, tw, off, tid, nthr);
+            off += (done > 0 ? 1 << done : 0);
+            done += 1;
+        }
+        cx<T>* t = s;
+        s = d;
+        d = t;
+    }
+    return s;
 }
 
 // Radix schedule of fft_batched for a length 2^log2n with PPT points

@@ -154,6 +154,12 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         }
         return;
     }
+    // U: the physical rows (the WENO sweep's input), Bf: the sweep's output and
+    // the forward transform's buffer.  ROW_RHS runs its transforms out of
+    // place, between the two buffers (one barrier per pass instead of two),
+    // so which buffer ends up holding what depends on the number of passes.
+    c2* U = X;
+    c2* Bf = Y;
     if constexpr (MODE == ROW_RHS_MED) {
         const float* u0 = a.uphys + 2 * base;
         for (int i = tid; i < nx; i += nthr) st_real<f2, true>(X, i, f2(__ldcg(u0 + i), __ldcg(u0 + nx + i)));
@@ -163,7 +169,12 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         __syncthreads();
         c2r_pre<f2, true>(X, n, P.tw2, tid, nthr);
         __syncthreads();
-        fft_batched<f2, PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
+        if constexpr (MODE == ROW_RHS) {
+            U = fft_batched_pp<f2, PPT, false, true, true>(X, Y, log2n, 0, 1, 0, tw, tid, nthr);
+            Bf = U == X ? Y : X;
+        } else {
+            fft_batched<f2, PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
+        }
     }
 
     float sa1 = 0, sa2 = 0, mxa = 0, sb1 = 0, sb2 = 0, mxb = 0;
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         if (MODE == ROW_RHS && a.u_out) {
             float* d0 = a.u_out + 2 * base;
             for (int i = tid; i < nx; i += nthr) {
-                const f2 w = ld_real<f2, true>(X, i);
+                const f2 w = ld_real<f2, true>(U, i);
                 d0[i] = w.v.x;
                 d0[nx + i] = w.v.y;
             }
@@ -202,19 +213,19 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
                 const double c1 = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * (row + 1));
                 wc.c = f2((float)c0, (float)c1);
                 wc.alpha = f2((float)(fabs(c0) + (double)a.wc.alpha), (float)(fabs(c1) + (double)a.wc.alpha));
-                weno_row_chunk<f2, true, true>(X, Y, nx, k0, Q, wc);
+                weno_row_chunk<f2, true, true>(U, Bf, nx, k0, Q, wc);
             } else {
-                weno_row_chunk<f2, true>(X, Y, nx, k0, Q, wc);
+                weno_row_chunk<f2, true>(U, Bf, nx, k0, Q, wc);
             }
-            if (a.diag_rows) pair_stats(X, k0, Q, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
+            if (a.diag_rows) pair_stats(U, k0, Q, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
         }
         if (a.diag_rows) pair_diag_partial(red, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
         __syncthreads();
         if (a.diag_rows && tid < 8) pair_diag_final(red, a.diag_rows + ((long long)inst * a.ny + row) * 4);
-        // the rows to subtract (both rows: 2n float2, contiguous) into X, free
-        // from here on, while the forward transform runs
+        // the rows to subtract (both rows: 2n float2, contiguous) into U, free
+        // from here on, while the forward transform runs (in place, then)
         if constexpr (SUB) {
-            const unsigned xs = (unsigned)__cvta_generic_to_shared(X);
+            const unsigned xs = (unsigned)__cvta_generic_to_shared(U);
             for (int i = tid; i < n; i += nthr)
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(xs + 16u * i),
                              "l"(P.sub + base + 2 * i)
@@ -223,18 +234,20 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         if constexpr (MODE == ROW_RHS_MED) {
             const float* by0 = a.by + 2 * base;
             for (int k = tid; k < nx; k += nthr)
-                st_real<f2, true>(Y, k, ld_real<f2, true>(Y, k) + f2(__ldcg(by0 + k), __ldcg(by0 + nx + k)));
+                st_real<f2, true>(Bf, k, ld_real<f2, true>(Bf, k) + f2(__ldcg(by0 + k), __ldcg(by0 + nx + k)));
             __syncthreads();
         }
-        fft_batched<f2, PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
+        c2* Z = Bf;
+        if constexpr (MODE == ROW_RHS && !SUB) Z = fft_batched_pp<f2, PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
+        else fft_batched<f2, PPT, false, false, true>(Bf, log2n, 0, 1, 0, tw, tid, nthr);
         if constexpr (SUB) {
             asm volatile("cp.async.wait_all;" ::: "memory");
             __syncthreads();
         }
-        const float2* Xs = reinterpret_cast<const float2*>(X);
+        const float2* Xs = reinterpret_cast<const float2*>(U);
         for (int k = tid; k <= n / 2; k += nthr) {
             c2 xk, xnk;
-            r2c_post_pair<f2, true>(Y, n, k, P.tw2, xk, xnk);
+            r2c_post_pair<f2, true>(Z, n, k, P.tw2, xk, xnk);
             float2 k0a = lane0(xk), k0b = lane1(xk), kna = lane0(xnk), knb = lane1(xnk);
             if (a.cA != 0.0f) {
                 // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx), each row
