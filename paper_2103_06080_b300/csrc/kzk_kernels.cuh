@@ -103,6 +103,33 @@ __device__ __forceinline__ void block_diag_t(double* red, T s1, T s2, T mx, int 
     }
 }
 
+// block_diag_t split at a barrier the caller has anyway: diag_partial before
+// it (shuffles, lane 0 of each warp stores its partials), diag_final after it
+// by threads 0..3 (component c summed over the warps in warp order, as
+// block_diag_t's thread 0 does): the same results.
+template <typename T>
+__device__ __forceinline__ void diag_partial(double* red, T s1, T s2, T mx, int nf)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        double* r = red + 4 * (threadIdx.x >> 5);
+        r[0] = (double)s1; r[1] = (double)s2; r[2] = (double)mx; r[3] = (double)nf;
+    }
+}
+__device__ __forceinline__ void diag_final(const double* red, double* dst)
+{
+    const int c = threadIdx.x, nw = (blockDim.x + 31) >> 5;
+    double v = 0;
+    for (int w = 0; w < nw; w++) v = c == 2 ? fmax(v, red[4 * w + c]) : v + red[4 * w + c];
+    dst[c] = v;
+}
+
 // C2R pre-processing in place: packed half spectrum X (n = nx/2 slots) ->
 // Z with IFFT_n(Z) = nx * (x_even + i x_odd), Z_k = (X_k + conj X_{n-k})
 // + i conj(W^k) (X_k - conj X_{n-k}), W = exp(-2 pi i / nx).
@@ -217,18 +244,29 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
             if (k != 0 && 2 * k != n) a.out[base + n - k] = scale<T>(xnk, a.out_scale);
         }
     } else {
+        // U: the physical row (the WENO sweep's input), Bf: the sweep's output
+        // and the forward transform's buffer.  The b passes run their
+        // transforms out of place between the two (one barrier per pass), so
+        // which buffer holds what depends on the number of passes.
+        cx<T>* U = X;
+        cx<T>* Bf = Y;
         if constexpr (MODE == ROW_RHS_MED) {
             // the physical row, written by the ROW_INV pass of this stage
             const T* urow = a.uphys + 2 * base;
             for (int i = tid; i < nx; i += nthr) st_real<T, true>(X, i, __ldcg(urow + i));
             __syncthreads();
         } else {
-            // spectral row -> physical row in X
+            // spectral row -> physical row
             load_row<T>(a.in + base, X, n, tid, nthr);
             __syncthreads();
             c2r_pre<T, true>(X, n, a.tw, tid, nthr);
             __syncthreads();
-            fft_batched<T, ROW_PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
+            if constexpr (MODE == ROW_RHS) {
+                U = fft_batched_pp<T, ROW_PPT, false, true, true>(X, Y, log2n, 0, 1, 0, tw, tid, nthr);
+                Bf = U == X ? Y : X;
+            } else {
+                fft_batched<T, ROW_PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
+            }
         }
 
         T s1 = 0, s2 = 0, mx = 0;
@@ -246,7 +284,7 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
             if (a.u_out) {
                 // the stage state in physical space, for the adjoint sweep
                 T* dst = a.u_out + 2 * base;
-                for (int i = tid; i < nx; i += nthr) dst[i] = ld_real<T, true>(X, i);
+                for (int i = tid; i < nx; i += nthr) dst[i] = ld_real<T, true>(U, i);
             }
             // chunks of at least 16 points (the sweep's pre-roll is 3 centres)
             const int Q = nx / nthr >= 16 ? nx / nthr : (nx >= 16 ? 16 : nx);
@@ -258,24 +296,27 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
                     const double cj = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * row);
                     wc.c = (T)cj;
                     wc.alpha = (T)(fabs(cj) + (double)a.wc.alpha);
-                    weno_row_chunk<T, true, true>(X, Y, nx, k0, Q, wc);
+                    weno_row_chunk<T, true, true>(U, Bf, nx, k0, Q, wc);
                 } else {
-                    weno_row_chunk<T, true>(X, Y, nx, k0, Q, a.wc);
+                    weno_row_chunk<T, true>(U, Bf, nx, k0, Q, a.wc);
                 }
-                if (a.diag_rows) row_stats<T, true>(X, k0, Q, s1, s2, mx, nf);
+                if (a.diag_rows) row_stats<T, true>(U, k0, Q, s1, s2, mx, nf);
             }
+            // the row statistics reduced across the barrier that ends the sweep
+            if (a.diag_rows) diag_partial<T>(red, s1, s2, mx, nf);
             __syncthreads();
+            if (a.diag_rows && tid < 4) diag_final(red, a.diag_rows + ((long long)inst * a.ny + row) * 4);
             if constexpr (MODE == ROW_RHS_MED) {
                 // plus the y-flux difference and source of this row
                 const T* byrow = a.by + 2 * base;
-                for (int k = tid; k < nx; k += nthr) st_real<T, true>(Y, k, ld_real<T, true>(Y, k) + __ldcg(byrow + k));
+                for (int k = tid; k < nx; k += nthr) st_real<T, true>(Bf, k, ld_real<T, true>(Bf, k) + __ldcg(byrow + k));
                 __syncthreads();
             }
-            fft_batched<T, ROW_PPT, false, false, true>(Y, log2n, 0, 1, 0, tw, tid, nthr);
+            const cx<T>* Z = fft_batched_pp<T, ROW_PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
             const cx<T>* vin = a.in + base;
             for (int k = tid; k <= n / 2; k += nthr) {
                 cx<T> xk, xnk;
-                r2c_post_pair<T, true>(Y, n, k, a.tw, xk, xnk);
+                r2c_post_pair<T, true>(Z, n, k, a.tw, xk, xnk);
                 if (a.cA != T(0)) {
                     // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
                     if (k == 0) {
@@ -297,7 +338,6 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
                 a.out[base + k] = xk;
                 if (k != 0 && 2 * k != n) a.out[base + n - k] = xnk;
             }
-            if (a.diag_rows) block_diag_t<T>(red, s1, s2, mx, nf, a.diag_rows + ((long long)inst * a.ny + row) * 4);
         }
     }
 }
