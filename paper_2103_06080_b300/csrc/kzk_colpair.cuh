@@ -24,9 +24,12 @@
 // bulk copy (the plan stores them pair-major, as lane pairs, with their rows
 // permuted by pair_tab_row so that the digit-reversed row indices the warps
 // read hit distinct banks).  The state tiles (16-byte rows, one per y) come by
-// TMA; the tensor engine takes them at about one row per cycle, which is why
-// nothing else goes through it (no L2 prefetch of later tiles either: that
-// doubled the rows it had to process and made both passes slower).  Elements of
+// TMA; the tensor engine takes them at about one row per cycle, so the
+// copies are ordered for overlap (STAGE1: b1 first, transformed while V and
+// the tables arrive; V again into the freed b1 region for the last pass; V*
+// out by a tensor store) and nothing else goes through it (no L2 prefetch of
+// later tiles: that doubled the rows it had to process and made both passes
+// slower; STAGE2 takes b2 - b1 from the row pass, two tiles in).  Elements of
 // the work tiles sit at psw(i) = i ^ ((i >> 3) & 7) (16-byte slots), which
 // makes every pass's shared-memory accesses conflict-free.  The packed column
 // m = 0 (its row l is coupled with row ny - l) takes a separate pass between
