@@ -131,3 +131,15 @@ def test_colpair_in_the_adjoint_recompute():
                       torch.tensor(g_end, dtype=torch.float32, device="cuda"), w.n_steps, ckpt_every=3)
     got = g0.double().cpu().numpy()
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 3e-3
+
+
+def test_colpair_with_single_row_passes(monkeypatch):
+    """KZK_ROWPAIR=0: the single-row passes store b2 itself, and the
+    column-pair stage 2 forms b2 - b1 from its two tiles."""
+    w = inputs.config(2, nx=128, ny=512, n_steps=15)
+    a = _run32(w, w.u0, 15)
+    monkeypatch.setenv("KZK_ROWPAIR", "0")
+    b = _run32(w, w.u0, 15)
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, 15, threads=True)
+    assert rel_l2(b, ref) < 1e-5
+    assert rel_l2(a, b) < 1e-6
