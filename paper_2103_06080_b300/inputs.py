@@ -14,7 +14,6 @@ output i of seed s is mix64(s + (i+1) * 0x9E3779B97F4A7C15), converted to
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -243,4 +242,3 @@ def oracle_params(w: Workload, **over):
     return d
 
 
-_ = math  # keep import for callers doing arithmetic on configs
