@@ -112,14 +112,20 @@ def col_bytes(nx, ny, w, stage, comp=False, diff=False):
     return (3 * unit + 2 * tab + lo) if stage == 1 else ((3 if diff else 4) * unit + tab + lo)
 
 
+# WENO5 per point and evaluation: the Jiang-Shu reconstruction counted as
+# written (about 130 additions and multiplications for the split fluxes, the
+# candidate stencils, the smoothness indicators, the weights and the
+# difference) plus its 8 divisions, each counted as one operation
+WENO5_FLOPS = 130 + 8
+
+
 def row_flops(nx, ny, profile=True):
     """Row pass FLOPs (add, mul, div = 1; FMA = 2): two real FFTs of length nx
-    (2.5 nx log2(nx/2) each, as complex FFTs of nx/2 points, plus 8 per point
-    for the real pre/post-processing), WENO5 (166 per point: 9 for the split
-    fluxes, 2 x 77 for the two reconstructions, 3 for the difference),
+    (2.5 nx log2(nx/2) each, as complex FFTs of nx/2 points, plus 4 per point
+    for the real pre/post-processing), WENO5 (WENO5_FLOPS per point),
     diagnostics (3) and the absorption-deviation term (5 with a profile)."""
     lg = np.log2(nx // 2)
-    per_pt = 2 * (2.5 * lg + 4) + 166 + 3 + (5 if profile else 0)
+    per_pt = 2 * (2.5 * lg + 4) + WENO5_FLOPS + 3 + (5 if profile else 0)
     return per_pt * nx * ny
 
 
@@ -302,9 +308,10 @@ def run_ours(args, rank, world, local_rank):
     kt = plan.kernel_times(u, min(args.steps, 20), sigma0=0.0)
     names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
     fl = [row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 1), row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 2)]
-    comp = fp32 and os.environ.get("KZK_COMPSTATE", "1") != "0"
-    diff = comp and 256 <= w.ny <= 4096 and all(os.environ.get(v, "1") != "0"
-                                                for v in ("KZK_ROWPAIR", "KZK_COLPAIR", "KZK_COLPIPE"))
+    info = plan.info()
+    comp = fp32 and info["fp32_state"] == "compensated"
+    # row and column pairs both in use: the stage-2 row pass stores b2 - b1
+    diff = info["row_kernel"] == "pair" and info["col_kernel"] == "pair"
     by = [row_bytes(w.nx, w.ny, wsz), col_bytes(w.nx, w.ny, wsz, 1, comp), row_bytes(w.nx, w.ny, wsz, diff),
           col_bytes(w.nx, w.ny, wsz, 2, comp, diff)]
     dom = int(np.argmax(kt))
@@ -421,7 +428,7 @@ def medium_step_work(nx, ny, w):
     N w (N = nx ny); FP32 adds the lo part of E' (half a unit)."""
     lg = np.log2(nx // 2)
     fft_pt = 2.5 * lg + 4
-    stage_flops = nx * ny * (fft_pt + (166 + 3) + (2 * fft_pt + 166 + 3 + 3))
+    stage_flops = nx * ny * (fft_pt + (WENO5_FLOPS + 3) + (2 * fft_pt + WENO5_FLOPS + 3 + 3))
     flops = 2 * stage_flops + col_flops(nx, ny, 1) + col_flops(nx, ny, 2)
     units = 2 * (2 + 2 + 3) + 2.5 + (4.0 if w == 4 else 3.5) + 4.5
     return flops, units * nx * ny * w
@@ -489,9 +496,10 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
     torch.cuda.synchronize()
     ms3 = e0.elapsed_time(e1)
     kt3 = p3.kernel_times(u3, 20)
-    comp3 = os.environ.get("KZK_COMPSTATE", "1") != "0"
+    info3 = p3.info()
+    comp3 = info3["fp32_state"] == "compensated"
     # row and column pairs both in use: the stage-2 row pass stores b2 - b1
-    diff3 = comp3 and all(os.environ.get(v, "1") != "0" for v in ("KZK_ROWPAIR", "KZK_COLPAIR", "KZK_COLPIPE"))
+    diff3 = info3["row_kernel"] == "pair" and info3["col_kernel"] == "pair"
     by3 = [row_bytes(4096, 2048, 4), col_bytes(4096, 2048, 4, 1, comp3), row_bytes(4096, 2048, 4, diff3),
            col_bytes(4096, 2048, 4, 2, comp3, diff3)]
     names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
@@ -649,7 +657,7 @@ def main():
     ap.add_argument("--err-nx", type=int, default=1024)
     ap.add_argument("--err-ny", type=int, default=512)
     ap.add_argument("--err-steps", type=int, default=2000)
-    ap.add_argument("--adj-steps", type=int, default=128)
+    ap.add_argument("--adj-steps", type=int, default=1000)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=20)
