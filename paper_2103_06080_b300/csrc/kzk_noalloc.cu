@@ -13,9 +13,18 @@
 // holds until the process exits.
 //
 // Scratch contents are not cleared between calls: every element a call reads
-// is written earlier in the same call.  All calls share the one array, so
-// calls whose GPU work overlaps (different streams, or different host
-// threads) race on it; serialise them (one stream, or explicit ordering).
+// is written earlier in the same call, except the twiddle tables, which a call
+// leaves in place for the next call with the same nx and precision on the
+// same context.  All calls share the one array, so calls whose GPU work
+// overlaps (different streams, or different host threads) race on it;
+// serialise them (one stream, or explicit ordering).
+//
+// Per-device set-up (the array's device address, the kernels' shared-memory
+// limit, which twiddle tables the array holds) is cached under the id of the
+// device's current CUDA context: if that context is destroyed and re-created
+// (cudaDeviceReset), the module is loaded afresh, and the next call sees a new
+// id and repeats the set-up.
+#include <cuda.h>
 #include <mutex>
 
 #include "../../include/kzk.h"
@@ -35,11 +44,47 @@ constexpr size_t kScratchBytes = 2 * kSpecBytes + (size_t)kMaxNx * 16 + (size_t)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch per device, found once per device.
+// Set-up per device, valid for the context whose id it records.
 constexpr int kMaxDevices = 64;
+struct DevSetup {
+    unsigned long long ctx_id;  // cuCtxGetId of the context the entries below belong to (0: none)
+    void* scratch;              // device address of g_noalloc_scratch in that context
+    int tw_nx;                  // nx and precision of the twiddle tables in the array (0: none)
+    int tw_prec;
+};
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-bool g_attr_done[kMaxDevices] = {false};
+DevSetup g_dev[kMaxDevices] = {};
+
+// cuCtxGetCurrent / cuCtxGetId from the driver, looked up once through the
+// runtime (no link-time dependency on libcuda)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+template <typename F>
+F driver_fn(const char* name)
+{
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return reinterpret_cast<F>(f);
+}
+
+// id of the calling thread's current context; with none current, device
+// dev's primary context is made current first (cudaSetDevice, which creates
+// it if needed); 0 on failure
+unsigned long long current_ctx_id(int dev)
+{
+    static const CtxGetCurrentFn get_cur = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+    static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+    if (!get_cur || !get_id) return 0;
+    CUcontext c = nullptr;
+    if (get_cur(&c) != CUDA_SUCCESS) return 0;
+    if (!c && (cudaSetDevice(dev) != cudaSuccess || get_cur(&c) != CUDA_SUCCESS || !c)) return 0;
+    unsigned long long id = 0;
+    if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 template <typename T>
 __global__ void noalloc_twiddles(cx<T>* tw, int nx)
@@ -76,8 +121,8 @@ __global__ void noalloc_staged_twiddles(cx<T>* tws, int log2n, int ppt)
 double horner4(const double* c, double s) { return ((c[3] * s + c[2]) * s + c[1]) * s + c[0]; }
 
 template <typename T>
-kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch, const void* u, void* b,
-               double sigma, cudaStream_t st, int dev)
+kzk_status run(void* scratch, bool tables_valid, const kzk_grid* g, const kzk_coeffs* c, int batch, const void* u,
+               void* b, double sigma, cudaStream_t st)
 {
     const int nx = g->nx, ny = g->ny, n = nx / 2;
     const int log2nx = ilog2((unsigned)nx);
@@ -88,26 +133,10 @@ kzk_status run(void* scratch, const kzk_grid* g, const kzk_coeffs* c, int batch,
     cx<T>* tws = (cx<T>*)(base + 2 * kSpecBytes + (size_t)kMaxNx * 16);
     const int thr = row_threads<T>(nx);
     const size_t smem = row_smem_bytes<T>(nx);
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_attr_done[dev]) {
-            // lift the dynamic shared-memory limit of the three row kernels once
-            // per device (an attribute, not an allocation)
-            int optin = 0;
-            if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-                return KZK_ERR_CUDA;
-            for (cudaError_t e : {cudaFuncSetAttribute(row_kernel<double, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<double, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<double, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<float, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<float, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
-                                  cudaFuncSetAttribute(row_kernel<float, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)})
-                if (e != cudaSuccess) return KZK_ERR_CUDA;
-            g_attr_done[dev] = true;
-        }
+    if (!tables_valid) {
+        noalloc_twiddles<T><<<(nx + 255) / 256, 256, 0, st>>>(tw, nx);
+        noalloc_staged_twiddles<T><<<(n + 255) / 256, 256, 0, st>>>(tws, log2nx - 1, row_ppt_of<T>());
     }
-    noalloc_twiddles<T><<<(nx + 255) / 256, 256, 0, st>>>(tw, nx);
-    noalloc_staged_twiddles<T><<<(n + 255) / 256, 256, 0, st>>>(tws, log2nx - 1, row_ppt_of<T>());
 
     RowArgs<T> a{};
     a.tw = tw;
@@ -165,26 +194,57 @@ extern "C" kzk_status kzk_rhs_noalloc(const kzk_grid* grid, const kzk_coeffs* co
         return set_error(KZK_ERR_SIZE, "kzk_rhs_noalloc: batch * nx * ny exceeds KZK_NOALLOC_MAX_POINTS (262144)");
     if (!(grid->tau_max > grid->tau_min) || !(coeffs->B > 0) || !(coeffs->lf_umax > 0) || !(coeffs->A >= 0))
         return set_error(KZK_ERR_ARG, "kzk_rhs_noalloc: need tau_max > tau_min, B > 0, A >= 0, lf_umax > 0");
+    // an error left pending by the caller's earlier work would be read back
+    // as a failure of this call's launches: refuse to run, and leave it pending
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        return set_error(KZK_ERR_CUDA, "kzk_rhs_noalloc: a CUDA error from earlier work was pending before the call "
+                                       "(left pending, nothing launched)");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return set_error(KZK_ERR_CUDA, "kzk_rhs_noalloc: no usable current device");
+    const unsigned long long ctx = current_ctx_id(dev);
+    if (!ctx) return set_error(KZK_ERR_CUDA, "kzk_rhs_noalloc: could not identify the current CUDA context");
+    const int prec = grid->prec == KZK_FP64 ? 8 : 4;
     void* scratch = nullptr;
+    bool tables_valid = false;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_ptr[dev]) {
-            // set-up, once per device, with that device current: the array's
-            // name is only a host-side stand-in; its device address comes from
-            // the runtime
+        DevSetup& d = g_dev[dev];
+        if (d.ctx_id != ctx) {
+            // set-up, once per device and context, with that device current:
+            // the array's name is only a host-side stand-in; its device address
+            // comes from the runtime
+            d = DevSetup{};
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
                 return set_error(KZK_ERR_CUDA, "kzk_rhs_noalloc: cudaGetSymbolAddress of the scratch array failed");
-            g_scratch_ptr[dev] = p;
+            // lift the dynamic shared-memory limit of the row kernels (an
+            // attribute, not an allocation)
+            int optin = 0;
+            if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+                return set_error(KZK_ERR_CUDA, "kzk_rhs_noalloc: device attribute query failed");
+            for (cudaError_t e : {cudaFuncSetAttribute(row_kernel<double, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<double, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<double, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<float, ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<float, ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+                                  cudaFuncSetAttribute(row_kernel<float, ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)})
+                if (e != cudaSuccess)
+                    return set_error(KZK_ERR_CUDA, "kzk_rhs_noalloc: setting the kernels' shared-memory limit failed");
+            d.scratch = p;
+            d.ctx_id = ctx;
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = d.scratch;
+        tables_valid = d.tw_nx == grid->nx && d.tw_prec == prec;
+        // the tables this call leaves in the array (its launches write them
+        // first when they are not there)
+        d.tw_nx = grid->nx;
+        d.tw_prec = prec;
     }
     cudaStream_t st = (cudaStream_t)stream;
     const kzk_status s = grid->prec == KZK_FP64
-                             ? run<double>(scratch, grid, coeffs, batch, u, b, sigma, st, dev)
-                             : run<float>(scratch, grid, coeffs, batch, u, b, sigma, st, dev);
+                             ? run<double>(scratch, tables_valid, grid, coeffs, batch, u, b, sigma, st)
+                             : run<float>(scratch, tables_valid, grid, coeffs, batch, u, b, sigma, st);
     return s == KZK_OK ? s : set_error(s, "kzk_rhs_noalloc: CUDA launch or attribute call failed");
 }

@@ -49,7 +49,11 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec,nx,ny,batch", [("fp64", 512, 256, 2), ("fp32", 256, 128, 1)])
+@pytest.mark.parametrize("prec,nx,ny,batch", [("fp64", 512, 256, 2), ("fp32", 256, 128, 1),
+                                               # the limits of the fixed scratch layout: the longest row
+                                               # (largest twiddle tables and shared-memory request) at
+                                               # exactly KZK_NOALLOC_MAX_POINTS points, and FP32 batches
+                                               ("fp64", 8192, 32, 1), ("fp32", 1024, 64, 4)])
 def test_noalloc_rhs_matches_plan_rhs_on_two_calls(prec, nx, ny, batch):
     import torch
 
@@ -75,3 +79,35 @@ def test_noalloc_rhs_matches_plan_rhs_on_two_calls(prec, nx, ny, batch):
         else:
             assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-5
     plan.close()
+
+
+@pytest.mark.gpu
+def test_noalloc_call_leaves_device_memory_untouched():
+    """The property the entry point exists for: after a warm-up (the first call
+    in the context looks up the array and loads the kernels), further calls
+    change the device's free memory by nothing.  No tensor is created between
+    the two readings."""
+    import torch
+    cases = []
+    for prec, nx, ny in (("fp64", 512, 128), ("fp32", 2048, 64)):
+        w = inputs.config(2, nx=nx, ny=ny, n_steps=50)
+        g, c = _grid_coeffs(w, prec)
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        u = torch.tensor(w.u0, dtype=dt, device="cuda")
+        cases.append((g, c, u, torch.empty_like(u)))
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def call_all(sigma):
+        for g, c, u, b in cases:
+            st = L.lib().kzk_rhs_noalloc(ctypes.byref(g), ctypes.byref(c), 1, u.data_ptr(), b.data_ptr(), sigma, sp)
+            assert st == L.KZK_OK, L.lib().kzk_last_error()
+
+    call_all(0.1)                       # warm-up: set-up and kernel loading
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    call_all(0.2)
+    call_all(0.3)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
