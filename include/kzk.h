@@ -66,28 +66,17 @@ typedef struct {
                                        sizes in [8, 16384] x [2, 32768] with nx/2 and ny
                                        free of prime factors above 7 (the paper's
                                        7*2^k x 1250*2^k grids, Table 1: mixed-radix
-                                       transforms; KZK_MIXED=1 in the environment selects
-                                       them for power-of-two grids too) */
+                                       transforms) */
     double tau_min, tau_max, y_min, y_max;
     int32_t prec;                   /* kzk_precision of state and bulk arithmetic.
                                        KZK_FP32 plans keep the spectral state as a
-                                       compensated pair hi + lo (FP32 hi, bf16 lo): the
-                                       column passes transform only the increment of a
-                                       stage ((E - 1) V + dsigma Phi1 b1 of Eq. 11) and add
-                                       it to hi + lo exactly (TwoSum), so the rounding of
-                                       a full-state transform pair does not accumulate
-                                       over thousands of steps (KZK_COMPSTATE=0 in the
-                                       environment: a plain FP32 state).  KZK_FP32 row
-                                       passes run on row pairs in packed FP32
-                                       (KZK_ROWPAIR=0: single rows); with the compensated
-                                       state and 256 <= ny <= 4096 their column passes run
-                                       on column pairs in packed FP32 with in-place
-                                       transforms (KZK_COLPAIR=0: Stockham tiles staged by
-                                       the tensor memory accelerator, the column passes of
-                                       the other KZK_FP32 plans; KZK_COLPIPE=0: per-tile
-                                       kernels with plain loads; KZK_COLPIPE=2: the TMA
-                                       Stockham kernels for KZK_FP64 too).
-                                       The environment is read at plan creation. */
+                                       compensated pair hi + lo (FP32 hi, bf16 lo) by
+                                       default: the column passes transform only the
+                                       increment of a stage ((E - 1) V + dsigma Phi1 b1 of
+                                       Eq. 11) and add it to hi + lo exactly (TwoSum), so the
+                                       rounding of a full-state transform pair does not
+                                       accumulate over thousands of steps (kzk_options
+                                       selects a plain FP32 state instead). */
 } kzk_grid;
 
 #define KZK_MAX_RELAX 2
@@ -134,6 +123,48 @@ typedef struct {
 
 typedef struct kzk_plan_s kzk_plan;
 
+/* Kernel and state choices of a plan (kzk_plan_create_ex).  Zero-initialise
+ * and set only what should be pinned: all zero (KZK_AUTO) gives the defaults
+ * below, which are what kzk_plan_create uses.  A choice the grid or the
+ * precision cannot take is refused with KZK_ERR_SIZE (kernel choices) or
+ * KZK_ERR_ARG (unknown values).  kzk_plan_info reports the choices in effect. */
+#define KZK_AUTO 0
+/* row_kernel: the tau passes (C2R, WENO5, R2C of one row)                    */
+#define KZK_ROW_PAIR 1          /* KZK_FP32, even ny: two rows per CTA as the lanes of
+                                   packed FP32 values (default for those plans)        */
+#define KZK_ROW_SINGLE 2        /* one row per CTA (default and only choice for KZK_FP64
+                                   and mixed-radix grids)                               */
+/* col_kernel: the y passes (transforms fused with the phi-multiplies)        */
+#define KZK_COL_PAIR 1          /* KZK_FP32 with the compensated state, 256 <= ny <= 4096,
+                                   nx >= 8: two spectral columns per CTA in packed FP32,
+                                   in-place transforms, tiles staged by the tensor memory
+                                   accelerator (default for those plans)               */
+#define KZK_COL_TMA 2           /* Stockham tiles staged by the tensor memory
+                                   accelerator (default for the other KZK_FP32 plans it
+                                   fits: ny >= 16, ny * TC / 8 <= 512 threads)          */
+#define KZK_COL_TILE 3          /* per-tile Stockham kernels with plain loads (default for
+                                   KZK_FP64 and for the plans no other kernel fits)     */
+/* fp32_state (KZK_FP32 plans)                                                 */
+#define KZK_STATE_COMPENSATED 1 /* hi + lo spectral state (default)                 */
+#define KZK_STATE_PLAIN 2       /* plain FP32 state; its propagator E and the state
+                                   transforms' twiddles are two-float (hi + lo)        */
+/* transforms                                                                  */
+#define KZK_TRANSFORMS_MIXED 1  /* the mixed-radix kernels for every grid (default:
+                                   radix-8/16 kernels for powers of two, mixed radix for
+                                   the other grids); row_kernel / col_kernel then take
+                                   no other value than KZK_AUTO / KZK_ROW_SINGLE        */
+typedef struct {
+    int32_t row_kernel;         /* KZK_AUTO, KZK_ROW_PAIR, KZK_ROW_SINGLE            */
+    int32_t col_kernel;         /* KZK_AUTO, KZK_COL_PAIR, KZK_COL_TMA, KZK_COL_TILE */
+    int32_t fp32_state;         /* KZK_AUTO, KZK_STATE_COMPENSATED, KZK_STATE_PLAIN  */
+    int32_t transforms;         /* KZK_AUTO, KZK_TRANSFORMS_MIXED                    */
+    int32_t autotune;           /* nonzero: every kernel choice left at KZK_AUTO is
+                                   made by timing instead -- each eligible (row_kernel,
+                                   col_kernel) combination advances a zero state for one
+                                   untimed and two timed steps (CUDA events) at plan
+                                   creation, and the fastest is kept                   */
+} kzk_options;
+
 /* Create a plan for `batch` independent propagations sharing grid,
  * coefficients and step dt (= dsigma of Eq. 5).  Builds the FP64 phi tables of
  * Eq. 11 on the device (rounded once to float for KZK_FP32), the twiddle
@@ -146,6 +177,18 @@ typedef struct kzk_plan_s kzk_plan;
  * failure. */
 kzk_status kzk_plan_create(const kzk_grid *grid, const kzk_coeffs *coeffs, double dt,
                            int32_t batch, kzk_plan **out);
+
+/* kzk_plan_create with explicit kernel and state choices (opts, host,
+ * nullable: NULL = all KZK_AUTO, which is kzk_plan_create).  Errors as
+ * kzk_plan_create, plus KZK_ERR_SIZE for a kernel choice the grid or precision
+ * cannot take, and KZK_ERR_ARG for an unknown option value. */
+kzk_status kzk_plan_create_ex(const kzk_grid *grid, const kzk_coeffs *coeffs, double dt, int32_t batch,
+                              const kzk_options *opts, kzk_plan **out);
+
+/* The choices in effect for a (non-batched) plan: every field resolved (no
+ * KZK_AUTO; fp32_state is KZK_AUTO for KZK_FP64 plans, transforms KZK_AUTO
+ * for the radix-8/16 kernels; autotune echoes the request).  out: host. */
+kzk_status kzk_plan_info(kzk_plan *plan, kzk_options *out);
 
 /* Random inhomogeneous medium (Sec. 2, Algorithm 1): the velocity field
  *   U(sigma, y) = sum_n U~_n cos(|K_n| lambda (sigma cos theta_n + y sin theta_n) + phi_n),
@@ -235,27 +278,41 @@ kzk_status kzk_adjoint(kzk_plan *plan, const void *u0, const void *g_end, void *
 
 /* Flags of kzk_plan_create_batched. */
 #define KZK_BATCH_AUTOTUNE 1
-/* Instead of the persistent kernel: each kzk_advance_batched call replays a
- * CUDA graph in which every instance runs the launches of kzk_advance (the
- * single-plan kernels, sized for that instance) on its own captured stream,
- * the instances concurrently.  The graph is cached per (n_steps, sigma0,
- * state pointers). */
+/* Each kzk_advance_batched call replays a CUDA graph in which every instance
+ * runs the launches of kzk_advance (its own plan's kernels, sized for its
+ * grid) on its own captured stream, the instances concurrently.  The graph is
+ * cached per (n_steps, sigma0, state pointers).  This is the default mode (no
+ * mode flag). */
 #define KZK_BATCH_STREAMS 2
+/* Instead: one persistent cooperative kernel launch per call for all
+ * instances (captured once per step count in a CUDA graph and replayed). */
+#define KZK_BATCH_PERSISTENT 4
 
 /* Plan for n independent propagations with their own grids (same precision),
- * coefficients and steps dts[i], all advanced by one persistent cooperative
- * kernel launch per kzk_advance_batched call (captured once in a CUDA graph
- * and replayed).  The launch runs every pass of every step for all instances
- * -- rows of all instances for the row passes, column tiles of all instances
- * for the column passes, the same computation as kzk_advance (KZK_FP32: with
- * the plans' compensated state, on the single-row and per-tile column bodies,
- * as KZK_ROWPAIR=0 KZK_COLPIPE=0 plans compute it) -- separated by
- * grid barriers whose waits are bounded (KZK_ERR_TIMEOUT).  With
- * KZK_BATCH_AUTOTUNE the column-tile width is chosen by timing two steps of
- * each candidate at creation.  Each grid must be a power of two, nx <= 8192
- * (with KZK_BATCH_STREAMS any grid kzk_plan_create accepts). */
+ * coefficients and steps dts[i], advanced together by one graph launch per
+ * kzk_advance_batched call.
+ * Streams mode (default, or KZK_BATCH_STREAMS): the graph holds every
+ * instance's kzk_advance launches on its own captured stream; any grid
+ * kzk_plan_create accepts.  With KZK_BATCH_AUTOTUNE every instance's kernel
+ * choices are made by timing (kzk_options.autotune).
+ * KZK_BATCH_PERSISTENT: the graph holds one persistent cooperative kernel that
+ * runs every pass of every step for all instances -- rows of all instances for
+ * the row passes, column tiles of all instances for the column passes, the
+ * same computation as kzk_advance (KZK_FP32: with the plans' compensated
+ * state, on the single-row and per-tile column bodies, as plans with
+ * KZK_ROW_SINGLE and KZK_COL_TILE compute it) -- separated by grid barriers
+ * whose waits are bounded (KZK_ERR_TIMEOUT).  With KZK_BATCH_AUTOTUNE the
+ * column-tile width is chosen by timing two steps of each candidate at
+ * creation.  Each grid must be a power of two, nx <= 8192.
+ * Errors as kzk_plan_create, and KZK_ERR_ARG for both mode flags. */
 kzk_status kzk_plan_create_batched(const kzk_grid *grids, const kzk_coeffs *coeffs, const double *dts,
                                    int32_t n, int32_t flags, kzk_plan **out);
+
+/* kzk_plan_create_batched whose instances take the kernel and state choices
+ * opts (host, nullable; as kzk_plan_create_ex).  In the persistent mode only
+ * fp32_state matters (the persistent kernel has its own bodies). */
+kzk_status kzk_plan_create_batched_ex(const kzk_grid *grids, const kzk_coeffs *coeffs, const double *dts,
+                                      int32_t n, int32_t flags, const kzk_options *opts, kzk_plan **out);
 
 /* Advance the n states u[i] (device pointers, [ny_i][nx_i], in place) by
  * n_steps steps each from sigma0.  diag_out (host, n entries, nullable)
@@ -265,15 +322,15 @@ kzk_status kzk_advance_batched(kzk_plan *plan, void *const *u, int64_t n_steps, 
 
 /* Launch configuration of a batched plan: CTAs of the persistent launch,
  * log2 cap on the column-tile width (the autotuner's choice), dynamic shared
- * memory per CTA (all 0 for a KZK_BATCH_STREAMS plan). */
+ * memory per CTA (all 0 for a plan in streams mode). */
 kzk_status kzk_batch_info(kzk_plan *plan, int32_t *grid_ctas, int32_t *tile_cap, int64_t *smem_bytes);
 
 /* Testing hook of the bounded grid barrier: later batched launches of this
  * plan wait for extra_blocks more CTAs than they launch (extra_blocks > 0
  * makes every barrier wait run out) with a wait bound of timeout_ms; such
  * launches are not graph-captured.  extra_blocks = 0 restores normal
- * operation (the bound stays timeout_ms).  KZK_ERR_STATE for a
- * KZK_BATCH_STREAMS plan. */
+ * operation (the bound stays timeout_ms).  KZK_ERR_STATE for a plan in
+ * streams mode. */
 kzk_status kzk_batch_test_barrier(kzk_plan *plan, int32_t extra_blocks, int64_t timeout_ms);
 
 /* kzk_advance that also keeps, inside the plan, the spectral state every
@@ -332,11 +389,17 @@ kzk_status kzk_alu_peak(int32_t prec, void *stream, double *flops_per_s);
  * caller's input and output; b = b(sigma, u) exactly as kzk_rhs computes it.
  * The intermediates live in one file-scope device array of
  * 2 * 8 * KZK_NOALLOC_MAX_POINTS + 16 * 12288 bytes (about 4.2 MB) that every
- * GPU loading the library keeps until the process exits.  The first call on a
- * device looks up that array's device address (and lifts the kernels' shared-
- * memory limit) for the current device; make that first call before any
- * stream capture.  All calls share the array, so calls whose GPU work
- * overlaps race: serialise them.  Errors: KZK_ERR_ARG (null, aliasing, bad
+ * GPU loading the library keeps until the process exits.  The first call in a
+ * CUDA context (per device; again after cudaDeviceReset re-creates the
+ * context, which the call notices by the context's id) looks up that array's
+ * device address and lifts the kernels' shared-memory limit; make that first
+ * call before any stream capture.  The array keeps the last call's contents:
+ * the twiddle tables of the last (nx, precision) stay and are reused by the
+ * next call with the same pair; everything else a call reads it writes first.
+ * All calls share the array, so calls whose GPU work overlaps (different
+ * streams or host threads) race: serialise them.  A CUDA error already pending
+ * on entry (cudaPeekAtLastError) is left pending and the call returns
+ * KZK_ERR_CUDA without launching.  Errors: KZK_ERR_ARG (null, aliasing, bad
  * precision or coefficients), KZK_ERR_SIZE (nx not a power of two in
  * [8, 8192], ny not a power of two, or batch * nx * ny above
  * KZK_NOALLOC_MAX_POINTS), KZK_ERR_CUDA.  Calls no cudaMalloc / cudaFree. */

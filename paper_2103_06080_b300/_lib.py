@@ -42,6 +42,22 @@ class KzkMedium(ctypes.Structure):
                 ("amp", ctypes.POINTER(ctypes.c_double))]
 
 
+class KzkOptions(ctypes.Structure):
+    _fields_ = [("row_kernel", ctypes.c_int32), ("col_kernel", ctypes.c_int32),
+                ("fp32_state", ctypes.c_int32), ("transforms", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
+
+
+# kzk_options values (include/kzk.h), by option
+KZK_AUTO = 0
+OPTION_VALUES = {
+    "row_kernel": {"auto": 0, "pair": 1, "single": 2},
+    "col_kernel": {"auto": 0, "pair": 1, "tma": 2, "tile": 3},
+    "fp32_state": {"auto": 0, "compensated": 1, "plain": 2},
+    "transforms": {"auto": 0, "mixed": 1},
+}
+
+
 class KzkDiag(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_double), ("energy", ctypes.c_double),
                 ("max_abs", ctypes.c_double), ("nonfinite", ctypes.c_double),
@@ -64,6 +80,9 @@ _VP = ctypes.c_void_p
 _SIGS = [
     ("kzk_plan_create", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs), ctypes.c_double,
                                        ctypes.c_int32, ctypes.POINTER(_VP)]),
+    ("kzk_plan_create_ex", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs), ctypes.c_double,
+                                          ctypes.c_int32, ctypes.POINTER(KzkOptions), ctypes.POINTER(_VP)]),
+    ("kzk_plan_info", ctypes.c_int, [_VP, ctypes.POINTER(KzkOptions)]),
     ("kzk_advance", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_double, _VP, ctypes.POINTER(KzkDiag)]),
     ("kzk_diag_history", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, _VP]),
     ("kzk_rhs", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP]),
@@ -84,6 +103,9 @@ _SIGS = [
     ("kzk_plan_create_batched", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs),
                                                ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(_VP)]),
+    ("kzk_plan_create_batched_ex", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs),
+                                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.POINTER(KzkOptions), ctypes.POINTER(_VP)]),
     ("kzk_advance_batched", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int64, ctypes.c_double, _VP,
                                            ctypes.POINTER(KzkDiag)]),
     ("kzk_batch_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
@@ -99,6 +121,7 @@ _SIGS = [
 NOALLOC_MAX_POINTS = 1 << 18
 KZK_BATCH_AUTOTUNE = 1
 KZK_BATCH_STREAMS = 2
+KZK_BATCH_PERSISTENT = 4
 KZK_EXPRK22 = 0
 KZK_EXPEULER = 1
 

@@ -21,6 +21,30 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> int:
     return int(s.cuda_stream)
 
 
+def make_options(row_kernel: str = "auto", col_kernel: str = "auto", fp32_state: str = "auto",
+                 transforms: str = "auto", autotune: bool = False) -> "L.KzkOptions":
+    """kzk_options from names: row_kernel auto|pair|single, col_kernel
+    auto|pair|tma|tile, fp32_state auto|compensated|plain, transforms
+    auto|mixed; autotune times the open kernel choices at plan creation."""
+    vals = {}
+    for key, name in (("row_kernel", row_kernel), ("col_kernel", col_kernel), ("fp32_state", fp32_state),
+                      ("transforms", transforms)):
+        table = L.OPTION_VALUES[key]
+        if name not in table:
+            raise ValueError(f"{key} must be one of {sorted(table)}, got {name!r}")
+        vals[key] = table[name]
+    return L.KzkOptions(autotune=int(bool(autotune)), **vals)
+
+
+def _option_names(o: "L.KzkOptions") -> dict:
+    out = {}
+    for key, table in L.OPTION_VALUES.items():
+        inv = {v: k for k, v in table.items()}
+        out[key] = inv.get(getattr(o, key), getattr(o, key))
+    out["autotune"] = bool(o.autotune)
+    return out
+
+
 class Plan:
     """One plan: grid, coefficients and step dsigma shared by `batch` propagations."""
 
@@ -30,7 +54,8 @@ class Plan:
                  B_prof: Sequence[float] = (1.0, 0.0, 0.0, 0.0), A_prof: Sequence[float] = (1.0, 0.0, 0.0, 0.0),
                  has_profile: bool = False, diffraction: float = 0.0, reg_eps: float = 0.0,
                  weno_eps: float = 0.0, relax_C: Sequence[float] = (), relax_theta: Sequence[float] = (),
-                 method: str = "exprk22"):
+                 method: str = "exprk22", row_kernel: str = "auto", col_kernel: str = "auto",
+                 fp32_state: str = "auto", transforms: str = "auto", autotune: bool = False):
         if method not in ("exprk22", "expeuler"):
             raise ValueError("method must be 'exprk22' or 'expeuler'")
         if precision not in ("fp64", "fp32"):
@@ -48,9 +73,11 @@ class Plan:
                         has_profile=int(bool(has_profile)), n_relax=len(relax_C), relax_C=pad(relax_C),
                         relax_theta=pad(relax_theta),
                         method=L.KZK_EXPEULER if method == "expeuler" else L.KZK_EXPRK22)
-        self._grid, self._coeffs = g, c
+        o = make_options(row_kernel, col_kernel, fp32_state, transforms, autotune)
+        self._grid, self._coeffs, self._opts = g, c, o
         h = ctypes.c_void_p()
-        L.check(L.lib().kzk_plan_create(ctypes.byref(g), ctypes.byref(c), self.dt, self.batch, ctypes.byref(h)))
+        L.check(L.lib().kzk_plan_create_ex(ctypes.byref(g), ctypes.byref(c), self.dt, self.batch, ctypes.byref(o),
+                                           ctypes.byref(h)))
         self._h = h
 
     @classmethod
@@ -87,6 +114,12 @@ class Plan:
         L.check(L.lib().kzk_medium_eval(self.handle, float(sigma), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         ctypes.byref(mx), _stream_ptr(stream)))
         return out[:, 0].copy(), out[:, 1].copy(), out[:, 2].copy(), float(mx.value)
+
+    def info(self) -> dict:
+        """The kernel and state choices in effect (names as in make_options)."""
+        o = L.KzkOptions()
+        L.check(L.lib().kzk_plan_info(self.handle, ctypes.byref(o)))
+        return _option_names(o)
 
     # -- helpers -------------------------------------------------------------
     def _check_state(self, t: torch.Tensor, name: str) -> None:
@@ -216,12 +249,13 @@ def _grid_coeffs(w, precision):
 
 class BatchedPlan:
     """Many independent propagations (own grid, coefficients and dsigma each)
-    advanced by one graph launch per call: mode "persistent" -- one
-    persistent cooperative kernel for all instances; mode "streams" -- every
-    instance's own kernels on its own captured stream, concurrently."""
+    advanced by one graph launch per call: mode "streams" (default) -- every
+    instance's own kernels on its own captured stream, concurrently; mode
+    "persistent" -- one persistent cooperative kernel for all instances.
+    Keyword options (fp32_state, row_kernel, ...) apply to every instance."""
 
     def __init__(self, workloads: Sequence, precision: str = "fp32", autotune: bool = True,
-                 mode: str = "persistent"):
+                 mode: str = "streams", **options):
         if mode not in ("persistent", "streams"):
             raise ValueError("mode must be 'persistent' or 'streams'")
         if precision not in ("fp64", "fp32"):
@@ -237,8 +271,10 @@ class BatchedPlan:
             gs[i], cs[i] = _grid_coeffs(w, precision)
             dts[i] = w.dt
         h = ctypes.c_void_p()
-        flags = (L.KZK_BATCH_AUTOTUNE if autotune else 0) | (L.KZK_BATCH_STREAMS if mode == "streams" else 0)
-        L.check(L.lib().kzk_plan_create_batched(gs, cs, dts, n, flags, ctypes.byref(h)))
+        flags = (L.KZK_BATCH_AUTOTUNE if autotune else 0) | (L.KZK_BATCH_STREAMS if mode == "streams"
+                                                             else L.KZK_BATCH_PERSISTENT)
+        o = make_options(**options)
+        L.check(L.lib().kzk_plan_create_batched_ex(gs, cs, dts, n, flags, ctypes.byref(o), ctypes.byref(h)))
         self.mode = mode
         self._h = h
         self.n = n

@@ -69,6 +69,7 @@ double horner(const double* c, double s) { return ((c[3] * s + c[2]) * s + c[1])
 struct kzk_plan_s {
     kzk_grid g;
     kzk_coeffs c;
+    kzk_options opt;            // the choices requested at creation (KZK_AUTO where left open)
     double dt;
     int batch;
     int prec;
@@ -89,7 +90,9 @@ struct kzk_plan_s {
     long long hist_steps;
     int row_thr, col_thr, log2tc, adj_row_thr;
     size_t row_smem, col_smem, adj_smem;
-    // persistent TMA-staged column kernels (kzk_colpipe.cuh); colp_log2tc < 0: not used
+    // TMA-staged Stockham column kernels (kzk_colpipe.cuh): colp_ok = the plan
+    // fits them (configuration colp_l2 ...); colp_log2tc < 0: not in use
+    int colp_ok, colp_l2;
     int colp_log2tc, colp_thr, colp_by, colp_nby, colp_bt, colp_nbt, sm_count;
     size_t colp_smem1, colp_smem2;
     int* colp_flag;             // device: FLAG_TIMEOUT from a copy wait that ran out
@@ -126,7 +129,7 @@ struct kzk_plan_s {
     unsigned test_extra_blocks; // testing hook: barrier waits for this many extra CTAs
     long long timeout_ns;
     cudaStream_t cap_stream;    // capturable stream for building the graph
-    // KZK_BATCH_STREAMS: the graph advances every instance on its own stream
+    // streams mode (the default): the graph advances every instance on its own stream
     int batch_streams;
     double graph_sigma0;
     std::vector<void*>* graph_u;        // state pointers the cached graph was captured with
@@ -147,13 +150,14 @@ struct kzk_plan_s {
     int comp;
     void *Vlo, *vslo;           // lo parts of V and V*
     void* Em1;                  // (E - 1)/ny, folded as E'
-    // FP32 plans: row passes on row pairs in packed FP32 (kzk_rowpair.cuh)
-    int rowpair;
+    // FP32 plans: row passes on row pairs in packed FP32 (kzk_rowpair.cuh);
+    // rowpair_ok = the plan fits them, rowpair = in use
+    int rowpair_ok, rowpair;
     size_t rowpair_smem;
     void *twr2, *tws2;          // the tau twiddle tables with every entry as a lane pair
     // FP32 plans with the compensated state: column passes on column pairs
-    // (kzk_colpair.cuh); colpair = 0: not used
-    int colpair, cpair_by, cpair_nby;
+    // (kzk_colpair.cuh); colpair_ok = the plan fits them, colpair = in use
+    int colpair_ok, colpair, cpair_by, cpair_nby;
     int cpair_diff;             // row pairs store b2 - b1 for the column-pair STAGE2 (both kernels in use)
     size_t cpair_smem1, cpair_smem2;
     void *Em1p, *P1p, *P2p;     // (E - 1)', P1', P2' as pair tables [nx/4][pair_tab_rows(ny)]
@@ -233,18 +237,14 @@ void table_boxes(int nl, int row_bytes, int* bt, int* nbt)
 // Widest column tile (TC <= 16 columns) of the TMA-staged column kernels:
 // ny TC / 8 threads (at most COLP_THREADS, at least one warp), rows of at
 // least 16 bytes (TMA's innermost extent and coordinate alignment), and both
-// stages' shared memory within the device limit.  FP32 plans only by default;
-// in the environment KZK_COLPIPE=0 selects the per-tile kernels (col_kernel)
-// for every plan, KZK_COLPIPE=2 the TMA-staged ones for FP64 plans too.
+// stages' shared memory within the device limit.  Sets colp_ok and the
+// configuration; whether the kernels are used is select_kernels' choice.
 template <typename T>
 void colp_configure(kzk_plan* p, int optin)
 {
+    p->colp_ok = 0;
     p->colp_log2tc = -1;
-    const char* env = getenv("KZK_COLPIPE");
-    if ((env && env[0] == '0') || p->log2ny < 4 || !encode_tiled()) return;
-    // FP64 column passes are bound by the FP64 pipe, not by memory latency:
-    // the per-tile kernels (two CTAs per SM) keep it busier
-    if (sizeof(T) == 8 && !(env && env[0] == '2')) return;
+    if (p->log2ny < 4 || !encode_tiled()) return;
     for (int l2 = 4; l2 >= 0; l2--) {
         const int TC = 1 << l2;
         if (TC > p->n || TC * (int)sizeof(cx<T>) < 16) continue;
@@ -255,7 +255,8 @@ void colp_configure(kzk_plan* p, int optin)
         const size_t s1 = colp_layout<T, COL_STAGE1>(p->ny, l2, bt, nbt).total;
         const size_t s2 = colp_layout<T, COL_STAGE2>(p->ny, l2, bt, nbt).total;
         if (std::max(s1, s2) > (size_t)optin) continue;
-        p->colp_log2tc = l2;
+        p->colp_ok = 1;
+        p->colp_l2 = l2;
         p->colp_thr = (int)thr;
         p->colp_bt = bt;
         p->colp_nbt = nbt;
@@ -268,8 +269,7 @@ void colp_configure(kzk_plan* p, int optin)
 }
 
 // Column-pair kernels (kzk_colpair.cuh): FP32 plans with the compensated
-// state, 256 <= ny <= 4096, unless KZK_COLPAIR=0 (then the TMA Stockham tile
-// kernels) or KZK_COLPIPE=0 (the per-tile kernels) in the environment.
+// state, 256 <= ny <= 4096; sets colpair_ok when the plan fits them.
 template <int L>
 kzk_status cpair_attr(kzk_plan* p, int optin)
 {
@@ -286,17 +286,15 @@ kzk_status cpair_attr(kzk_plan* p, int optin)
     if (per_sm < 1) return KZK_OK;
     p->cpair_smem1 = s1;
     p->cpair_smem2 = s2;
-    p->colpair = 1;
+    p->colpair_ok = 1;
     return KZK_OK;
 }
 template <typename T>
 kzk_status cpair_configure(kzk_plan* p, int optin)
 {
+    p->colpair_ok = 0;
     p->colpair = 0;
-    const char* env = getenv("KZK_COLPAIR");
-    const char* penv = getenv("KZK_COLPIPE");
-    if (sizeof(T) != 4 || !p->comp || p->mixed || (env && env[0] == '0') || (penv && penv[0] == '0'))
-        return KZK_OK;
+    if (sizeof(T) != 4 || !p->comp || p->mixed) return KZK_OK;
     if (p->log2ny < 8 || p->log2ny > 12 || p->n < 2 || !encode_tiled()) return KZK_OK;
     p->cpair_by = std::min(p->ny, 256);
     p->cpair_nby = p->ny / p->cpair_by;
@@ -307,6 +305,23 @@ kzk_status cpair_configure(kzk_plan* p, int optin)
     case 11: return cpair_attr<11>(p, optin);
     default: return cpair_attr<12>(p, optin);
     }
+}
+
+// Put a row / column kernel choice (KZK_ROW_*, KZK_COL_*; both eligible) in use.
+void select_kernels(kzk_plan* p, int row, int col)
+{
+    p->rowpair = row == KZK_ROW_PAIR ? 1 : 0;
+    p->colpair = col == KZK_COL_PAIR ? 1 : 0;
+    p->colp_log2tc = col == KZK_COL_TMA ? p->colp_l2 : -1;
+    // row pairs storing b2 - b1 feed the column-pair STAGE2 directly
+    p->cpair_diff = p->colpair && p->rowpair;
+}
+
+// The row / column kernels in use, as KZK_ROW_* / KZK_COL_* values.
+int row_choice(const kzk_plan* p) { return p->rowpair ? KZK_ROW_PAIR : KZK_ROW_SINGLE; }
+int col_choice(const kzk_plan* p)
+{
+    return p->colpair ? KZK_COL_PAIR : p->colp_log2tc >= 0 ? KZK_COL_TMA : KZK_COL_TILE;
 }
 
 // Mixed-radix plans: one row per CTA; column tiles of the widest power of two
@@ -392,12 +407,11 @@ kzk_status configure(kzk_plan* p)
     KZK_TRY((set_adj_col_attr<T, ADJ_COL_2>(sm)));
     KZK_TRY((set_adj_col_attr<T, ADJ_COL_1>(sm)));
     KZK_CUDA(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    // FP32: row pairs in packed FP32 unless KZK_ROWPAIR=0 in the environment
-    const char* renv = getenv("KZK_ROWPAIR");
+    // FP32: row pairs in packed FP32 (even ny, the pair row fits)
     p->rowpair = 0;
-    if (sizeof(T) == 4 && !(renv && renv[0] == '0') && p->ny % 2 == 0 &&
-        rowpair_smem_bytes(p->nx) <= (size_t)optin) {
-        p->rowpair = 1;
+    p->rowpair_ok = 0;
+    if (sizeof(T) == 4 && p->ny % 2 == 0 && rowpair_smem_bytes(p->nx) <= (size_t)optin) {
+        p->rowpair_ok = 1;
         p->rowpair_smem = rowpair_smem_bytes(p->nx);
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -409,8 +423,8 @@ kzk_status configure(kzk_plan* p)
     }
     colp_configure<T>(p, optin);
     KZK_TRY(cpair_configure<T>(p, optin));
-    p->cpair_diff = p->colpair && p->rowpair;
-    if (p->colp_log2tc >= 0) {
+    p->cpair_diff = 0;
+    if (p->colp_ok) {
         KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(colp_kernel<T, COL_STAGE1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -1012,7 +1026,7 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
     KZK_CUDA(cudaMemcpy(p->twc, tcs.data(), tcs.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
     if (p->twc_lo)
         KZK_CUDA(cudaMemcpy(p->twc_lo, tcl.data(), tcl.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
-    if (p->rowpair) {
+    if (p->twr2) {
         // every FP32 entry (wr, wi) as ((wr, wr), (wi, wi))
         auto pairs = [](const std::vector<cx<T>>& w) {
             std::vector<float4> q(w.size());
@@ -1024,7 +1038,7 @@ kzk_status build_tables(kzk_plan* p, cudaStream_t st)
         KZK_CUDA(cudaMemcpy(p->twr2, r2.data(), r2.size() * sizeof(float4), cudaMemcpyHostToDevice));
         KZK_CUDA(cudaMemcpy(p->tws2, s2.data(), s2.size() * sizeof(float4), cudaMemcpyHostToDevice));
     }
-    if (p->colpair) {
+    if (p->Em1p) {
         switch (p->log2ny) {
         case 8: KZK_TRY(build_pair_tables<8>(p, tcf, st)); break;
         case 9: KZK_TRY(build_pair_tables<9>(p, tcf, st)); break;
@@ -1556,6 +1570,57 @@ kzk_status batch_autotune(kzk_plan* p, cudaStream_t st)
     return batch_configure<T>(p, best_cap, st);
 }
 
+// Autotuner of a single plan: every eligible (row, column) kernel combination
+// the options leave open advances a zero state of the plan's shape for one
+// untimed and two timed steps (CUDA events on st); the fastest is kept.
+template <typename T>
+kzk_status plan_autotune(kzk_plan* p, cudaStream_t st)
+{
+    std::vector<int> rows, cols;
+    if (p->opt.row_kernel != KZK_AUTO) rows.push_back(p->opt.row_kernel);
+    else {
+        if (p->rowpair_ok) rows.push_back(KZK_ROW_PAIR);
+        rows.push_back(KZK_ROW_SINGLE);
+    }
+    if (p->opt.col_kernel != KZK_AUTO) cols.push_back(p->opt.col_kernel);
+    else {
+        if (p->colpair_ok) cols.push_back(KZK_COL_PAIR);
+        if (p->colp_ok) cols.push_back(KZK_COL_TMA);
+        cols.push_back(KZK_COL_TILE);
+    }
+    if (rows.size() * cols.size() < 2) return KZK_OK;
+    const int row0 = row_choice(p), col0 = col_choice(p);
+    const size_t bytes = (size_t)p->batch * p->nx * p->ny * sizeof(T);
+    void* u = nullptr;
+    KZK_CUDA(cudaMalloc(&u, bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    kzk_status status = KZK_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        status = fail(KZK_ERR_CUDA, "autotune events");
+    int best_row = row0, best_col = col0;
+    float best = 1e30f;
+    for (int r : rows)
+        for (int c : cols) {
+            if (status != KZK_OK) break;
+            select_kernels(p, r, c);
+            if (cudaMemsetAsync(u, 0, bytes, st) != cudaSuccess) { status = fail(KZK_ERR_CUDA, "autotune memset"); break; }
+            if ((status = advance_impl<T>(p, u, 1, 0.0, st, nullptr)) != KZK_OK) break;   // warm-up
+            cudaEventRecord(e0, st);
+            if ((status = advance_impl<T>(p, u, 2, 0.0, st, nullptr)) != KZK_OK) break;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { status = fail(KZK_ERR_CUDA, "autotune timing"); break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_row = r; best_col = c; }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(u);
+    select_kernels(p, best_row, best_col);
+    p->hist_steps = 0;
+    return status;
+}
+
 template <typename T>
 kzk_status advance_batched_impl(kzk_plan* p, void* const* u, long long n_steps, double sigma0, cudaStream_t st,
                                 kzk_diag* dout)
@@ -1584,7 +1649,7 @@ kzk_status advance_batched_impl(kzk_plan* p, void* const* u, long long n_steps, 
     return KZK_OK;
 }
 
-// KZK_BATCH_STREAMS: one CUDA graph per (n_steps, sigma0, state pointers) in
+// Streams mode: one CUDA graph per (n_steps, sigma0, state pointers) in
 // which every instance runs kzk_advance's launches on its own captured
 // stream, forked from and joined back into one origin stream, so the
 // instances' kernels run concurrently; replayed on the caller's stream.
@@ -1854,18 +1919,23 @@ const char* kzk_last_error(void) { return g_err; }
 
 int64_t kzk_launch_count(void) { return (int64_t)g_launches.load(); }
 
-kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, double dt, int32_t batch,
-                           kzk_plan** out)
+kzk_status kzk_plan_create_ex(const kzk_grid* grid, const kzk_coeffs* coeffs, double dt, int32_t batch,
+                              const kzk_options* opts, kzk_plan** out)
 {
     if (!out) return fail(KZK_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!grid || !coeffs) return fail(KZK_ERR_ARG, "grid or coeffs is NULL");
     if (grid->prec != KZK_FP64 && grid->prec != KZK_FP32) return fail(KZK_ERR_ARG, "bad precision %d", grid->prec);
+    kzk_options o{};
+    if (opts) o = *opts;
+    if (o.row_kernel < KZK_AUTO || o.row_kernel > KZK_ROW_SINGLE || o.col_kernel < KZK_AUTO ||
+        o.col_kernel > KZK_COL_TILE || o.fp32_state < KZK_AUTO || o.fp32_state > KZK_STATE_PLAIN ||
+        o.transforms < KZK_AUTO || o.transforms > KZK_TRANSFORMS_MIXED)
+        return fail(KZK_ERR_ARG, "unknown option value");
     // powers of two: the radix-8/16 kernels; other even sizes with no prime
-    // factor above 7 (the paper's 7 * 2^k x 1250 * 2^k grids): the mixed-radix
-    // kernels (KZK_MIXED=1 in the environment selects them for every grid)
-    const char* menv = getenv("KZK_MIXED");
-    const bool mixed = !(is_pow2(grid->nx) && is_pow2(grid->ny)) || (menv && menv[0] == '1');
+    // factor above 7 (the paper's 7 * 2^k x 1250 * 2^k grids), or
+    // KZK_TRANSFORMS_MIXED: the mixed-radix kernels
+    const bool mixed = !(is_pow2(grid->nx) && is_pow2(grid->ny)) || o.transforms == KZK_TRANSFORMS_MIXED;
     if (!mixed && (grid->nx < 8 || grid->nx > 8192 || grid->ny < 2 || grid->ny > 4096))
         return fail(KZK_ERR_SIZE, "nx = %d, ny = %d: powers of two in [8, 8192] x [2, 4096] required",
                     grid->nx, grid->ny);
@@ -1873,6 +1943,8 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
                   (grid->ny & 1)))
         return fail(KZK_ERR_SIZE, "nx = %d, ny = %d: even sizes in [8, 16384] x [2, 32768] required",
                     grid->nx, grid->ny);
+    if (mixed && (o.row_kernel == KZK_ROW_PAIR || o.col_kernel != KZK_AUTO))
+        return fail(KZK_ERR_SIZE, "mixed-radix plans run single rows and the mixed-radix column kernels only");
     if (!(grid->tau_max > grid->tau_min) || !(grid->y_max > grid->y_min))
         return fail(KZK_ERR_ARG, "empty domain");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(KZK_ERR_ARG, "dt must be positive and finite");
@@ -1893,6 +1965,7 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     memset(p, 0, sizeof(*p));
     p->g = *grid;
     p->c = *coeffs;
+    p->opt = o;
     if (!(p->c.diffraction > 0)) p->c.diffraction = 1.0 / (4.0 * M_PI);
     // epsilon of the precision the multiplier is evaluated in: the tables are
     // generated in FP64 for both plan precisions
@@ -1914,12 +1987,38 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
     p->csz = p->prec == KZK_FP64 ? sizeof(double2) : sizeof(float2);
     p->inst_stride = (long long)p->ny * p->n;
     p->mixed = mixed ? 1 : 0;
-    // FP32: compensated spectral state unless KZK_COMPSTATE=0 in the environment
-    const char* cenv = getenv("KZK_COMPSTATE");
-    p->comp = (p->prec == KZK_FP32 && !(cenv && cenv[0] == '0')) ? 1 : 0;
+    // FP32: compensated spectral state unless a plain one is asked for
+    p->comp = (p->prec == KZK_FP32 && o.fp32_state != KZK_STATE_PLAIN) ? 1 : 0;
 
     kzk_status s = p->prec == KZK_FP64 ? configure<double>(p) : configure<float>(p);
     if (s != KZK_OK) { plan_free(p); return s; }
+
+    // kernel choices: explicit ones must fit; open ones take the defaults (row
+    // and column pairs where they fit, else TMA Stockham tiles for FP32, else
+    // per-tile kernels), or with autotune every fitting candidate is kept
+    // available and timed below
+    int row = KZK_ROW_SINGLE, col = KZK_COL_TILE;
+    bool keep_rowpair = false, keep_colpair = false;
+    if (!mixed) {
+        if (o.row_kernel == KZK_ROW_PAIR && !p->rowpair_ok) {
+            plan_free(p);
+            return fail(KZK_ERR_SIZE, "row pairs need an FP32 plan with even ny whose row pair fits shared memory");
+        }
+        if (o.col_kernel == KZK_COL_PAIR && !p->colpair_ok) {
+            plan_free(p);
+            return fail(KZK_ERR_SIZE, "column pairs need an FP32 plan with the compensated state and 256 <= ny <= 4096");
+        }
+        if (o.col_kernel == KZK_COL_TMA && !p->colp_ok) {
+            plan_free(p);
+            return fail(KZK_ERR_SIZE, "the TMA-staged column tiles do not fit ny = %d", p->ny);
+        }
+        row = o.row_kernel != KZK_AUTO ? o.row_kernel : (p->rowpair_ok ? KZK_ROW_PAIR : KZK_ROW_SINGLE);
+        col = o.col_kernel != KZK_AUTO ? o.col_kernel
+                                        : (p->colpair_ok ? KZK_COL_PAIR
+                                                         : (p->colp_ok && p->prec == KZK_FP32 ? KZK_COL_TMA : KZK_COL_TILE));
+        keep_rowpair = p->rowpair_ok && (row == KZK_ROW_PAIR || (o.autotune && o.row_kernel == KZK_AUTO));
+        keep_colpair = p->colpair_ok && (col == KZK_COL_PAIR || (o.autotune && o.col_kernel == KZK_AUTO));
+    }
 
     const size_t arr = (size_t)batch * p->inst_stride * p->csz;
     const size_t tab = (size_t)(p->ny / 2 + 1) * p->n * p->csz;
@@ -1947,14 +2046,14 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
         if (e == cudaSuccess) e = cudaMalloc(&p->vslo, lo_arr);
         if (e == cudaSuccess) e = cudaMalloc(&p->Em1, tab);
     }
-    if (p->colpair) {
+    if (keep_colpair) {
         const size_t ptab = (size_t)pair_tab_rows(p->ny) * p->n * sizeof(float2);
         void** ptabs[] = {&p->Em1p, &p->P1p, &p->P2p};
         for (void** t : ptabs)
             if (e == cudaSuccess) e = cudaMalloc(t, ptab);
         if (e == cudaSuccess) e = cudaMalloc(&p->twcp, (size_t)p->ny * sizeof(float4));
     }
-    if (p->rowpair) {
+    if (keep_rowpair) {
         if (e == cudaSuccess) e = cudaMalloc(&p->twr2, (size_t)p->nx * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc(&p->tws2, (size_t)p->n * sizeof(float4));
     }
@@ -1969,9 +2068,32 @@ kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, doubl
         return fail(e == cudaErrorMemoryAllocation ? KZK_ERR_OOM : KZK_ERR_CUDA, "plan allocation: %s",
                     cudaGetErrorString(e));
     }
+    select_kernels(p, row, col);
     s = p->prec == KZK_FP64 ? build_tables<double>(p, 0) : build_tables<float>(p, 0);
+    if (s == KZK_OK && o.autotune && !mixed)
+        s = p->prec == KZK_FP64 ? plan_autotune<double>(p, 0) : plan_autotune<float>(p, 0);
     if (s != KZK_OK) { plan_free(p); return s; }
     *out = p;
+    return KZK_OK;
+}
+
+kzk_status kzk_plan_create(const kzk_grid* grid, const kzk_coeffs* coeffs, double dt, int32_t batch,
+                           kzk_plan** out)
+{
+    return kzk_plan_create_ex(grid, coeffs, dt, batch, nullptr, out);
+}
+
+kzk_status kzk_plan_info(kzk_plan* p, kzk_options* out)
+{
+    if (!p || !out) return fail(KZK_ERR_ARG, "NULL argument");
+    if (p->batched) return fail(KZK_ERR_STATE, "batched plan");
+    kzk_options o{};
+    o.row_kernel = row_choice(p);
+    o.col_kernel = p->mixed ? KZK_AUTO : col_choice(p);
+    o.fp32_state = p->prec == KZK_FP32 ? (p->comp ? KZK_STATE_COMPENSATED : KZK_STATE_PLAIN) : KZK_AUTO;
+    o.transforms = p->mixed ? KZK_TRANSFORMS_MIXED : KZK_AUTO;
+    o.autotune = p->opt.autotune;
+    *out = o;
     return KZK_OK;
 }
 
@@ -2053,14 +2175,32 @@ kzk_status kzk_medium_eval(kzk_plan* p, double sigma, double* out, double* max_u
     return KZK_OK;
 }
 
-kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coeffs, const double* dts, int32_t n,
-                                   int32_t flags, kzk_plan** out)
+kzk_status kzk_plan_create_batched_ex(const kzk_grid* grids, const kzk_coeffs* coeffs, const double* dts, int32_t n,
+                                      int32_t flags, const kzk_options* opts, kzk_plan** out)
 {
     if (!out) return fail(KZK_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!grids || !coeffs || !dts || n < 1) return fail(KZK_ERR_ARG, "need grids, coeffs, dts and n >= 1");
+    if ((flags & KZK_BATCH_STREAMS) && (flags & KZK_BATCH_PERSISTENT))
+        return fail(KZK_ERR_ARG, "KZK_BATCH_STREAMS and KZK_BATCH_PERSISTENT are exclusive");
+    if (flags & ~(KZK_BATCH_AUTOTUNE | KZK_BATCH_STREAMS | KZK_BATCH_PERSISTENT))
+        return fail(KZK_ERR_ARG, "unknown batched-plan flag");
+    const bool persistent = (flags & KZK_BATCH_PERSISTENT) != 0;
     for (int i = 1; i < n; i++)
         if (grids[i].prec != grids[0].prec) return fail(KZK_ERR_ARG, "all instances must share one precision");
+    // instance plans: streams mode runs their own kernels (autotuned with
+    // KZK_BATCH_AUTOTUNE); the persistent kernel has its own bodies, so its
+    // instances take the single-row / per-tile choices, which allocate nothing
+    // for the pair kernels
+    kzk_options io{};
+    if (opts) io = *opts;
+    if (persistent) {
+        io.row_kernel = KZK_ROW_SINGLE;
+        io.col_kernel = KZK_COL_TILE;
+        io.autotune = 0;
+    } else if (flags & KZK_BATCH_AUTOTUNE) {
+        io.autotune = 1;
+    }
     kzk_plan* p = new (std::nothrow) kzk_plan_s();
     if (!p) return fail(KZK_ERR_OOM, "host allocation failed");
     memset(p, 0, sizeof(*p));
@@ -2072,13 +2212,12 @@ kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coef
     if (!p->subs) { delete p; return fail(KZK_ERR_OOM, "host allocation failed"); }
     for (int i = 0; i < n; i++) {
         kzk_plan* q = nullptr;
-        kzk_status s = kzk_plan_create(&grids[i], &coeffs[i], dts[i], 1, &q);
+        kzk_status s = kzk_plan_create_ex(&grids[i], &coeffs[i], dts[i], 1, &io, &q);
         if (s != KZK_OK) { plan_free(p); return s; }
         p->subs->push_back(q);
-        if (q->nx > 8192) { plan_free(p); return fail(KZK_ERR_SIZE, "instance %d too large", i); }
-        if (q->mixed && !(flags & KZK_BATCH_STREAMS)) {
+        if (persistent && (q->nx > 8192 || q->mixed)) {
             plan_free(p);
-            return fail(KZK_ERR_SIZE, "instance %d: the persistent batched kernel needs power-of-two grids", i);
+            return fail(KZK_ERR_SIZE, "instance %d: the persistent batched kernel needs power-of-two grids, nx <= 8192", i);
         }
     }
     cudaError_t e = cudaMalloc(&p->binst, (size_t)n * std::max(sizeof(BatchInst<float>), sizeof(BatchInst<double>)));
@@ -2087,7 +2226,7 @@ kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coef
     if (e == cudaSuccess) e = cudaMalloc(&p->bar, 4 * sizeof(unsigned));
     if (e != cudaSuccess) { plan_free(p); return fail(KZK_ERR_OOM, "batched plan allocation: %s", cudaGetErrorString(e)); }
     kzk_status s;
-    if (flags & KZK_BATCH_STREAMS) {
+    if (!persistent) {
         p->batch_streams = 1;
         *out = p;
         return KZK_OK;
@@ -2099,6 +2238,12 @@ kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coef
     if (s != KZK_OK) { plan_free(p); return s; }
     *out = p;
     return KZK_OK;
+}
+
+kzk_status kzk_plan_create_batched(const kzk_grid* grids, const kzk_coeffs* coeffs, const double* dts, int32_t n,
+                                   int32_t flags, kzk_plan** out)
+{
+    return kzk_plan_create_batched_ex(grids, coeffs, dts, n, flags, nullptr, out);
 }
 
 kzk_status kzk_advance_batched(kzk_plan* p, void* const* u, int64_t n_steps, double sigma0, void* stream,
@@ -2130,7 +2275,7 @@ kzk_status kzk_batch_info(kzk_plan* p, int32_t* grid_ctas, int32_t* tile_cap, in
 kzk_status kzk_batch_test_barrier(kzk_plan* p, int32_t extra_blocks, int64_t timeout_ms)
 {
     if (!p || !p->batched) return fail(KZK_ERR_STATE, "not a batched plan");
-    if (p->batch_streams) return fail(KZK_ERR_STATE, "a KZK_BATCH_STREAMS plan has no grid barrier");
+    if (p->batch_streams) return fail(KZK_ERR_STATE, "a batched plan in streams mode has no grid barrier");
     if (extra_blocks < 0 || timeout_ms < 1 || timeout_ms > 60000) return fail(KZK_ERR_ARG, "bad barrier test values");
     p->test_extra_blocks = (unsigned)extra_blocks;
     p->timeout_ns = timeout_ms * 1000000LL;

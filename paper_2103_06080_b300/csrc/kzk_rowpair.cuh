@@ -13,7 +13,7 @@
 // statistics and the per-row random-medium speeds are written for the pair.
 // The arithmetic of every lane is the FP32 arithmetic of the single-row kernel
 // (FMAs may be contracted differently, so the two agree to rounding, not bit
-// for bit); KZK_ROWPAIR=0 in the environment selects the single-row kernel.
+// for bit); the plan option row_kernel = KZK_ROW_SINGLE selects the single-row kernel.
 #pragma once
 #include "kzk_kernels.cuh"
 

@@ -79,6 +79,41 @@ def test_null_arguments_are_rejected():
     assert lib.kzk_medium_eval(None, 0.0, None, None, None) == L.KZK_ERR_ARG
 
 
+@pytest.mark.parametrize("field,value,code", [
+    ("row_kernel", 3, L.KZK_ERR_ARG), ("col_kernel", 4, L.KZK_ERR_ARG), ("fp32_state", -1, L.KZK_ERR_ARG),
+    ("transforms", 2, L.KZK_ERR_ARG)])
+def test_unknown_option_values_are_rejected(field, value, code):
+    # refused before any device work
+    g = L.KzkGrid(nx=64, ny=32, tau_min=-4, tau_max=4, y_min=-8, y_max=8, prec=L.KZK_FP32)
+    c = L.KzkCoeffs(B=0.05, A=7e-6, lf_umax=1.0)
+    o = L.KzkOptions()
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    assert L.lib().kzk_plan_create_ex(ctypes.byref(g), ctypes.byref(c), 0.01, 1, ctypes.byref(o), ctypes.byref(h)) == code
+    assert not h.value
+
+
+def test_mixed_radix_plans_refuse_pair_kernels():
+    g = L.KzkGrid(nx=56, ny=50, tau_min=-4, tau_max=4, y_min=-8, y_max=8, prec=L.KZK_FP32)
+    c = L.KzkCoeffs(B=0.05, A=7e-6, lf_umax=1.0)
+    h = ctypes.c_void_p()
+    for field, value in (("row_kernel", 1), ("col_kernel", 1), ("col_kernel", 3)):
+        o = L.KzkOptions()
+        setattr(o, field, value)
+        st = L.lib().kzk_plan_create_ex(ctypes.byref(g), ctypes.byref(c), 0.01, 1, ctypes.byref(o), ctypes.byref(h))
+        assert st == L.KZK_ERR_SIZE and not h.value
+
+
+def test_batched_mode_flags_are_exclusive():
+    g = (L.KzkGrid * 1)(L.KzkGrid(nx=64, ny=32, tau_min=-4, tau_max=4, y_min=-8, y_max=8, prec=L.KZK_FP32))
+    c = (L.KzkCoeffs * 1)(L.KzkCoeffs(B=0.05, A=7e-6, lf_umax=1.0))
+    dts = (ctypes.c_double * 1)(0.01)
+    h = ctypes.c_void_p()
+    st = L.lib().kzk_plan_create_batched(g, c, dts, 1, L.KZK_BATCH_STREAMS | L.KZK_BATCH_PERSISTENT, ctypes.byref(h))
+    assert st == L.KZK_ERR_ARG and not h.value
+    assert L.lib().kzk_plan_create_batched(g, c, dts, 1, 64, ctypes.byref(h)) == L.KZK_ERR_ARG
+
+
 def test_binding_structs_match_the_header(tmp_path):
     """The ctypes mirrors have the sizes and field offsets the C compiler gives
     the structs of include/kzk.h."""
@@ -87,7 +122,8 @@ def test_binding_structs_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"kzk_grid": L.KzkGrid, "kzk_coeffs": L.KzkCoeffs, "kzk_diag": L.KzkDiag, "kzk_medium": L.KzkMedium}
+    structs = {"kzk_grid": L.KzkGrid, "kzk_coeffs": L.KzkCoeffs, "kzk_diag": L.KzkDiag, "kzk_medium": L.KzkMedium,
+               "kzk_options": L.KzkOptions}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "kzk.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')

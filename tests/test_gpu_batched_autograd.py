@@ -16,28 +16,25 @@ def _small_batch(precision):
     return ws
 
 
-@pytest.mark.parametrize("prec,mode", [("fp64", "persistent"), ("fp32", "persistent"), ("fp32", "persistent-plain"),
-                                       ("fp64", "streams"), ("fp32", "streams")])
-def test_batched_matches_single_plans(prec, mode, monkeypatch):
+@pytest.mark.parametrize("prec,mode,state", [("fp64", "persistent", "auto"), ("fp32", "persistent", "compensated"),
+                                              ("fp32", "persistent", "plain"), ("fp64", "streams", "auto"),
+                                              ("fp32", "streams", "compensated"), ("fp32", "streams", "plain")])
+def test_batched_matches_single_plans(prec, mode, state):
     from paper_2103_06080_b300 import api
-    if mode.startswith("persistent"):
-        # the persistent kernel runs the per-tile column bodies and the
-        # single-row bodies (FP32: with the compensated state unless
-        # KZK_COMPSTATE=0): compare with single plans on the same kernels,
-        # bit for bit
-        monkeypatch.setenv("KZK_COLPIPE", "0")
-        monkeypatch.setenv("KZK_ROWPAIR", "0")
-        if mode == "persistent-plain":
-            monkeypatch.setenv("KZK_COMPSTATE", "0")
-        mode = "persistent"
+    # the persistent kernel runs the per-tile column bodies and the
+    # single-row bodies (FP32: with the compensated or the plain state):
+    # compare with single plans on the same kernels, bit for bit; streams mode
+    # runs the instances' own default kernels
+    kw = dict(fp32_state=state) if prec == "fp32" else {}
+    single = dict(row_kernel="single", col_kernel="tile") if mode == "persistent" else {}
     dt = torch.float64 if prec == "fp64" else torch.float32
     ws = _small_batch(prec)
-    bp = api.BatchedPlan(ws, precision=prec, autotune=True, mode=mode)
+    bp = api.BatchedPlan(ws, precision=prec, autotune=(mode == "persistent"), mode=mode, **kw)
     us = [torch.tensor(w.u0, dtype=dt, device="cuda") for w in ws]
     st, diags = bp.advance(us, 20, diag=True)
     assert st == 0
     for w, u, d in zip(ws, us, diags):
-        p = api.Plan.from_workload(w, precision=prec)
+        p = api.Plan.from_workload(w, precision=prec, **kw, **single)
         v = torch.tensor(w.u0, dtype=dt, device="cuda")
         p.advance(v, 20)
         assert torch.equal(u, v), (w.nx, w.ny)
@@ -48,13 +45,28 @@ def test_batched_matches_single_plans(prec, mode, monkeypatch):
     bp.close()
 
 
+def test_batched_streams_autotuned_matches_oracle():
+    """Streams mode with autotuned instances (each instance's kernel choice
+    made by timing at creation) against the FP64 oracle."""
+    from paper_2103_06080_b300 import api
+    ws = _small_batch("fp32")[:3]
+    bp = api.BatchedPlan(ws, precision="fp32", autotune=True, mode="streams")
+    us = [torch.tensor(w.u0, dtype=torch.float32, device="cuda") for w in ws]
+    bp.advance(us, 20)
+    for w, u in zip(ws, us):
+        ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, 20, threads=True)
+        got = u.double().cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5, (w.nx, w.ny)
+    bp.close()
+
+
 def test_batched_fp32_persistent_accuracy():
     """The persistent launch carries the compensated FP32 state: against the
     FP64 oracle after 200 steps, relative l2 within 1e-5."""
     from paper_2103_06080_b300 import api
     # workloads whose atmosphere profiles span the 200 steps
     ws = inputs.batched_config(seed=5, count=4, n_steps=200, scale=8)[:2]
-    bp = api.BatchedPlan(ws, precision="fp32", autotune=False)
+    bp = api.BatchedPlan(ws, precision="fp32", autotune=False, mode="persistent")
     us = [torch.tensor(w.u0, dtype=torch.float32, device="cuda") for w in ws]
     bp.advance(us, 200)
     for w, u in zip(ws, us):
@@ -67,7 +79,7 @@ def test_batched_fp32_persistent_accuracy():
 def test_batched_fp64_matches_oracle():
     from paper_2103_06080_b300 import api
     ws = _small_batch("fp64")[:2]
-    bp = api.BatchedPlan(ws, precision="fp64", autotune=False)
+    bp = api.BatchedPlan(ws, precision="fp64", autotune=False, mode="persistent")
     us = [torch.tensor(w.u0, dtype=torch.float64, device="cuda") for w in ws]
     bp.advance(us, 10)
     for w, u in zip(ws, us):
@@ -82,7 +94,7 @@ def test_batched_barrier_timeout_is_reported_and_recoverable():
     from paper_2103_06080_b300 import _lib as L
     from paper_2103_06080_b300 import api
     ws = _small_batch("fp32")[:2]
-    bp = api.BatchedPlan(ws, precision="fp32", autotune=False)
+    bp = api.BatchedPlan(ws, precision="fp32", autotune=False, mode="persistent")
     us = [torch.tensor(w.u0, dtype=torch.float32, device="cuda") for w in ws]
     bp.test_barrier(1, 200)
     with pytest.raises(L.KzkError) as e:

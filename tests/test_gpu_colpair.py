@@ -2,7 +2,7 @@
 supported length ny = 256 .. 4096, batches, both stages of the step, the
 packed column 0, the exponential Euler step (output over its input), the
 random medium, and agreement with the Stockham tile kernels they replace
-(KZK_COLPAIR=0).  FP32 against the FP64 oracle: relative l2 within 1e-5."""
+(col_kernel="tma").  FP32 against the FP64 oracle: relative l2 within 1e-5."""
 import numpy as np
 import pytest
 
@@ -51,11 +51,10 @@ def test_colpair_batch_of_two():
 
 
 @pytest.mark.parametrize("ny", [256, 2048])
-def test_colpair_agrees_with_stockham_kernels(ny, monkeypatch):
+def test_colpair_agrees_with_stockham_kernels(ny):
     w = inputs.config(2, nx=128, ny=ny, n_steps=20)
-    a = _run32(w, w.u0, 20)
-    monkeypatch.setenv("KZK_COLPAIR", "0")
-    b = _run32(w, w.u0, 20)
+    a = _run32(w, w.u0, 20, col_kernel="pair")
+    b = _run32(w, w.u0, 20, col_kernel="tma")
     assert rel_l2(a, b) < 1e-6
     assert np.max(np.abs(a - b)) > 0   # different kernels: the switch took effect
 
@@ -133,13 +132,12 @@ def test_colpair_in_the_adjoint_recompute():
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 3e-3
 
 
-def test_colpair_with_single_row_passes(monkeypatch):
-    """KZK_ROWPAIR=0: the single-row passes store b2 itself, and the
+def test_colpair_with_single_row_passes():
+    """row_kernel="single": the single-row passes store b2 itself, and the
     column-pair stage 2 forms b2 - b1 from its two tiles."""
     w = inputs.config(2, nx=128, ny=512, n_steps=15)
-    a = _run32(w, w.u0, 15)
-    monkeypatch.setenv("KZK_ROWPAIR", "0")
-    b = _run32(w, w.u0, 15)
+    a = _run32(w, w.u0, 15, row_kernel="pair", col_kernel="pair")
+    b = _run32(w, w.u0, 15, row_kernel="single", col_kernel="pair")
     ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, 15, threads=True)
     assert rel_l2(b, ref) < 1e-5
     assert rel_l2(a, b) < 1e-6
