@@ -200,7 +200,7 @@ def test_batched_streams_with_mixed_and_power_of_two_instances(prec):
     for w in ws:
         w.precision = prec
     dt = torch.float64 if prec == "fp64" else torch.float32
-    bp = api.BatchedPlan(ws, precision=prec, mode="streams")
+    bp = api.BatchedPlan(ws, precision=prec, mode="streams", autotune=False)
     us = [_dev(w.u0, dt) for w in ws]
     st, _ = bp.advance(us, 6, diag=True)
     assert st == 0
@@ -232,7 +232,9 @@ def test_adjoint_matches_oracle(nx, ny, prec, tol, method, medium):
 
 def test_adjoint_finite_differences_on_a_paper_grid_shape():
     from fd_util import central_fd_torch, fd_bound
-    # Set 1 of Table 1 (448 x 1250), a few steps: <g0, v> against central differences
+    # Set 1 of Table 1 (448 x 1250), a few steps: <g0, v> against central
+    # differences with h = 3e-4 (fd_util: h where truncation and rounding of
+    # the difference balance; with h = 1e-6 its rounding alone is ~4e-5)
     api = _api()
     w = inputs.config(2, nx=448, ny=1250, n_steps=4)
     plan = api.Plan.from_workload(w)
@@ -245,5 +247,5 @@ def test_adjoint_finite_differences_on_a_paper_grid_shape():
     for _ in range(2):
         v = _dev(rng.standard_normal(w.u0.shape))
         v /= v.norm()
-        ad, fd = central_fd_torch(plan, u0, v, 1e-6, w.n_steps, w.dtau, g0)
+        ad, fd = central_fd_torch(plan, u0, v, 3e-4, w.n_steps, w.dtau, g0)
         assert abs(ad - fd) <= fd_bound(1e-6, fd, float(g0.norm()), g0.numel()), (ad, fd)
