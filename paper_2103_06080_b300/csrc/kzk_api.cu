@@ -162,6 +162,21 @@ struct kzk_plan_s {
     size_t cpair_smem1, cpair_smem2;
     void *Em1p, *P1p, *P2p;     // (E - 1)', P1', P2' as pair tables [nx/4][pair_tab_rows(ny)]
     void* twcp;                 // twiddles of the pair schedule, as lane pairs
+    // FP64 plans on the per-tile column kernels: the state's normalised
+    // y-spectrum Sigma = FFT_y(V) / ny carried between steps (column modes
+    // FWD / S1 / S2, four y-transforms per step); ysig_ok = the plan has the
+    // arrays, the path is in use while the per-tile kernels are
+    int ysig_ok;
+    void *ysig, *ytmp;          // Sigma and the stage-1 intermediate T, [batch][ny][nx/2]
+    // kzk_advance from captured graphs: gx[0] advances GRAPH_CHUNK steps,
+    // gx[1] one step, both on the plan's arrays; the sigma-dependent values of
+    // the steps a replay covers come from dcoef ([GRAPH_CHUNK][2][4]: sigma,
+    // B, B M, nx (A - A0) of each stage), written before each replay; the
+    // replays write their diagnostics to dhist, copied to diag_hist after each
+    cudaGraphExec_t gx[2];
+    long long gx_kernels[2];    // kernels in each (counted by kzk_launch_count at every replay)
+    double* dcoef;
+    double* dhist;
 };
 
 namespace {
@@ -307,9 +322,19 @@ kzk_status cpair_configure(kzk_plan* p, int optin)
     }
 }
 
+void drop_step_graphs(kzk_plan* p)
+{
+    for (cudaGraphExec_t& g : p->gx)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
 // Put a row / column kernel choice (KZK_ROW_*, KZK_COL_*; both eligible) in use.
 void select_kernels(kzk_plan* p, int row, int col)
 {
+    drop_step_graphs(p);   // captured with the previous kernels
     p->rowpair = row == KZK_ROW_PAIR ? 1 : 0;
     p->colpair = col == KZK_COL_PAIR ? 1 : 0;
     p->colp_log2tc = col == KZK_COL_TMA ? p->colp_l2 : -1;
@@ -402,6 +427,13 @@ kzk_status configure(kzk_plan* p)
     KZK_CUDA(cudaFuncSetAttribute(ysweepT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     KZK_TRY((set_col_attr<T, COL_STAGE1>(sm)));
     KZK_TRY((set_col_attr<T, COL_STAGE2>(sm)));
+    p->ysig_ok = 0;
+    if (sizeof(T) == 8 && p->c.method == KZK_EXPRK22) {
+        KZK_TRY((set_col_attr<T, COL_FWD>(sm)));
+        KZK_TRY((set_col_attr<T, COL_S1>(sm)));
+        KZK_TRY((set_col_attr<T, COL_S2>(sm)));
+        p->ysig_ok = 1;
+    }
     KZK_TRY((set_adj_row_attr<T, ADJ_ROW_2>(sm)));
     KZK_TRY((set_adj_row_attr<T, ADJ_ROW_1>(sm)));
     KZK_TRY((set_adj_col_attr<T, ADJ_COL_2>(sm)));
@@ -717,10 +749,34 @@ ColArgs<T> col_args(const kzk_plan* p)
     return a;
 }
 
+// The y-spectral state path (column modes FWD / S1 / S2) is in use: FP64
+// ExpRK22 plans while the per-tile column kernels are selected.
+bool ysig_on(const kzk_plan* p) { return p->ysig_ok && !p->mixed && !p->colpair && p->colp_log2tc < 0; }
+
+template <typename T, int MODE>
+kzk_status launch_col_tile(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t st)
+{
+    col_kernel<T, MODE><<<dim3(p->n >> p->log2tc, p->batch), p->col_thr, p->col_smem, st>>>(a);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
+// Sigma = FFT_y(V) / ny of a state just loaded into V (y-spectral path).
+template <typename T>
+kzk_status col_fwd(const kzk_plan* p, const void* V, cudaStream_t st)
+{
+    ColArgs<T> a = col_args<T>(p);
+    a.a = (const cx<T>*)V;
+    a.out = (cx<T>*)p->ysig;
+    a.yscale = (T)(1.0 / p->ny);
+    return launch_col_tile<T, COL_FWD>(p, a, st);
+}
+
 // Random-medium coefficients at sigma into stage buffer `stage` (0 or 1).
-kzk_status launch_medium(kzk_plan* p, double sigma, int stage, cudaStream_t st)
+kzk_status launch_medium(kzk_plan* p, double sigma, int stage, cudaStream_t st, const double* dsig = nullptr)
 {
     MedArgs m{};
+    m.sig = dsig;
     m.Ty = (const double2*)p->med_Ty;
     m.a_sig = p->med_mode;
     m.phase = p->med_mode + p->med_n;
@@ -743,12 +799,14 @@ kzk_status launch_medium(kzk_plan* p, double sigma, int stage, cudaStream_t st)
 // diag_rows, u_out: nullable (u_out: where the physical rows are kept).
 template <typename T>
 kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, double* diag_rows, void* u_out,
-                     int stage, cudaStream_t st)
+                     int stage, cudaStream_t st, const double* dcoef = nullptr)
 {
+    // dcoef (nullable): this stage's {sigma, B, B M, nx (A - A0)} in device
+    // memory, used in place of sigma (launches captured into a graph)
     if (p->med_n > 0) {
         // the physical stage state: into u_out when the adjoint sweep keeps it
         void* phys = u_out ? u_out : p->uphys;
-        KZK_TRY(launch_medium(p, sigma, stage, st));
+        KZK_TRY(launch_medium(p, sigma, stage, st, dcoef));
         RowArgs<T> ri = row_args<T>(p, Vin, phys, 0.0, diag_rows);
         KZK_TRY((launch_row<T, ROW_INV>(p, ri, st)));
         YSweepArgs<T> y{};
@@ -767,12 +825,14 @@ kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, dou
         ysweep_kernel<T><<<yg, YSWEEP_THREADS, ysweep_smem<T>(y.Q), st>>>(y);
         KZK_LAUNCHED();
         RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, nullptr);
+        r.coef = dcoef;
         r.uphys = (const T*)phys;
         r.by = (const T*)p->by;
         r.med_coef = p->med_coef + (size_t)stage * 3 * p->ny;
         return launch_row<T, ROW_RHS_MED>(p, r, st, stage == 1 && p->cpair_diff ? p->b1 : nullptr);
     }
     RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, diag_rows);
+    r.coef = dcoef;
     r.u_out = (T*)u_out;
     // column-pair plans on row pairs: the second stage stores b2 - b1 (C2's
     // input), the subtraction done once per element in the row pass
@@ -809,15 +869,54 @@ kzk_status reset_lo(kzk_plan* p, cudaStream_t st);
 // One ExpRK22 step on the spectral state p->V (Algorithm 2, STEP 1-4).
 // diag_hist_step: where C1 writes this step's diagnostics (nullable).
 // vs_out / b1_out / b2_out: destinations (default: plan workspace).
+// ev (nullable): five events recorded around the four passes (R1, C1, R2, C2).
+// On the y-spectral path p->ysig must hold FFT_y(V) / ny on entry; it leaves
+// FFT_y(V_out) / ny there.
 template <typename T>
 kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_step, void* V, void* vs,
-                void* V_out = nullptr, void* u_n = nullptr, void* u_s = nullptr)
+                void* V_out = nullptr, void* u_n = nullptr, void* u_s = nullptr, cudaEvent_t* ev = nullptr,
+                const double* dcoef = nullptr)
 {
+    // dcoef (nullable): the step's sigma-dependent values in device memory
+    // ([2][4], stage 1 then stage 2: see rhs_stage), used in place of sigma
     // V is read-only; the result goes to V_out (default: in place).  u_n, u_s
     // (nullable): where the row passes also store the physical u^n and u*.
     if (!V_out) V_out = V;
     const bool euler = p->c.method == KZK_EXPEULER;
-    KZK_TRY(rhs_stage<T>(p, sigma, V, p->b1, diag_hist_step ? p->diag_rows : nullptr, u_n, 0, st));
+    auto mark = [&](int i) -> kzk_status {
+        if (ev) KZK_CUDA(cudaEventRecord(ev[i], st));
+        return KZK_OK;
+    };
+    KZK_TRY(mark(0));
+    KZK_TRY(rhs_stage<T>(p, sigma, V, p->b1, diag_hist_step ? p->diag_rows : nullptr, u_n, 0, st, dcoef));
+    KZK_TRY(mark(1));
+    if (ysig_on(p) && !euler) {
+        // STEP 2: V* = IFFT_y(X), X = ny E' Sigma + P1' FFT_y(b1); T = X - P2' FFT_y(b1)
+        ColArgs<T> c1 = col_args<T>(p);
+        c1.a = (const cx<T>*)p->ysig;
+        c1.b = (const cx<T>*)p->b1;
+        c1.out = (cx<T>*)vs;
+        c1.out2 = (cx<T>*)p->ytmp;
+        c1.Ta = (const cx<T>*)p->E;
+        c1.Tb = (const cx<T>*)p->P1;
+        c1.Tc = (const cx<T>*)p->P2;
+        c1.yscale = (T)p->ny;
+        c1.diag_rows = diag_hist_step ? p->diag_rows : nullptr;
+        c1.diag_hist = diag_hist_step;
+        KZK_TRY((launch_col_tile<T, COL_S1>(p, c1, st)));
+        KZK_TRY(mark(2));
+        KZK_TRY(rhs_stage<T>(p, sigma + p->dt, vs, p->b2, nullptr, u_s, 1, st, dcoef ? dcoef + 4 : nullptr));
+        KZK_TRY(mark(3));
+        // STEP 4: Sigma' = T + P2' FFT_y(b2), V' = IFFT_y(Sigma')
+        ColArgs<T> c2 = col_args<T>(p);
+        c2.a = (const cx<T>*)p->ytmp;
+        c2.b = (const cx<T>*)p->b2;
+        c2.out = (cx<T>*)V_out;
+        c2.out2 = (cx<T>*)p->ysig;
+        c2.Ta = (const cx<T>*)p->P2;
+        KZK_TRY((launch_col_tile<T, COL_S2>(p, c2, st)));
+        return mark(4);
+    }
     ColArgs<T> c1 = col_args<T>(p);
     c1.a = (const cx<T>*)V;
     c1.b = (const cx<T>*)p->b1;
@@ -829,8 +928,13 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     c1.diag_rows = diag_hist_step ? p->diag_rows : nullptr;
     c1.diag_hist = diag_hist_step;
     KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
-    if (euler) return KZK_OK;
-    KZK_TRY(rhs_stage<T>(p, sigma + p->dt, vs, p->b2, nullptr, u_s, 1, st));
+    KZK_TRY(mark(2));
+    if (euler) {
+        KZK_TRY(mark(3));
+        return mark(4);
+    }
+    KZK_TRY(rhs_stage<T>(p, sigma + p->dt, vs, p->b2, nullptr, u_s, 1, st, dcoef ? dcoef + 4 : nullptr));
+    KZK_TRY(mark(3));
     ColArgs<T> c2 = col_args<T>(p);
     c2.a = (const cx<T>*)p->b1;
     c2.b = (const cx<T>*)p->b2;
@@ -839,7 +943,7 @@ kzk_status step(kzk_plan* p, double sigma, cudaStream_t st, double* diag_hist_st
     c2.Ta = (const cx<T>*)p->P2;
     stage2_lo<T>(p, c2);
     KZK_TRY((launch_col<T, COL_STAGE2>(p, c2, st)));
-    return KZK_OK;
+    return mark(4);
 }
 
 // zero lo part after a state is (re)loaded into p->V in spectral form
@@ -856,8 +960,11 @@ kzk_status to_spectral(kzk_plan* p, const void* u, void* V, cudaStream_t st)
     RowArgs<T> a = row_args<T>(p, u, V, 0.0, nullptr);
     a.out_scale = (T)(1.0 / p->nx);
     KZK_TRY((launch_row<T, ROW_FWD>(p, a, st)));
-    // a state loaded into the plan's state array starts with a zero lo part
-    return V == p->V ? reset_lo(p, st) : KZK_OK;
+    if (V != p->V) return KZK_OK;
+    // a state loaded into the plan's state array starts with a zero lo part,
+    // and on the y-spectral path with its y-spectrum
+    KZK_TRY(reset_lo(p, st));
+    return ysig_on(p) ? col_fwd<T>(p, V, st) : KZK_OK;
 }
 
 template <typename T>
@@ -918,14 +1025,123 @@ kzk_status finish_diag(kzk_plan* p, long long n_steps, cudaStream_t st, kzk_diag
     return KZK_OK;
 }
 
+// Stage values of GRAPH_CHUNK-step replays: for local step s of a replay
+// starting at global step s0, stage 1 at sigma = sigma0 + (s0 + s) dt and
+// stage 2 at sigma + dt, each {sigma, B(sigma), B(sigma) M, nx (A(sigma) - A)}
+// -- the host's expressions of B_of / dA_of / row_args, evaluated in FP64 with
+// every product and sum rounded on its own (as the host computes them), so a
+// replay uses bit for bit the values a direct launch would.
+constexpr int GRAPH_CHUNK = 16;
+struct StepCoefArgs {
+    double* out;
+    int count;
+    long long s0;
+    double sigma0, dt, B, A, M, nx;
+    double Bp[4], Ap[4];
+    int has_profile;
+};
+__global__ void step_coef_kernel(StepCoefArgs a)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.count) return;
+    auto horner = [](const double* c, double x) {
+        return __dadd_rn(__dmul_rn(__dadd_rn(__dmul_rn(__dadd_rn(__dmul_rn(c[3], x), c[2]), x), c[1]), x), c[0]);
+    };
+    const double s1 = __dadd_rn(a.sigma0, __dmul_rn((double)(a.s0 + s), a.dt));
+    const double sg[2] = {s1, __dadd_rn(s1, a.dt)};
+    for (int k = 0; k < 2; k++) {
+        const double B = a.has_profile ? __dmul_rn(a.B, horner(a.Bp, sg[k])) : a.B;
+        const double dA = a.has_profile ? __dadd_rn(__dmul_rn(a.A, horner(a.Ap, sg[k])), -a.A) : 0.0;
+        double* o = a.out + 8 * s + 4 * k;
+        o[0] = sg[k];
+        o[1] = B;
+        o[2] = __dmul_rn(B, a.M);
+        o[3] = __dmul_rn(a.nx, dA);
+    }
+}
+
+kzk_status launch_step_coef(kzk_plan* p, int count, long long s0, double sigma0, cudaStream_t st)
+{
+    StepCoefArgs a{};
+    a.out = p->dcoef;
+    a.count = count;
+    a.s0 = s0;
+    a.sigma0 = sigma0;
+    a.dt = p->dt;
+    a.B = p->c.B;
+    a.A = p->c.A;
+    a.M = p->c.lf_umax;
+    a.nx = (double)p->nx;
+    memcpy(a.Bp, p->c.B_prof, sizeof(a.Bp));
+    memcpy(a.Ap, p->c.A_prof, sizeof(a.Ap));
+    a.has_profile = p->c.has_profile;
+    step_coef_kernel<<<1, GRAPH_CHUNK, 0, st>>>(a);
+    KZK_LAUNCHED();
+    return KZK_OK;
+}
+
+// Capture the step graphs of the plan (GRAPH_CHUNK steps and one step) on its
+// own stream; the launches read their sigma values from p->dcoef and write
+// their diagnostics to p->dhist.
 template <typename T>
-kzk_status advance_impl(kzk_plan* p, void* u, long long n_steps, double sigma0, cudaStream_t st, kzk_diag* dout)
+kzk_status capture_step_graphs(kzk_plan* p)
+{
+    if (!p->dcoef) KZK_CUDA(cudaMalloc(&p->dcoef, (size_t)GRAPH_CHUNK * 8 * sizeof(double)));
+    if (!p->dhist) KZK_CUDA(cudaMalloc(&p->dhist, (size_t)GRAPH_CHUNK * p->batch * 4 * sizeof(double)));
+    if (!p->cap_stream) KZK_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    const int counts[2] = {GRAPH_CHUNK, 1};
+    for (int g = 0; g < 2; g++) {
+        if (p->gx[g]) continue;
+        cudaGraph_t graph = nullptr;
+        KZK_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        kzk_status s = KZK_OK;
+        // captured launches run at replays: count them there, not here
+        const long long n0 = g_launches.load();
+        for (int i = 0; i < counts[g] && s == KZK_OK; i++)
+            s = step<T>(p, 0.0, p->cap_stream, p->dhist + (size_t)i * p->batch * 4, p->V, p->vs, nullptr, nullptr,
+                        nullptr, nullptr, p->dcoef + 8 * i);
+        const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+        p->gx_kernels[g] = g_launches.load() - n0;
+        g_launches.fetch_sub(p->gx_kernels[g]);
+        if (s != KZK_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (s != KZK_OK) return s;
+            return fail(KZK_ERR_CUDA, "capture of the step graph: %s", cudaGetErrorString(e));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&p->gx[g], graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            p->gx[g] = nullptr;
+            return fail(KZK_ERR_CUDA, "step graph instantiate: %s", cudaGetErrorString(ei));
+        }
+    }
+    return KZK_OK;
+}
+
+// direct: launch every kernel (no step graphs), as inside another capture
+template <typename T>
+kzk_status advance_impl(kzk_plan* p, void* u, long long n_steps, double sigma0, cudaStream_t st, kzk_diag* dout,
+                        bool direct = false)
 {
     KZK_TRY(ensure_hist(p, std::max(1LL, n_steps)));
     KZK_TRY(to_spectral<T>(p, u, p->V, st));
-    for (long long s = 0; s < n_steps; s++) {
-        const double sigma = sigma0 + (double)s * p->dt;
-        KZK_TRY(step<T>(p, sigma, st, p->diag_hist + (size_t)s * p->batch * 4, p->V, p->vs));
+    if (!direct && p->opt.graph != KZK_GRAPH_OFF && n_steps > 0) {
+        KZK_TRY(capture_step_graphs<T>(p));
+        for (long long s = 0; s < n_steps;) {
+            const int count = n_steps - s >= GRAPH_CHUNK ? GRAPH_CHUNK : 1;
+            KZK_TRY(launch_step_coef(p, count, s, sigma0, st));
+            const int g = count == GRAPH_CHUNK ? 0 : 1;
+            KZK_CUDA(cudaGraphLaunch(p->gx[g], st));
+            g_launches.fetch_add(p->gx_kernels[g], std::memory_order_relaxed);
+            KZK_CUDA(cudaMemcpyAsync(p->diag_hist + (size_t)s * p->batch * 4, p->dhist,
+                                     (size_t)count * p->batch * 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            s += count;
+        }
+    } else {
+        for (long long s = 0; s < n_steps; s++) {
+            const double sigma = sigma0 + (double)s * p->dt;
+            KZK_TRY(step<T>(p, sigma, st, p->diag_hist + (size_t)s * p->batch * 4, p->V, p->vs));
+        }
     }
     KZK_TRY(to_physical<T>(p, p->V, u, 1.0, p->diag_rows, st));
     diag_reduce_kernel<<<p->batch, 256, 0, st>>>(p->diag_rows, p->ny, 1.0 / ((double)p->nx * p->ny),
@@ -1060,6 +1276,8 @@ void plan_free(kzk_plan* p)
         p->subs = nullptr;
     }
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (cudaGraphExec_t& g : p->gx)
+        if (g) cudaGraphExecDestroy(g);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (p->side) {
         for (cudaStream_t q : *p->side) cudaStreamDestroy(q);
@@ -1078,7 +1296,7 @@ void plan_free(kzk_plan* p)
                     p->diag_rows, p->diag_hist, p->diag_final, p->lam, p->mu, p->nu, p->ls,
                     p->seg, p->ckpt, p->colp_flag, p->med_Ty, p->med_mode, p->med_coef, p->med_bmax,
                     p->uphys, p->by, p->mpos_row, p->mpos_col, p->mipos_col, p->wsc, p->twr2, p->tws2,
-                    p->Vlo, p->vslo, p->Em1, p->Em1p, p->P1p, p->P2p, p->twcp};
+                    p->Vlo, p->vslo, p->Em1, p->Em1p, p->P1p, p->P2p, p->twcp, p->ysig, p->ytmp, p->dcoef, p->dhist};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1322,7 +1540,10 @@ kzk_status reverse_sweep(kzk_plan* p, const void* g_end, void* g0, cudaStream_t 
         for (long long s = s0; s < s1; s++) {
             const long long i = s - s0;
             void* Vn = i == 0 ? arr_at(p->ckpt, c) : p->V;
-            if (i == 0) KZK_TRY(reset_lo(p, st));     // checkpoints keep the hi part
+            if (i == 0) {
+                KZK_TRY(reset_lo(p, st));     // checkpoints keep the hi part
+                if (ysig_on(p)) KZK_TRY(col_fwd<T>(p, Vn, st));
+            }
             KZK_TRY(step<T>(p, sigma0 + (double)s * p->dt, st, nullptr, Vn, p->vs, p->V, arr_at(p->seg, 2 * i),
                             arr_at(p->seg, 2 * i + 1)));
         }
@@ -1604,9 +1825,9 @@ kzk_status plan_autotune(kzk_plan* p, cudaStream_t st)
             if (status != KZK_OK) break;
             select_kernels(p, r, c);
             if (cudaMemsetAsync(u, 0, bytes, st) != cudaSuccess) { status = fail(KZK_ERR_CUDA, "autotune memset"); break; }
-            if ((status = advance_impl<T>(p, u, 1, 0.0, st, nullptr)) != KZK_OK) break;   // warm-up
+            if ((status = advance_impl<T>(p, u, 1, 0.0, st, nullptr, true)) != KZK_OK) break;   // warm-up
             cudaEventRecord(e0, st);
-            if ((status = advance_impl<T>(p, u, 2, 0.0, st, nullptr)) != KZK_OK) break;
+            if ((status = advance_impl<T>(p, u, 2, 0.0, st, nullptr, true)) != KZK_OK) break;
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) { status = fail(KZK_ERR_CUDA, "autotune timing"); break; }
             float ms = 0;
@@ -1689,7 +1910,7 @@ kzk_status advance_streams_impl(kzk_plan* p, void* const* u, long long n_steps, 
         for (int i = 0; i < n && e == cudaSuccess && s == KZK_OK; i++) {
             cudaStream_t q = (*p->side)[i];
             e = cudaStreamWaitEvent(q, (*p->evs)[0], 0);
-            if (e == cudaSuccess) s = advance_impl<T>((*p->subs)[i], u[i], n_steps, sigma0, q, nullptr);
+            if (e == cudaSuccess) s = advance_impl<T>((*p->subs)[i], u[i], n_steps, sigma0, q, nullptr, true);
             if (e == cudaSuccess && s == KZK_OK) e = cudaEventRecord((*p->evs)[i + 1], q);
             if (e == cudaSuccess && s == KZK_OK) e = cudaStreamWaitEvent(p->cap_stream, (*p->evs)[i + 1], 0);
         }
@@ -1824,43 +2045,8 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
     KZK_TRY(to_spectral<T>(p, u, p->V, st));
     for (long long s = 0; s < n_steps; s++) {
         const double sigma = sigma0 + (double)s * p->dt;
-        KZK_CUDA(cudaEventRecord(ev[0], st));
-        KZK_TRY(rhs_stage<T>(p, sigma, p->V, p->b1, p->diag_rows, nullptr, 0, st));
-        KZK_CUDA(cudaEventRecord(ev[1], st));
-        ColArgs<T> c1 = col_args<T>(p);
-        const bool euler = p->c.method == KZK_EXPEULER;
-        c1.a = (const cx<T>*)p->V;
-        c1.b = (const cx<T>*)p->b1;
-        c1.out = (cx<T>*)(euler ? p->V : p->vs);
-        stage1_tables<T>(p, c1, euler);
-        c1.Tb = (const cx<T>*)p->P1;
-        c1.diag_rows = p->diag_rows;
-        c1.diag_hist = p->diag_hist + (size_t)s * p->batch * 4;
-        KZK_TRY((launch_col<T, COL_STAGE1>(p, c1, st)));
-        KZK_CUDA(cudaEventRecord(ev[2], st));
-        if (euler) {
-            // exponential Euler: no second stage
-            KZK_CUDA(cudaEventRecord(ev[3], st));
-            KZK_CUDA(cudaEventRecord(ev[4], st));
-            KZK_CUDA(cudaEventSynchronize(ev[4]));
-            for (int k = 0; k < 4; k++) {
-                float t = 0;
-                KZK_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
-                acc[k] += t;
-            }
-            continue;
-        }
-        KZK_TRY(rhs_stage<T>(p, sigma + p->dt, p->vs, p->b2, nullptr, nullptr, 1, st));
-        KZK_CUDA(cudaEventRecord(ev[3], st));
-        ColArgs<T> c2 = col_args<T>(p);
-        c2.a = (const cx<T>*)p->b1;
-        c2.b = (const cx<T>*)p->b2;
-        c2.c = (const cx<T>*)p->vs;
-        c2.out = (cx<T>*)p->V;
-        c2.Ta = (const cx<T>*)p->P2;
-        stage2_lo<T>(p, c2);
-        KZK_TRY((launch_col<T, COL_STAGE2>(p, c2, st)));
-        KZK_CUDA(cudaEventRecord(ev[4], st));
+        KZK_TRY(step<T>(p, sigma, st, p->diag_hist + (size_t)s * p->batch * 4, p->V, p->vs, nullptr, nullptr,
+                        nullptr, ev));
         KZK_CUDA(cudaEventSynchronize(ev[4]));
         for (int k = 0; k < 4; k++) {
             float t = 0;
@@ -1930,7 +2116,8 @@ kzk_status kzk_plan_create_ex(const kzk_grid* grid, const kzk_coeffs* coeffs, do
     if (opts) o = *opts;
     if (o.row_kernel < KZK_AUTO || o.row_kernel > KZK_ROW_SINGLE || o.col_kernel < KZK_AUTO ||
         o.col_kernel > KZK_COL_TILE || o.fp32_state < KZK_AUTO || o.fp32_state > KZK_STATE_PLAIN ||
-        o.transforms < KZK_AUTO || o.transforms > KZK_TRANSFORMS_MIXED)
+        o.transforms < KZK_AUTO || o.transforms > KZK_TRANSFORMS_MIXED || o.graph < KZK_AUTO ||
+        o.graph > KZK_GRAPH_OFF)
         return fail(KZK_ERR_ARG, "unknown option value");
     // powers of two: the radix-8/16 kernels; other even sizes with no prime
     // factor above 7 (the paper's 7 * 2^k x 1250 * 2^k grids), or
@@ -2046,6 +2233,10 @@ kzk_status kzk_plan_create_ex(const kzk_grid* grid, const kzk_coeffs* coeffs, do
         if (e == cudaSuccess) e = cudaMalloc(&p->vslo, lo_arr);
         if (e == cudaSuccess) e = cudaMalloc(&p->Em1, tab);
     }
+    if (p->ysig_ok) {
+        if (e == cudaSuccess) e = cudaMalloc(&p->ysig, arr);
+        if (e == cudaSuccess) e = cudaMalloc(&p->ytmp, arr);
+    }
     if (keep_colpair) {
         const size_t ptab = (size_t)pair_tab_rows(p->ny) * p->n * sizeof(float2);
         void** ptabs[] = {&p->Em1p, &p->P1p, &p->P2p};
@@ -2093,6 +2284,7 @@ kzk_status kzk_plan_info(kzk_plan* p, kzk_options* out)
     o.fp32_state = p->prec == KZK_FP32 ? (p->comp ? KZK_STATE_COMPENSATED : KZK_STATE_PLAIN) : KZK_AUTO;
     o.transforms = p->mixed ? KZK_TRANSFORMS_MIXED : KZK_AUTO;
     o.autotune = p->opt.autotune;
+    o.graph = p->opt.graph == KZK_GRAPH_OFF ? KZK_GRAPH_OFF : KZK_GRAPH_ON;
     *out = o;
     return KZK_OK;
 }
@@ -2109,6 +2301,7 @@ kzk_status kzk_plan_set_medium(kzk_plan* p, const kzk_medium* m)
         if (!std::isfinite(m->klam[n]) || !std::isfinite(m->theta[n]) || !std::isfinite(m->phase[n]) ||
             !std::isfinite(m->amp[n]))
             return fail(KZK_ERR_ARG, "mode %d: non-finite value", n);
+    drop_step_graphs(p);   // captured without (or with another) medium
     void* old[] = {p->med_Ty, p->med_mode, p->med_coef, p->med_bmax, p->uphys, p->by};
     for (void* q : old)
         if (q) KZK_CUDA(cudaFree(q));

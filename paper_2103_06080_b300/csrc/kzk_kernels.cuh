@@ -47,7 +47,29 @@ struct RowArgs {
     const T* uphys;         // physical rows [batch][ny][nx]
     const T* by;            // the y-flux difference and source of every point [batch][ny][nx] (ysweep_kernel)
     const double* med_coef; // [ny][3]: U_par, U_perp, d U_perp / dy at this sigma
+    // nullable: this stage's sigma-dependent values from device memory,
+    // {sigma, B(sigma), B(sigma) M, nx (A(sigma) - A)} (FP64), in place of
+    // wc.B, wc.alpha and cA (launches replayed from a captured graph)
+    const double* coef;
 };
+
+// The stage's WENO coefficients and absorption-deviation factor (from
+// RowArgs::coef when it is set).
+template <typename T>
+__device__ __forceinline__ WenoCoef<T> stage_wc(const RowArgs<T>& a)
+{
+    WenoCoef<T> w = a.wc;
+    if (a.coef) {
+        w.B = (T)__ldg(a.coef + 1);
+        w.alpha = (T)__ldg(a.coef + 2);
+    }
+    return w;
+}
+template <typename T>
+__device__ __forceinline__ T stage_cA(const RowArgs<T>& a)
+{
+    return a.coef ? (T)__ldg(a.coef + 3) : a.cA;
+}
 
 // Block reduction of the four diagnostics (FP64 across threads, fixed
 // order: deterministic).  blockDim.x must be a power of two; red holds
@@ -290,15 +312,15 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
             const int Q = nx / nthr >= 16 ? nx / nthr : (nx >= 16 ? 16 : nx);
             const int k0 = tid * Q;
             if (k0 < nx) {
+                WenoCoef<T> wc = stage_wc(a);
                 if constexpr (MODE == ROW_RHS_MED) {
                     // this row's advection speed c = 2 pi U_par and LF speed |c| + B M
-                    WenoCoef<T> wc = a.wc;
                     const double cj = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * row);
+                    wc.alpha = (T)(fabs(cj) + (double)wc.alpha);
                     wc.c = (T)cj;
-                    wc.alpha = (T)(fabs(cj) + (double)a.wc.alpha);
                     weno_row_chunk<T, true, true>(U, Bf, nx, k0, Q, wc);
                 } else {
-                    weno_row_chunk<T, true>(U, Bf, nx, k0, Q, a.wc);
+                    weno_row_chunk<T, true>(U, Bf, nx, k0, Q, wc);
                 }
                 if (a.diag_rows) row_stats<T, true>(U, k0, Q, s1, s2, mx, nf);
             }
@@ -314,24 +336,25 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
             }
             const cx<T>* Z = fft_batched_pp<T, ROW_PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
             const cx<T>* vin = a.in + base;
+            const T cA = stage_cA(a);
             for (int k = tid; k <= n / 2; k += nthr) {
                 cx<T> xk, xnk;
                 r2c_post_pair<T, true>(Z, n, k, a.tw, xk, xnk);
-                if (a.cA != T(0)) {
+                if (cA != T(0)) {
                     // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
                     if (k == 0) {
                         const T kN = a.kscale * T(n);
-                        xk.y -= a.cA * kN * kN * __ldcg(vin).y;
+                        xk.y -= cA * kN * kN * __ldcg(vin).y;
                     } else {
                         const T kt = a.kscale * T(k);
                         const cx<T> v = __ldcg(vin + k);
-                        xk.x -= a.cA * kt * kt * v.x;
-                        xk.y -= a.cA * kt * kt * v.y;
+                        xk.x -= cA * kt * kt * v.x;
+                        xk.y -= cA * kt * kt * v.y;
                         if (2 * k != n) {
                             const T kt2 = a.kscale * T(n - k);
                             const cx<T> w = __ldcg(vin + n - k);
-                            xnk.x -= a.cA * kt2 * kt2 * w.x;
-                            xnk.y -= a.cA * kt2 * kt2 * w.y;
+                            xnk.x -= cA * kt2 * kt2 * w.x;
+                            xnk.y -= cA * kt2 * kt2 * w.y;
                         }
                     }
                 }
@@ -361,7 +384,17 @@ __host__ __forceinline__ size_t row_smem_bytes(int nx)
     return 2 * (size_t)row_buf_len(nx / 2) * sizeof(cx<T>) + 4 * (size_t)row_threads<T>(nx) * sizeof(double);
 }
 
-enum ColMode { COL_STAGE1 = 0, COL_STAGE2 = 1 };
+// STAGE1 / STAGE2: the two column passes of a step on the tau-spectral state
+// V (five y-transforms per step).  FWD, S1, S2 (FP64 plans on the per-tile
+// kernels): the same step with the state's normalised y-spectrum
+// Sigma = FFT_y(V) / ny carried between steps, so stage 1 no longer
+// transforms V (four y-transforms per step):
+//   FWD: Sigma = FFT_y(V) / ny                      (once per loaded state)
+//   S1:  B1 = FFT_y(b1);  X = ny E' Sigma + P1' B1;  T = X - P2' B1;
+//        V* = IFFT_y(X), and T kept                 (STEP 2, Eq. 11)
+//   S2:  B2 = FFT_y(b2);  Sigma' = T + P2' B2;  V' = IFFT_y(Sigma')
+//                                                   (STEP 4: E V + ds[(Phi1 - Phi2) b1 + Phi2 b2])
+enum ColMode { COL_STAGE1 = 0, COL_STAGE2 = 1, COL_FWD = 2, COL_S1 = 3, COL_S2 = 4 };
 
 template <typename T>
 struct ColArgs {
@@ -386,6 +419,12 @@ struct ColArgs {
     // (hi: c) and writes lo of V' (hi: out).  nullptr: plain state.
     const lo_t<T>* lo_in;
     lo_t<T>* lo_out;
+    // y-spectral state (modes FWD, S1, S2): the second output (S1: T, S2:
+    // Sigma'), S1's third table (P2'), and the power-of-two scale (FWD: 1/ny,
+    // S1: ny)
+    cx<T>* out2;
+    const cx<T>* Tc;
+    T yscale;
 };
 
 // Table entry at (l, m) applied to a column-FFT'd value z (zm: the value at
@@ -546,6 +585,107 @@ __device__ __forceinline__ void col_body(const ColArgs<T>& a, int tile, int inst
         } else {
             for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = SA[padx(e)];
         }
+    } else if constexpr (MODE == COL_FWD) {
+        // Sigma = FFT_y(V) / ny of a loaded state
+        {
+            int e = tid;
+            for (; e + 3 * nthr < total; e += 4 * nthr) {
+                cx<T> va[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) va[q] = __ldcg(a.a + gidx(e + q * nthr));
+#pragma unroll
+                for (int q = 0; q < 4; q++) SA[padx(e + q * nthr)] = va[q];
+            }
+            for (; e < total; e += nthr) SA[padx(e)] = __ldcg(a.a + gidx(e));
+        }
+        __syncthreads();
+        fft_batched<T, COL_PPT, true, false, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
+        for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = scale<T>(SA[padx(e)], a.yscale);
+    } else if constexpr (MODE == COL_S1 || MODE == COL_S2) {
+        if constexpr (MODE == COL_S1) {
+            // diagnostics of the state this step started from (rows written by R)
+            if (tile == 0 && a.diag_rows && a.diag_hist) {
+                double* red = reinterpret_cast<double*>(smem_raw);
+                double s1 = 0, s2 = 0, mx = 0, nf = 0;
+                const double* dr = a.diag_rows + (long long)inst * ny * 4;
+                for (int r = tid; r < ny; r += nthr) {
+                    s1 += __ldcg(dr + 4 * r); s2 += __ldcg(dr + 4 * r + 1);
+                    mx = fmax(mx, __ldcg(dr + 4 * r + 2)); nf += __ldcg(dr + 4 * r + 3);
+                }
+                double tmp[4];
+                block_diag(red, s1, s2, mx, nf, tmp);
+                if (tid == 0) {
+                    double* d = a.diag_hist + inst * 4;
+                    d[0] = tmp[0] * a.inv_count;
+                    d[1] = tmp[1] * a.cell;
+                    d[2] = tmp[2];
+                    d[3] = tmp[3];
+                }
+            }
+        }
+        // SA: the y-spectral tile (S1: Sigma, S2: T); SB: the b tile
+        {
+            int e = tid;
+            for (; e + 3 * nthr < total; e += 4 * nthr) {
+                cx<T> va[4], vb[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) { va[q] = __ldcg(a.a + gidx(e + q * nthr)); vb[q] = __ldcg(a.b + gidx(e + q * nthr)); }
+#pragma unroll
+                for (int q = 0; q < 4; q++) { SA[padx(e + q * nthr)] = va[q]; SB[padx(e + q * nthr)] = vb[q]; }
+            }
+            for (; e < total; e += nthr) {
+                const long long g = gidx(e);
+                SA[padx(e)] = __ldcg(a.a + g);
+                SB[padx(e)] = __ldcg(a.b + g);
+            }
+        }
+        __syncthreads();
+        fft_batched<T, COL_PPT, true, false, true, false>(SB, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
+        for (int e = tid; e < total; e += nthr) {
+            const int l = e >> a.log2tc, c = e & (TC - 1), m = m0 + c;
+            if (m == 0) continue;
+            const int lf = l <= (ny >> 1) ? l : ny - l;
+            const long long ti = (long long)lf * n + m;
+            const cx<T> zs = SA[padx(e)], zb = SB[padx(e)];
+            cx<T> r;
+            if constexpr (MODE == COL_S1) {
+                r = fma_c<T>(a.Tb[ti], zb, scale<T>(mul<T>(a.Ta[ti], zs), a.yscale));
+                const cx<T> t = a.Tc[ti];
+                a.out2[gidx(e)] = fma_c<T>(mk<T>(-t.x, -t.y), zb, r);
+            } else {
+                r = fma_c<T>(a.Ta[ti], zb, zs);
+                a.out2[gidx(e)] = r;
+            }
+            SA[padx(e)] = r;
+        }
+        if (m0 == 0) {
+            // the packed column 0 couples rows l and ny - l (see mult_entry)
+            for (int l = tid; l <= (ny >> 1); l += nthr) {
+                const int lm = (ny - l) & (ny - 1);
+                const long long ti = (long long)l * n;
+                const int e = padx(l << a.log2tc), em = padx(lm << a.log2tc);
+                const cx<T> zs = SA[e], zsm = SA[em], zb = SB[e], zbm = SB[em];
+                cx<T> r, rm;
+                if constexpr (MODE == COL_S1) {
+                    r = add<T>(scale<T>(mult_entry<T>(a.Ta[ti], zs, zsm, true), a.yscale),
+                               mult_entry<T>(a.Tb[ti], zb, zbm, true));
+                    rm = add<T>(scale<T>(mult_entry<T>(a.Ta[ti], zsm, zs, true), a.yscale),
+                                mult_entry<T>(a.Tb[ti], zbm, zb, true));
+                    a.out2[gidx(l << a.log2tc)] = sub<T>(r, mult_entry<T>(a.Tc[ti], zb, zbm, true));
+                    if (lm != l) a.out2[gidx(lm << a.log2tc)] = sub<T>(rm, mult_entry<T>(a.Tc[ti], zbm, zb, true));
+                } else {
+                    r = add<T>(zs, mult_entry<T>(a.Ta[ti], zb, zbm, true));
+                    rm = add<T>(zsm, mult_entry<T>(a.Ta[ti], zbm, zb, true));
+                    a.out2[gidx(l << a.log2tc)] = r;
+                    if (lm != l) a.out2[gidx(lm << a.log2tc)] = rm;
+                }
+                SA[e] = r;
+                if (lm != l) SA[em] = rm;
+            }
+        }
+        __syncthreads();
+        fft_batched<T, COL_PPT, true, true, true, false>(SA, a.log2ny, a.log2tc, TC, 1, twp, tid, nthr);
+        for (int e = tid; e < total; e += nthr) a.out[gidx(e)] = SA[padx(e)];
     } else {
         {
             int e = tid;

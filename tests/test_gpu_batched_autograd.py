@@ -24,7 +24,10 @@ def test_batched_matches_single_plans(prec, mode, state):
     # the persistent kernel runs the per-tile column bodies and the
     # single-row bodies (FP32: with the compensated or the plain state):
     # compare with single plans on the same kernels, bit for bit; streams mode
-    # runs the instances' own default kernels
+    # runs the instances' own default kernels.  FP64 single plans on the
+    # per-tile kernels carry the state's y-spectrum between steps (four
+    # y-transforms per step, the persistent kernel five): the same step to
+    # rounding, compared at 1e-13
     kw = dict(fp32_state=state) if prec == "fp32" else {}
     single = dict(row_kernel="single", col_kernel="tile") if mode == "persistent" else {}
     dt = torch.float64 if prec == "fp64" else torch.float32
@@ -37,7 +40,10 @@ def test_batched_matches_single_plans(prec, mode, state):
         p = api.Plan.from_workload(w, precision=prec, **kw, **single)
         v = torch.tensor(w.u0, dtype=dt, device="cuda")
         p.advance(v, 20)
-        assert torch.equal(u, v), (w.nx, w.ny)
+        if prec == "fp64" and mode == "persistent":
+            assert float((u - v).abs().max() / v.abs().max()) < 1e-13, (w.nx, w.ny)
+        else:
+            assert torch.equal(u, v), (w.nx, w.ny)
         assert np.isfinite(d["energy"]) and d["run_nonfinite"] == 0
         p.close()
     # a second call replays the captured graph
