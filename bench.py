@@ -478,6 +478,41 @@ def paper_grid_reports(api, torch, dev, sets=None, precisions=("fp64", "fp32"), 
     return rep
 
 
+def small_grid_graph_report(api, torch, dev, reps=5):
+    """The plain-method workload (512 x 256, 200 steps) with kzk_advance
+    replaying captured step graphs (the default) and with direct launches:
+    its arrays (4 x 1 MB FP64) stay in L2 and its kernels are short, so the
+    launch path, not HBM, bounds it.  Median of `reps` timed 200-step calls
+    after one untimed call."""
+    w = inputs.config(1)
+    rep = {"workload": "fp64/fp32 512x256 N-wave, 200 steps per call (L2-resident: launch-bound, "
+                       "no HBM roofline applies)", "unit": UNIT}
+    for prec, dtype in (("fp64", torch.float64), ("fp32", torch.float32)):
+        row = {}
+        for g in ("on", "off"):
+            plan = api.Plan.from_workload(w, precision=prec, graph=g)
+            u0 = torch.tensor(w.u0, dtype=dtype, device=dev)
+            u = u0.clone()
+            plan.advance(u, w.n_steps)
+            times = []
+            for _ in range(reps):
+                u.copy_(u0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                plan.advance(u, w.n_steps)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            row["graph" if g == "on" else "direct"] = {"value": w.nx * w.ny * w.n_steps / (ms * 1e-3),
+                                                       "ms_per_step": ms / w.n_steps}
+            plan.close()
+        row["graph_speedup"] = row["direct"]["ms_per_step"] / row["graph"]["ms_per_step"]
+        rep[prec] = row
+    return rep
+
+
 def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
     """FP32 throughput + error, the adjoint/forward cost ratio, the batched
     launch and the cuFFT comparison."""
@@ -605,6 +640,7 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
                          "the instances concurrently")}
             bp.close()
             del us
+    out["small_grid_graphs"] = small_grid_graph_report(api, torch, dev)
     # random medium of Algorithm 1 (the paper's inhomogeneous workload) on the same grid
     wm = inputs.medium_config(4096, 2048, 500)
     med = {"workload": f"N-wave through the random medium of Algorithm 1 ({wm.medium.n_modes} modes), 4096x2048, "

@@ -153,6 +153,14 @@ typedef struct kzk_plan_s kzk_plan;
                                    radix-8/16 kernels for powers of two, mixed radix for
                                    the other grids); row_kernel / col_kernel then take
                                    no other value than KZK_AUTO / KZK_ROW_SINGLE        */
+/* graph                                                                       */
+#define KZK_GRAPH_ON 1          /* kzk_advance replays CUDA graphs of captured steps
+                                   (default): chunks of 16 steps and single steps, each
+                                   captured once per plan (at the first kzk_advance) and
+                                   replayed for any sigma0, the sigma-dependent
+                                   coefficients of each chunk written to device memory by
+                                   one kernel before it                                  */
+#define KZK_GRAPH_OFF 2         /* kzk_advance launches every kernel directly        */
 typedef struct {
     int32_t row_kernel;         /* KZK_AUTO, KZK_ROW_PAIR, KZK_ROW_SINGLE            */
     int32_t col_kernel;         /* KZK_AUTO, KZK_COL_PAIR, KZK_COL_TMA, KZK_COL_TILE */
@@ -163,6 +171,7 @@ typedef struct {
                                    col_kernel) combination advances a zero state for one
                                    untimed and two timed steps (CUDA events) at plan
                                    creation, and the fastest is kept                   */
+    int32_t graph;              /* KZK_AUTO (= KZK_GRAPH_ON), KZK_GRAPH_ON, KZK_GRAPH_OFF */
 } kzk_options;
 
 /* Create a plan for `batch` independent propagations sharing grid,
@@ -231,7 +240,10 @@ kzk_status kzk_medium_eval(kzk_plan *plan, double sigma, double *out, double *ma
  * synchronises the stream, fills the diagnostics and returns
  * KZK_ERR_NONFINITE if any NaN/Inf was seen, else KZK_ERR_CFL if max|u|
  * exceeded lf_umax, else KZK_OK.  Without diag_out the call is asynchronous
- * and performs no host synchronisation. */
+ * and performs no host synchronisation.  Unless the plan's options say
+ * KZK_GRAPH_OFF, the steps are replayed from CUDA graphs that the first call
+ * captures (on a plan-owned stream; that first call must not itself be inside
+ * a stream capture); results equal the direct launches bit for bit. */
 kzk_status kzk_advance(kzk_plan *plan, void *u, int64_t n_steps, double sigma0, void *stream,
                        kzk_diag *diag_out);
 
@@ -355,7 +367,8 @@ const char *kzk_status_string(kzk_status s);
 /* One-line description of the last failure on the calling thread. */
 const char *kzk_last_error(void);
 
-/* Number of kernel launches the library has issued since load (all plans). */
+/* Number of kernels the library has launched since load (all plans), counting
+ * every kernel of a replayed graph. */
 int64_t kzk_launch_count(void);
 
 /* Measurement helper (no counterpart in the paper).  Advances u (device,

@@ -45,7 +45,7 @@ class KzkMedium(ctypes.Structure):
 class KzkOptions(ctypes.Structure):
     _fields_ = [("row_kernel", ctypes.c_int32), ("col_kernel", ctypes.c_int32),
                 ("fp32_state", ctypes.c_int32), ("transforms", ctypes.c_int32),
-                ("autotune", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 # kzk_options values (include/kzk.h), by option
@@ -55,6 +55,7 @@ OPTION_VALUES = {
     "col_kernel": {"auto": 0, "pair": 1, "tma": 2, "tile": 3},
     "fp32_state": {"auto": 0, "compensated": 1, "plain": 2},
     "transforms": {"auto": 0, "mixed": 1},
+    "graph": {"auto": 0, "on": 1, "off": 2},
 }
 
 

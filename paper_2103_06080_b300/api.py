@@ -22,13 +22,14 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> int:
 
 
 def make_options(row_kernel: str = "auto", col_kernel: str = "auto", fp32_state: str = "auto",
-                 transforms: str = "auto", autotune: bool = False) -> "L.KzkOptions":
+                 transforms: str = "auto", autotune: bool = False, graph: str = "auto") -> "L.KzkOptions":
     """kzk_options from names: row_kernel auto|pair|single, col_kernel
     auto|pair|tma|tile, fp32_state auto|compensated|plain, transforms
-    auto|mixed; autotune times the open kernel choices at plan creation."""
+    auto|mixed, graph auto|on|off (advance from replayed step graphs);
+    autotune times the open kernel choices at plan creation."""
     vals = {}
     for key, name in (("row_kernel", row_kernel), ("col_kernel", col_kernel), ("fp32_state", fp32_state),
-                      ("transforms", transforms)):
+                      ("transforms", transforms), ("graph", graph)):
         table = L.OPTION_VALUES[key]
         if name not in table:
             raise ValueError(f"{key} must be one of {sorted(table)}, got {name!r}")
@@ -55,7 +56,8 @@ class Plan:
                  has_profile: bool = False, diffraction: float = 0.0, reg_eps: float = 0.0,
                  weno_eps: float = 0.0, relax_C: Sequence[float] = (), relax_theta: Sequence[float] = (),
                  method: str = "exprk22", row_kernel: str = "auto", col_kernel: str = "auto",
-                 fp32_state: str = "auto", transforms: str = "auto", autotune: bool = False):
+                 fp32_state: str = "auto", transforms: str = "auto", autotune: bool = False,
+                 graph: str = "auto"):
         if method not in ("exprk22", "expeuler"):
             raise ValueError("method must be 'exprk22' or 'expeuler'")
         if precision not in ("fp64", "fp32"):
@@ -73,7 +75,7 @@ class Plan:
                         has_profile=int(bool(has_profile)), n_relax=len(relax_C), relax_C=pad(relax_C),
                         relax_theta=pad(relax_theta),
                         method=L.KZK_EXPEULER if method == "expeuler" else L.KZK_EXPRK22)
-        o = make_options(row_kernel, col_kernel, fp32_state, transforms, autotune)
+        o = make_options(row_kernel, col_kernel, fp32_state, transforms, autotune, graph)
         self._grid, self._coeffs, self._opts = g, c, o
         h = ctypes.c_void_p()
         L.check(L.lib().kzk_plan_create_ex(ctypes.byref(g), ctypes.byref(c), self.dt, self.batch, ctypes.byref(o),

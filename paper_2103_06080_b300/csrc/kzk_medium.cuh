@@ -29,6 +29,7 @@ struct MedArgs {
     const double* w;        // [3][N]: -|U~_n| sin(theta_n), |U~_n| cos(theta_n), -|U~_n| cos(theta_n) c_n
     int n_modes, ny;
     double sigma;
+    const double* sig;      // nullable: sigma read from device memory (replayed graphs)
     double* coef;           // [ny][3]: U_par, U_perp, d U_perp / dy
     double* bmax;           // [gridDim.x]: max |U_perp| over the CTA's rows
 };
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(MED_ROWS * MED_GROUPS) medium_kernel(MedArgs a
     const int tid = threadIdx.x, nthr = blockDim.x;
     for (int n = tid; n < a.n_modes; n += nthr) {
         double s, c;
-        sincos(fma(a.a_sig[n], a.sigma, a.phase[n]), &s, &c);
+        sincos(fma(a.a_sig[n], a.sig ? __ldg(a.sig) : a.sigma, a.phase[n]), &s, &c);
         eA[n] = make_double2(c, s);
     }
     __syncthreads();

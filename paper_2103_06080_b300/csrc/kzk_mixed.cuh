@@ -369,14 +369,14 @@ __global__ void __launch_bounds__(MIX_ROW_MAX_THREADS) mix_row_kernel(MixRowArgs
     const int k0 = tid * Q;
     if (k0 < nx) {
         const int Qt = min(Q, nx - k0);
+        WenoCoef<T> wc = stage_wc(a);
         if constexpr (MODE == ROW_RHS_MED) {
-            WenoCoef<T> wc = a.wc;
             const double cj = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * row);
+            wc.alpha = (T)(fabs(cj) + (double)wc.alpha);
             wc.c = (T)cj;
-            wc.alpha = (T)(fabs(cj) + (double)a.wc.alpha);
             weno_row_chunk<T, false, true, false>(X, Y, nx, k0, Qt, wc);
         } else {
-            weno_row_chunk<T, false, false, false>(X, Y, nx, k0, Qt, a.wc);
+            weno_row_chunk<T, false, false, false>(X, Y, nx, k0, Qt, wc);
         }
         if (a.diag_rows) row_stats<T, false>(X, k0, Qt, s1, s2, mx, nf);
     }
@@ -388,25 +388,26 @@ __global__ void __launch_bounds__(MIX_ROW_MAX_THREADS) mix_row_kernel(MixRowArgs
     }
     mix_forward<T, false>(Y, A.f, 0, a.tw, nullptr, tid, nthr);
     const cx<T>* vin = a.in + base;
+    const T cA = stage_cA(a);
     for (int k = tid; k <= n / 2; k += nthr) {
         const int kn = k == 0 ? 0 : n - k;
         cx<T> xk, xnk;
         r2c_vals<T>(Y[__ldg(pos + k)], Y[__ldg(pos + kn)], __ldg(a.tw + k), k, n, xk, xnk);
-        if (a.cA != T(0)) {
+        if (cA != T(0)) {
             // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
             if (k == 0) {
                 const T kN = a.kscale * T(n);
-                xk.y -= a.cA * kN * kN * __ldcg(vin).y;
+                xk.y -= cA * kN * kN * __ldcg(vin).y;
             } else {
                 const T kt = a.kscale * T(k);
                 const cx<T> v = __ldcg(vin + k);
-                xk.x -= a.cA * kt * kt * v.x;
-                xk.y -= a.cA * kt * kt * v.y;
+                xk.x -= cA * kt * kt * v.x;
+                xk.y -= cA * kt * kt * v.y;
                 if (2 * k != n) {
                     const T kt2 = a.kscale * T(n - k);
                     const cx<T> w = __ldcg(vin + n - k);
-                    xnk.x -= a.cA * kt2 * kt2 * w.x;
-                    xnk.y -= a.cA * kt2 * kt2 * w.y;
+                    xnk.x -= cA * kt2 * kt2 * w.x;
+                    xnk.y -= cA * kt2 * kt2 * w.y;
                 }
             }
         }

@@ -201,18 +201,19 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         const int Q = nx / nthr >= 16 ? nx / nthr : (nx >= 16 ? 16 : nx);
         const int k0 = tid * Q;
         if (k0 < nx) {
+            const WenoCoef<float> ws = stage_wc(a);
             WenoCoef<f2> wc;
-            wc.B = f2(a.wc.B);
-            wc.alpha = f2(a.wc.alpha);
-            wc.eps = f2(a.wc.eps);
-            wc.inv_dtau = f2(a.wc.inv_dtau);
+            wc.B = f2(ws.B);
+            wc.alpha = f2(ws.alpha);
+            wc.eps = f2(ws.eps);
+            wc.inv_dtau = f2(ws.inv_dtau);
             wc.c = f2(0.0f);
             if constexpr (MODE == ROW_RHS_MED) {
                 // each row's advection speed c = 2 pi U_par and LF speed |c| + B M
                 const double c0 = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * row);
                 const double c1 = 2.0 * 3.14159265358979323846 * __ldg(a.med_coef + 3 * (row + 1));
                 wc.c = f2((float)c0, (float)c1);
-                wc.alpha = f2((float)(fabs(c0) + (double)a.wc.alpha), (float)(fabs(c1) + (double)a.wc.alpha));
+                wc.alpha = f2((float)(fabs(c0) + (double)ws.alpha), (float)(fabs(c1) + (double)ws.alpha));
                 weno_row_chunk<f2, true, true>(U, Bf, nx, k0, Q, wc);
             } else {
                 weno_row_chunk<f2, true>(U, Bf, nx, k0, Q, wc);
@@ -245,25 +246,26 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             __syncthreads();
         }
         const float2* Xs = reinterpret_cast<const float2*>(U);
+        const float cA = stage_cA(a);
         for (int k = tid; k <= n / 2; k += nthr) {
             c2 xk, xnk;
             r2c_post_pair<f2, true>(Z, n, k, P.tw2, xk, xnk);
             float2 k0a = lane0(xk), k0b = lane1(xk), kna = lane0(xnk), knb = lane1(xnk);
-            if (a.cA != 0.0f) {
+            if (cA != 0.0f) {
                 // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx), each row
                 const float2* va = in + base;
                 const float2* vb = in + base + n;
                 if (k == 0) {
-                    const float kN = a.kscale * (float)n, f = a.cA * kN * kN;
+                    const float kN = a.kscale * (float)n, f = cA * kN * kN;
                     k0a.y -= f * __ldcg(va).y;
                     k0b.y -= f * __ldcg(vb).y;
                 } else {
-                    const float kt = a.kscale * (float)k, f = a.cA * kt * kt;
+                    const float kt = a.kscale * (float)k, f = cA * kt * kt;
                     const float2 v0 = __ldcg(va + k), v1 = __ldcg(vb + k);
                     k0a.x -= f * v0.x; k0a.y -= f * v0.y;
                     k0b.x -= f * v1.x; k0b.y -= f * v1.y;
                     if (2 * k != n) {
-                        const float kt2 = a.kscale * (float)(n - k), g = a.cA * kt2 * kt2;
+                        const float kt2 = a.kscale * (float)(n - k), g = cA * kt2 * kt2;
                         const float2 w0 = __ldcg(va + n - k), w1 = __ldcg(vb + n - k);
                         kna.x -= g * w0.x; kna.y -= g * w0.y;
                         knb.x -= g * w1.x; knb.y -= g * w1.y;

@@ -428,3 +428,55 @@ def test_fp32_compensated_state_short_runs(method):
             plan.advance(u, w.n_steps)
             assert rel_l2(u.double().cpu().numpy(), ref) < 1e-5, (state, col)
             plan.close()
+
+
+# kzk_advance from replayed step graphs (the default) against direct launches:
+# the graphs' sigma-dependent values come from device memory, computed with
+# the host's expressions, so the results and the diagnostics agree bit for bit
+@pytest.mark.parametrize("prec,kind", [("fp64", "stratified"), ("fp32", "stratified"), ("fp64", "medium"),
+                                       ("fp32", "medium"), ("fp64", "mixed"), ("fp32", "euler")])
+def test_graph_replay_matches_direct_launches(prec, kind):
+    api = _api()
+    kw = {}
+    if kind == "medium":
+        w = inputs.medium_config(128, 64, 40)
+    elif kind == "mixed":
+        w = inputs.config(2, nx=56, ny=50, n_steps=40)
+    else:
+        w = inputs.config(2, nx=256, ny=256, n_steps=40)
+        if kind == "euler":
+            kw["method"] = "expeuler"
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plans = {g: api.Plan.from_workload(w, precision=prec, graph=g, **kw) for g in ("on", "off")}
+    assert plans["on"].info()["graph"] == "on" and plans["off"].info()["graph"] == "off"
+    for steps, sigma0 in ((37, 0.0), (5, 0.41 * w.n_steps * w.dt), (16, 0.8 * w.n_steps * w.dt)):
+        res = {}
+        for g, plan in plans.items():
+            u = _dev(w.u0, dt)
+            st, d = plan.advance(u, steps, sigma0=sigma0, diag=True)
+            assert st == 0
+            res[g] = (u, plan.diag_history(steps), d[0])
+        assert torch.equal(res["on"][0], res["off"][0]), (steps, sigma0)
+        assert np.array_equal(res["on"][1], res["off"][1])
+        assert res["on"][2] == res["off"][2]
+    for plan in plans.values():
+        plan.close()
+
+
+def test_graph_launches_are_counted():
+    """kzk_launch_count counts every kernel a replayed graph runs: the same
+    number as the direct launches of the same steps."""
+    api = _api()
+    w = inputs.config(2, nx=256, ny=128, n_steps=40)
+    counts = {}
+    for g in ("on", "off"):
+        plan = api.Plan.from_workload(w, graph=g)
+        u = _dev(w.u0)
+        plan.advance(u, 2)                     # graphs captured on the first call
+        torch.cuda.synchronize()
+        n0 = api.launch_count()
+        plan.advance(u, 21)
+        counts[g] = api.launch_count() - n0
+        plan.close()
+    # per replay one kernel writes the chunk's sigma values (two replays: 16 + 5 x 1 = 6)
+    assert counts["on"] == counts["off"] + 6, counts
