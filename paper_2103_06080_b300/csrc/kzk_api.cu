@@ -556,6 +556,8 @@ kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st, c
             P.tw2 = (const c2*)p->twr2;
             P.tws2 = (const c2*)p->tws2;
             P.sub = (const float2*)sub;
+            P.flag = p->colp_flag;
+            P.timeout_ns = 2000000000LL;
             if constexpr (MODE == ROW_RHS || MODE == ROW_RHS_MED) {
                 if (sub) {
                     rowpair_kernel<MODE, true><<<dim3(p->ny / 2, p->batch), p->row_thr, p->rowpair_smem, st>>>(P);

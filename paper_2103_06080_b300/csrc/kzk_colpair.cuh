@@ -126,17 +126,6 @@ __global__ void pair_table_kernel(const float2* __restrict__ T, c2* __restrict__
     PT[(long long)m * pair_tab_rows(1 << L) + pair_tab_row<L>(r)] = pack2(x, y);
 }
 
-// contiguous copy global -> shared (16-byte aligned, size a multiple of 16),
-// completing on mbarrier b
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* b)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_addr(b))
-        : "memory");
-}
-
 // The lo part of the compensated state is stored pair-major for these
 // kernels: the bf16 pairs of column pair m (both columns of a row side by
 // side) form one contiguous run of ny rows, [batch][n/2][ny][2].

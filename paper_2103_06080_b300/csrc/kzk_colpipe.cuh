@@ -83,6 +83,17 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m, int
         : "memory");
 }
 
+// contiguous copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing on mbarrier b
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* b)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_addr(b))
+        : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Stockham passes over a column tile with pluggable loads and stores.
 // Element i = l * TC + c is row l of column c.  A loader fills v[0..R) with

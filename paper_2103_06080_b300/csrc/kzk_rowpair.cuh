@@ -14,8 +14,16 @@
 // The arithmetic of every lane is the FP32 arithmetic of the single-row kernel
 // (FMAs may be contracted differently, so the two agree to rounding, not bit
 // for bit); the plan option row_kernel = KZK_ROW_SINGLE selects the single-row kernel.
+//
+// The b passes (ROW_RHS) take their two input rows -- contiguous in the
+// spectral state, 16 n bytes -- by one bulk copy of the tensor memory
+// accelerator into buffer X as they lie; the C2R pre-processing reads them
+// there and writes the packed pairs into Y, where the inverse transform starts
+// (no separate load pass).  The copy's wait is bounded (FLAG_TIMEOUT).  The
+// absorption-deviation term at the end issues all its loads of V before it
+// computes, so their latencies overlap.
 #pragma once
-#include "kzk_kernels.cuh"
+#include "kzk_colpipe.cuh"
 
 namespace kzk {
 
@@ -65,6 +73,8 @@ struct RowPairArgs {
     const c2* tws2;         // staged twiddles of the length-nx/2 FFT, as pairs
     const float2* sub;      // ROW_RHS / ROW_RHS_MED (nullable): spectral rows subtracted from the result
                             // (the second stage of column-pair plans stores b2 - b1 for C2)
+    int* flag;              // FLAG_TIMEOUT when the row copy does not arrive in time
+    long long timeout_ns;
 };
 
 __device__ __forceinline__ c2 pack2(float2 a, float2 b) { return c2{f2(a.x, b.x), f2(a.y, b.y)}; }
@@ -117,6 +127,42 @@ __device__ __forceinline__ void pair_diag_final(const double* red, double* dst)
     dst[c] = v;   // row j: dst[0..3], row j + 1: dst[4..7]
 }
 
+// The mbarrier of the ROW_RHS row copy: the last 16 bytes of the reduction
+// area (4 doubles per thread; the statistics use 8 doubles per warp).
+__device__ __forceinline__ unsigned long long* pair_bar(double* red, int nthr)
+{
+    return reinterpret_cast<unsigned long long*>(red + 4 * nthr - 2);
+}
+
+// c2r_pre of the two rows of Vb (row j at Vb[0, n), row j + 1 at Vb[n, 2n),
+// as they lie in the state), written as packed pairs into the padded buffer
+// X (the same arithmetic per lane as c2r_pre on packed rows).
+__device__ __forceinline__ void c2r_pre_pair(const float2* Vb, c2* X, int n, const c2* __restrict__ tw, int tid,
+                                             int nthr)
+{
+    for (int k = tid; k <= n / 2; k += nthr) {
+        if (k == 0) {
+            const float2 r0 = Vb[0], r1 = Vb[n];
+            const c2 z = pack2(r0, r1);
+            X[0] = c2{z.x + z.y, z.x - z.y};
+        } else if (2 * k == n) {
+            const c2 a = pack2(Vb[k], Vb[n + k]);
+            X[padx(k)] = c2{f2(2.0f) * a.x, f2(-2.0f) * a.y};
+        } else {
+            const c2 a = pack2(Vb[k], Vb[n + k]), b = pack2(Vb[n - k], Vb[2 * n - k]);
+            const c2 w = tw[k];
+            c2 s = add<f2>(a, conj<f2>(b)), d = sub<f2>(a, conj<f2>(b));
+            c2 r = mul_si<f2, 1>(mulc<f2>(d, w));
+            const c2 zk = add<f2>(s, r);
+            s = add<f2>(b, conj<f2>(a));
+            d = sub<f2>(b, conj<f2>(a));
+            r = mul_si<f2, -1>(mul<f2>(d, w));
+            X[padx(k)] = zk;
+            X[padx(n - k)] = add<f2>(s, r);
+        }
+    }
+}
+
 template <int MODE, bool SUB = false>
 __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs P)
 {
@@ -164,17 +210,40 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         const float* u0 = a.uphys + 2 * base;
         for (int i = tid; i < nx; i += nthr) st_real<f2, true>(X, i, f2(__ldcg(u0 + i), __ldcg(u0 + nx + i)));
         __syncthreads();
+    } else if constexpr (MODE == ROW_RHS) {
+        // both rows (2 n float2, contiguous) by one bulk copy into X as they
+        // lie; the pre-processing packs them into Y
+        unsigned long long* bar = pair_bar(red, nthr);
+        float2* Vraw = reinterpret_cast<float2*>(X);
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            mbar_fence_init();
+            mbar_expect(bar, 16u * (unsigned)n);
+            bulk_load(Vraw, in + base, 16u * (unsigned)n, bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait(bar, 0u, P.timeout_ns);
+        if (__syncthreads_or(!ok)) {
+            // give the copy a second bounded wait before the CTA leaves, so no
+            // write into this CTA's shared memory is still on its way
+            if (tid == 0) {
+                atomicOr(P.flag, FLAG_TIMEOUT);
+                mbar_wait(bar, 0u, P.timeout_ns);
+            }
+            __syncthreads();
+            return;
+        }
+        c2r_pre_pair(Vraw, Y, n, P.tw2, tid, nthr);
+        __syncthreads();
+        if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+        U = fft_batched_pp<f2, PPT, false, true, true>(Y, X, log2n, 0, 1, 0, tw, tid, nthr);
+        Bf = U == X ? Y : X;
     } else {
         for (int i = tid; i < n; i += nthr) X[padx(i)] = pack2(__ldcg(in + base + i), __ldcg(in + base + n + i));
         __syncthreads();
         c2r_pre<f2, true>(X, n, P.tw2, tid, nthr);
         __syncthreads();
-        if constexpr (MODE == ROW_RHS) {
-            U = fft_batched_pp<f2, PPT, false, true, true>(X, Y, log2n, 0, 1, 0, tw, tid, nthr);
-            Bf = U == X ? Y : X;
-        } else {
-            fft_batched<f2, PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
-        }
+        fft_batched<f2, PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
     }
 
     float sa1 = 0, sa2 = 0, mxa = 0, sb1 = 0, sb2 = 0, mxb = 0;
@@ -247,28 +316,48 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         }
         const float2* Xs = reinterpret_cast<const float2*>(U);
         const float cA = stage_cA(a);
-        for (int k = tid; k <= n / 2; k += nthr) {
+        // the V values of the absorption-deviation term, all loads issued
+        // before the arithmetic.  The loop below takes k = tid + i nthr for
+        // i < ITER: with nthr = max(32, n / 8) threads, k <= n/2 needs at most
+        // five iterations.
+        constexpr int ITER = 5;
+        float2 vk0[ITER], vk1[ITER], vn0[ITER], vn1[ITER];
+        if (cA != 0.0f) {
+            const float2* va = in + base;
+            const float2* vb = in + base + n;
+#pragma unroll
+            for (int i = 0; i < ITER; i++) {
+                const int k = tid + i * nthr;
+                if (k <= n / 2) {
+                    const int kn = k == 0 ? 0 : n - k;
+                    vk0[i] = __ldcg(va + k);
+                    vk1[i] = __ldcg(vb + k);
+                    vn0[i] = __ldcg(va + kn);
+                    vn1[i] = __ldcg(vb + kn);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ITER; i++) {
+            const int k = tid + i * nthr;
+            if (k > n / 2) break;
             c2 xk, xnk;
             r2c_post_pair<f2, true>(Z, n, k, P.tw2, xk, xnk);
             float2 k0a = lane0(xk), k0b = lane1(xk), kna = lane0(xnk), knb = lane1(xnk);
             if (cA != 0.0f) {
                 // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx), each row
-                const float2* va = in + base;
-                const float2* vb = in + base + n;
                 if (k == 0) {
                     const float kN = a.kscale * (float)n, f = cA * kN * kN;
-                    k0a.y -= f * __ldcg(va).y;
-                    k0b.y -= f * __ldcg(vb).y;
+                    k0a.y -= f * vk0[i].y;
+                    k0b.y -= f * vk1[i].y;
                 } else {
                     const float kt = a.kscale * (float)k, f = cA * kt * kt;
-                    const float2 v0 = __ldcg(va + k), v1 = __ldcg(vb + k);
-                    k0a.x -= f * v0.x; k0a.y -= f * v0.y;
-                    k0b.x -= f * v1.x; k0b.y -= f * v1.y;
+                    k0a.x -= f * vk0[i].x; k0a.y -= f * vk0[i].y;
+                    k0b.x -= f * vk1[i].x; k0b.y -= f * vk1[i].y;
                     if (2 * k != n) {
                         const float kt2 = a.kscale * (float)(n - k), g = cA * kt2 * kt2;
-                        const float2 w0 = __ldcg(va + n - k), w1 = __ldcg(vb + n - k);
-                        kna.x -= g * w0.x; kna.y -= g * w0.y;
-                        knb.x -= g * w1.x; knb.y -= g * w1.y;
+                        kna.x -= g * vn0[i].x; kna.y -= g * vn0[i].y;
+                        knb.x -= g * vn1[i].x; knb.y -= g * vn1[i].y;
                     }
                 }
             }
