@@ -452,6 +452,11 @@ kzk_status configure(kzk_plan* p)
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_RHS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_RHS_MED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       optin));
+        const void* ct[] = {(const void*)rowpair_kernel<ROW_RHS, false, 9>, (const void*)rowpair_kernel<ROW_RHS, true, 9>,
+                            (const void*)rowpair_kernel<ROW_RHS, false, 10>, (const void*)rowpair_kernel<ROW_RHS, true, 10>,
+                            (const void*)rowpair_kernel<ROW_RHS, false, 11>, (const void*)rowpair_kernel<ROW_RHS, true, 11>,
+                            (const void*)rowpair_kernel<ROW_RHS, false, 12>, (const void*)rowpair_kernel<ROW_RHS, true, 12>};
+        for (const void* f : ct) KZK_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     }
     colp_configure<T>(p, optin);
     KZK_TRY(cpair_configure<T>(p, optin));
@@ -558,14 +563,32 @@ kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st, c
             P.sub = (const float2*)sub;
             P.flag = p->colp_flag;
             P.timeout_ns = 2000000000LL;
+            const dim3 grid(p->ny / 2, p->batch);
+            if constexpr (MODE == ROW_RHS) {
+                // the length-specialised b passes for nx = 1024 ... 8192
+                switch (p->log2nx - 1) {
+#define KZK_ROWPAIR_CT(L)                                                                              \
+    case L:                                                                                            \
+        if (sub) rowpair_kernel<ROW_RHS, true, L><<<grid, p->row_thr, p->rowpair_smem, st>>>(P);      \
+        else rowpair_kernel<ROW_RHS, false, L><<<grid, p->row_thr, p->rowpair_smem, st>>>(P);         \
+        KZK_LAUNCHED();                                                                                \
+        return KZK_OK;
+                    KZK_ROWPAIR_CT(9)
+                    KZK_ROWPAIR_CT(10)
+                    KZK_ROWPAIR_CT(11)
+                    KZK_ROWPAIR_CT(12)
+#undef KZK_ROWPAIR_CT
+                default: break;
+                }
+            }
             if constexpr (MODE == ROW_RHS || MODE == ROW_RHS_MED) {
                 if (sub) {
-                    rowpair_kernel<MODE, true><<<dim3(p->ny / 2, p->batch), p->row_thr, p->rowpair_smem, st>>>(P);
+                    rowpair_kernel<MODE, true><<<grid, p->row_thr, p->rowpair_smem, st>>>(P);
                     KZK_LAUNCHED();
                     return KZK_OK;
                 }
             }
-            rowpair_kernel<MODE><<<dim3(p->ny / 2, p->batch), p->row_thr, p->rowpair_smem, st>>>(P);
+            rowpair_kernel<MODE><<<grid, p->row_thr, p->rowpair_smem, st>>>(P);
             KZK_LAUNCHED();
             return KZK_OK;
         }
@@ -2040,25 +2063,35 @@ kzk_status alu_peak_impl(cudaStream_t st, double* out)
 template <typename T>
 kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sigma0, cudaStream_t st, double* ms)
 {
-    cudaEvent_t ev[5];
-    for (auto& e : ev) KZK_CUDA(cudaEventCreate(&e));
+    // five events per step, all recorded before one synchronisation at the
+    // end: no host wait between steps, so no launch latency lands inside an
+    // interval
+    std::vector<cudaEvent_t> ev((size_t)std::max(0LL, n_steps) * 5, nullptr);
+    kzk_status status = KZK_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { status = fail(KZK_ERR_CUDA, "event creation"); break; }
     double acc[4] = {0, 0, 0, 0};
-    KZK_TRY(ensure_hist(p, std::max(1LL, n_steps)));
-    KZK_TRY(to_spectral<T>(p, u, p->V, st));
-    for (long long s = 0; s < n_steps; s++) {
+    if (status == KZK_OK) status = ensure_hist(p, std::max(1LL, n_steps));
+    if (status == KZK_OK) status = to_spectral<T>(p, u, p->V, st);
+    for (long long s = 0; s < n_steps && status == KZK_OK; s++) {
         const double sigma = sigma0 + (double)s * p->dt;
-        KZK_TRY(step<T>(p, sigma, st, p->diag_hist + (size_t)s * p->batch * 4, p->V, p->vs, nullptr, nullptr,
-                        nullptr, ev));
-        KZK_CUDA(cudaEventSynchronize(ev[4]));
+        status = step<T>(p, sigma, st, p->diag_hist + (size_t)s * p->batch * 4, p->V, p->vs, nullptr, nullptr,
+                         nullptr, &ev[(size_t)s * 5]);
+    }
+    if (status == KZK_OK) status = to_physical<T>(p, p->V, u, 1.0, nullptr, st);
+    if (status == KZK_OK && cudaStreamSynchronize(st) != cudaSuccess) status = fail(KZK_ERR_CUDA, "synchronise");
+    for (long long s = 0; s < n_steps && status == KZK_OK; s++)
         for (int k = 0; k < 4; k++) {
             float t = 0;
-            KZK_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            if (cudaEventElapsedTime(&t, ev[(size_t)s * 5 + k], ev[(size_t)s * 5 + k + 1]) != cudaSuccess) {
+                status = fail(KZK_ERR_CUDA, "event timing");
+                break;
+            }
             acc[k] += t;
         }
-    }
-    KZK_TRY(to_physical<T>(p, p->V, u, 1.0, nullptr, st));
-    KZK_CUDA(cudaStreamSynchronize(st));
-    for (auto& e : ev) cudaEventDestroy(e);
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (status != KZK_OK) return status;
     for (int k = 0; k < 4; k++) ms[k] = n_steps > 0 ? acc[k] / (double)n_steps : 0.0;
     return KZK_OK;
 }

@@ -273,6 +273,39 @@ __device__ __forceinline__ cx<T>* fft_batched_pp(cx<T>* a, cx<T>* b, int log2n, 
     return s;
 }
 
+// fft_batched / fft_batched_pp with the length 2^LOG2N known at compile
+// time: the same passes in the same order (the schedule unrolled by template
+// recursion), so every stride, twiddle offset and trip count is a constant.
+template <int PPT, int REM>
+__host__ __device__ constexpr int ct_log2_radix()
+{
+    return (PPT >= 16 && REM >= 4) ? 4 : (PPT >= 8 && REM >= 3) ? 3 : (PPT >= 4 && REM >= 2) ? 2 : 1;
+}
+template <typename T, int PPT, bool COLS, bool INV, bool PAD, bool ACC, int LOG2N, int DONE = 0, int OFF = 0>
+__device__ __forceinline__ void fft_batched_ct(cx<T>* buf, const Tw<T>& tw, int tid, int nthr)
+{
+    if constexpr (DONE < LOG2N) {
+        constexpr int LR = ct_log2_radix<PPT, LOG2N - DONE>();
+        constexpr int R = 1 << LR;
+        fft_pass<T, R, PPT, COLS, INV, PAD, ACC>(buf, LOG2N, 0, 1, 0, DONE, tw, OFF, tid, nthr);
+        fft_batched_ct<T, PPT, COLS, INV, PAD, ACC, LOG2N, DONE + LR, OFF + (DONE > 0 ? (R - 1) << DONE : 0)>(
+            buf, tw, tid, nthr);
+    }
+}
+template <typename T, int PPT, bool COLS, bool INV, bool PAD, bool ACC, int LOG2N, int DONE = 0, int OFF = 0>
+__device__ __forceinline__ cx<T>* fft_batched_pp_ct(cx<T>* a, cx<T>* b, const Tw<T>& tw, int tid, int nthr)
+{
+    if constexpr (DONE >= LOG2N) {
+        return a;
+    } else {
+        constexpr int LR = ct_log2_radix<PPT, LOG2N - DONE>();
+        constexpr int R = 1 << LR;
+        fft_pass<T, R, PPT, COLS, INV, PAD, ACC, true>(a, b, LOG2N, 0, 1, 0, DONE, tw, OFF, tid, nthr);
+        return fft_batched_pp_ct<T, PPT, COLS, INV, PAD, ACC, LOG2N, DONE + LR,
+                                 OFF + (DONE > 0 ? (R - 1) << DONE : 0)>(b, a, tw, tid, nthr);
+    }
+}
+
 // Radix schedule of fft_batched for a length 2^log2n with PPT points
 // per thread, as (log2 R, log2 Ns) pairs.
 __host__ __device__ inline int fft_schedule(int log2n, int ppt, int* lr, int* lns)

@@ -83,14 +83,23 @@ __device__ __forceinline__ float2 lane1(c2 z) { return make_float2(z.x.v.y, z.y.
 
 // statistics of both rows (FP32, as row_stats): sum, sum of squares, max |u|
 // and non-finite count of the points [k0, k0 + Q)
+// (Q16: Q == 16 and k0 a multiple of 16, the points at constant offsets, as
+// in weno_row_chunk)
+template <bool Q16 = false>
 __device__ __forceinline__ void pair_stats(const c2* u, int k0, int Q, float& sa1, float& sa2, float& mxa, int& nfa,
                                            float& sb1, float& sb2, float& mxb, int& nfb)
 {
-    for (int k = k0; k < k0 + Q; k++) {
-        const f2 w = ld_real<f2, true>(u, k);
+    auto acc = [&](f2 w) {
         const float v0 = w.v.x, v1 = w.v.y;
         if (isfinite(v0)) { sa1 += v0; sa2 = fmaf(v0, v0, sa2); mxa = fmaxf(mxa, fabsf(v0)); } else { nfa += 1; }
         if (isfinite(v1)) { sb1 += v1; sb2 = fmaf(v1, v1, sb2); mxb = fmaxf(mxb, fabsf(v1)); } else { nfb += 1; }
+    };
+    if constexpr (Q16) {
+        const f2* pr = reinterpret_cast<const f2*>(u) + 2 * padx(k0 >> 1);
+#pragma unroll
+        for (int j = 0; j < 16; j++) acc(pr[j]);
+    } else {
+        for (int k = k0; k < k0 + Q; k++) acc(ld_real<f2, true>(u, k));
     }
 }
 
@@ -163,14 +172,25 @@ __device__ __forceinline__ void c2r_pre_pair(const float2* Vb, c2* X, int n, con
     }
 }
 
-template <int MODE, bool SUB = false>
+// LOG2N > 0 (ROW_RHS only): the instantiation for rows of nx = 2^(LOG2N + 1)
+// points, launched with max(32, 2^LOG2N / 8) threads: lengths, thread count,
+// transform schedule and WENO chunks are compile-time constants.
+template <int LOG2N>
+__host__ __device__ constexpr int rowpair_ct_threads()
+{
+    return (1 << LOG2N) / 8 > 32 ? (1 << LOG2N) / 8 : 32;
+}
+
+template <int MODE, bool SUB = false, int LOG2N = 0>
 __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs P)
 {
+    static_assert(LOG2N == 0 || (MODE == ROW_RHS && LOG2N >= 8), "length-specialised b passes only");
+    constexpr bool CT = LOG2N > 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const RowArgs<float>& a = P.r;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x, nthr = CT ? rowpair_ct_threads<LOG2N>() : blockDim.x;
     const int row = 2 * blockIdx.x, inst = blockIdx.y;
-    const int nx = 1 << a.log2nx, n = nx >> 1, log2n = a.log2nx - 1;
+    const int nx = CT ? 2 << LOG2N : 1 << a.log2nx, n = nx >> 1, log2n = CT ? LOG2N : a.log2nx - 1;
     c2* X = reinterpret_cast<c2*>(smem_raw);
     c2* Y = X + row_buf_len(n);
     double* red = reinterpret_cast<double*>(Y + row_buf_len(n));
@@ -236,7 +256,8 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         c2r_pre_pair(Vraw, Y, n, P.tw2, tid, nthr);
         __syncthreads();
         if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-        U = fft_batched_pp<f2, PPT, false, true, true>(Y, X, log2n, 0, 1, 0, tw, tid, nthr);
+        if constexpr (CT) U = fft_batched_pp_ct<f2, PPT, false, true, true, false, LOG2N>(Y, X, tw, tid, nthr);
+        else U = fft_batched_pp<f2, PPT, false, true, true>(Y, X, log2n, 0, 1, 0, tw, tid, nthr);
         Bf = U == X ? Y : X;
     } else {
         for (int i = tid; i < n; i += nthr) X[padx(i)] = pack2(__ldcg(in + base + i), __ldcg(in + base + n + i));
@@ -285,9 +306,9 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
                 wc.alpha = f2((float)(fabs(c0) + (double)ws.alpha), (float)(fabs(c1) + (double)ws.alpha));
                 weno_row_chunk<f2, true, true>(U, Bf, nx, k0, Q, wc);
             } else {
-                weno_row_chunk<f2, true>(U, Bf, nx, k0, Q, wc);
+                weno_row_chunk<f2, true, false, true, CT>(U, Bf, nx, k0, Q, wc);
             }
-            if (a.diag_rows) pair_stats(U, k0, Q, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
+            if (a.diag_rows) pair_stats<CT>(U, k0, Q, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
         }
         if (a.diag_rows) pair_diag_partial(red, sa1, sa2, mxa, nfa, sb1, sb2, mxb, nfb);
         __syncthreads();
@@ -308,7 +329,9 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             __syncthreads();
         }
         c2* Z = Bf;
-        if constexpr (MODE == ROW_RHS && !SUB) Z = fft_batched_pp<f2, PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
+        if constexpr (CT && !SUB) Z = fft_batched_pp_ct<f2, PPT, false, false, true, false, LOG2N>(Bf, U, tw, tid, nthr);
+        else if constexpr (CT) fft_batched_ct<f2, PPT, false, false, true, false, LOG2N>(Bf, tw, tid, nthr);
+        else if constexpr (MODE == ROW_RHS && !SUB) Z = fft_batched_pp<f2, PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
         else fft_batched<f2, PPT, false, false, true>(Bf, log2n, 0, 1, 0, tw, tid, nthr);
         if constexpr (SUB) {
             asm volatile("cp.async.wait_all;" ::: "memory");

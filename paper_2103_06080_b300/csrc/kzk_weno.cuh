@@ -100,7 +100,8 @@ __device__ __forceinline__ void rec_parts(T vm2, T vm1, T v0, T v1, T v2, T t0, 
 // k in [k0, k0 + Q) in order.  eps4: the Jiang-Shu epsilon for that scaling
 // (64 eps).  Every smoothness indicator is computed once per stencil centre
 // and every interface once.
-template <typename T, typename Load, typename Store>
+// QC > 0: Q == QC known at compile time (the interface loop fully unrolled).
+template <typename T, int QC = 0, typename Load, typename Store>
 __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Store store)
 {
     T fp[6], fm[6];
@@ -171,12 +172,22 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
         // FP32: two hardware reciprocals (the product of the two denominators
         // could underflow)
         T Fprev = fast_div(np, dp) + fast_div(nm, dm);
+        if constexpr (QC > 0) {
+#pragma unroll
+            for (int j = 0; j < QC; j++) {
+                parts(k0 + j, np, dp, nm, dm);
+                const T F = fast_div(np, dp) + fast_div(nm, dm);
+                store(k0 + j, F - Fprev);
+                Fprev = F;
+            }
+        } else {
 #pragma unroll 2
-        for (k = k0; k < k0 + Q; k++) {
-            parts(k, np, dp, nm, dm);
-            const T F = fast_div(np, dp) + fast_div(nm, dm);
-            store(k, F - Fprev);
-            Fprev = F;
+            for (k = k0; k < k0 + Q; k++) {
+                parts(k, np, dp, nm, dm);
+                const T F = fast_div(np, dp) + fast_div(nm, dm);
+                store(k, F - Fprev);
+                Fprev = F;
+            }
         }
     }
 }
@@ -185,12 +196,27 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
 // memory, PAD layout), written to out at the same points.  ADV: the flux of
 // the random medium, f(u) = -c u - B u^2 / 2 (Eq. 7).  POW2: nx is a power of
 // two (the periodic wrap is a mask); otherwise any nx >= 8.
-template <typename T, bool PAD, bool ADV = false, bool POW2 = true>
+// Q16: Q == 16 and k0 a multiple of 16 (PAD layout): the chunk's 8 complex
+// slots never straddle a padding slot, so its points sit at constant offsets
+// from the first (real index 2 padx(k0 / 2) + j); only the halo points take
+// the general index.
+template <typename T, bool PAD, bool ADV = false, bool POW2 = true, bool Q16 = false>
 __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int nx, int k0, int Q,
                                                const WenoCoef<T>& c)
 {
+    static_assert(!Q16 || PAD, "the constant-offset chunk is for the padded layout");
     const int msk = nx - 1;
     auto wrap = [&](int kk) { return POW2 ? (kk & msk) : (kk < 0 ? kk + nx : (kk >= nx ? kk - nx : kk)); };
+    const int ib = 2 * padx(k0 >> 1);
+    const T* pr = reinterpret_cast<const T*>(u) + ib;
+    T* pw = reinterpret_cast<T*>(out) + ib;
+    auto rd = [&](int kk) -> T {
+        if constexpr (Q16) {
+            const int j = kk - k0;
+            if (j >= 0 && j < 16) return pr[j];
+        }
+        return ld_real<T, PAD>(u, wrap(kk));
+    };
     // the split fluxes are carried as 4 f+- (no halves):
     //   4 f+ = v (2 (alpha - c) - B v),   4 f- = -v (2 (alpha + c) + B v)
     // so the reconstruction is 4 F, the indicators take 64 eps, and the 1/4
@@ -199,12 +225,15 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
     const T ap = T(2) * (ADV ? c.alpha - c.c : c.alpha);
     const T am = T(2) * (ADV ? c.alpha + c.c : c.alpha);
     auto load = [&](int kk, T& p, T& m) {
-        const T v = ld_real<T, PAD>(u, wrap(kk));
+        const T v = rd(kk);
         p = v * fma(-c.B, v, ap);
         m = -v * fma(c.B, v, am);
     };
-    auto store = [&](int k, T d) { st_real<T, PAD>(out, k, d * scale); };
-    weno_sweep<T>(k0, Q, T(64) * c.eps, load, store);
+    auto store = [&](int k, T d) {
+        if constexpr (Q16) pw[k - k0] = d * scale;
+        else st_real<T, PAD>(out, k, d * scale);
+    };
+    weno_sweep<T, Q16 ? 16 : 0>(k0, Q, T(64) * c.eps, load, store);
 }
 
 // sum u, sum u^2, max|u| and non-finite count of the points [k0, k0 + Q).
