@@ -516,7 +516,8 @@ __global__ void __launch_bounds__(PairSched<L>::T, 512 / PairSched<L>::T) colpai
     const c2* T0 = reinterpret_cast<const c2*>(smem + y.t0);
     const c2* T1 = reinterpret_cast<const c2*>(smem + y.t1);
     const c2* tw = P.tw;
-    if (!colp_wait(smem, 0, 0u, P.timeout_ns, P.flag)) return;
+    // copies in flight: STAGE1 and D2 issued barriers 0 and 1 up front
+    if (!colp_wait(smem, 0, 0u, P.timeout_ns, P.flag, MODE == COL_STAGE1 || D2 ? 3u : 1u)) return;
     const SwzIO ia{A};
     if constexpr (MODE == COL_STAGE1) {
         pair_forward_head<L>(B, DenseIn{B}, tw, tid);

@@ -544,12 +544,23 @@ __device__ __forceinline__ void colp_prefetch(const ColPipeArgs<T>& P, int q)
         for (int k = 0; k < P.nbt; k++) tma_prefetch_2d(&P.mt0, x, k * P.bt);
 }
 
-// every thread waits on barrier i; a timeout anywhere ends the CTA uniformly
-__device__ __forceinline__ bool colp_wait(unsigned char* smem, int i, unsigned ph, long long timeout_ns, int* flag)
+// every thread waits on barrier i; a timeout anywhere ends the CTA uniformly.
+// pending: the barriers whose copies may still be in flight at this point
+// (bit j: barrier j; 0 selects barrier i alone).  On a timeout thread 0 gives
+// each of them a second bounded wait before it leaves, so that no copy is
+// still writing into the CTA's shared memory once the CTA has ended.
+__device__ __forceinline__ bool colp_wait(unsigned char* smem, int i, unsigned ph, long long timeout_ns, int* flag,
+                                          unsigned pending = 0u)
 {
-    const bool ok = mbar_wait(reinterpret_cast<unsigned long long*>(smem) + i, ph, timeout_ns);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem);
+    const bool ok = mbar_wait(bar + i, ph, timeout_ns);
     if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0) atomicOr(flag, FLAG_TIMEOUT);
+        if (threadIdx.x == 0) {
+            atomicOr(flag, FLAG_TIMEOUT);
+            const unsigned m = pending ? pending : 1u << i;
+            for (int j = 0; j < 8; j++)
+                if (m & (1u << j)) mbar_wait(bar + j, ph, timeout_ns);
+        }
         return false;
     }
     return true;
