@@ -153,7 +153,8 @@ struct kzk_plan_s {
     // FP32 plans: row passes on row pairs in packed FP32 (kzk_rowpair.cuh);
     // rowpair_ok = the plan fits them, rowpair = in use
     int rowpair_ok, rowpair;
-    size_t rowpair_smem;
+    size_t rowpair_smem, rowpair_ct_smem;   // the length-specialised b passes also hold the row twiddles
+    int rowpair_ct_ok;                      // ... and fit the device's shared memory
     void *twr2, *tws2;          // the tau twiddle tables with every entry as a lane pair
     // FP32 plans with the compensated state: column passes on column pairs
     // (kzk_colpair.cuh); colpair_ok = the plan fits them, colpair = in use
@@ -445,6 +446,8 @@ kzk_status configure(kzk_plan* p)
     if (sizeof(T) == 4 && p->ny % 2 == 0 && rowpair_smem_bytes(p->nx) <= (size_t)optin) {
         p->rowpair_ok = 1;
         p->rowpair_smem = rowpair_smem_bytes(p->nx);
+        p->rowpair_ct_smem = rowpair_ct_smem_bytes(p->nx);
+        p->rowpair_ct_ok = p->rowpair_ct_smem <= (size_t)optin;
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
         KZK_CUDA(cudaFuncSetAttribute(rowpair_kernel<ROW_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -566,11 +569,11 @@ kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st, c
             const dim3 grid(p->ny / 2, p->batch);
             if constexpr (MODE == ROW_RHS) {
                 // the length-specialised b passes for nx = 1024 ... 8192
-                switch (p->log2nx - 1) {
+                switch (p->rowpair_ct_ok ? p->log2nx - 1 : 0) {
 #define KZK_ROWPAIR_CT(L)                                                                              \
     case L:                                                                                            \
-        if (sub) rowpair_kernel<ROW_RHS, true, L><<<grid, p->row_thr, p->rowpair_smem, st>>>(P);      \
-        else rowpair_kernel<ROW_RHS, false, L><<<grid, p->row_thr, p->rowpair_smem, st>>>(P);         \
+        if (sub) rowpair_kernel<ROW_RHS, true, L><<<grid, p->row_thr, p->rowpair_ct_smem, st>>>(P);   \
+        else rowpair_kernel<ROW_RHS, false, L><<<grid, p->row_thr, p->rowpair_ct_smem, st>>>(P);      \
         KZK_LAUNCHED();                                                                                \
         return KZK_OK;
                     KZK_ROWPAIR_CT(9)

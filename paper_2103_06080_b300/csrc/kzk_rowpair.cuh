@@ -142,6 +142,9 @@ __device__ __forceinline__ unsigned long long* pair_bar(double* red, int nthr)
 {
     return reinterpret_cast<unsigned long long*>(red + 4 * nthr - 2);
 }
+// Length-specialised ROW_RHS: the shared copy of the staged twiddles (n - 1
+// lane-pair entries) after the reduction area.
+__device__ __forceinline__ c2* pair_tws(double* red, int nthr) { return reinterpret_cast<c2*>(red + 4 * nthr); }
 
 // c2r_pre of the two rows of Vb (row j at Vb[0, n), row j + 1 at Vb[n, 2n),
 // as they lie in the state), written as packed pairs into the padded buffer
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
     double* red = reinterpret_cast<double*>(Y + row_buf_len(n));
     const long long base = (long long)inst * a.inst_stride + (long long)row * n;   // row j; row j + 1 at + n
     const Tw<f2> tw{P.tws2, nullptr, -1};
+    const Tw<f2> tws_s{pair_tws(red, nthr), nullptr, -1};   // length-specialised ROW_RHS: the shared copy
     constexpr int PPT = 8;
     const float2* in = reinterpret_cast<const float2*>(a.in);
     float2* out = reinterpret_cast<float2*>(a.out);
@@ -238,8 +242,12 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         if (tid == 0) {
             mbar_init(bar, 1);
             mbar_fence_init();
-            mbar_expect(bar, 16u * (unsigned)n);
+            // the length-specialised kernels also take the staged twiddles of
+            // the row transform (n - 1 entries) into shared memory
+            const unsigned twb = CT ? 16u * (unsigned)(n - 1) : 0u;
+            mbar_expect(bar, 16u * (unsigned)n + twb);
             bulk_load(Vraw, in + base, 16u * (unsigned)n, bar);
+            if (CT) bulk_load(pair_tws(red, nthr), P.tws2, twb, bar);
         }
         __syncthreads();
         const bool ok = mbar_wait(bar, 0u, P.timeout_ns);
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         c2r_pre_pair(Vraw, Y, n, P.tw2, tid, nthr);
         __syncthreads();
         if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-        if constexpr (CT) U = fft_batched_pp_ct<f2, PPT, false, true, true, false, LOG2N>(Y, X, tw, tid, nthr);
+        if constexpr (CT) U = fft_batched_pp_ct<f2, PPT, false, true, true, false, LOG2N>(Y, X, tws_s, tid, nthr);
         else U = fft_batched_pp<f2, PPT, false, true, true>(Y, X, log2n, 0, 1, 0, tw, tid, nthr);
         Bf = U == X ? Y : X;
     } else {
@@ -329,8 +337,8 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             __syncthreads();
         }
         c2* Z = Bf;
-        if constexpr (CT && !SUB) Z = fft_batched_pp_ct<f2, PPT, false, false, true, false, LOG2N>(Bf, U, tw, tid, nthr);
-        else if constexpr (CT) fft_batched_ct<f2, PPT, false, false, true, false, LOG2N>(Bf, tw, tid, nthr);
+        if constexpr (CT && !SUB) Z = fft_batched_pp_ct<f2, PPT, false, false, true, false, LOG2N>(Bf, U, tws_s, tid, nthr);
+        else if constexpr (CT) fft_batched_ct<f2, PPT, false, false, true, false, LOG2N>(Bf, tws_s, tid, nthr);
         else if constexpr (MODE == ROW_RHS && !SUB) Z = fft_batched_pp<f2, PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
         else fft_batched<f2, PPT, false, false, true>(Bf, log2n, 0, 1, 0, tw, tid, nthr);
         if constexpr (SUB) {
@@ -411,10 +419,12 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
 }
 
 // threads and shared memory of one pair CTA: as the FP32 single-row kernel,
-// with 16-byte elements
+// with 16-byte elements; the length-specialised b passes add the staged
+// twiddles (nx/2 - 1 entries)
 __host__ __forceinline__ size_t rowpair_smem_bytes(int nx)
 {
     return 2 * (size_t)row_buf_len(nx / 2) * sizeof(c2) + 4 * (size_t)row_threads<float>(nx) * sizeof(double);
 }
+__host__ __forceinline__ size_t rowpair_ct_smem_bytes(int nx) { return rowpair_smem_bytes(nx) + 16 * (size_t)(nx / 2); }
 
 }  // namespace kzk
