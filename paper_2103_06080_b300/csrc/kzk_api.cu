@@ -421,6 +421,11 @@ kzk_status configure(kzk_plan* p)
         return fail(KZK_ERR_SIZE, "grid %d x %d needs more shared memory than the device offers", p->nx, p->ny);
     const size_t sm = (size_t)optin;
     KZK_TRY((set_row_attr<T, ROW_RHS>(sm)));
+    if (sizeof(T) == 8) {
+        const void* ct[] = {(const void*)row_kernel<T, ROW_RHS, 9>, (const void*)row_kernel<T, ROW_RHS, 10>,
+                            (const void*)row_kernel<T, ROW_RHS, 11>, (const void*)row_kernel<T, ROW_RHS, 12>};
+        for (const void* f : ct) KZK_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    }
     KZK_TRY((set_row_attr<T, ROW_FWD>(sm)));
     KZK_TRY((set_row_attr<T, ROW_INV>(sm)));
     KZK_TRY((set_row_attr<T, ROW_RHS_MED>(sm)));
@@ -605,6 +610,22 @@ kzk_status launch_row(const kzk_plan* p, const RowArgs<T>& a, cudaStream_t st, c
         mix_row_kernel<T, MODE><<<dim3(p->ny, p->batch), p->mrow_thr, p->mrow_smem, st>>>(m);
         KZK_LAUNCHED();
         return KZK_OK;
+    }
+    if constexpr (MODE == ROW_RHS && std::is_same<T, double>::value) {
+        // the length-specialised FP64 b passes for nx = 1024 ... 8192
+        switch (p->log2nx - 1) {
+#define KZK_ROW_CT(L)                                                                                  \
+    case L:                                                                                            \
+        row_kernel<T, ROW_RHS, L><<<dim3(p->ny, p->batch), p->row_thr, p->row_smem, st>>>(a);          \
+        KZK_LAUNCHED();                                                                                \
+        return KZK_OK;
+            KZK_ROW_CT(9)
+            KZK_ROW_CT(10)
+            KZK_ROW_CT(11)
+            KZK_ROW_CT(12)
+#undef KZK_ROW_CT
+        default: break;
+        }
     }
     row_kernel<T, MODE><<<dim3(p->ny, p->batch), p->row_thr, p->row_smem, st>>>(a);
     KZK_LAUNCHED();

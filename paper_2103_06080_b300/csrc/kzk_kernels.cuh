@@ -241,11 +241,16 @@ constexpr int ROW_MAX_THREADS = 512; // n / 8 for nx = 8192
 // State arrays are read with L2-coherent loads (__ldcg) so that the body is
 // also correct inside one persistent launch, where they are rewritten by
 // other CTAs between passes.
-template <typename T, int MODE>
+// LOG2N > 0 (ROW_RHS only): the body for rows of nx = 2^(LOG2N + 1) points run
+// by 2^LOG2N / 8 threads (LOG2N >= 8): lengths, thread count, transform
+// schedule and WENO chunks are compile-time constants.
+template <typename T, int MODE, int LOG2N = 0>
 __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst, unsigned char* smem_raw)
 {
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int nx = 1 << a.log2nx, n = nx >> 1, log2n = a.log2nx - 1;
+    static_assert(LOG2N == 0 || (MODE == ROW_RHS && LOG2N >= 8), "length-specialised b passes only");
+    constexpr bool CT = LOG2N > 0;
+    const int tid = threadIdx.x, nthr = CT ? (1 << LOG2N) / 8 : blockDim.x;
+    const int nx = CT ? 2 << LOG2N : 1 << a.log2nx, n = nx >> 1, log2n = CT ? LOG2N : a.log2nx - 1;
     cx<T>* X = reinterpret_cast<cx<T>*>(smem_raw);       // buffer U
     cx<T>* Y = X + row_buf_len(n);                         // buffer B
     double* red = reinterpret_cast<double*>(Y + row_buf_len(n));
@@ -283,7 +288,10 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
             __syncthreads();
             c2r_pre<T, true>(X, n, a.tw, tid, nthr);
             __syncthreads();
-            if constexpr (MODE == ROW_RHS) {
+            if constexpr (CT) {
+                U = fft_batched_pp_ct<T, ROW_PPT, false, true, true, false, LOG2N>(X, Y, tw, tid, nthr);
+                Bf = U == X ? Y : X;
+            } else if constexpr (MODE == ROW_RHS) {
                 U = fft_batched_pp<T, ROW_PPT, false, true, true>(X, Y, log2n, 0, 1, 0, tw, tid, nthr);
                 Bf = U == X ? Y : X;
             } else {
@@ -320,9 +328,9 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
                     wc.c = (T)cj;
                     weno_row_chunk<T, true, true>(U, Bf, nx, k0, Q, wc);
                 } else {
-                    weno_row_chunk<T, true>(U, Bf, nx, k0, Q, wc);
+                    weno_row_chunk<T, true, false, true, CT>(U, Bf, nx, k0, Q, wc);
                 }
-                if (a.diag_rows) row_stats<T, true>(U, k0, Q, s1, s2, mx, nf);
+                if (a.diag_rows) row_stats<T, true, CT>(U, k0, Q, s1, s2, mx, nf);
             }
             // the row statistics reduced across the barrier that ends the sweep
             if (a.diag_rows) diag_partial<T>(red, s1, s2, mx, nf);
@@ -334,7 +342,9 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
                 for (int k = tid; k < nx; k += nthr) st_real<T, true>(Bf, k, ld_real<T, true>(Bf, k) + __ldcg(byrow + k));
                 __syncthreads();
             }
-            const cx<T>* Z = fft_batched_pp<T, ROW_PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
+            const cx<T>* Z;
+            if constexpr (CT) Z = fft_batched_pp_ct<T, ROW_PPT, false, false, true, false, LOG2N>(Bf, U, tw, tid, nthr);
+            else Z = fft_batched_pp<T, ROW_PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
             const cx<T>* vin = a.in + base;
             const T cA = stage_cA(a);
             for (int k = tid; k <= n / 2; k += nthr) {
@@ -365,11 +375,11 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
     }
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int LOG2N = 0>
 __global__ void __launch_bounds__(ROW_MAX_THREADS, sizeof(T) == 4 ? 2 : 1) row_kernel(RowArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    row_body<T, MODE>(a, blockIdx.x, blockIdx.y, smem_raw);
+    row_body<T, MODE, LOG2N>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // Threads and dynamic shared memory of one row CTA.

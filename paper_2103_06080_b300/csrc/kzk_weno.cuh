@@ -152,21 +152,28 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
         // F = N / D with N = np dm + nm dp, D = dp dm; two interfaces share one
         // division: 1 / (D1 D2) gives both quotients
         T Fprev = fma(np, dm, nm * dp) / (dp * dm);
-#pragma unroll 1
-        for (k = k0; k + 1 < k0 + Q; k += 2) {
-            parts(k, np, dp, nm, dm);
+        auto two = [&](int kk) {
+            parts(kk, np, dp, nm, dm);
             const T N1 = fma(np, dm, nm * dp), D1 = dp * dm;
-            parts(k + 1, np, dp, nm, dm);
+            parts(kk + 1, np, dp, nm, dm);
             const T N2 = fma(np, dm, nm * dp), D2 = dp * dm;
             const T inv = T(1) / (D1 * D2);
             const T F1 = N1 * D2 * inv, F2 = N2 * D1 * inv;
-            store(k, F1 - Fprev);
-            store(k + 1, F2 - F1);
+            store(kk, F1 - Fprev);
+            store(kk + 1, F2 - F1);
             Fprev = F2;
-        }
-        if (k < k0 + Q) {
-            parts(k, np, dp, nm, dm);
-            store(k, fma(np, dm, nm * dp) / (dp * dm) - Fprev);
+        };
+        if constexpr (QC > 0) {
+            static_assert(QC % 2 == 0, "pairs of interfaces");
+#pragma unroll
+            for (int j = 0; j < QC; j += 2) two(k0 + j);
+        } else {
+#pragma unroll 1
+            for (k = k0; k + 1 < k0 + Q; k += 2) two(k);
+            if (k < k0 + Q) {
+                parts(k, np, dp, nm, dm);
+                store(k, fma(np, dm, nm * dp) / (dp * dm) - Fprev);
+            }
         }
     } else {
         // FP32: two hardware reciprocals (the product of the two denominators
@@ -236,13 +243,20 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
     weno_sweep<T, Q16 ? 16 : 0>(k0, Q, T(64) * c.eps, load, store);
 }
 
-// sum u, sum u^2, max|u| and non-finite count of the points [k0, k0 + Q).
-template <typename T, bool PAD>
+// sum u, sum u^2, max|u| and non-finite count of the points [k0, k0 + Q)
+// (Q16: Q == 16, k0 a multiple of 16, constant offsets as in weno_row_chunk).
+template <typename T, bool PAD, bool Q16 = false>
 __device__ __forceinline__ void row_stats(const cx<T>* u, int k0, int Q, T& s1, T& s2, T& mx, int& nf)
 {
-    for (int k = k0; k < k0 + Q; k++) {
-        const T v = ld_real<T, PAD>(u, k);
+    auto acc = [&](T v) {
         if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf += 1; }
+    };
+    if constexpr (Q16) {
+        const T* pr = reinterpret_cast<const T*>(u) + 2 * padx(k0 >> 1);
+#pragma unroll
+        for (int j = 0; j < 16; j++) acc(pr[j]);
+    } else {
+        for (int k = k0; k < k0 + Q; k++) acc(ld_real<T, PAD>(u, k));
     }
 }
 
