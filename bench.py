@@ -50,7 +50,8 @@ def _peaks():
 _ROW_SRC = ("kzk_common.cuh", "kzk_fft.cuh", "kzk_weno.cuh", "kzk_kernels.cuh")
 KERNEL_SOURCES = {
     ("row_stage1", "fp64"): _ROW_SRC, ("row_stage2", "fp64"): _ROW_SRC,
-    ("row_stage1", "fp32"): _ROW_SRC + ("kzk_rowpair.cuh",), ("row_stage2", "fp32"): _ROW_SRC + ("kzk_rowpair.cuh",),
+    ("row_stage1", "fp32"): _ROW_SRC + ("kzk_colpipe.cuh", "kzk_rowpair.cuh"),
+    ("row_stage2", "fp32"): _ROW_SRC + ("kzk_colpipe.cuh", "kzk_rowpair.cuh"),
     ("col_stage1", "fp64"): _ROW_SRC, ("col_stage2", "fp64"): _ROW_SRC,
     ("col_stage1", "fp32"): _ROW_SRC + ("kzk_colpipe.cuh", "kzk_rowpair.cuh", "kzk_colpair.cuh"),
     ("col_stage2", "fp32"): _ROW_SRC + ("kzk_colpipe.cuh", "kzk_rowpair.cuh", "kzk_colpair.cuh"),
