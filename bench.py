@@ -130,13 +130,17 @@ def row_flops(nx, ny, profile=True):
     return per_pt * nx * ny
 
 
-def col_flops(nx, ny, stage):
+def col_flops(nx, ny, stage, ysig=False):
     """Column pass FLOPs: complex FFTs of length ny (5 ny log2 ny each) on
     nx/2 columns -- three in stage 1 (two forward, one inverse) plus two
     complex multiply-adds per element; two in stage 2 plus one complex multiply
-    and two complex adds per element."""
+    and two complex adds per element.  ysig (FP64 plans carrying the state's
+    y-spectrum): two transforms in each stage; stage 1 forms three complex
+    products and two sums per element, stage 2 one product and one sum."""
     lg = np.log2(ny)
     ncol = nx // 2
+    if ysig:
+        return ncol * (2 * 5 * ny * lg + ny * (22 if stage == 1 else 8))
     if stage == 1:
         return ncol * (3 * 5 * ny * lg + ny * 14)
     return ncol * (2 * 5 * ny * lg + ny * 10)
@@ -308,8 +312,9 @@ def run_ours(args, rank, world, local_rank):
     # per-kernel device times (CUDA events on the launch stream)
     kt = plan.kernel_times(u, min(args.steps, 20), sigma0=0.0)
     names = ["row_stage1", "col_stage1", "row_stage2", "col_stage2"]
-    fl = [row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 1), row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 2)]
     info = plan.info()
+    ysig = not fp32 and info["col_kernel"] == "tile"     # FP64 per-tile columns: the y-spectral state
+    fl = [row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 1, ysig), row_flops(w.nx, w.ny), col_flops(w.nx, w.ny, 2, ysig)]
     comp = fp32 and info["fp32_state"] == "compensated"
     # row and column pairs both in use: the stage-2 row pass stores b2 - b1
     diff = info["row_kernel"] == "pair" and info["col_kernel"] == "pair"
