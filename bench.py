@@ -563,6 +563,23 @@ def secondary_reports(args, api, torch, dev, peaks, ms_fp64=None):
         "achieved": fl3[dom] / (kt3[dom] * 1e-3) / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
         "frac": fl3[dom] / (kt3[dom] * 1e-3) / fp32_peak,
         "peak_source": "measured FP32 FMA throughput (kzk_alu_peak: max of FFMA and FFMA2 chains) on this GPU"}
+    if info3["col_kernel"] == "pair":
+        # the column passes' tiles (16-byte rows of a column pair, 2048 rows at a
+        # 16 KB pitch) go through the tensor memory accelerator; its copy rate
+        # for that pattern, measured alone, bounds them before HBM does
+        unit = 4096 * 2048 * 4                              # one spectral array
+        tab = (2048 // 2 + 8) * 16 * (4096 // 4)            # one pair table (pair_tab_rows x 16 B per pair)
+        tma1 = 3 * unit + 2 * tab + unit                    # C1: b1, V, V again, two tables in; V* out
+        tma2 = (2 if diff3 else 3) * unit + tab             # C2: b2 - b1 (or b1, b2), V*, P2' in
+        strip = api.tile_copy_rate(2048, 2048, "strip")
+        contig = api.tile_copy_rate(2048, 2048, "contiguous")
+        out["fp32"]["roofline"]["tile_copy_ceiling"] = {
+            "strip_gbs": strip / 1e9, "contiguous_gbs": contig / 1e9,
+            "col_stage1_tma_gbs": tma1 / (kt3[1] * 1e-3) / 1e9, "col_stage2_tma_gbs": tma2 / (kt3[3] * 1e-3) / 1e9,
+            "note": "kzk_tile_copy_rate: copy-only kernel, one CTA per column pair, as many CTAs per SM as the "
+                    "stage-1 column pass; strip = the column passes' tile boxes, contiguous = the same bytes per "
+                    "CTA as one run; col_stage*_tma = bytes the column passes move through the tensor memory "
+                    "accelerator per launch / kernel time"}
     p3.close()
     del u3
     # FP32 error of the precision workload (1024 x 512, 2000 steps, and the full
@@ -702,7 +719,7 @@ def main():
     ap.add_argument("--adj-steps", type=int, default=1000)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-count", type=int, default=64)
-    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--paper-set", type=int, choices=[1, 2, 3, 4], default=None,
                     help="instead of the headline: the random-medium step on Set S of the paper's Table 1 "
                          "(mixed-radix grid), --steps timed steps at --precision; prints that report")

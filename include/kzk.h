@@ -389,6 +389,26 @@ kzk_status kzk_kernel_times(kzk_plan *plan, void *u, int64_t n_steps, double sig
  * Synchronises the stream. */
 kzk_status kzk_alu_peak(int32_t prec, void *stream, double *flops_per_s);
 
+/* Patterns of kzk_tile_copy_rate. */
+#define KZK_COPY_STRIP 0       /* column strips: 16-byte rows, ny rows at a pitch of 8 n bytes */
+#define KZK_COPY_CONTIGUOUS 1  /* the same bytes per CTA as one contiguous run */
+
+/* Measurement helper (no counterpart in the paper): the rate, in bytes per
+ * second, at which this device's tensor memory accelerator copies the tiles
+ * of the FP32 column passes from HBM into shared memory, with no arithmetic.
+ * Two arrays of [ny][n] complex FP32 values (n complex columns, n even; ny a
+ * power of two in [256, 4096]; n * ny <= 2^28), allocated here and released
+ * before returning; one CTA per column pair copies that pair's tile of both
+ * arrays -- KZK_COPY_STRIP: in the boxes the column-pair kernels use (ny rows
+ * of 16 bytes at a pitch of 8 n bytes), KZK_COPY_CONTIGUOUS: the same number
+ * of bytes as contiguous runs -- with as many CTAs per SM as the stage-1
+ * column pass, then leaves.  The L2 cache is overwritten before every timed
+ * launch; the result is the best of 7 launches (bytes of both arrays / event
+ * time).  Errors: KZK_ERR_ARG (null output, bad pattern), KZK_ERR_SIZE (n or ny
+ * out of range), KZK_ERR_OOM / KZK_ERR_CUDA, KZK_ERR_TIMEOUT (a bounded wait of
+ * the copy kernel ran out).  Synchronises the stream. */
+kzk_status kzk_tile_copy_rate(int32_t n, int32_t ny, int32_t pattern, void *stream, double *bytes_per_s);
+
 /* Largest batch * nx * ny accepted by kzk_rhs_noalloc. */
 #define KZK_NOALLOC_MAX_POINTS (1 << 18)
 

@@ -99,6 +99,8 @@ _SIGS = [
     ("kzk_kernel_times", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_double, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     ("kzk_alu_peak", ctypes.c_int, [ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_double)]),
+    ("kzk_tile_copy_rate", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP,
+                                          ctypes.POINTER(ctypes.c_double)]),
     ("kzk_advance_checkpointed", ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, _VP]),
     ("kzk_adjoint_checkpointed", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("kzk_plan_create_batched", ctypes.c_int, [ctypes.POINTER(KzkGrid), ctypes.POINTER(KzkCoeffs),
@@ -123,6 +125,8 @@ NOALLOC_MAX_POINTS = 1 << 18
 KZK_BATCH_AUTOTUNE = 1
 KZK_BATCH_STREAMS = 2
 KZK_BATCH_PERSISTENT = 4
+KZK_COPY_STRIP = 0
+KZK_COPY_CONTIGUOUS = 1
 KZK_EXPRK22 = 0
 KZK_EXPEULER = 1
 

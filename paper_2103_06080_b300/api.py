@@ -329,6 +329,17 @@ def launch_count() -> int:
     return int(L.lib().kzk_launch_count())
 
 
+def tile_copy_rate(n: int, ny: int, pattern: str = "strip", stream=None) -> float:
+    """Bytes per second the tensor memory accelerator copies the FP32
+    column-pass tiles at (n complex columns, ny rows): pattern "strip" (the
+    column pairs' 16-byte rows) or "contiguous" (the same bytes per CTA as one
+    run); no arithmetic."""
+    pat = {"strip": L.KZK_COPY_STRIP, "contiguous": L.KZK_COPY_CONTIGUOUS}[pattern]
+    out = ctypes.c_double()
+    L.check(L.lib().kzk_tile_copy_rate(int(n), int(ny), pat, _stream_ptr(stream), ctypes.byref(out)))
+    return float(out.value)
+
+
 def alu_peak(precision: str = "fp64", stream=None) -> float:
     """Measured FMA throughput (FLOP/s) of the current device."""
     out = ctypes.c_double()

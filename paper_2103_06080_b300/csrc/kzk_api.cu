@@ -20,6 +20,7 @@
 // after the FP64 headers: the pair type's overloads (kzk_rowpair.cuh) would hide
 // the scalar math functions they call inside namespace kzk
 #include "kzk_colpair.cuh"
+#include "kzk_copyrate.cuh"
 
 using namespace kzk;
 
@@ -2120,6 +2121,91 @@ kzk_status kernel_times_impl(kzk_plan* p, void* u, long long n_steps, double sig
     return KZK_OK;
 }
 
+// Copy-rate ceiling of the FP32 column-pair tiles (bytes per second): the
+// fastest of 7 timed launches of tile_copy_kernel after one untimed one, the
+// L2 cache overwritten before each.  Owns its buffers (freed on every path).
+struct CopyRateScratch {
+    unsigned char* a = nullptr;
+    unsigned char* b = nullptr;
+    unsigned char* flush = nullptr;
+    int* flag = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~CopyRateScratch()
+    {
+        cudaFree(a);
+        cudaFree(b);
+        cudaFree(flush);
+        cudaFree(flag);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+size_t pair_stage1_smem(int log2ny)
+{
+    switch (log2ny) {
+    case 8: return pair_layout<8, COL_STAGE1>().total;
+    case 9: return pair_layout<9, COL_STAGE1>().total;
+    case 10: return pair_layout<10, COL_STAGE1>().total;
+    case 11: return pair_layout<11, COL_STAGE1>().total;
+    default: return pair_layout<12, COL_STAGE1>().total;
+    }
+}
+
+kzk_status tile_copy_rate_impl(int n, int ny, int contiguous, cudaStream_t st, double* out)
+{
+    CopyRateScratch m;
+    const size_t arr = (size_t)n * ny * 2 * sizeof(float);
+    const size_t flush_bytes = 256ull << 20;   // twice the L2 cache
+    KZK_CUDA(cudaMalloc(&m.a, arr));
+    KZK_CUDA(cudaMalloc(&m.b, arr));
+    KZK_CUDA(cudaMalloc(&m.flush, flush_bytes));
+    KZK_CUDA(cudaMalloc(&m.flag, sizeof(int)));
+    KZK_CUDA(cudaMemsetAsync(m.a, 0, arr, st));
+    KZK_CUDA(cudaMemsetAsync(m.b, 0, arr, st));
+    KZK_CUDA(cudaMemsetAsync(m.flag, 0, sizeof(int), st));
+    TileCopyArgs P;
+    memset(&P, 0, sizeof(P));
+    P.by = std::min(ny, 256);
+    P.nby = ny / P.by;
+    P.total = n / 2;
+    P.contiguous = contiguous;
+    P.tile_bytes = (unsigned)ny * 16u;
+    P.a = m.a;
+    P.b = m.b;
+    P.flag = m.flag;
+    P.timeout_ns = 2000000000LL;
+    const cuuint64_t dims[3] = {2ull * n, (cuuint64_t)ny, 1ull};
+    const cuuint64_t str[2] = {2ull * n * sizeof(float), 2ull * n * ny * sizeof(float)};
+    const cuuint32_t box[3] = {4u, (cuuint32_t)P.by, 1u};
+    KZK_TRY(encode_map<float>(&P.ma, 3, m.a, dims, str, box));
+    KZK_TRY(encode_map<float>(&P.mb, 3, m.b, dims, str, box));
+    int log2ny = 0;
+    while ((1 << log2ny) < ny) log2ny++;
+    const size_t smem = std::max<size_t>(pair_stage1_smem(log2ny), 128 + 2 * (size_t)P.tile_bytes);
+    KZK_CUDA(cudaFuncSetAttribute(tile_copy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KZK_CUDA(cudaEventCreate(&m.e0));
+    KZK_CUDA(cudaEventCreate(&m.e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 8; rep++) {
+        KZK_CUDA(cudaMemsetAsync(m.flush, rep, flush_bytes, st));
+        KZK_CUDA(cudaEventRecord(m.e0, st));
+        tile_copy_kernel<<<P.total, 256, smem, st>>>(P);
+        KZK_LAUNCHED();
+        KZK_CUDA(cudaEventRecord(m.e1, st));
+        KZK_CUDA(cudaEventSynchronize(m.e1));
+        float ms = 0;
+        KZK_CUDA(cudaEventElapsedTime(&ms, m.e0, m.e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    int flag = 0;
+    KZK_CUDA(cudaMemcpy(&flag, m.flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & FLAG_TIMEOUT) return fail(KZK_ERR_TIMEOUT, "tile copy: a bounded wait ran out");
+    if (flag) return fail(KZK_ERR_CUDA, "tile copy: bad launch (flag %d)", flag);
+    *out = 2.0 * (double)arr / (best * 1e-3);
+    return KZK_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -2143,6 +2229,15 @@ kzk_status kzk_alu_peak(int32_t prec, void* stream, double* flops)
     return prec == KZK_FP64 ? alu_peak_impl<double>(st, flops) : alu_peak_impl<float>(st, flops);
 }
 
+
+kzk_status kzk_tile_copy_rate(int32_t n, int32_t ny, int32_t pattern, void* stream, double* bytes_per_s)
+{
+    if (!bytes_per_s) return fail(KZK_ERR_ARG, "bytes_per_s is NULL");
+    if (pattern != KZK_COPY_STRIP && pattern != KZK_COPY_CONTIGUOUS) return fail(KZK_ERR_ARG, "bad pattern %d", pattern);
+    if (n < 2 || (n & 1) || ny < 256 || ny > 4096 || !is_pow2(ny) || (long long)n * ny > (1ll << 28))
+        return fail(KZK_ERR_SIZE, "tile copy: n = %d, ny = %d (n even, ny a power of two in [256, 4096])", n, ny);
+    return tile_copy_rate_impl(n, ny, pattern == KZK_COPY_CONTIGUOUS, (cudaStream_t)stream, bytes_per_s);
+}
 
 const char* kzk_status_string(kzk_status s)
 {

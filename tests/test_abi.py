@@ -140,3 +140,13 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_tile_copy_rate_rejects_bad_arguments():
+    # refused before any device work
+    lib = L.lib()
+    out = ctypes.c_double()
+    assert lib.kzk_tile_copy_rate(2048, 2048, L.KZK_COPY_STRIP, None, None) == L.KZK_ERR_ARG
+    assert lib.kzk_tile_copy_rate(2048, 2048, 2, None, ctypes.byref(out)) == L.KZK_ERR_ARG
+    for n, ny in ((2047, 2048), (0, 2048), (2048, 128), (2048, 8192), (2048, 3000), (1 << 18, 2048)):
+        assert lib.kzk_tile_copy_rate(n, ny, L.KZK_COPY_STRIP, None, ctypes.byref(out)) == L.KZK_ERR_SIZE

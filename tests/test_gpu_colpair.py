@@ -141,3 +141,12 @@ def test_colpair_with_single_row_passes():
     ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, 15, threads=True)
     assert rel_l2(b, ref) < 1e-5
     assert rel_l2(a, b) < 1e-6
+
+
+@pytest.mark.parametrize("pattern", ["strip", "contiguous"])
+def test_tile_copy_rate_is_a_plausible_bandwidth(pattern):
+    # the ceiling the column passes' tile copies are compared with: a finite
+    # rate between 0.1 and 20 TB/s for the 4096 x 2048 FP32 tiles
+    from paper_2103_06080_b300 import api
+    r = api.tile_copy_rate(2048, 2048, pattern)
+    assert np.isfinite(r) and 1e11 < r < 2e13
