@@ -82,9 +82,23 @@ template <typename T, int R, int S, bool ACC> struct RegDFT {
     static __device__ __forceinline__ void combine(cx<T>* v, const cx<T>* e, const cx<T>* o)
     {
         if constexpr (K < R / 2) {
-            cx<T> t = rot<T, R, K, S, ACC>(o[K]);
-            v[K] = add<T>(e[K], t);
-            v[K + R / 2] = sub<T>(e[K], t);
+            constexpr int j = (K * (16 / R)) & 15;   // the root's angle 2 pi j / 16
+            if constexpr (!ACC && (j & 3) == 2) {
+                // |cos| = |sin| = h: o_K times the root is h (A + i B) with A, B
+                // sums of +-o_K's parts, and e_K +- h (A + i B) are fused
+                // multiply-adds (six operations instead of eight)
+                constexpr bool cp = cos16(j) > 0, sp = S * sin16(j) > 0;
+                constexpr T h = (T)cos16(2), mh = (T)(-cos16(2));
+                const cx<T> x = o[K];
+                const T A = (cp ? x.x : -x.x) - (sp ? x.y : -x.y);
+                const T B = (sp ? x.x : -x.x) + (cp ? x.y : -x.y);
+                v[K] = mk<T>(fma(h, A, e[K].x), fma(h, B, e[K].y));
+                v[K + R / 2] = mk<T>(fma(mh, A, e[K].x), fma(mh, B, e[K].y));
+            } else {
+                cx<T> t = rot<T, R, K, S, ACC>(o[K]);
+                v[K] = add<T>(e[K], t);
+                v[K + R / 2] = sub<T>(e[K], t);
+            }
             combine<K + 1>(v, e, o);
         }
     }

@@ -160,9 +160,9 @@ __global__ void __launch_bounds__(YSWEEP_THREADS) ysweep_kernel(YSweepArgs<T> a)
     // plus the source (d_y U_perp) u
     auto store = [&](int jj, T d) {
         const int r = jj - (j0 - 4);
-        by[(long long)jj * nx] = fma(d, scale, dp[r] * tile[r * YSWEEP_THREADS + tid]);
+        by[(long long)jj * nx] = fma(dp[r], tile[r * YSWEEP_THREADS + tid], d);
     };
-    weno_sweep<T>(j0, Q, eps4, load, store);
+    weno_sweep<T>(j0, Q, eps4, scale, load, store);
 }
 
 // ---------------------------------------------------------------------------

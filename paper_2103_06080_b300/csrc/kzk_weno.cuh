@@ -86,23 +86,23 @@ __device__ __forceinline__ void rec_parts(T vm2, T vm1, T v0, T v1, T v2, T t0, 
     const T q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0));
     const T q1 = fma(T(5), v0, fma(T(2), v1, -vm1));
     const T q2 = fma(T(2), v0, fma(T(5), v1, -v2));
-    // linear weights 1/10, 6/10, 3/10 scaled by 10 (the factor cancels)
-    const T a0 = t1 * t2;
-    const T a1 = T(6) * (t0 * t2);
-    const T a2 = T(3) * (t0 * t1);
-    den = a0 + a1 + a2;
-    num6 = fma(a0, q0, fma(a1, q1, a2 * q2));
+    // linear weights 1/10, 6/10, 3/10 scaled by 10 (the factor cancels):
+    // a0 = t1 t2, a1 = 6 t0 t2, a2 = 3 t0 t1, with t0 factored out of a1, a2
+    const T p12 = t1 * t2, h1 = T(3) * t1, h2 = T(6) * t2;
+    den = fma(t0, h2 + h1, p12);
+    num6 = fma(p12, q0, t0 * fma(h2, q1, h1 * q2));
 }
 
 // Sliding WENO5 sweep over the interfaces k0 - 1/2 .. k0 + Q - 1/2 of a
 // periodic line.  load(kk, p, m) gives the split fluxes (scaled: 4 f+ and
-// 4 f-) at point kk; store(k, d) receives d = 24 (F_{k+1/2} - F_{k-1/2}) for
-// k in [k0, k0 + Q) in order.  eps4: the Jiang-Shu epsilon for that scaling
+// 4 f-) at point kk; store(k, d) receives d = 24 scale (F_{k+1/2} -
+// F_{k-1/2}) for k in [k0, k0 + Q) in order (FP64: the factor scale rides on
+// the shared division).  eps4: the Jiang-Shu epsilon for that scaling
 // (64 eps).  Every smoothness indicator is computed once per stencil centre
 // and every interface once.
 // QC > 0: Q == QC known at compile time (the interface loop fully unrolled).
 template <typename T, int QC = 0, typename Load, typename Store>
-__device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Store store)
+__device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, T scale, Load load, Store store)
 {
     T fp[6], fm[6];
     // window slot s <-> point k - 2 + s for interface k + 1/2; start at
@@ -150,14 +150,14 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
     parts(k, np, dp, nm, dm);
     if constexpr (std::is_same<T, double>::value) {
         // F = N / D with N = np dm + nm dp, D = dp dm; two interfaces share one
-        // division: 1 / (D1 D2) gives both quotients
-        T Fprev = fma(np, dm, nm * dp) / (dp * dm);
+        // division: scale / (D1 D2) gives both (scaled) quotients
+        T Fprev = fma(np, dm, nm * dp) * scale / (dp * dm);
         auto two = [&](int kk) {
             parts(kk, np, dp, nm, dm);
             const T N1 = fma(np, dm, nm * dp), D1 = dp * dm;
             parts(kk + 1, np, dp, nm, dm);
             const T N2 = fma(np, dm, nm * dp), D2 = dp * dm;
-            const T inv = T(1) / (D1 * D2);
+            const T inv = scale * (T(1) / (D1 * D2));
             const T F1 = N1 * D2 * inv, F2 = N2 * D1 * inv;
             store(kk, F1 - Fprev);
             store(kk + 1, F2 - F1);
@@ -172,7 +172,7 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
             for (k = k0; k + 1 < k0 + Q; k += 2) two(k);
             if (k < k0 + Q) {
                 parts(k, np, dp, nm, dm);
-                store(k, fma(np, dm, nm * dp) / (dp * dm) - Fprev);
+                store(k, fma(np, dm, nm * dp) * scale / (dp * dm) - Fprev);
             }
         }
     } else {
@@ -184,7 +184,7 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
             for (int j = 0; j < QC; j++) {
                 parts(k0 + j, np, dp, nm, dm);
                 const T F = fast_div(np, dp) + fast_div(nm, dm);
-                store(k0 + j, F - Fprev);
+                store(k0 + j, (F - Fprev) * scale);
                 Fprev = F;
             }
         } else {
@@ -192,7 +192,7 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, Load load, Sto
             for (k = k0; k < k0 + Q; k++) {
                 parts(k, np, dp, nm, dm);
                 const T F = fast_div(np, dp) + fast_div(nm, dm);
-                store(k, F - Fprev);
+                store(k, (F - Fprev) * scale);
                 Fprev = F;
             }
         }
@@ -237,10 +237,10 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
         m = -v * fma(c.B, v, am);
     };
     auto store = [&](int k, T d) {
-        if constexpr (Q16) pw[k - k0] = d * scale;
-        else st_real<T, PAD>(out, k, d * scale);
+        if constexpr (Q16) pw[k - k0] = d;
+        else st_real<T, PAD>(out, k, d);
     };
-    weno_sweep<T, Q16 ? 16 : 0>(k0, Q, T(64) * c.eps, load, store);
+    weno_sweep<T, Q16 ? 16 : 0>(k0, Q, T(64) * c.eps, scale, load, store);
 }
 
 // sum u, sum u^2, max|u| and non-finite count of the points [k0, k0 + Q)
