@@ -168,14 +168,12 @@ __device__ __forceinline__ void c2r_pre(cx<T>* X, int n, const cx<T>* __restrict
         } else {
             const cx<T> a = X[sidx<PAD>(k)], b = X[sidx<PAD>(n - k)];
             const cx<T> w = tw[k];                      // W^k
-            cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
-            cx<T> r = mul_si<T, 1>(mulc<T>(d, w));      // i conj(W^k) d
-            const cx<T> zk = add<T>(s, r);
-            // n - k: W^{n-k} = -conj(W^k)  =>  conj(W^{n-k}) = -W^k
-            s = add<T>(b, conj<T>(a)); d = sub<T>(b, conj<T>(a));
-            r = mul_si<T, -1>(mul<T>(d, w));            // i (-W^k) d
-            X[sidx<PAD>(k)] = zk;
-            X[sidx<PAD>(n - k)] = add<T>(s, r);
+            const cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
+            const cx<T> r = mul_si<T, 1>(mulc<T>(d, w));    // i conj(W^k) d
+            // n - k: its s and d are conj(s) and -conj(d), and with
+            // conj(W^{n-k}) = -W^k its r is -conj(r): Z_{n-k} = conj(s - r)
+            X[sidx<PAD>(k)] = add<T>(s, r);
+            X[sidx<PAD>(n - k)] = conj<T>(sub<T>(s, r));
         }
     }
 }
@@ -197,14 +195,13 @@ __device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, cons
         Xnk = Xk;
     } else {
         const cx<T> a = Z[sidx<PAD>(k)], b = Z[sidx<PAD>(n - k)];
-        const cx<T> w = tw[k];
-        cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
-        cx<T> r = mul_si<T, -1>(mul<T>(w, d));            // -i W^k d
-        Xk = scale<T>(add<T>(s, r), h);
-        // n-k: W^{n-k} = -conj(W^k)  =>  -i W^{n-k} d' = i conj(W^k) d'
-        s = add<T>(b, conj<T>(a)); d = sub<T>(b, conj<T>(a));
-        r = mul_si<T, 1>(mulc<T>(d, w));
-        Xnk = scale<T>(add<T>(s, r), h);
+        const cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
+        // r = -i W^k d / 2 (the halving exact, on the twiddle): X_k = s/2 + r;
+        // n - k: its s and d are conj(s) and -conj(d), and with
+        // W^{n-k} = -conj(W^k) its r is -conj(r): X_{n-k} = conj(s/2 - r)
+        const cx<T> r = mul_si<T, -1>(mul<T>(scale<T>(tw[k], h), d));
+        Xk = mk<T>(fma(h, s.x, r.x), fma(h, s.y, r.y));
+        Xnk = mk<T>(fma(h, s.x, -r.x), fma(-h, s.y, r.y));
     }
 }
 

@@ -248,11 +248,10 @@ __device__ __forceinline__ void c2r_vals(cx<T> a, cx<T> b, cx<T> w, int k, int n
         zk = mk<T>(T(2) * a.x, T(-2) * a.y);
         znk = zk;
     } else {
-        cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
-        zk = add<T>(s, mul_si<T, 1>(mulc<T>(d, w)));
-        s = add<T>(b, conj<T>(a));
-        d = sub<T>(b, conj<T>(a));
-        znk = add<T>(s, mul_si<T, -1>(mul<T>(d, w)));
+        const cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
+        const cx<T> r = mul_si<T, 1>(mulc<T>(d, w));
+        zk = add<T>(s, r);
+        znk = conj<T>(sub<T>(s, r));              // n - k: conj(s - r), as in c2r_pre
     }
 }
 
@@ -268,11 +267,10 @@ __device__ __forceinline__ void r2c_vals(cx<T> a, cx<T> b, cx<T> w, int k, int n
         xk = conj<T>(a);
         xnk = xk;
     } else {
-        cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
-        xk = scale<T>(add<T>(s, mul_si<T, -1>(mul<T>(w, d))), h);
-        s = add<T>(b, conj<T>(a));
-        d = sub<T>(b, conj<T>(a));
-        xnk = scale<T>(add<T>(s, mul_si<T, 1>(mulc<T>(d, w))), h);
+        const cx<T> s = add<T>(a, conj<T>(b)), d = sub<T>(a, conj<T>(b));
+        const cx<T> r = mul_si<T, -1>(mul<T>(scale<T>(w, h), d));   // as in r2c_post_pair
+        xk = mk<T>(fma(h, s.x, r.x), fma(h, s.y, r.y));
+        xnk = mk<T>(fma(h, s.x, -r.x), fma(-h, s.y, r.y));
     }
 }
 

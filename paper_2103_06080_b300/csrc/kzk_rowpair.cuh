@@ -163,14 +163,11 @@ __device__ __forceinline__ void c2r_pre_pair(const float2* Vb, c2* X, int n, con
         } else {
             const c2 a = pack2(Vb[k], Vb[n + k]), b = pack2(Vb[n - k], Vb[2 * n - k]);
             const c2 w = tw[k];
-            c2 s = add<f2>(a, conj<f2>(b)), d = sub<f2>(a, conj<f2>(b));
-            c2 r = mul_si<f2, 1>(mulc<f2>(d, w));
-            const c2 zk = add<f2>(s, r);
-            s = add<f2>(b, conj<f2>(a));
-            d = sub<f2>(b, conj<f2>(a));
-            r = mul_si<f2, -1>(mul<f2>(d, w));
-            X[padx(k)] = zk;
-            X[padx(n - k)] = add<f2>(s, r);
+            const c2 s = add<f2>(a, conj<f2>(b)), d = sub<f2>(a, conj<f2>(b));
+            const c2 r = mul_si<f2, 1>(mulc<f2>(d, w));
+            // n - k: conj(s - r) (as c2r_pre)
+            X[padx(k)] = add<f2>(s, r);
+            X[padx(n - k)] = conj<f2>(sub<f2>(s, r));
         }
     }
 }
