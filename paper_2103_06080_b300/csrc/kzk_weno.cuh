@@ -64,9 +64,9 @@ __device__ __forceinline__ void st_real(cx<T>* buf, int k, T v)
 // shared part 13/3 S^2 + 4 eps is formed once.  eps4 = 4 eps (for a flux
 // scaled by s, pass 4 s^2 eps: the weights are unchanged).
 template <typename T>
-__device__ __forceinline__ void indicators(T fm1, T f0, T fp1, T eps4, T& tl, T& tc, T& tr)
+__device__ __forceinline__ void indicators(T fm1, T f0, T fp1, T eps4, T& tl, T& tc, T& tr, T& S)
 {
-    const T S = fm1 - T(2) * f0 + fp1;
+    S = fm1 - T(2) * f0 + fp1;
     const T D = fp1 - fm1;
     const T Pe = fma((T(13) / T(3)) * S, S, eps4);
     const T xl = fma(T(2), S, D), xr = fma(T(-2), S, D);
@@ -78,14 +78,12 @@ __device__ __forceinline__ void indicators(T fm1, T f0, T fp1, T eps4, T& tl, T&
     tr = br * br;
 }
 
-// 6 * numerator and denominator of one reconstruction from v_{-2..2} and the
-// squared shifted indicators t0 (stencil -2..0), t1 (-1..1), t2 (0..2).
+// 6 * numerator and denominator of one reconstruction from its three
+// candidate values (times 6) q0 (stencil -2..0), q1 (-1..1), q2 (0..2) and
+// the squared shifted indicators t0, t1, t2 of the same stencils.
 template <typename T>
-__device__ __forceinline__ void rec_parts(T vm2, T vm1, T v0, T v1, T v2, T t0, T t1, T t2, T& num6, T& den)
+__device__ __forceinline__ void rec_parts(T q0, T q1, T q2, T t0, T t1, T t2, T& num6, T& den)
 {
-    const T q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0));
-    const T q1 = fma(T(5), v0, fma(T(2), v1, -vm1));
-    const T q2 = fma(T(2), v0, fma(T(5), v1, -v2));
     // linear weights 1/10, 6/10, 3/10 scaled by 10 (the factor cancels):
     // a0 = t1 t2, a1 = 6 t0 t2, a2 = 3 t0 t1, with t0 factored out of a1, a2
     const T p12 = t1 * t2, h1 = T(3) * t1, h2 = T(6) * t2;
@@ -111,21 +109,28 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, T scale, Load 
 #pragma unroll
     for (int s = 0; s < 5; s++) load(k - 3 + s, fp[s + 1], fm[s + 1]);   // points k0-4 .. k0
     T tLp3, tLp2, tLp1, tCp2, tCp1, tRp1, tLm2, tLm1, tCm1, tx;
+    // second differences S_c = f_{c-1} - 2 f_c + f_{c+1} of the centres and
+    // their differences dS_c = S_c - S_{c-1} give two of each side's three
+    // candidate values from the third (below)
+    T Sp0, Sp1, Sp2, Sm0, Sm1, Sm2;
     // centre k0 - 2 (points k0-3, k0-2, k0-1 = slots 2, 3, 4)
-    indicators<T>(fp[2], fp[3], fp[4], eps4, tLp2, tx, tx);
-    indicators<T>(fm[2], fm[3], fm[4], eps4, tx, tx, tx);
+    indicators<T>(fp[2], fp[3], fp[4], eps4, tLp2, tx, tx, Sp0);
+    indicators<T>(fm[2], fm[3], fm[4], eps4, tx, tx, tx, Sm0);
     // centre k0 - 1 (slots 3, 4, 5)
-    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tx);
-    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tx, tx);
+    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tx, Sp1);
+    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tx, tx, Sm1);
     // age the history by one centre before computing centre k0
     tLp3 = tLp2; tLp2 = tLp1; tCp2 = tCp1;
     tLm2 = tLm1;
 #pragma unroll
     for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
-    load(k0 + 1, fp[5], fm[5]);                                           // slots: points k0-3 .. k0+1
+    load(k0 + 1, fp[5], fm[5]);                                           // slots: points k0-4 .. k0+1
     // centre k0 (slots 3, 4, 5)
-    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tRp1);
-    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tCm1, tx);
+    indicators<T>(fp[3], fp[4], fp[5], eps4, tLp1, tCp1, tRp1, Sp2);
+    indicators<T>(fm[3], fm[4], fm[5], eps4, tLm1, tCm1, tx, Sm2);
+    // at the top of interface k: SpL = S_{k+1}, dpA = dS_k, dpB = dS_{k+1}
+    // (+ side), SmL, dmB likewise (- side)
+    T SpL = Sp2, dpA = Sp1 - Sp0, dpB = Sp2 - Sp1, SmL = Sm2, dmB = Sm2 - Sm1;
     // invariant at the top of interface k: tX1 = centre k+1, tX2 = centre k,
     // tLp3 = centre k-1; each interface adds centre k+2.  parts(): slide the
     // window by one point and return 6 x the numerator and the denominator of
@@ -134,12 +139,21 @@ __device__ __forceinline__ void weno_sweep(int k0, int Q, T eps4, T scale, Load 
 #pragma unroll
         for (int s = 0; s < 5; s++) { fp[s] = fp[s + 1]; fm[s] = fm[s + 1]; }
         load(kk + 3, fp[5], fm[5]);
-        T tLpN, tCpN, tRpN, tLmN, tCmN, tRmN;
-        indicators<T>(fp[3], fp[4], fp[5], eps4, tLpN, tCpN, tRpN);
-        indicators<T>(fm[3], fm[4], fm[5], eps4, tLmN, tCmN, tRmN);
+        T tLpN, tCpN, tRpN, tLmN, tCmN, tRmN, SpN, SmN;
+        indicators<T>(fp[3], fp[4], fp[5], eps4, tLpN, tCpN, tRpN, SpN);
+        indicators<T>(fm[3], fm[4], fm[5], eps4, tLmN, tCmN, tRmN, SmN);
+        const T dpN = SpN - SpL, dmN = SmN - SmL;
+        // candidate values x 6: the centred one directly, the other two from
+        // it, q0 - q1 and q2 - q1 being (multiples of) third differences:
+        //   + side (f_{k-2} .. f_{k+2}): q0 = q1 - 2 dS_k,     q2 = q1 - dS_{k+1};
+        //   - side (mirrored, g_{k+3} .. g_{k-1}): q0 = q1 + 2 dS_{k+2}, q2 = q1 + dS_{k+1}
+        const T q1p = fma(T(5), fp[2], fma(T(2), fp[3], -fp[1]));
+        const T q1m = fma(T(5), fm[3], fma(T(2), fm[2], -fm[4]));
         // + side: left(k-1), centre(k), right(k+1); - side: right(k+2), centre(k+1), left(k)
-        rec_parts<T>(fp[0], fp[1], fp[2], fp[3], fp[4], tLp3, tCp2, tRp1, np, dp);
-        rec_parts<T>(fm[5], fm[4], fm[3], fm[2], fm[1], tRmN, tCm1, tLm2, nm, dm);
+        rec_parts<T>(fma(T(-2), dpA, q1p), q1p, q1p - dpB, tLp3, tCp2, tRp1, np, dp);
+        rec_parts<T>(fma(T(2), dmN, q1m), q1m, q1m + dmB, tRmN, tCm1, tLm2, nm, dm);
+        SpL = SpN; dpA = dpB; dpB = dpN;
+        SmL = SmN; dmB = dmN;
         tLp3 = tLp2; tLp2 = tLp1; tLp1 = tLpN;
         tCp2 = tCp1; tCp1 = tCpN;
         tRp1 = tRpN;
