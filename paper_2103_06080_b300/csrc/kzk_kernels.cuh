@@ -344,24 +344,25 @@ __device__ __forceinline__ void row_body(const RowArgs<T>& a, int row, int inst,
             else Z = fft_batched_pp<T, ROW_PPT, false, false, true>(Bf, U, log2n, 0, 1, 0, tw, tid, nthr);
             const cx<T>* vin = a.in + base;
             const T cA = stage_cA(a);
+            // nx (A(sigma) - A) k_tau^2 = cA kscale^2 k^2, k^2 an exact integer
+            const T cAk = cA * a.kscale * a.kscale;
             for (int k = tid; k <= n / 2; k += nthr) {
                 cx<T> xk, xnk;
                 r2c_post_pair<T, true>(Z, n, k, a.tw, xk, xnk);
                 if (cA != T(0)) {
                     // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
                     if (k == 0) {
-                        const T kN = a.kscale * T(n);
-                        xk.y -= cA * kN * kN * __ldcg(vin).y;
+                        xk.y -= cAk * T((long long)n * n) * __ldcg(vin).y;
                     } else {
-                        const T kt = a.kscale * T(k);
+                        const T f = cAk * T((long long)k * k);
                         const cx<T> v = __ldcg(vin + k);
-                        xk.x -= cA * kt * kt * v.x;
-                        xk.y -= cA * kt * kt * v.y;
+                        xk.x = fma(-f, v.x, xk.x);
+                        xk.y = fma(-f, v.y, xk.y);
                         if (2 * k != n) {
-                            const T kt2 = a.kscale * T(n - k);
+                            const T g = cAk * T((long long)(n - k) * (n - k));
                             const cx<T> w = __ldcg(vin + n - k);
-                            xnk.x -= cA * kt2 * kt2 * w.x;
-                            xnk.y -= cA * kt2 * kt2 * w.y;
+                            xnk.x = fma(-g, w.x, xnk.x);
+                            xnk.y = fma(-g, w.y, xnk.y);
                         }
                     }
                 }

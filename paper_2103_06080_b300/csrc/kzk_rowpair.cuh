@@ -344,6 +344,8 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         }
         const float2* Xs = reinterpret_cast<const float2*>(U);
         const float cA = stage_cA(a);
+        // nx (A(sigma) - A) k_tau^2 = cA kscale^2 k^2, k^2 an exact integer (k <= 4096)
+        const float cAk = cA * a.kscale * a.kscale;
         // the V values of the absorption-deviation term, all loads issued
         // before the arithmetic.  The loop below takes k = tid + i nthr for
         // i < ITER: with nthr = max(32, n / 8) threads, k <= n/2 needs at most
@@ -375,15 +377,15 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             if (cA != 0.0f) {
                 // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx), each row
                 if (k == 0) {
-                    const float kN = a.kscale * (float)n, f = cA * kN * kN;
+                    const float f = cAk * (float)(n * n);
                     k0a.y -= f * vk0[i].y;
                     k0b.y -= f * vk1[i].y;
                 } else {
-                    const float kt = a.kscale * (float)k, f = cA * kt * kt;
+                    const float f = cAk * (float)(k * k);
                     k0a.x -= f * vk0[i].x; k0a.y -= f * vk0[i].y;
                     k0b.x -= f * vk1[i].x; k0b.y -= f * vk1[i].y;
                     if (2 * k != n) {
-                        const float kt2 = a.kscale * (float)(n - k), g = cA * kt2 * kt2;
+                        const float g = cAk * (float)((n - k) * (n - k));
                         kna.x -= g * vn0[i].x; kna.y -= g * vn0[i].y;
                         knb.x -= g * vn1[i].x; knb.y -= g * vn1[i].y;
                     }

@@ -262,8 +262,16 @@ __device__ __forceinline__ void weno_row_chunk(const cx<T>* u, cx<T>* out, int n
 template <typename T, bool PAD, bool Q16 = false>
 __device__ __forceinline__ void row_stats(const cx<T>* u, int k0, int Q, T& s1, T& s2, T& mx, int& nf)
 {
+    // FP64: the finiteness test and the running max |u| on the bit patterns
+    // (non-negative doubles order as their bits), off the FP64 pipe
+    unsigned long long mb = 0;
     auto acc = [&](T v) {
-        if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf += 1; }
+        if constexpr (std::is_same<T, double>::value) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+            if (b < 0x7ff0000000000000ULL) { s1 += v; s2 = fma(v, v, s2); mb = b > mb ? b : mb; } else { nf += 1; }
+        } else {
+            if (isfinite(v)) { s1 += v; s2 = fma(v, v, s2); mx = fmax(mx, fabs(v)); } else { nf += 1; }
+        }
     };
     if constexpr (Q16) {
         const T* pr = reinterpret_cast<const T*>(u) + 2 * padx(k0 >> 1);
@@ -272,6 +280,7 @@ __device__ __forceinline__ void row_stats(const cx<T>* u, int k0, int Q, T& s1, 
     } else {
         for (int k = k0; k < k0 + Q; k++) acc(ld_real<T, PAD>(u, k));
     }
+    if constexpr (std::is_same<T, double>::value) mx = fmax(mx, __longlong_as_double((long long)mb));
 }
 
 }  // namespace kzk
