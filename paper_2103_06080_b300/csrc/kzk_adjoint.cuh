@@ -81,13 +81,17 @@ __device__ __forceinline__ void weno5_grad(T vm2, T vm1, T v0, T v1, T v2, T eps
 
 // The sliding form of weno5_grad for the row sweep.  Every 3-point stencil
 // centre c contributes S = f_{c-1} - 2 f_c + f_{c+1}, D = f_{c+1} - f_{c-1}
-// and Pe = 13/3 S^2 + eps4 once; a reconstruction takes its three stencils'
-// (s_r, t_r, E_r = t_r^2 + Pe) from the centres it spans, the t_r being the
-// combinations D + 2S, -D, 2S - D of weno5_grad's (s, t) pairs (mirrored for
-// the downwind side).
+// and Pe = 13/3 S^2 + eps4 once (with kS = 13/3 S, which also carries the
+// s_r-terms of the gradient: -52/3 C s = -4 C kS); a reconstruction takes its
+// three stencils' (kS_r, t_r, E_r = t_r^2 + Pe) from the centres it spans,
+// the t_r being the combinations D + 2S, -D, 2S - D of weno5_grad's (s, t)
+// pairs (mirrored for the downwind side), and its outer candidates from the
+// centred one and differences of neighbouring S (third differences), as the
+// forward sweep does.
 template <typename T>
 struct GradCentre {
     T S, D, Pe;
+    __device__ __forceinline__ T kS() const { return (T(13) / T(3)) * S; }
 };
 template <typename T>
 __device__ __forceinline__ GradCentre<T> grad_centre(T fm1, T f0, T fp1, T eps4)
@@ -95,23 +99,21 @@ __device__ __forceinline__ GradCentre<T> grad_centre(T fm1, T f0, T fp1, T eps4)
     GradCentre<T> c;
     c.S = fma(T(-2), f0, fm1 + fp1);
     c.D = fp1 - fm1;
-    c.Pe = fma((T(13) / T(3)) * c.S, c.S, eps4);
+    c.Pe = fma(c.kS(), c.S, eps4);
     return c;
 }
 template <typename T>
 struct GradPart {
-    T Q0, Q1, Q2, s0, t0, s1, t1, s2, t2, E0, E1, E2, a0, a1, a2, Ssum, e01, e012;
+    T Q0, Q1, Q2, k0, t0, k1, t1, k2, t2, E0, E1, E2, a0, a1, a2, Ssum, e01, e012;
 };
-// candidates, weights and X = S E0 E1 E2 of one reconstruction from v_{-2..2}
-// and its stencils' (s, t, Pe)
+// weights and X = S E0 E1 E2 of one reconstruction from its candidates
+// (times 6) and its stencils' (kS, t, Pe)
 template <typename T>
-__device__ __forceinline__ void grad_prep(GradPart<T>& q, T vm2, T vm1, T v0, T v1, T v2, T s0, T t0, T Pe0, T s1,
-                                          T t1, T Pe1, T s2, T t2, T Pe2)
+__device__ __forceinline__ void grad_prep(GradPart<T>& q, T Q0, T Q1, T Q2, T k0, T t0, T Pe0, T k1, T t1, T Pe1,
+                                          T k2, T t2, T Pe2)
 {
-    q.Q0 = fma(T(2), vm2, fma(T(-7), vm1, T(11) * v0));
-    q.Q1 = fma(T(5), v0, fma(T(2), v1, -vm1));
-    q.Q2 = fma(T(2), v0, fma(T(5), v1, -v2));
-    q.s0 = s0; q.t0 = t0; q.s1 = s1; q.t1 = t1; q.s2 = s2; q.t2 = t2;
+    q.Q0 = Q0; q.Q1 = Q1; q.Q2 = Q2;
+    q.k0 = k0; q.t0 = t0; q.k1 = k1; q.t1 = t1; q.k2 = k2; q.t2 = t2;
     q.E0 = fma(t0, t0, Pe0);
     q.E1 = fma(t1, t1, Pe1);
     q.E2 = fma(t2, t2, Pe2);
@@ -123,30 +125,34 @@ __device__ __forceinline__ void grad_prep(GradPart<T>& q, T vm2, T vm1, T v0, T 
     q.e01 = q.E0 * q.E1;
     q.e012 = q.e01 * q.E2;
 }
-// g[j] = 6 w6 dF/dv_j (as weno5_grad), given r = 1 / (S E0 E1 E2) (FP64)
+// g[j] = 6 w6 dF/dv_j (as weno5_grad), given r = 1 / (S E0 E1 E2) (FP64); the
+// factor w6 rides on the weights' reciprocal (omega_r w6) and so on every
+// term of g
 template <typename T>
 __device__ __forceinline__ void grad_finish(const GradPart<T>& q, T r, T w6, T* g)
 {
-    T inv, iE0, iE1, iE2;
+    T inv, iE0, iE1, iE2;                                    // 1/S and -4/E_r
     if constexpr (sizeof(T) == 8) {
         inv = r * q.e012;
-        const T rS = r * q.Ssum;
+        const T rS = T(-4) * (r * q.Ssum);
         iE0 = rS * (q.E1 * q.E2); iE1 = rS * (q.E0 * q.E2); iE2 = rS * q.e01;
     } else {
-        inv = __frcp_rn(q.Ssum); iE0 = __frcp_rn(q.E0); iE1 = __frcp_rn(q.E1); iE2 = __frcp_rn(q.E2);
+        inv = __frcp_rn(q.Ssum);
+        iE0 = T(-4) * __frcp_rn(q.E0); iE1 = T(-4) * __frcp_rn(q.E1); iE2 = T(-4) * __frcp_rn(q.E2);
     }
-    const T o0 = q.a0 * inv, o1 = q.a1 * inv, o2 = q.a2 * inv;
-    const T F6 = fma(o0, q.Q0, fma(o1, q.Q1, o2 * q.Q2));
+    const T F6 = fma(q.a0, q.Q0, fma(q.a1, q.Q1, q.a2 * q.Q2)) * inv;
+    const T wi = w6 * inv;
+    const T o0 = q.a0 * wi, o1 = q.a1 * wi, o2 = q.a2 * wi;  // w6 omega_r
+    // -4 w6 C_r with C_r = omega_r (Q_r - F6) / E_r; A_r = -52/3 C_r s_r, B_r = -4 C_r t_r (times w6)
     const T C0 = o0 * (q.Q0 - F6) * iE0, C1 = o1 * (q.Q1 - F6) * iE1, C2 = o2 * (q.Q2 - F6) * iE2;
-    const T k52 = T(-52) / T(3);
-    const T A0 = (k52 * C0) * q.s0, B0 = (T(-4) * C0) * q.t0;
-    const T A1 = (k52 * C1) * q.s1, B1 = (T(-4) * C1) * q.t1;
-    const T A2 = (k52 * C2) * q.s2, B2 = (T(-4) * C2) * q.t2;
-    g[0] = w6 * fma(T(2), o0, A0 + B0);
-    g[1] = w6 * (fma(T(-7), o0, A1 + B1 - o1) - fma(T(2), A0, T(4) * B0));
-    g[2] = w6 * (fma(T(11), o0, fma(T(5), o1, T(2) * o2)) + fma(T(3), B0 + B2, A0 + A2) - T(2) * A1);
-    g[3] = w6 * (fma(T(2), o1, fma(T(5), o2, A1 - B1)) - fma(T(2), A2, T(4) * B2));
-    g[4] = w6 * (A2 + B2 - o2);
+    const T A0 = C0 * q.k0, B0 = C0 * q.t0;
+    const T A1 = C1 * q.k1, B1 = C1 * q.t1;
+    const T A2 = C2 * q.k2, B2 = C2 * q.t2;
+    g[0] = fma(T(2), o0, A0 + B0);
+    g[1] = fma(T(-7), o0, A1 + B1 - o1) - fma(T(2), A0, T(4) * B0);
+    g[2] = fma(T(11), o0, fma(T(5), o1, T(2) * o2)) + fma(T(3), B0 + B2, A0 + A2) - T(2) * A1;
+    g[3] = fma(T(2), o1, fma(T(5), o2, A1 - B1)) - fma(T(2), A2, T(4) * B2);
+    g[4] = A2 + B2 - o2;
 }
 
 // J_WENO(u)^T mu over the points [k0, k0+Q) of one periodic row (u, mu, g:
@@ -189,19 +195,26 @@ __device__ __forceinline__ void weno_row_chunk_T(const cx<T>* u, const cx<T>* mu
         const GradCentre<T> cpC = grad_centre<T>(fp[2], fp[3], fp[4], eps4);   // + side, centre k + 1
         const GradCentre<T> cmC = grad_centre<T>(fm[3], fm[4], fm[5], eps4);   // - side, centre k + 2
         T gp[5], gm[5];
+        // differences of neighbouring S (+ side: S_k - S_{k-1}, S_{k+1} - S_k;
+        // - side: S_{k+1} - S_k, S_{k+2} - S_{k+1})
+        const T dpAB = cpB.S - cpA.S, dpBC = cpC.S - cpB.S, dmAB = cmB.S - cmA.S, dmBC = cmC.S - cmB.S;
         {
+            // candidates x 6: q0 = q1 - 2 (S_k - S_{k-1}), q2 = q1 - (S_{k+1} - S_k)
+            const T Q1 = fma(T(5), fp[2], fma(T(2), fp[3], -fp[1]));
             GradPart<T> q;
-            grad_prep<T>(q, fp[0], fp[1], fp[2], fp[3], fp[4],
-                         cpA.S, fma(T(2), cpA.S, cpA.D), cpA.Pe, cpB.S, -cpB.D, cpB.Pe,
-                         cpC.S, fma(T(2), cpC.S, -cpC.D), cpC.Pe);
+            grad_prep<T>(q, fma(T(-2), dpAB, Q1), Q1, Q1 - dpBC,
+                         cpA.kS(), fma(T(2), cpA.S, cpA.D), cpA.Pe, cpB.kS(), -cpB.D, cpB.Pe,
+                         cpC.kS(), fma(T(2), cpC.S, -cpC.D), cpC.Pe);
             // X = S E0 E1 E2 >= eps^7: one FP64 division gives 1/S and the 1/E_r
             grad_finish<T>(q, sizeof(T) == 8 ? T(1) / (q.Ssum * q.e012) : T(0), psi6, gp);
         }
         {
+            // mirrored: q0 = q1 + 2 (S_{k+2} - S_{k+1}), q2 = q1 + (S_{k+1} - S_k)
+            const T Q1 = fma(T(5), fm[3], fma(T(2), fm[2], -fm[4]));
             GradPart<T> q;
-            grad_prep<T>(q, fm[5], fm[4], fm[3], fm[2], fm[1],
-                         cmC.S, fma(T(2), cmC.S, -cmC.D), cmC.Pe, cmB.S, cmB.D, cmB.Pe,
-                         cmA.S, fma(T(2), cmA.S, cmA.D), cmA.Pe);
+            grad_prep<T>(q, fma(T(2), dmBC, Q1), Q1, Q1 + dmAB,
+                         cmC.kS(), fma(T(2), cmC.S, -cmC.D), cmC.Pe, cmB.kS(), cmB.D, cmB.Pe,
+                         cmA.kS(), fma(T(2), cmA.S, cmA.D), cmA.Pe);
             grad_finish<T>(q, sizeof(T) == 8 ? T(1) / (q.Ssum * q.e012) : T(0), psi6, gm);
         }
         cpA = cpB; cpB = cpC;
@@ -314,6 +327,8 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS) adj_row_kernel(AdjRowArgs<T> 
         __syncthreads();
     }
     fft_batched<T, PPT, false, false, true>(G, log2n, 0, 1, 0, tw, tid, nthr);
+    // (A(sigma) - A) k_tau^2 = dA kscale^2 k^2, k^2 an exact integer
+    const T dAk = a.dA * a.kscale * a.kscale;
     for (int k = tid; k <= n / 2; k += nthr) {
         cx<T> xk, xnk;
         r2c_post_pair<T, true>(G, n, k, a.tw, xk, xnk);
@@ -322,19 +337,18 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS) adj_row_kernel(AdjRowArgs<T> 
         const cx<T> mk0 = __ldcg(a.m + base + k);
         const cx<T> lk = __ldcg(a.l + base + k);
         if (k == 0) {
-            const T kN = a.kscale * T(n);
-            xk.y -= a.dA * kN * kN * mk0.y;
+            xk.y -= dAk * T((long long)n * n) * mk0.y;
             a.out[base] = add<T>(lk, xk);
         } else {
-            const T kt = a.kscale * T(k);
-            xk.x -= a.dA * kt * kt * mk0.x;
-            xk.y -= a.dA * kt * kt * mk0.y;
+            const T f = dAk * T((long long)k * k);
+            xk.x = fma(-f, mk0.x, xk.x);
+            xk.y = fma(-f, mk0.y, xk.y);
             a.out[base + k] = add<T>(lk, xk);
             if (2 * k != n) {
-                const T kt2 = a.kscale * T(n - k);
+                const T g = dAk * T((long long)(n - k) * (n - k));
                 const cx<T> mk2 = __ldcg(a.m + base + n - k);
-                xnk.x -= a.dA * kt2 * kt2 * mk2.x;
-                xnk.y -= a.dA * kt2 * kt2 * mk2.y;
+                xnk.x = fma(-g, mk2.x, xnk.x);
+                xnk.y = fma(-g, mk2.y, xnk.y);
                 a.out[base + n - k] = add<T>(__ldcg(a.l + base + n - k), xnk);
             }
         }
