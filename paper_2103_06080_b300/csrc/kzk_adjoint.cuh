@@ -274,8 +274,11 @@ enum AdjRowMode { ADJ_ROW_2 = 0, ADJ_ROW_1 = 1 };
 // and the C2R of the cotangent row, WENO5 transpose, R2C, plus the
 // absorption-deviation term and the additive row.
 // Three padded buffers of nx reals, then the spill slots of the sweep.
-template <typename T, int PPT, int MODE>
-__global__ void __launch_bounds__(ROW_MAX_THREADS) adj_row_kernel(AdjRowArgs<T> a)
+// MAXT, MINB: launch bounds (the FP64 kernel for rows of up to 2048 points,
+// 128 threads, takes up to 168 registers at the three CTAs per SM its shared
+// memory allows anyway, instead of spilling at 128)
+template <typename T, int PPT, int MODE, int MAXT = ROW_MAX_THREADS, int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) adj_row_kernel(AdjRowArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, nthr = blockDim.x;

@@ -211,6 +211,9 @@ kzk_status set_adj_row_attr(size_t smem)
 {
     KZK_CUDA(cudaFuncSetAttribute(adj_row_kernel<T, row_ppt<T>(), MODE>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if constexpr (sizeof(T) == 8)
+        KZK_CUDA(cudaFuncSetAttribute(adj_row_kernel<T, row_ppt<T>(), MODE, 128, 3>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return KZK_OK;
 }
 template <typename T, int MODE>
@@ -1450,6 +1453,13 @@ kzk_status adj_row_stage(kzk_plan* p, const void* m, const void* u, const void* 
         mix_adj_row_kernel<T, MODE><<<rgrid, p->madj_thr, p->madj_smem, st>>>(m);
         KZK_LAUNCHED();
         return KZK_OK;
+    }
+    if constexpr (sizeof(T) == 8) {
+        if (p->adj_row_thr <= 128) {
+            adj_row_kernel<T, row_ppt<T>(), MODE, 128, 3><<<rgrid, p->adj_row_thr, adj_row_smem<T>(p), st>>>(r);
+            KZK_LAUNCHED();
+            return KZK_OK;
+        }
     }
     adj_row_kernel<T, row_ppt<T>(), MODE><<<rgrid, p->adj_row_thr, adj_row_smem<T>(p), st>>>(r);
     KZK_LAUNCHED();
