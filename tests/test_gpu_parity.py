@@ -309,6 +309,22 @@ def test_adjoint_matches_oracle_adjoint(prec, tol):
     assert rel_linf(g0.double().cpu().numpy(), ref) < tol
 
 
+@pytest.mark.parametrize("nx,ny,steps", [(4096, 8, 4), (8192, 4, 3)])
+def test_adjoint_long_rows_match_oracle_adjoint(nx, ny, steps):
+    # rows of 4096 and 8192 points: the FP64 adjoint row pass at 256 and 512
+    # threads (the launch variant for longer rows than the 2048 of the
+    # adjoint workload)
+    api = _api()
+    w = inputs.config(2, nx=nx, ny=ny, n_steps=steps)
+    plan = api.Plan.from_workload(w, precision="fp64")
+    p = oracle.Params(**inputs.oracle_params(w))
+    u_end = oracle.run(p, w.u0, w.n_steps)
+    g_end = 2 * w.dtau * u_end
+    ref = oracle.adjoint(p, w.u0, g_end, w.n_steps)
+    g0 = plan.adjoint(_dev(w.u0), _dev(g_end), w.n_steps, ckpt_every=2)
+    assert rel_linf(g0.double().cpu().numpy(), ref) < 1e-10
+
+
 def test_adjoint_finite_differences_fp64():
     # central differences on seeded unit directions (FP64),
     # |ad - fd| <= 1e-6 max(|fd|, 0.1 |g0| / sqrt(N)) (fd_util.py: factorised
