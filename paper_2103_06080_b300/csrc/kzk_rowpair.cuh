@@ -149,9 +149,39 @@ __device__ __forceinline__ c2* pair_tws(double* red, int nthr) { return reinterp
 // c2r_pre of the two rows of Vb (row j at Vb[0, n), row j + 1 at Vb[n, 2n),
 // as they lie in the state), written as packed pairs into the padded buffer
 // X (the same arithmetic per lane as c2r_pre on packed rows).
+// ITER > 0: the caller's n / (2 nthr) + 1 (compile-time): each thread's
+// twiddles are all loaded before the first is used.
+template <int ITER = 0>
 __device__ __forceinline__ void c2r_pre_pair(const float2* Vb, c2* X, int n, const c2* __restrict__ tw, int tid,
                                              int nthr)
 {
+    if constexpr (ITER > 0) {
+        c2 wv[ITER];
+#pragma unroll
+        for (int i = 0; i < ITER; i++) {
+            const int k = tid + i * nthr;
+            if (k <= n / 2) wv[i] = tw[k];
+        }
+#pragma unroll
+        for (int i = 0; i < ITER; i++) {
+            const int k = tid + i * nthr;
+            if (k > n / 2) break;
+            if (k == 0) {
+                const c2 z = pack2(Vb[0], Vb[n]);
+                X[0] = c2{z.x + z.y, z.x - z.y};
+            } else if (2 * k == n) {
+                const c2 a = pack2(Vb[k], Vb[n + k]);
+                X[padx(k)] = c2{f2(2.0f) * a.x, f2(-2.0f) * a.y};
+            } else {
+                const c2 a = pack2(Vb[k], Vb[n + k]), b = pack2(Vb[n - k], Vb[2 * n - k]);
+                const c2 s = add<f2>(a, conj<f2>(b)), d = sub<f2>(a, conj<f2>(b));
+                const c2 r = mul_si<f2, 1>(mulc<f2>(d, wv[i]));
+                X[padx(k)] = add<f2>(s, r);
+                X[padx(n - k)] = conj<f2>(sub<f2>(s, r));
+            }
+        }
+        return;
+    }
     for (int k = tid; k <= n / 2; k += nthr) {
         if (k == 0) {
             const float2 r0 = Vb[0], r1 = Vb[n];
@@ -258,7 +288,8 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             __syncthreads();
             return;
         }
-        c2r_pre_pair(Vraw, Y, n, P.tw2, tid, nthr);
+        if constexpr (CT) c2r_pre_pair<(1 << LOG2N) / (2 * rowpair_ct_threads<LOG2N>()) + 1>(Vraw, Y, n, P.tw2, tid, nthr);
+        else c2r_pre_pair(Vraw, Y, n, P.tw2, tid, nthr);
         __syncthreads();
         if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
         if constexpr (CT) U = fft_batched_pp_ct<f2, PPT, false, true, true, false, LOG2N>(Y, X, tws_s, tid, nthr);
