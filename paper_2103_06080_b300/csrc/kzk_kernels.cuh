@@ -182,8 +182,7 @@ __device__ __forceinline__ void c2r_pre(cx<T>* X, int n, const cx<T>* __restrict
 // X_k = 1/2 [(Z_k + conj Z_{n-k}) - i W^k (Z_k - conj Z_{n-k})].
 // Returns the pair (X_k, X_{n-k}) for 0 < k < n/2, handles k = 0 and n/2.
 template <typename T, bool PAD = false>
-__device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, const cx<T>* __restrict__ tw,
-                                              cx<T>& Xk, cx<T>& Xnk)
+__device__ __forceinline__ void r2c_post_pair_w(const cx<T>* Z, int n, int k, cx<T> wk, cx<T>& Xk, cx<T>& Xnk)
 {
     const T h = T(0.5);
     if (k == 0) {
@@ -199,10 +198,17 @@ __device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, cons
         // r = -i W^k d / 2 (the halving exact, on the twiddle): X_k = s/2 + r;
         // n - k: its s and d are conj(s) and -conj(d), and with
         // W^{n-k} = -conj(W^k) its r is -conj(r): X_{n-k} = conj(s/2 - r)
-        const cx<T> r = mul_si<T, -1>(mul<T>(scale<T>(tw[k], h), d));
+        const cx<T> r = mul_si<T, -1>(mul<T>(scale<T>(wk, h), d));
         Xk = mk<T>(fma(h, s.x, r.x), fma(h, s.y, r.y));
         Xnk = mk<T>(fma(h, s.x, -r.x), fma(-h, s.y, r.y));
     }
+}
+// the same with the twiddle W^k read from the table (0 <= k <= n/2)
+template <typename T, bool PAD = false>
+__device__ __forceinline__ void r2c_post_pair(const cx<T>* Z, int n, int k, const cx<T>* __restrict__ tw,
+                                              cx<T>& Xk, cx<T>& Xnk)
+{
+    r2c_post_pair_w<T, PAD>(Z, n, k, tw[k], Xk, Xnk);
 }
 
 // Row of n complex values from global memory into a padded shared buffer:

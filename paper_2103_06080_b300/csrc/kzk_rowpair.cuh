@@ -180,24 +180,24 @@ __device__ __forceinline__ void c2r_pre_pair(const float2* Vb, c2* X, int n, con
                 X[padx(n - k)] = conj<f2>(sub<f2>(s, r));
             }
         }
-        return;
-    }
-    for (int k = tid; k <= n / 2; k += nthr) {
-        if (k == 0) {
-            const float2 r0 = Vb[0], r1 = Vb[n];
-            const c2 z = pack2(r0, r1);
-            X[0] = c2{z.x + z.y, z.x - z.y};
-        } else if (2 * k == n) {
-            const c2 a = pack2(Vb[k], Vb[n + k]);
-            X[padx(k)] = c2{f2(2.0f) * a.x, f2(-2.0f) * a.y};
-        } else {
-            const c2 a = pack2(Vb[k], Vb[n + k]), b = pack2(Vb[n - k], Vb[2 * n - k]);
-            const c2 w = tw[k];
-            const c2 s = add<f2>(a, conj<f2>(b)), d = sub<f2>(a, conj<f2>(b));
-            const c2 r = mul_si<f2, 1>(mulc<f2>(d, w));
-            // n - k: conj(s - r) (as c2r_pre)
-            X[padx(k)] = add<f2>(s, r);
-            X[padx(n - k)] = conj<f2>(sub<f2>(s, r));
+    } else {
+        for (int k = tid; k <= n / 2; k += nthr) {
+            if (k == 0) {
+                const float2 r0 = Vb[0], r1 = Vb[n];
+                const c2 z = pack2(r0, r1);
+                X[0] = c2{z.x + z.y, z.x - z.y};
+            } else if (2 * k == n) {
+                const c2 a = pack2(Vb[k], Vb[n + k]);
+                X[padx(k)] = c2{f2(2.0f) * a.x, f2(-2.0f) * a.y};
+            } else {
+                const c2 a = pack2(Vb[k], Vb[n + k]), b = pack2(Vb[n - k], Vb[2 * n - k]);
+                const c2 w = tw[k];
+                const c2 s = add<f2>(a, conj<f2>(b)), d = sub<f2>(a, conj<f2>(b));
+                const c2 r = mul_si<f2, 1>(mulc<f2>(d, w));
+                // n - k: conj(s - r) (as c2r_pre)
+                X[padx(k)] = add<f2>(s, r);
+                X[padx(n - k)] = conj<f2>(sub<f2>(s, r));
+            }
         }
     }
 }
@@ -398,12 +398,19 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
                 }
             }
         }
+        // this thread's packing twiddles, all loaded before the first is used
+        c2 wv[ITER];
+#pragma unroll
+        for (int i = 0; i < ITER; i++) {
+            const int k = tid + i * nthr;
+            if (k <= n / 2) wv[i] = P.tw2[k];
+        }
 #pragma unroll
         for (int i = 0; i < ITER; i++) {
             const int k = tid + i * nthr;
             if (k > n / 2) break;
             c2 xk, xnk;
-            r2c_post_pair<f2, true>(Z, n, k, P.tw2, xk, xnk);
+            r2c_post_pair_w<f2, true>(Z, n, k, wv[i], xk, xnk);
             float2 k0a = lane0(xk), k0b = lane1(xk), kna = lane0(xnk), knb = lane1(xnk);
             if (cA != 0.0f) {
                 // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx), each row
