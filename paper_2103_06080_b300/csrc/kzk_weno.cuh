@@ -19,12 +19,17 @@
 //    each is computed once per centre and reused by the three interfaces
 //    that need it (a sliding window over the row);
 //  * the quotient sum a_r q_r / sum a_r is formed after multiplying numerator
-//    and denominator by prod (eps + beta_r)^2, so a_r -> d_r prod_{s != r} t_s;
+//    and denominator by prod (eps + beta_r)^2, so a_r -> d_r prod_{s != r} t_s,
+//    with t0 factored out of the two terms that contain it;
+//  * the centred candidate q1 is formed from its stencil, the outer ones from
+//    it: q0 - q1 and q2 - q1 are multiples of third differences, i.e. of
+//    differences of neighbouring centres' S (two operations each);
 //  * the 1/6 of the candidate values q_r is folded into 1/dtau, and common
 //    factors of the weights (16 in (eps + beta)^2, 10 in d_r) are dropped;
 //  * FP64: both halves F+ and F- and two neighbouring interfaces share one
-//    division; FP32: two hardware reciprocals per interface (the product of
-//    the denominators could underflow).
+//    division, which also carries the final scale; FP32: two hardware
+//    reciprocals per interface (the product of the denominators could
+//    underflow).
 #pragma once
 #include "kzk_common.cuh"
 #include "kzk_fft.cuh"
