@@ -21,6 +21,7 @@
 // the scalar math functions they call inside namespace kzk
 #include "kzk_colpair.cuh"
 #include "kzk_copyrate.cuh"
+#include "kzk_ysweep_pair.cuh"
 
 using namespace kzk;
 
@@ -399,6 +400,8 @@ kzk_status configure_mixed(kzk_plan* p)
     KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C1V>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(ysweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    if constexpr (sizeof(T) == 4)
+        KZK_CUDA(cudaFuncSetAttribute(ysweep_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return KZK_OK;
 }
 
@@ -434,6 +437,8 @@ kzk_status configure(kzk_plan* p)
     KZK_TRY((set_row_attr<T, ROW_INV>(sm)));
     KZK_TRY((set_row_attr<T, ROW_RHS_MED>(sm)));
     KZK_CUDA(cudaFuncSetAttribute(ysweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if constexpr (sizeof(T) == 4)
+        KZK_CUDA(cudaFuncSetAttribute(ysweep_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     KZK_CUDA(cudaFuncSetAttribute(ysweepT_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     KZK_TRY((set_col_attr<T, COL_STAGE1>(sm)));
     KZK_TRY((set_col_attr<T, COL_STAGE2>(sm)));
@@ -874,8 +879,15 @@ kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, dou
         y.inst_elems = (long long)p->nx * p->ny;
         y.eps = (T)p->c.weno_eps;
         y.inv_dy = (T)(p->ny / (p->g.y_max - p->g.y_min));
-        const dim3 yg((p->nx + YSWEEP_THREADS - 1) / YSWEEP_THREADS, (p->ny + y.Q - 1) / y.Q, p->batch);
-        ysweep_kernel<T><<<yg, YSWEEP_THREADS, ysweep_smem<T>(y.Q), st>>>(y);
+        if constexpr (sizeof(T) == 4) {
+            // FP32: column pairs in packed FP32 (kzk_ysweep_pair.cuh)
+            y.Q = std::min(p->ny, 32);
+            const dim3 yg((p->nx + 2 * YSWEEP_THREADS - 1) / (2 * YSWEEP_THREADS), (p->ny + y.Q - 1) / y.Q, p->batch);
+            ysweep_pair_kernel<<<yg, YSWEEP_THREADS, ysweep_pair_smem(y.Q), st>>>(y);
+        } else {
+            const dim3 yg((p->nx + YSWEEP_THREADS - 1) / YSWEEP_THREADS, (p->ny + y.Q - 1) / y.Q, p->batch);
+            ysweep_kernel<T><<<yg, YSWEEP_THREADS, ysweep_smem<T>(y.Q), st>>>(y);
+        }
         KZK_LAUNCHED();
         RowArgs<T> r = row_args<T>(p, Vin, bout, sigma, nullptr);
         r.coef = dcoef;
