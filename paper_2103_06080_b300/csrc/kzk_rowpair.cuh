@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
         const float* u0 = a.uphys + 2 * base;
         for (int i = tid; i < nx; i += nthr) st_real<f2, true>(X, i, f2(__ldcg(u0 + i), __ldcg(u0 + nx + i)));
         __syncthreads();
-    } else if constexpr (MODE == ROW_RHS) {
+    } else if constexpr (MODE == ROW_RHS || MODE == ROW_INV) {
         // both rows (2 n float2, contiguous) by one bulk copy into X as they
         // lie; the pre-processing packs them into Y
         unsigned long long* bar = pair_bar(red, nthr);
@@ -289,18 +289,12 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
             return;
         }
         if constexpr (CT) c2r_pre_pair<(1 << LOG2N) / (2 * rowpair_ct_threads<LOG2N>()) + 1>(Vraw, Y, n, P.tw2, tid, nthr);
-        else c2r_pre_pair(Vraw, Y, n, P.tw2, tid, nthr);
+        else c2r_pre_pair<5>(Vraw, Y, n, P.tw2, tid, nthr);   // nthr = max(32, n/8): k <= n/2 in five steps
         __syncthreads();
         if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
         if constexpr (CT) U = fft_batched_pp_ct<f2, PPT, false, true, true, false, LOG2N>(Y, X, tws_s, tid, nthr);
         else U = fft_batched_pp<f2, PPT, false, true, true>(Y, X, log2n, 0, 1, 0, tw, tid, nthr);
         Bf = U == X ? Y : X;
-    } else {
-        for (int i = tid; i < n; i += nthr) X[padx(i)] = pack2(__ldcg(in + base + i), __ldcg(in + base + n + i));
-        __syncthreads();
-        c2r_pre<f2, true>(X, n, P.tw2, tid, nthr);
-        __syncthreads();
-        fft_batched<f2, PPT, false, true, true>(X, log2n, 0, 1, 0, tw, tid, nthr);
     }
 
     float sa1 = 0, sa2 = 0, mxa = 0, sb1 = 0, sb2 = 0, mxb = 0;
@@ -308,7 +302,7 @@ __global__ void __launch_bounds__(ROW_MAX_THREADS, 1) rowpair_kernel(RowPairArgs
     if constexpr (MODE == ROW_INV) {
         float* d0 = reinterpret_cast<float*>(out + base);
         for (int i = tid; i < nx; i += nthr) {
-            const f2 w = ld_real<f2, true>(X, i);
+            const f2 w = ld_real<f2, true>(U, i);
             const float v0 = w.v.x * a.out_scale, v1 = w.v.y * a.out_scale;
             d0[i] = v0;
             d0[nx + i] = v1;
