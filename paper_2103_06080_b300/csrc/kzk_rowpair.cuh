@@ -2,9 +2,10 @@
 // FP32 arithmetic of sm_100+ (one FADD2 / FMUL2 / FFMA2 instruction carries
 // one operation for each of two rows).
 //
-// The FP32 row pass is bound by instruction issue, not by memory or by the
-// FMA pipe: about three hundred warp instructions per grid point for the two
-// real FFTs and the WENO5 sweep.  Rows j and j + 1 of one instance follow
+// The FP32 row pass is bound by instruction issue and latency, not by memory:
+// about 105 thread instructions per grid point for the two real FFTs and the
+// WENO5 sweep (27.6 M warp instructions for the 8.4 M points of a 4096 x 2048
+// pass) with the FMA pipe about half busy.  Rows j and j + 1 of one instance follow
 // exactly the same sequence of operations (same sigma, same tables, same
 // stencils), so they are carried as the two lanes of one 64-bit value `f2`,
 // and a complex value of the pair as `c2` = {(re_j, re_j+1), (im_j, im_j+1)}.
@@ -15,11 +16,11 @@
 // (FMAs may be contracted differently, so the two agree to rounding, not bit
 // for bit); the plan option row_kernel = KZK_ROW_SINGLE selects the single-row kernel.
 //
-// The b passes (ROW_RHS) take their two input rows -- contiguous in the
-// spectral state, 16 n bytes -- by one bulk copy of the tensor memory
-// accelerator into buffer X as they lie; the C2R pre-processing reads them
-// there and writes the packed pairs into Y, where the inverse transform starts
-// (no separate load pass).  The copy's wait is bounded (FLAG_TIMEOUT).  The
+// The b passes (ROW_RHS) and the inverse pass to physical rows (ROW_INV) take
+// their two input rows -- contiguous in the spectral state, 16 n bytes -- by
+// one bulk copy of the tensor memory accelerator into buffer X as they lie;
+// the C2R pre-processing reads them there and writes the packed pairs into Y,
+// where the inverse transform starts (no separate load pass).  The copy's wait is bounded (FLAG_TIMEOUT).  The
 // absorption-deviation term at the end issues all its loads of V before it
 // computes, so their latencies overlap.
 #pragma once
