@@ -16,6 +16,10 @@
 //   E V + ds[(Phi1 - Phi2) b1 + Phi2 b2] = V* + ds Phi2 (b2 - b1),
 // which needs neither E nor Phi1 again.  The 1/nx, 1/ny normalisations and
 // dsigma are folded into the tables (powers of two: exact).
+// FP64 plans also carry Sigma = FFT_y(V) / ny between steps (modes COL_FWD,
+// COL_S1, COL_S2 below): C1 then transforms only b1 (X = ny E' Sigma + P1' B1,
+// T = X - P2' B1 kept, V* = IFFT_y(X)) and C2 only b2 (Sigma' = T + P2' B2,
+// V' = IFFT_y(Sigma')), four y-transforms per step instead of five.
 #pragma once
 #include "kzk_common.cuh"
 #include "kzk_fft.cuh"
