@@ -66,9 +66,12 @@ def test_run_fp64_parity():
     assert rel_linf(u.cpu().numpy(), ref) < 1e-11
 
 
-def test_run_fp32_error():
+@pytest.mark.parametrize("nx,ny,steps", [(512, 256, 40), (64, 16, 10), (1536, 40, 10)])
+def test_run_fp32_error(nx, ny, steps):
+    # FP32 y-flux sweep on column pairs: whole and partial CTAs of 256 columns,
+    # 32-row blocks with a short last one, fewer rows than one block
     api = _api()
-    w = inputs.medium_config(512, 256, 40)
+    w = inputs.medium_config(nx, ny, steps)
     plan = api.Plan.from_workload(w, precision="fp32")
     u = _dev(w.u0, torch.float32)
     plan.advance(u, w.n_steps)
