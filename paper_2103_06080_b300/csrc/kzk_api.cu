@@ -371,6 +371,9 @@ kzk_status configure_mixed(kzk_plan* p)
     p->mrow_smem = mix_row_smem<T>(p->nx, p->mrow_thr);
     int lc = 0;
     while (lc < 4 && p->n % (2 << lc) == 0 && (size_t)p->ny * (2 << lc) * sizeof(cx<T>) <= 96 * 1024) lc++;
+    // FP32 columns too long for two per tile at two CTAs per SM still take two (one CTA per SM) where
+    // they fit: the 8-byte rows of a single column use a quarter of each 32-byte sector
+    if (sizeof(T) == 4 && lc == 0 && p->n % 2 == 0 && (size_t)p->ny * 2 * sizeof(cx<T>) <= (size_t)optin) lc = 1;
     p->mcol_lc = lc;
     p->mcol_smem = std::max(((size_t)p->ny << lc) * sizeof(cx<T>), 4 * (size_t)MIX_COL_THREADS * sizeof(double));
     if (p->mrow_smem > (size_t)optin || p->mcol_smem > (size_t)optin)
