@@ -401,6 +401,7 @@ kzk_status configure_mixed(kzk_plan* p)
     KZK_CUDA(cudaFuncSetAttribute(mix_row_kernel<T, ROW_RHS_MED>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C1B>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C1V>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C1V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(mix_col_kernel<T, MIX_C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     KZK_CUDA(cudaFuncSetAttribute(ysweep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     if constexpr (sizeof(T) == 4)
@@ -772,7 +773,8 @@ kzk_status launch_mix_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t s
     if (MODE == COL_STAGE1) {
         mix_col_kernel<T, MIX_C1B><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
         KZK_LAUNCHED();
-        mix_col_kernel<T, MIX_C1V><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+        if (sizeof(T) == 4 && a.lo_out) mix_col_kernel<T, MIX_C1V, true><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+        else mix_col_kernel<T, MIX_C1V><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
         KZK_LAUNCHED();
     } else {
         mix_col_kernel<T, MIX_C2><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);

@@ -434,7 +434,10 @@ struct MixColArgs {
 
 constexpr int MIX_COL_THREADS = 512;
 
-template <typename T, int MODE>
+// INC: the FP32 compensated state, whose transforms carry only the stage
+// increment (R12): plain FP32 constants suffice there, the two-float ones are
+// for the transform of a plain FP32 state.
+template <typename T, int MODE, bool INC = false>
 __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
     const int m0 = tile * TC;
     const long long ibase = (long long)inst * a.inst_stride;
     const int total = ny << lc;
-    constexpr bool ACC = (MODE == MIX_C1V) && sizeof(T) == 4;
+    constexpr bool ACC = (MODE == MIX_C1V) && sizeof(T) == 4 && !INC;
     auto gidx = [&](int e) -> long long { return ibase + (long long)(e >> lc) * n + m0 + (e & (TC - 1)); };
 
     if (MODE == MIX_C1V && tile == 0 && a.diag_rows && a.diag_hist) {
