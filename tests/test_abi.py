@@ -81,7 +81,7 @@ def test_null_arguments_are_rejected():
 
 @pytest.mark.parametrize("field,value,code", [
     ("row_kernel", 3, L.KZK_ERR_ARG), ("col_kernel", 4, L.KZK_ERR_ARG), ("fp32_state", -1, L.KZK_ERR_ARG),
-    ("transforms", 2, L.KZK_ERR_ARG)])
+    ("transforms", 2, L.KZK_ERR_ARG), ("graph", 3, L.KZK_ERR_ARG), ("graph", -1, L.KZK_ERR_ARG)])
 def test_unknown_option_values_are_rejected(field, value, code):
     # refused before any device work
     g = L.KzkGrid(nx=64, ny=32, tau_min=-4, tau_max=4, y_min=-8, y_max=8, prec=L.KZK_FP32)
