@@ -11,6 +11,8 @@ finite differences); the paper's largest grid (3584 x 10000) is checked
 against the closed form of a propagating Fourier mode, which holds at any
 size.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -79,6 +81,31 @@ def test_run_fp64_parity(nx, ny, steps):
     assert np.allclose(gh[1:, 1], hist[:-1, 1], rtol=1e-11)
     assert abs(d[0]["energy"] - hist[-1, 1]) < 1e-11 * hist[-1, 1]
     assert np.max(np.abs(gh[:, 0] - gh[0, 0])) < 1e-14
+
+
+# Columns of 10000 points (the column length of Set 4, Table 1) with the
+# nonlinear term: FP32 runs them as tiles of two columns at one CTA per SM
+# (the compensated state's transforms on plain FP32 twiddles), FP64 as single
+# columns; both against the oracle.  The y extent grows with ny so that dy is
+# that of the 4096 x 2048 grid: on [-8, 8] the diffraction phase
+# dsigma ky^2 / (4 pi k_tau) of the highest ky would reach 1e5-1e6 rad, where
+# one rounding of the phase in either side's FP64 tables is already ~1e-10.
+@pytest.mark.parametrize("prec,nx,steps", [("fp32", 56, 20), ("fp64", 56, 10)])
+def test_run_long_columns(prec, nx, steps):
+    api = _api()
+    w = inputs.config(2, nx=nx, ny=10000, n_steps=steps)
+    w = dataclasses.replace(w, y_min=-8.0 * 10000 / 2048, y_max=8.0 * 10000 / 2048)
+    plan = api.Plan.from_workload(w, precision=prec)
+    u = _dev(w.u0, torch.float64 if prec == "fp64" else torch.float32)
+    st, _ = plan.advance(u, w.n_steps, diag=True)
+    assert st == 0
+    ref = oracle.run(oracle.Params(**inputs.oracle_params(w)), w.u0, w.n_steps, threads=True)
+    got = u.double().cpu().numpy()
+    if prec == "fp64":
+        assert rel_linf(got, ref) < 1e-11
+    else:
+        assert rel_l2(got, ref) < 1e-5
+        assert rel_linf(got, ref) < 1e-4
 
 
 def test_one_step_stages_match_oracle():
