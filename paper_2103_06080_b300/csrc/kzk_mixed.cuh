@@ -471,11 +471,29 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
             d[3] = tmp[3];
         }
     }
-    for (int e = tid; e < total; e += nthr) {
-        const long long g = gidx(e);
-        if (MODE == MIX_C1B) S[e] = __ldcg(a.b + g);
-        else if (MODE == MIX_C1V) S[e] = __ldcg(a.a + g);
-        else S[e] = sub<T>(__ldcg(a.b + g), __ldcg(a.a + g));
+    // The element loops below take this thread's elements e = tid + i nthr in
+    // batches of MU, every load of a batch issued before the first is used:
+    // the row segments of a tile are 8- or 16-byte pieces at the pitch of a
+    // row, so these passes wait on the latency of their loads, and one load
+    // in flight per thread left them there (FP32: ~0.8 TB/s).
+    constexpr int MU = sizeof(T) == 4 ? 8 : 4;
+    for (int e0 = tid; e0 < total; e0 += MU * nthr) {
+        cx<T> v[MU], w[MU];
+#pragma unroll
+        for (int q = 0; q < MU; q++) {
+            const int e = e0 + q * nthr;
+            if (e < total) {
+                const long long g = gidx(e);
+                if (MODE == MIX_C1B) v[q] = __ldcg(a.b + g);
+                else if (MODE == MIX_C1V) v[q] = __ldcg(a.a + g);
+                else { v[q] = __ldcg(a.b + g); w[q] = __ldcg(a.a + g); }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MU; q++) {
+            const int e = e0 + q * nthr;
+            if (e < total) S[e] = MODE == MIX_C2 ? sub<T>(v[q], w[q]) : v[q];
+        }
     }
     __syncthreads();
     mix_forward<T, ACC>(S, A.f, lc, a.tw, a.tw_lo, tid, nthr);
@@ -483,23 +501,45 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
     // the diagonal propagator at the frequency of each position; the packed
     // column 0 (first tile only) couples frequencies l and ny - l, so one
     // thread owns each such pair
-    for (int e = tid; e < total; e += nthr) {
-        const int c = e & (TC - 1), m = m0 + c;
-        if (m == 0) continue;
-        const int l = __ldg(A.ipos + (e >> lc));
-        const int lf = l <= (ny >> 1) ? l : ny - l;
-        const long long ti = (long long)lf * n + m;
-        const cx<T> z = S[e];
-        if constexpr (MODE == MIX_C1B) {
-            A.w[gidx(e)] = mul<T>(__ldg(a.Tb + ti), z);
-        } else if constexpr (MODE == MIX_C1V) {
-            cx<T> r = mul<T>(__ldg(a.Ta + ti), z);
-            if constexpr (ACC) {
-                if (a.Ta_lo) r = fma_c<T>(__ldg(a.Ta_lo + ti), z, r);
+    for (int e0 = tid; e0 < total; e0 += MU * nthr) {
+        // frequency positions, then the table entries (and W) of the batch
+        int lq[MU];
+#pragma unroll
+        for (int q = 0; q < MU; q++) {
+            const int e = e0 + q * nthr;
+            lq[q] = e < total ? __ldg(A.ipos + (e >> lc)) : 0;
+        }
+        cx<T> tq[MU], tl[MU], wq[MU];
+#pragma unroll
+        for (int q = 0; q < MU; q++) {
+            const int e = e0 + q * nthr, m = m0 + (e & (TC - 1));
+            if (e < total && m != 0) {
+                const int l = lq[q];
+                const int lf = l <= (ny >> 1) ? l : ny - l;
+                const long long ti = (long long)lf * n + m;
+                tq[q] = __ldg((MODE == MIX_C1B ? a.Tb : a.Ta) + ti);
+                if constexpr (ACC) {
+                    if (a.Ta_lo) tl[q] = __ldg(a.Ta_lo + ti);
+                }
+                if constexpr (MODE == MIX_C1V) wq[q] = __ldcg(A.w + gidx(e));
             }
-            S[e] = add<T>(r, __ldcg(A.w + gidx(e)));
-        } else {
-            S[e] = mul<T>(__ldg(a.Ta + ti), z);
+        }
+#pragma unroll
+        for (int q = 0; q < MU; q++) {
+            const int e = e0 + q * nthr, m = m0 + (e & (TC - 1));
+            if (e >= total || m == 0) continue;
+            const cx<T> z = S[e];
+            if constexpr (MODE == MIX_C1B) {
+                A.w[gidx(e)] = mul<T>(tq[q], z);
+            } else if constexpr (MODE == MIX_C1V) {
+                cx<T> r = mul<T>(tq[q], z);
+                if constexpr (ACC) {
+                    if (a.Ta_lo) r = fma_c<T>(tl[q], z, r);
+                }
+                S[e] = add<T>(r, wq[q]);
+            } else {
+                S[e] = mul<T>(tq[q], z);
+            }
         }
     }
     if (m0 == 0) {
@@ -532,16 +572,34 @@ __global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> 
     if constexpr (MODE == MIX_C1B) return;
     __syncthreads();
     mix_inverse<T, ACC>(S, A.f, lc, a.tw, a.tw_lo, tid, nthr);
-    for (int e = tid; e < total; e += nthr) {
-        const long long g = gidx(e);
-        if (a.lo_out) {
-            // compensated state: the transforms carried the increment
-            cx<T> h, l;
-            comp_add<T>(__ldcg((MODE == MIX_C1V ? a.a : a.c) + g), lo_load<T>(a.lo_in + g), S[e], h, l);
-            a.out[g] = h;
-            lo_store<T>(a.lo_out + g, l);
-        } else {
-            a.out[g] = MODE == MIX_C1V ? S[e] : add<T>(__ldcg(a.c + g), S[e]);
+    for (int e0 = tid; e0 < total; e0 += MU * nthr) {
+        // the state hi (and lo) the result is added to, for the batch
+        cx<T> hq[MU], lq[MU];
+        if (a.lo_out || MODE == MIX_C2) {
+#pragma unroll
+            for (int q = 0; q < MU; q++) {
+                const int e = e0 + q * nthr;
+                if (e < total) {
+                    const long long g = gidx(e);
+                    hq[q] = __ldcg((MODE == MIX_C1V ? a.a : a.c) + g);
+                    if (a.lo_out) lq[q] = lo_load<T>(a.lo_in + g);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MU; q++) {
+            const int e = e0 + q * nthr;
+            if (e >= total) continue;
+            const long long g = gidx(e);
+            if (a.lo_out) {
+                // compensated state: the transforms carried the increment
+                cx<T> h, l;
+                comp_add<T>(hq[q], lq[q], S[e], h, l);
+                a.out[g] = h;
+                lo_store<T>(a.lo_out + g, l);
+            } else {
+                a.out[g] = MODE == MIX_C1V ? S[e] : add<T>(hq[q], S[e]);
+            }
         }
     }
 }
