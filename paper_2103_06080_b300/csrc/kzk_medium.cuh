@@ -105,6 +105,19 @@ struct YSweepArgs {
 
 constexpr int YSWEEP_THREADS = 128;
 
+// The y Lax-Friedrichs speed max_j |U_perp(sigma, y_j)| from the medium
+// kernel's per-block partial maxima bmax[0, n): each warp takes a strided
+// pass and a shuffle reduction (max is exact in any order, so every warp
+// gets the same value).  All 32 lanes of the warp must call it.
+__device__ __forceinline__ double bmax_all(const double* bmax, int n)
+{
+    double m = 0.0;
+    for (int i = threadIdx.x & 31; i < n; i += 32) m = fmax(m, __ldg(bmax + i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    return m;
+}
+
 // shared memory of one sweep CTA: Q + 7 rows of YSWEEP_THREADS columns, and
 // the split-flux factors and source coefficient of those rows
 template <typename T>
@@ -127,8 +140,7 @@ __global__ void __launch_bounds__(YSWEEP_THREADS) ysweep_kernel(YSweepArgs<T> a)
     T* cp = tile + (size_t)R * YSWEEP_THREADS; // [R]: 2 (U_perp + alpha_y)
     T* cm = cp + R;                            // [R]: 2 (U_perp - alpha_y)
     T* dp = cm + R;                            // [R]: d U_perp / dy
-    double ay = 0.0;
-    for (int i = 0; i < a.n_bmax; i++) ay = fmax(ay, __ldg(a.bmax + i));
+    const double ay = bmax_all(a.bmax, a.n_bmax);
     const T* u = a.u + (long long)blockIdx.z * a.inst_elems;
     // the CTA's rows (periodic in y), every load in flight at once
     for (int idx = tid; idx < R * YSWEEP_THREADS; idx += YSWEEP_THREADS) {
@@ -209,8 +221,7 @@ __global__ void __launch_bounds__(YSWEEP_THREADS) ysweepT_kernel(YSweepTArgs<T> 
     T* dgp = tm + (size_t)Rm * YSWEEP_THREADS;  // [Ru]: (U_perp + alpha_y) / 2
     T* dgm = dgp + Ru;                          // [Ru]: (U_perp - alpha_y) / 2
     T* dpr = dgm + Ru;                          // [Ru]: d U_perp / dy
-    double ay = 0.0;
-    for (int i = 0; i < a.n_bmax; i++) ay = fmax(ay, __ldg(a.bmax + i));
+    const double ay = bmax_all(a.bmax, a.n_bmax);
     const T* u = a.u + (long long)blockIdx.z * a.inst_elems;
     const T* mu = a.mu + (long long)blockIdx.z * a.inst_elems;
     for (int idx = tid; idx < Ru * YSWEEP_THREADS; idx += YSWEEP_THREADS) {

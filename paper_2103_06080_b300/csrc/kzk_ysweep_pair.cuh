@@ -36,14 +36,23 @@ __global__ void __launch_bounds__(YSWEEP_THREADS) ysweep_pair_kernel(YSweepArgs<
     float* cp = reinterpret_cast<float*>(tile + (size_t)R * YSWEEP_THREADS);   // [R]: 2 (U_perp + alpha_y)
     float* cm = cp + R;                                  // [R]: 2 (U_perp - alpha_y)
     float* dp = cm + R;                                  // [R]: d U_perp / dy
-    double ay = 0.0;
-    for (int i = 0; i < a.n_bmax; i++) ay = fmax(ay, __ldg(a.bmax + i));
+    const double ay = bmax_all(a.bmax, a.n_bmax);
     const float* u = a.u + (long long)blockIdx.z * a.inst_elems;
-    for (int idx = tid; idx < R * YSWEEP_THREADS; idx += YSWEEP_THREADS) {
-        const int r = idx / YSWEEP_THREADS, c = idx % YSWEEP_THREADS;
-        const int row = (((j0 - 4 + r) % ny) + ny) % ny;
-        tile[idx] = (k0 + 2 * c < nx) ? __ldg(reinterpret_cast<const float2*>(u + (long long)row * nx + k0 + 2 * c))
-                                      : make_float2(0.f, 0.f);
+    // this thread's column pair of the CTA's rows (periodic in y), loads
+    // issued in batches of 8 before they are stored
+    const bool live = k < nx;
+    for (int r0 = 0; r0 < R; r0 += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int r = r0 + q;
+            const int row = (((j0 - 4 + r) % ny) + ny) % ny;
+            v[q] = (live && r < R) ? __ldg(reinterpret_cast<const float2*>(u + (long long)row * nx + k))
+                                   : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (r0 + q < R) tile[(r0 + q) * YSWEEP_THREADS + tid] = v[q];
     }
     for (int r = tid; r < R; r += YSWEEP_THREADS) {
         const int row = (((j0 - 4 + r) % ny) + ny) % ny;
