@@ -328,19 +328,44 @@ __global__ void __launch_bounds__(MIX_ROW_MAX_THREADS) mix_row_kernel(MixRowArgs
         }
         return;
     }
+    // The row loops below take this thread's indices in batches of RB, all
+    // loads of a batch issued before the first is used (one load in flight
+    // per thread left these passes waiting on latency).
+    constexpr int RB = 4;
     if constexpr (MODE == ROW_RHS_MED) {
         const T* urow = a.uphys + 2 * base;
-        for (int i = tid; i < nx; i += nthr) st_real<T, false>(X, i, __ldcg(urow + i));
+        for (int i0 = tid; i0 < nx; i0 += RB * nthr) {
+            T v[RB];
+#pragma unroll
+            for (int q = 0; q < RB; q++) v[q] = i0 + q * nthr < nx ? __ldcg(urow + i0 + q * nthr) : T(0);
+#pragma unroll
+            for (int q = 0; q < RB; q++)
+                if (i0 + q * nthr < nx) st_real<T, false>(X, i0 + q * nthr, v[q]);
+        }
         __syncthreads();
     } else {
         // spectral row -> Z in digit-reversed order -> inverse passes
         const cx<T>* vin = a.in + base;
-        for (int k = tid; k <= n / 2; k += nthr) {
-            const int kn = k == 0 ? 0 : n - k;
-            cx<T> zk, znk;
-            c2r_vals<T>(__ldcg(vin + k), __ldcg(vin + kn), __ldg(a.tw + k), k, n, zk, znk);
-            X[__ldg(pos + k)] = zk;
-            if (k != 0 && 2 * k != n) X[__ldg(pos + kn)] = znk;
+        for (int k0 = tid; k0 <= n / 2; k0 += RB * nthr) {
+            cx<T> vk[RB], vn[RB];
+#pragma unroll
+            for (int q = 0; q < RB; q++) {
+                const int k = k0 + q * nthr;
+                if (k <= n / 2) {
+                    vk[q] = __ldcg(vin + k);
+                    vn[q] = __ldcg(vin + (k == 0 ? 0 : n - k));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RB; q++) {
+                const int k = k0 + q * nthr;
+                if (k > n / 2) break;
+                const int kn = k == 0 ? 0 : n - k;
+                cx<T> zk, znk;
+                c2r_vals<T>(vk[q], vn[q], __ldg(a.tw + k), k, n, zk, znk);
+                X[__ldg(pos + k)] = zk;
+                if (k != 0 && 2 * k != n) X[__ldg(pos + kn)] = znk;
+            }
         }
         __syncthreads();
         mix_inverse<T, false>(X, A.f, 0, a.tw, nullptr, tid, nthr);
@@ -381,36 +406,59 @@ __global__ void __launch_bounds__(MIX_ROW_MAX_THREADS) mix_row_kernel(MixRowArgs
     __syncthreads();
     if constexpr (MODE == ROW_RHS_MED) {
         const T* byrow = a.by + 2 * base;
-        for (int k = tid; k < nx; k += nthr) st_real<T, false>(Y, k, ld_real<T, false>(Y, k) + __ldcg(byrow + k));
+        for (int i0 = tid; i0 < nx; i0 += RB * nthr) {
+            T v[RB];
+#pragma unroll
+            for (int q = 0; q < RB; q++) v[q] = i0 + q * nthr < nx ? __ldcg(byrow + i0 + q * nthr) : T(0);
+#pragma unroll
+            for (int q = 0; q < RB; q++) {
+                const int k = i0 + q * nthr;
+                if (k < nx) st_real<T, false>(Y, k, ld_real<T, false>(Y, k) + v[q]);
+            }
+        }
         __syncthreads();
     }
     mix_forward<T, false>(Y, A.f, 0, a.tw, nullptr, tid, nthr);
     const cx<T>* vin = a.in + base;
     const T cA = stage_cA(a);
-    for (int k = tid; k <= n / 2; k += nthr) {
-        const int kn = k == 0 ? 0 : n - k;
-        cx<T> xk, xnk;
-        r2c_vals<T>(Y[__ldg(pos + k)], Y[__ldg(pos + kn)], __ldg(a.tw + k), k, n, xk, xnk);
+    for (int k0 = tid; k0 <= n / 2; k0 += RB * nthr) {
+        cx<T> vk[RB], vn[RB];
         if (cA != T(0)) {
-            // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
-            if (k == 0) {
-                const T kN = a.kscale * T(n);
-                xk.y -= cA * kN * kN * __ldcg(vin).y;
-            } else {
-                const T kt = a.kscale * T(k);
-                const cx<T> v = __ldcg(vin + k);
-                xk.x -= cA * kt * kt * v.x;
-                xk.y -= cA * kt * kt * v.y;
-                if (2 * k != n) {
-                    const T kt2 = a.kscale * T(n - k);
-                    const cx<T> w = __ldcg(vin + n - k);
-                    xnk.x -= cA * kt2 * kt2 * w.x;
-                    xnk.y -= cA * kt2 * kt2 * w.y;
+#pragma unroll
+            for (int q = 0; q < RB; q++) {
+                const int k = k0 + q * nthr;
+                if (k <= n / 2) {
+                    vk[q] = __ldcg(vin + k);
+                    vn[q] = __ldcg(vin + (k == 0 ? 0 : n - k));
                 }
             }
         }
-        a.out[base + k] = xk;
-        if (k != 0 && 2 * k != n) a.out[base + n - k] = xnk;
+#pragma unroll
+        for (int q = 0; q < RB; q++) {
+            const int k = k0 + q * nthr;
+            if (k > n / 2) break;
+            const int kn = k == 0 ? 0 : n - k;
+            cx<T> xk, xnk;
+            r2c_vals<T>(Y[__ldg(pos + k)], Y[__ldg(pos + kn)], __ldg(a.tw + k), k, n, xk, xnk);
+            if (cA != T(0)) {
+                // b_hat -= nx (A(sigma) - A) k_tau^2 V   (V = F(u)/nx)
+                if (k == 0) {
+                    const T kN = a.kscale * T(n);
+                    xk.y -= cA * kN * kN * vk[q].y;
+                } else {
+                    const T kt = a.kscale * T(k);
+                    xk.x -= cA * kt * kt * vk[q].x;
+                    xk.y -= cA * kt * kt * vk[q].y;
+                    if (2 * k != n) {
+                        const T kt2 = a.kscale * T(n - k);
+                        xnk.x -= cA * kt2 * kt2 * vn[q].x;
+                        xnk.y -= cA * kt2 * kt2 * vn[q].y;
+                    }
+                }
+            }
+            a.out[base + k] = xk;
+            if (k != 0 && 2 * k != n) a.out[base + n - k] = xnk;
+        }
     }
     if (a.diag_rows) block_diag_t<T>(red, s1, s2, mx, nf, a.diag_rows + ((long long)inst * a.ny + row) * 4);
 }
