@@ -143,7 +143,7 @@ struct kzk_plan_s {
     int *mpos_row, *mpos_col;   // device: position of each frequency after the forward passes
     int* mipos_col;             // device: frequency at each position (y)
     void* wsc;                  // device [batch][ny][nx/2]: P1' FFT_y(b1) between the two C1 launches
-    int mrow_thr, mcol_lc;
+    int mrow_thr, mcol_lc, mcol_thr;
     size_t mrow_smem, mcol_smem;
     int madj_thr, madj_Q;       // transposed row pass: threads, WENO chunk length (0: not available)
     size_t madj_smem;
@@ -375,7 +375,10 @@ kzk_status configure_mixed(kzk_plan* p)
     // they fit: the 8-byte rows of a single column use a quarter of each 32-byte sector
     if (sizeof(T) == 4 && lc == 0 && p->n % 2 == 0 && (size_t)p->ny * 2 * sizeof(cx<T>) <= (size_t)optin) lc = 1;
     p->mcol_lc = lc;
-    p->mcol_smem = std::max(((size_t)p->ny << lc) * sizeof(cx<T>), 4 * (size_t)MIX_COL_THREADS * sizeof(double));
+    // threads of the forward column passes: 512 (two CTAs per SM), or the
+    // FP32 maximum where one tile takes more than half of the SM
+    p->mcol_thr = ((size_t)p->ny << lc) * sizeof(cx<T>) > 96 * 1024 ? mix_col_max_threads<T>() : MIX_COL_THREADS;
+    p->mcol_smem = std::max(((size_t)p->ny << lc) * sizeof(cx<T>), 4 * (size_t)mix_col_max_threads<T>() * sizeof(double));
     if (p->mrow_smem > (size_t)optin || p->mcol_smem > (size_t)optin)
         return fail(KZK_ERR_SIZE, "grid %d x %d needs more shared memory than the device offers", p->nx, p->ny);
     p->colp_log2tc = -1;
@@ -771,13 +774,13 @@ kzk_status launch_mix_col(const kzk_plan* p, const ColArgs<T>& a, cudaStream_t s
     m.ipos = p->mipos_col;
     const dim3 grid(p->n >> p->mcol_lc, p->batch);
     if (MODE == COL_STAGE1) {
-        mix_col_kernel<T, MIX_C1B><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+        mix_col_kernel<T, MIX_C1B><<<grid, p->mcol_thr, p->mcol_smem, st>>>(m);
         KZK_LAUNCHED();
-        if (sizeof(T) == 4 && a.lo_out) mix_col_kernel<T, MIX_C1V, true><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
-        else mix_col_kernel<T, MIX_C1V><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+        if (sizeof(T) == 4 && a.lo_out) mix_col_kernel<T, MIX_C1V, true><<<grid, p->mcol_thr, p->mcol_smem, st>>>(m);
+        else mix_col_kernel<T, MIX_C1V><<<grid, p->mcol_thr, p->mcol_smem, st>>>(m);
         KZK_LAUNCHED();
     } else {
-        mix_col_kernel<T, MIX_C2><<<grid, MIX_COL_THREADS, p->mcol_smem, st>>>(m);
+        mix_col_kernel<T, MIX_C2><<<grid, p->mcol_thr, p->mcol_smem, st>>>(m);
         KZK_LAUNCHED();
     }
     return KZK_OK;

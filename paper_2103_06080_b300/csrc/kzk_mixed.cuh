@@ -481,12 +481,16 @@ struct MixColArgs {
 };
 
 constexpr int MIX_COL_THREADS = 512;
+// FP32 tiles that hold one CTA per SM (columns of ~10^4 points) run with 1024
+// threads: the latency of the strided loads is what bounds them, and their
+// registers (<= 64) allow it
+template <typename T> __host__ __device__ constexpr int mix_col_max_threads() { return sizeof(T) == 4 ? 1024 : 512; }
 
 // INC: the FP32 compensated state, whose transforms carry only the stage
 // increment (R12): plain FP32 constants suffice there, the two-float ones are
 // for the transform of a plain FP32 state.
 template <typename T, int MODE, bool INC = false>
-__global__ void __launch_bounds__(MIX_COL_THREADS) mix_col_kernel(MixColArgs<T> A)
+__global__ void __launch_bounds__(mix_col_max_threads<T>()) mix_col_kernel(MixColArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T>* S = reinterpret_cast<cx<T>*>(smem_raw);
