@@ -370,10 +370,17 @@ kzk_status configure_mixed(kzk_plan* p)
     p->mrow_thr = mix_row_threads(p->nx);
     p->mrow_smem = mix_row_smem<T>(p->nx, p->mrow_thr);
     int lc = 0;
-    while (lc < 4 && p->n % (2 << lc) == 0 && (size_t)p->ny * (2 << lc) * sizeof(cx<T>) <= 96 * 1024) lc++;
+    // widest tile within 96 KB (two CTAs per SM) that still leaves tiles for
+    // three quarters of the SMs (measured on the paper's grids: 28 tiles of
+    // eight columns lose to narrower ones; 112 of four beat 224 of two)
+    while (lc < 4 && p->n % (2 << lc) == 0 && (size_t)p->ny * (2 << lc) * sizeof(cx<T>) <= 96 * 1024 &&
+           4 * (p->n >> (lc + 1)) * p->batch >= 3 * p->sm_count)
+        lc++;
     // FP32 columns too long for two per tile at two CTAs per SM still take two (one CTA per SM) where
     // they fit: the 8-byte rows of a single column use a quarter of each 32-byte sector
-    if (sizeof(T) == 4 && lc == 0 && p->n % 2 == 0 && (size_t)p->ny * 2 * sizeof(cx<T>) <= (size_t)optin) lc = 1;
+    if (sizeof(T) == 4 && lc == 0 && p->n % 2 == 0 && (size_t)p->ny * 2 * sizeof(cx<T>) > 96 * 1024 &&
+        (size_t)p->ny * 2 * sizeof(cx<T>) <= (size_t)optin)
+        lc = 1;
     p->mcol_lc = lc;
     // threads of the forward column passes: 512 (two CTAs per SM), or the
     // FP32 maximum where one tile takes more than half of the SM
