@@ -890,17 +890,21 @@ kzk_status rhs_stage(kzk_plan* p, double sigma, const void* Vin, void* bout, dou
         y.n_bmax = p->med_nb;
         y.nx = p->nx;
         y.ny = p->ny;
-        y.Q = std::min(p->ny, 64);
         y.inst_elems = (long long)p->nx * p->ny;
         y.eps = (T)p->c.weno_eps;
         y.inv_dy = (T)(p->ny / (p->g.y_max - p->g.y_min));
+        // rows per CTA: 64 (FP64) / 32 (FP32), halved down to 16 while the
+        // grid would leave SMs without two CTAs (short, narrow grids)
+        const int xb = sizeof(T) == 4 ? (p->nx + 2 * YSWEEP_THREADS - 1) / (2 * YSWEEP_THREADS)
+                                      : (p->nx + YSWEEP_THREADS - 1) / YSWEEP_THREADS;
+        int q = sizeof(T) == 4 ? 32 : 64;
+        while (q > 16 && (long long)xb * ((p->ny + q - 1) / q) * p->batch < 2LL * p->sm_count) q >>= 1;
+        y.Q = std::min(p->ny, q);
+        const dim3 yg(xb, (p->ny + y.Q - 1) / y.Q, p->batch);
         if constexpr (sizeof(T) == 4) {
             // FP32: column pairs in packed FP32 (kzk_ysweep_pair.cuh)
-            y.Q = std::min(p->ny, 32);
-            const dim3 yg((p->nx + 2 * YSWEEP_THREADS - 1) / (2 * YSWEEP_THREADS), (p->ny + y.Q - 1) / y.Q, p->batch);
             ysweep_pair_kernel<<<yg, YSWEEP_THREADS, ysweep_pair_smem(y.Q), st>>>(y);
         } else {
-            const dim3 yg((p->nx + YSWEEP_THREADS - 1) / YSWEEP_THREADS, (p->ny + y.Q - 1) / y.Q, p->batch);
             ysweep_kernel<T><<<yg, YSWEEP_THREADS, ysweep_smem<T>(y.Q), st>>>(y);
         }
         KZK_LAUNCHED();
