@@ -131,10 +131,16 @@ def test_fp32_error_against_fp64_oracle():
     assert rel_linf(got, ref) < 1e-4
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
-def test_random_medium_run(prec, tol):
+# 448 x 250 (12 steps), and the exact grids of Sets 1 and 2 of Table 1 (448 x
+# 1250, 896 x 2500; a few steps) that bench.py times: their column tiles are
+# narrowed to leave tiles for most SMs and their y sweeps take 16-32 rows per
+# CTA, so these are the launch shapes of the paper-grid measurement
+@pytest.mark.parametrize("prec,tol,nx,ny,steps", [("fp64", 1e-11, 448, 250, 12), ("fp32", 1e-5, 448, 250, 12),
+                                                  ("fp64", 1e-11, 448, 1250, 4), ("fp32", 1e-5, 448, 1250, 4),
+                                                  ("fp64", 1e-11, 896, 2500, 3), ("fp32", 1e-5, 896, 2500, 3)])
+def test_random_medium_run(prec, tol, nx, ny, steps):
     api = _api()
-    w = inputs.medium_config(448, 250, 12)
+    w = inputs.medium_config(nx, ny, steps)
     plan = api.Plan.from_workload(w, precision=prec)
     dt = torch.float64 if prec == "fp64" else torch.float32
     u = _dev(w.u0, dt)
